@@ -1,0 +1,215 @@
+/* ns.h -- C ABI of the GB300 nonlinear seismic ground-response time stepper.
+ *
+ * One implicit Newmark-beta step (beta = 1/4, gamma = 1/2) of a 3D quadratic
+ * tetrahedral finite-element ground model, as stated in Sec. 2.1 (Eq. 1):
+ *   (4/dt^2 M + 2/dt C^n + K^n) du^n = f^n - q^{n-1} + C^n v^{n-1} + M (a^{n-1} + 4/dt v^{n-1}),
+ *   q^n = q^{n-1} + K^n du^n,  u^n = u^{n-1} + du^n,
+ *   v^n = -v^{n-1} + 2/dt du^n,  a^n = -a^{n-1} - 4/dt v^{n-1} + 4/dt^2 du^n,
+ * solved by an element-by-element (EBE) preconditioned CG (Sec. 2.2, Alg. 4),
+ * with K_e = sum_j w_j B^T D_j B (Eq. 2) and D from a multi-spring model of
+ * modified Ramberg-Osgood springs with the Masing rule (Sec. 2.1), whose
+ * 40-byte-per-spring state is kept in HBM or streamed from pinned host memory
+ * in chunks that overlap with compute (Alg. 3).  The stiffness is lagged: the
+ * solve of step n uses D left by step n-1 (Alg. 4).
+ *
+ * Conventions (all calls):
+ *  - Every call returns an int status: NS_OK (0) or a negative NS_ERR_* code;
+ *    ns_last_error(ctx) returns a static, human-readable message for the
+ *    last failure on that context.
+ *  - Inputs are caller-owned host buffers, read (copied) during the call and
+ *    never retained.  Outputs go into caller-owned host buffers.
+ *  - The context owns all device memory, pinned host memory, streams and
+ *    events it creates, until ns_destroy.
+ *  - A context is not thread-safe; different contexts are independent.
+ *  - Units are SI.  Node vectors are node-major [n][3] (x, y, z).
+ *  - Element node order: vertices 0-3 (positive orientation), then edge nodes
+ *    on (0,1) (1,2) (0,2) (0,3) (1,3) (2,3).  Elements must be straight-sided
+ *    (edge nodes at edge midpoints); geometry is taken from the vertices.
+ *  - Voigt order of strain/stress: xx yy zz yz xz xy, shear strains in
+ *    engineering form.  A 6x6 tangent D is returned full (36 doubles, row major).
+ */
+#ifndef NS_H
+#define NS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NS_OK 0
+#define NS_ERR_INVALID_ARG (-1)   /* bad size, pointer, value or call order */
+#define NS_ERR_OOM_DEVICE (-2)    /* device allocation failed */
+#define NS_ERR_OOM_PINNED (-3)    /* pinned host allocation failed */
+#define NS_ERR_CUDA (-4)          /* a CUDA runtime call failed */
+#define NS_ERR_BAD_MESH (-5)      /* non-positive volume, curved edge, bad index */
+#define NS_ERR_NOT_CONVERGED (-6) /* CG reached cg_max_iter; the step is not applied */
+#define NS_ERR_TIMEOUT (-7)       /* a bounded host wait on the device expired */
+#define NS_ERR_STATE (-8)         /* mesh/materials/boundary/input missing */
+
+#define NS_PREC_FP64 0   /* FP64 PCG with FP64 3x3 block-Jacobi (plain method) */
+#define NS_PREC_FP64_IR 1 /* FP64 outer CG, FP32 inner CG as preconditioner (paper's precision policy) */
+
+#define NS_SCATTER_ATOMIC 0 /* element results added with FP64/FP32 atomics (fast) */
+#define NS_SCATTER_COLOUR 1 /* greedy element colouring, plain stores (deterministic) */
+
+typedef struct ns_ctx ns_ctx;
+
+/* Solver and runtime configuration.  ns_config_default fills documented
+ * defaults; fields may then be changed before ns_create. */
+typedef struct {
+  int32_t n_springs;           /* springs per integration point, >= 5 (Sec. 2.1 uses 150) */
+  double dt;                   /* time step (s), > 0 */
+  double cg_tol;               /* relative residual ||r||/||b|| at convergence (Sec. 2.3: 1e-8) */
+  int32_t cg_max_iter;         /* CG iteration limit per step */
+  int32_t x0_prev;             /* 1: CG starts from the previous increment, 0: from zero */
+  int32_t precision;           /* NS_PREC_* */
+  int32_t scatter;             /* NS_SCATTER_* */
+  int64_t chunk_elems;         /* elements per streamed state chunk (Alg. 3 partition) */
+  int32_t ring_depth;          /* device chunk buffers, >= 2 (3 lets H2D, compute and D2H overlap) */
+  int64_t device_state_budget; /* bytes of spring state kept in HBM; elements beyond it are
+                                  host-resident and streamed; < 0: all resident */
+  double rayleigh_f1, rayleigh_f2; /* Rayleigh damping calibration frequencies (Hz) */
+  int64_t surface_ring_steps;  /* steps of surface response kept on the device */
+  int32_t device;              /* CUDA device ordinal */
+  int32_t timing;              /* 1: time kernels with CUDA events (ns_get_stats) */
+  int32_t inner_max_iter;      /* NS_PREC_FP64_IR: inner FP32 CG iterations per preconditioner call */
+  double inner_tol;            /* NS_PREC_FP64_IR: inner relative residual target */
+  double wait_timeout_s;       /* bound on each host wait for the device */
+} ns_config;
+
+/* Material of one element group (Sec. 2.1; parameters of the readings):
+ * density, S/P wave speeds, spring reference strain (secant modulus G0/2),
+ * maximum hysteretic damping of the Masing loops, Rayleigh damping ratio. */
+typedef struct {
+  double rho, vs, vp, gamma_ref, h_max, rayleigh_h;
+} ns_material;
+
+typedef struct {
+  int64_t steps;              /* steps taken */
+  int64_t cg_iters_total;     /* CG iterations summed over steps (outer for NS_PREC_FP64_IR) */
+  int32_t cg_iters_last;      /* CG iterations of the last step */
+  int32_t inner_iters_last;   /* inner FP32 iterations of the last step (NS_PREC_FP64_IR) */
+  double relres_last;         /* final relative residual of the last step */
+  int64_t kernel_launches;    /* this library's kernels launched since creation */
+  int64_t h2d_bytes, d2h_bytes; /* state bytes streamed since creation */
+  int64_t resident_elems, streamed_elems;
+  /* CUDA-event times (ms, summed since the last ns_reset_stats), valid when timing = 1 */
+  double ms_rhs, ms_jacobi, ms_solve, ms_newmark, ms_springs, ms_step;
+  int64_t n_ebe64, n_ebe32, n_spring;  /* launches of the FP64 operator, FP32 operator, spring kernel */
+  double ms_ebe64, ms_ebe32, ms_spring; /* their summed durations */
+  double ms_stream_wall;      /* multi-spring phase of the streamed part (first H2D to last D2H) */
+  double ms_advance;          /* CUDA-event time of ns_advance calls, all streams joined (always valid) */
+} ns_stats;
+
+/* Fill cfg with defaults: 10 springs, dt 0.01, tol 1e-8, 10000 iterations,
+ * x0_prev 1, NS_PREC_FP64, NS_SCATTER_ATOMIC, chunk 100000 elements (Sec. 2.3),
+ * ring 3, all state resident, Rayleigh 0.1/2.5 Hz, 64 surface steps,
+ * device 0, timing 0, inner 30 iterations / 1e-3, waits 120 s. */
+void ns_config_default(ns_config *cfg);
+
+/* Create a context on cfg->device.  *ctx is set on success. */
+int ns_create(ns_ctx **ctx, const ns_config *cfg);
+
+/* Upload the mesh: xyz [n_nodes][3], conn [n_elems][10] (order above), mat
+ * [n_elems] material indices.  Checks indices, positive volumes and straight
+ * edges (NS_ERR_BAD_MESH).  Builds the per-element geometry on the device and,
+ * for NS_SCATTER_COLOUR, the greedy element colouring.  Once per context. */
+int ns_upload_mesh(ns_ctx *ctx, int64_t n_nodes, const double *xyz, int64_t n_elems, const int32_t *conn,
+                   const int32_t *mat);
+
+/* Material table, n >= 1 entries (indices used by mat[] must be < n).
+ * After the mesh: allocates the spring state (virgin springs) and sets the
+ * initial tangent D to the elastic one. */
+int ns_set_materials(ns_ctx *ctx, int32_t n, const ns_material *mats);
+
+/* Absorbing faces (Sec. 2.1: semi-infinite bottom and sides, Lysmer dashpots):
+ * faces [n_faces][6] = three vertices then edge nodes (0,1) (1,2) (0,2);
+ * face_elem [n_faces] owning element (material); face_kind [n_faces] 0 =
+ * bottom (the input motion enters here), 1 = side.  surf_nodes [n_surf] are
+ * the nodes whose response ns_read_surface returns.  n_faces may be 0. */
+int ns_set_boundary(ns_ctx *ctx, int64_t n_faces, const int32_t *faces, const int32_t *face_elem,
+                    const int32_t *face_kind, int64_t n_surf, const int32_t *surf_nodes);
+
+/* Outcrop (2E) input acceleration acc [n_samples][3] at t = k*dt, k = 0..;
+ * dt must equal the context's dt.  The input velocity is its trapezoidal
+ * integral from zero; beyond the last sample the acceleration is zero.
+ * May be called again to replace the record (steps already taken stay). */
+int ns_set_ground_motion(ns_ctx *ctx, int64_t n_samples, double dt, const double *acc);
+
+/* Advance nsteps time steps.  Returns after the device work of all steps is
+ * complete.  On NS_ERR_NOT_CONVERGED the failing step is not applied and
+ * ns_get_stats().steps tells how many steps were taken. */
+int ns_advance(ns_ctx *ctx, int64_t nsteps);
+
+/* Surface response of steps [step0, step0 + nsteps) (1-based step numbers of
+ * states t = step*dt) into u, v, a, each [nsteps][n_surf][3]; NULL skips a
+ * field.  Only the last surface_ring_steps steps are available. */
+int ns_read_surface(ns_ctx *ctx, int64_t step0, int64_t nsteps, double *u, double *v, double *a);
+
+/* Spring state and tangent of elements [elem0, elem0 + n): theta
+ * [n][4][n_springs] records of 40 bytes {double tau, gR, tR, gmax; int32 dir,
+ * mode} (may be NULL), D [n][4][36] (may be NULL). */
+int ns_read_state(ns_ctx *ctx, int64_t elem0, int64_t n, void *theta, double *D);
+
+/* Overwrite the state of elements [elem0, elem0 + n) (same layouts; NULL skips). */
+int ns_write_state(ns_ctx *ctx, int64_t elem0, int64_t n, const void *theta, const double *D);
+
+#define NS_FIELD_U 0
+#define NS_FIELD_V 1
+#define NS_FIELD_A 2
+#define NS_FIELD_Q 3
+#define NS_FIELD_DU 4
+/* Read / overwrite one node vector [n_nodes][3]. */
+int ns_read_nodal(ns_ctx *ctx, int32_t field, double *out);
+int ns_write_nodal(ns_ctx *ctx, int32_t field, const double *in);
+
+#define NS_OP_K 0  /* K(D) */
+#define NS_OP_M 1  /* consistent mass */
+#define NS_OP_CB 2 /* boundary dashpots */
+#define NS_OP_A 3  /* 4/dt^2 M + 2/dt (Rayleigh(K) + C_b) + K, the matrix of Eq. 1 */
+#define NS_OP_CR 4 /* Rayleigh part alpha M + beta K */
+/* y = Op x with the current tangent D, x and y [n_nodes][3] host buffers
+ * (FP64 element-by-element operator on the device). */
+int ns_apply_operator(ns_ctx *ctx, int32_t op, const double *x, double *y);
+
+/* Multi-spring update of npts free-standing integration points on the device:
+ * mat [npts], eps and deps [npts][6] (total strain and increment), theta
+ * [npts][n_springs] 40-byte records updated in place, D [npts][36] out. */
+int ns_spring_points(ns_ctx *ctx, int64_t npts, const int32_t *mat, const double *eps, const double *deps,
+                     void *theta, double *D);
+
+int ns_get_stats(ns_ctx *ctx, ns_stats *st);
+int ns_reset_stats(ns_ctx *ctx);
+
+/* Checkpoint of the whole time-stepping state (step counter, u, v, a, q, du,
+ * D, spring state).  ns_checkpoint_size gives the byte count; the buffers are
+ * caller-owned host memory of at least that size. */
+int ns_checkpoint_size(ns_ctx *ctx, int64_t *bytes);
+int ns_checkpoint(ns_ctx *ctx, void *buf, int64_t bytes);
+int ns_restore(ns_ctx *ctx, const void *buf, int64_t bytes);
+
+void ns_destroy(ns_ctx *ctx);
+const char *ns_last_error(ns_ctx *ctx);
+
+/* ---- host-only helpers (no device work) ---------------------------------- */
+
+/* Spring directions q [S][6] and weight w of the multi-spring geometry:
+ * hemispherical Fibonacci plane normals, slip directions rotated by 2 pi
+ * frac(k sqrt2), shear projections made exactly isotropic so that
+ * w sum_k q_k q_k^T = diag(2,2,2,1,1,1) - (2/3) m m^T with w = 5/(2S). */
+int ns_spring_directions(int32_t S, double *q, double *w);
+
+/* Greedy first-fit element colouring in element order (elements sharing a
+ * node get different colours).  colour [n_elems]; *n_colours out. */
+int ns_colour_elements(int64_t n_elems, int64_t n_nodes, const int32_t *conn, int32_t *colour,
+                       int32_t *n_colours);
+
+/* Bytes of spring state for n_elems elements with S springs per point
+ * (4 points per element, 40 bytes per spring). */
+int64_t ns_state_bytes(int64_t n_elems, int32_t S);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,507 @@
+// Element-by-element kernels (Sec. 2.2, Alg. 4: EBE matrix-vector products):
+// geometry set-up, the operator y = mM M xm + mK M xk + kK K xk applied on the fly
+// (K_e = sum_q w_q B^T D_q B, Eq. 2), Lysmer dashpot faces, block-Jacobi diagonal
+// blocks and integration-point strains for the multi-spring update.
+#include "kern_common.cuh"
+
+namespace ns {
+
+// ------------------------------------------------------------------ geometry
+
+// grad L1..L3 are the rows of J^{-1}, J = [x1-x0, x2-x0, x3-x0] (columns); V = det J / 6.
+// bad[0] receives 1 + the index of an element with non-positive volume or a curved edge.
+__global__ void k_geometry(int64_t E, int64_t epad, const int32_t *__restrict__ conn, const double *__restrict__ xyz,
+                           double *geom, float *geom32, int32_t *bad) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double x[10][3];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    int64_t n = conn[i * epad + e];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[i][c] = xyz[n * 3 + c];
+  }
+  double J[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) J[r][c] = x[c + 1][r] - x[0][r];
+  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  bool ok = det > 0.0;
+  // inverse: Jinv[k][c] = cofactor(c,k)/det -> row k of Jinv is grad L_{k+1}
+  double inv[3][3];
+  inv[0][0] = c00 / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = c01 / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = c02 / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  // straight edges: edge node at the midpoint of its vertices
+  const int ea[6] = {0, 1, 0, 0, 1, 2}, eb[6] = {1, 2, 2, 3, 3, 3};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double len = 0.0, dev = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double d = x[eb[k]][c] - x[ea[k]][c];
+      double m = 0.5 * (x[eb[k]][c] + x[ea[k]][c]) - x[4 + k][c];
+      len += d * d;
+      dev += m * m;
+    }
+    if (!(dev <= 1e-18 * len)) ok = false;
+  }
+  if (!ok) atomicCAS(bad, 0, (int32_t)(e + 1));
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      geom[(3 * k + c) * epad + e] = inv[k][c];
+      geom32[(3 * k + c) * epad + e] = (float)inv[k][c];
+    }
+  geom[9 * epad + e] = det / 6.0;
+  geom32[9 * epad + e] = (float)(det / 6.0);
+}
+
+__global__ void k_face_geometry(int64_t F, int64_t fpad, const int32_t *__restrict__ fnode,
+                                const double *__restrict__ xyz, double *fgeom) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  double x[3][3];
+  for (int i = 0; i < 3; ++i) {
+    int64_t n = fnode[i * fpad + f];
+    for (int c = 0; c < 3; ++c) x[i][c] = xyz[n * 3 + c];
+  }
+  double a[3], b[3];
+  for (int c = 0; c < 3; ++c) {
+    a[c] = x[1][c] - x[0][c];
+    b[c] = x[2][c] - x[0][c];
+  }
+  double n0 = a[1] * b[2] - a[2] * b[1], n1 = a[2] * b[0] - a[0] * b[2], n2 = a[0] * b[1] - a[1] * b[0];
+  double len = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+  fgeom[0 * fpad + f] = 0.5 * len;
+  fgeom[1 * fpad + f] = n0 / len;
+  fgeom[2 * fpad + f] = n1 / len;
+  fgeom[3 * fpad + f] = n2 / len;
+}
+
+cudaError_t launch_geometry(const DevMesh &m, const double *xyz, int32_t *bad, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  k_geometry<<<(unsigned)((m.E + kBlock - 1) / kBlock), kBlock, 0, s>>>(m.E, m.epad, m.conn, xyz, m.geom, m.geom32,
+                                                                        bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_geometry(const DevMesh &m, const double *xyz, cudaStream_t s) {
+  if (m.F == 0) return cudaSuccess;
+  k_face_geometry<<<(unsigned)((m.F + kBlock - 1) / kBlock), kBlock, 0, s>>>(m.F, m.fpad, m.fnode, xyz, m.fgeom);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ operator
+
+// Stress of integration point Q: sig = w D_Q eps_Q(x).
+template <typename T, int Q>
+__device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], const T g[4][3],
+                                             const T *__restrict__ D, int64_t epad, int64_t e, T w, T sig[6]) {
+  T H[3][3], eps[6], d[21];
+  point_grad<T, Q>(x, P, g, H);
+  voigt_strain(H, eps);
+#pragma unroll
+  for (int k = 0; k < 21; ++k) d[k] = ldg(D + (Q * 21 + k) * epad + e);
+  sig[0] = w * (d[0] * eps[0] + d[1] * eps[1] + d[2] * eps[2] + d[3] * eps[3] + d[4] * eps[4] + d[5] * eps[5]);
+  sig[1] = w * (d[1] * eps[0] + d[6] * eps[1] + d[7] * eps[2] + d[8] * eps[3] + d[9] * eps[4] + d[10] * eps[5]);
+  sig[2] = w * (d[2] * eps[0] + d[7] * eps[1] + d[11] * eps[2] + d[12] * eps[3] + d[13] * eps[4] + d[14] * eps[5]);
+  sig[3] = w * (d[3] * eps[0] + d[8] * eps[1] + d[12] * eps[2] + d[15] * eps[3] + d[16] * eps[4] + d[17] * eps[5]);
+  sig[4] = w * (d[4] * eps[0] + d[9] * eps[1] + d[13] * eps[2] + d[16] * eps[3] + d[18] * eps[4] + d[19] * eps[5]);
+  sig[5] = w * (d[5] * eps[0] + d[10] * eps[1] + d[14] * eps[2] + d[17] * eps[3] + d[19] * eps[4] + d[20] * eps[5]);
+}
+
+// Operator kernel, one thread per element.  Phases keep the register footprint small:
+// (1) gather x, stresses at the four points; (2) nodal forces B^T sig; (3) consistent mass
+// one displacement component at a time (re-gathered from cache); (4) scatter.
+template <typename T, bool HAS_XM, bool ATOMIC, bool DOT>
+__global__ void __launch_bounds__(kBlock) k_ebe(int64_t e0, int64_t e1, const int32_t *__restrict__ ids,
+                                                const int32_t *__restrict__ conn, const T *__restrict__ geom,
+                                                const int32_t *__restrict__ mat, const T *__restrict__ D,
+                                                int64_t epad, const OpCoef *__restrict__ op,
+                                                const T *__restrict__ xm, const T *__restrict__ xk, T *y,
+                                                double *dot, const int32_t *skip) {
+  if (skip && *skip) return;
+  const int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = i < e1;
+  double mydot = 0.0;
+  if (active) {
+    const int64_t e = ids ? (int64_t)ids[i] : i;
+    int nd[10];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) nd[a] = ldg(conn + a * epad + e);
+    const int mt = ldg(mat + e);
+    const T cK = (T)op->kK[mt], cMk = (T)op->mK[mt];
+    const T cMm = HAS_XM ? (T)op->mM[mt] : (T)0;
+    T g[4][3], vol;
+    load_grads(geom, epad, e, g, vol);
+    T ye[10][3];
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) ye[a][r] = (T)0;
+    if (cK != (T)0) {
+      T sig[4][6];
+      {
+        T x[10][3], P[4][3];
+#pragma unroll
+        for (int a = 0; a < 10; ++a)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) x[a][r] = ldg(xk + 3 * (int64_t)nd[a] + r);
+        compute_P(x, P);
+        const T w = cK * vol * (T)0.25;
+        point_stress<T, 0>(x, P, g, D, epad, e, w, sig[0]);
+        point_stress<T, 1>(x, P, g, D, epad, e, w, sig[1]);
+        point_stress<T, 2>(x, P, g, D, epad, e, w, sig[2]);
+        point_stress<T, 3>(x, P, g, D, epad, e, w, sig[3]);
+      }
+      point_force<T, 0>(sig[0], g, ye);
+      point_force<T, 1>(sig[1], g, ye);
+      point_force<T, 2>(sig[2], g, ye);
+      point_force<T, 3>(sig[3], g, ye);
+    }
+    if (cMk != (T)0 || cMm != (T)0) {
+      const T c = vol * (T)(1.0 / 420.0);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        T w[10];
+#pragma unroll
+        for (int a = 0; a < 10; ++a) {
+          w[a] = cMk * ldg(xk + 3 * (int64_t)nd[a] + r);
+          if (HAS_XM) w[a] += cMm * ldg(xm + 3 * (int64_t)nd[a] + r);
+        }
+        mass_apply_1(w, c, ye, r);
+      }
+    }
+    if (DOT) {
+#pragma unroll
+      for (int a = 0; a < 10; ++a)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) mydot += (double)ldg(xk + 3 * (int64_t)nd[a] + r) * (double)ye[a][r];
+    }
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        T *dst = y + 3 * (int64_t)nd[a] + r;
+        if (ATOMIC)
+          atomic_add(dst, ye[a][r]);
+        else
+          *dst += ye[a][r];
+      }
+  }
+  if (DOT) {
+    double s = block_sum(mydot);
+    if (threadIdx.x == 0) dot[blockIdx.x] = s;
+  }
+}
+
+template <typename T, bool HAS_XM>
+static cudaError_t ebe_dispatch(const DevMesh &m, const T *D, const T *geom, const OpCoef *op, const T *xm,
+                                const T *xk, T *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic,
+                                double *dot, const int32_t *skip, cudaStream_t s) {
+  if (e1 <= e0) return cudaSuccess;
+  unsigned nb = (unsigned)((e1 - e0 + kBlock - 1) / kBlock);
+#define NS_EBE_LAUNCH(A, DT)                                                                              \
+  k_ebe<T, HAS_XM, A, DT><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, \
+                                                 dot, skip)
+  if (atomic) {
+    if (dot)
+      NS_EBE_LAUNCH(true, true);
+    else
+      NS_EBE_LAUNCH(true, false);
+  } else {
+    if (dot)
+      NS_EBE_LAUNCH(false, true);
+    else
+      NS_EBE_LAUNCH(false, false);
+  }
+#undef NS_EBE_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
+                         double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
+                         const int32_t *skip, cudaStream_t s) {
+  if (xm) return ebe_dispatch<double, true>(m, D, m.geom, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s);
+  return ebe_dispatch<double, false>(m, D, m.geom, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
+}
+
+cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
+                         const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
+                         cudaStream_t s) {
+  return ebe_dispatch<float, false>(m, D, m.geom32, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
+}
+
+// ------------------------------------------------------------------ dashpot faces
+
+// C_f = (A/180) Mtri (x) rho [Vs I + (Vp - Vs) n n^T]; Mtri*180/A: vertex 6 / -1, vertex vs
+// opposite edge -4 (else 0), edge 32 / 16.  Face nodes: v0 v1 v2 e01 e12 e02.
+template <typename T, bool ATOMIC, bool DOT>
+__global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const int32_t *__restrict__ ids,
+                                                  int64_t fpad, const int32_t *__restrict__ fnode,
+                                                  const double *__restrict__ fgeom, const int32_t *__restrict__ fmat,
+                                                  const int32_t *__restrict__ fkind, const MatConst *__restrict__ mc,
+                                                  T cC, const T *__restrict__ x, const double *__restrict__ vin,
+                                                  T *y, double *dot, const int32_t *skip) {
+  if (skip && *skip) return;
+  const int64_t i = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double mydot = 0.0;
+  if (i < f1) {
+    const int64_t f = ids ? (int64_t)ids[i] : i;
+    int nd[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) nd[a] = fnode[a * fpad + f];
+    const T area = (T)fgeom[f];
+    const T n[3] = {(T)fgeom[fpad + f], (T)fgeom[2 * fpad + f], (T)fgeom[3 * fpad + f]};
+    const MatConst &mm = mc[fmat[f]];
+    const T rvs = (T)(mm.rho * mm.vs), rvd = (T)(mm.rho * (mm.vp - mm.vs));
+    const bool inp = vin && fkind[f] == 0;
+    T w[6][3];
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) w[a][r] = x[3 * (int64_t)nd[a] + r] + (inp ? (T)vin[r] : (T)0);
+    T m[6][3];  // Mtri applied per component
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T sv = w[0][r] + w[1][r] + w[2][r], se = w[3][r] + w[4][r] + w[5][r];
+      m[0][r] = (T)7 * w[0][r] - sv - (T)4 * w[4][r];
+      m[1][r] = (T)7 * w[1][r] - sv - (T)4 * w[5][r];
+      m[2][r] = (T)7 * w[2][r] - sv - (T)4 * w[3][r];
+      m[3][r] = (T)16 * (w[3][r] + se) - (T)4 * w[2][r];
+      m[4][r] = (T)16 * (w[4][r] + se) - (T)4 * w[0][r];
+      m[5][r] = (T)16 * (w[5][r] + se) - (T)4 * w[1][r];
+    }
+    const T sc = cC * area * (T)(1.0 / 180.0);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const T nm = n[0] * m[a][0] + n[1] * m[a][1] + n[2] * m[a][2];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const T v = sc * (rvs * m[a][r] + rvd * n[r] * nm);
+        if (DOT) mydot += (double)x[3 * (int64_t)nd[a] + r] * (double)v;
+        T *dst = y + 3 * (int64_t)nd[a] + r;
+        if (ATOMIC)
+          atomic_add(dst, v);
+        else
+          *dst += v;
+      }
+    }
+  }
+  if (DOT) {
+    double s = block_sum(mydot);
+    if (threadIdx.x == 0) dot[blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+static cudaError_t faces_dispatch(const DevMesh &m, const MatConst *mc, T cC, const T *x, const double *vin, T *y,
+                                  const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
+                                  const int32_t *skip, cudaStream_t s) {
+  if (f1 <= f0) return cudaSuccess;
+  unsigned nb = (unsigned)((f1 - f0 + kBlock - 1) / kBlock);
+#define NS_F_LAUNCH(A, DT) \
+  k_faces<T, A, DT><<<nb, kBlock, 0, s>>>(f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, m.fkind, mc, cC, x, vin, y, \
+                                          dot, skip)
+  if (atomic) {
+    if (dot)
+      NS_F_LAUNCH(true, true);
+    else
+      NS_F_LAUNCH(true, false);
+  } else {
+    if (dot)
+      NS_F_LAUNCH(false, true);
+    else
+      NS_F_LAUNCH(false, false);
+  }
+#undef NS_F_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_faces64(const DevMesh &m, const MatConst *mc, double cC, const double *x, const double *vin,
+                           double *y, const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
+                           const int32_t *skip, cudaStream_t s) {
+  return faces_dispatch<double>(m, mc, cC, x, vin, y, ids, f0, f1, atomic, dot, skip, s);
+}
+
+cudaError_t launch_faces32(const DevMesh &m, const MatConst *mc, float cC, const float *x, float *y,
+                           const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot, const int32_t *skip,
+                           cudaStream_t s) {
+  return faces_dispatch<float>(m, mc, cC, x, nullptr, y, ids, f0, f1, atomic, dot, skip, s);
+}
+
+// ------------------------------------------------------------------ block-Jacobi diagonal blocks
+
+// For node i of the element: sum_q w_q B_i^T D_q B_i (3x3) + mass diagonal, packed xx yy zz yz xz xy.
+__global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1, const int32_t *__restrict__ ids,
+                                                         const int32_t *__restrict__ conn,
+                                                         const double *__restrict__ geom,
+                                                         const int32_t *__restrict__ mat,
+                                                         const double *__restrict__ D, int64_t epad,
+                                                         const OpCoef *__restrict__ op, double *Jd, bool atomic) {
+  const int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= e1) return;
+  const int64_t e = ids ? (int64_t)ids[i] : i;
+  const int mt = mat[e];
+  const double cK = op->kK[mt], cM = op->mK[mt];
+  double g[4][3], vol;
+  load_grads(geom, epad, e, g, vol);
+  double acc[10][6];
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[a][k] = 0.0;
+  const double w = cK * vol * 0.25;
+  for (int q = 0; q < 4; ++q) {
+    double d[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) d[k] = w * D[(q * 21 + k) * epad + e];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+      double gn[3];
+      if (a < 4) {
+        const double c = 4.0 * (a == q ? NS_QA : NS_QB) - 1.0;
+        for (int r = 0; r < 3; ++r) gn[r] = c * g[a][r];
+      } else {
+        const int ia[6] = {0, 1, 0, 0, 1, 2}, ib[6] = {1, 2, 2, 3, 3, 3};
+        const int pa = ia[a - 4], pb = ib[a - 4];
+        const double la = pa == q ? NS_QA : NS_QB, lb = pb == q ? NS_QA : NS_QB;
+        for (int r = 0; r < 3; ++r) gn[r] = 4.0 * (la * g[pb][r] + lb * g[pa][r]);
+      }
+      // columns of B_i: bx = (g0,0,0,0,g2,g1), by = (0,g1,0,g2,0,g0), bz = (0,0,g2,g1,g0,0)
+      double Dbx[6], Dby[6], Dbz[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        Dbx[r] = d[sym6(r, 0)] * gn[0] + d[sym6(r, 4)] * gn[2] + d[sym6(r, 5)] * gn[1];
+        Dby[r] = d[sym6(r, 1)] * gn[1] + d[sym6(r, 3)] * gn[2] + d[sym6(r, 5)] * gn[0];
+        Dbz[r] = d[sym6(r, 2)] * gn[2] + d[sym6(r, 3)] * gn[1] + d[sym6(r, 4)] * gn[0];
+      }
+      acc[a][0] += gn[0] * Dbx[0] + gn[2] * Dbx[4] + gn[1] * Dbx[5];  // xx
+      acc[a][1] += gn[1] * Dby[1] + gn[2] * Dby[3] + gn[0] * Dby[5];  // yy
+      acc[a][2] += gn[2] * Dbz[2] + gn[1] * Dbz[3] + gn[0] * Dbz[4];  // zz
+      acc[a][3] += gn[1] * Dbz[1] + gn[2] * Dbz[3] + gn[0] * Dbz[5];  // yz = by . D bz
+      acc[a][4] += gn[0] * Dbz[0] + gn[2] * Dbz[4] + gn[1] * Dbz[5];  // xz = bx . D bz
+      acc[a][5] += gn[0] * Dby[0] + gn[2] * Dby[4] + gn[1] * Dby[5];  // xy = bx . D by
+    }
+  }
+  const double mv = cM * vol * (6.0 / 420.0), me = cM * vol * (32.0 / 420.0);
+#pragma unroll
+  for (int a = 0; a < 10; ++a) {
+    const double md = a < 4 ? mv : me;
+    acc[a][0] += md;
+    acc[a][1] += md;
+    acc[a][2] += md;
+    const int64_t n = conn[a * epad + e];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (atomic)
+        atomicAdd(Jd + 6 * n + k, acc[a][k]);
+      else
+        Jd[6 * n + k] += acc[a][k];
+    }
+  }
+}
+
+__global__ void k_jacobi_faces(int64_t f0, int64_t f1, const int32_t *__restrict__ ids, int64_t fpad,
+                               const int32_t *__restrict__ fnode, const double *__restrict__ fgeom,
+                               const int32_t *__restrict__ fmat, const MatConst *__restrict__ mc, double cC,
+                               double *Jd, bool atomic) {
+  const int64_t i = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= f1) return;
+  const int64_t f = ids ? (int64_t)ids[i] : i;
+  const double area = fgeom[f], n[3] = {fgeom[fpad + f], fgeom[2 * fpad + f], fgeom[3 * fpad + f]};
+  const MatConst &mm = mc[fmat[f]];
+  const double rvs = mm.rho * mm.vs, rvd = mm.rho * (mm.vp - mm.vs);
+  const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+  for (int a = 0; a < 6; ++a) {
+    const double md = cC * area / 180.0 * (a < 3 ? 6.0 : 32.0);
+    const int64_t nd = fnode[a * fpad + f];
+    for (int k = 0; k < 6; ++k) {
+      const int r = pr[k][0], c = pr[k][1];
+      const double v = md * ((r == c ? rvs : 0.0) + rvd * n[r] * n[c]);
+      if (atomic)
+        atomicAdd(Jd + 6 * nd + k, v);
+      else
+        Jd[6 * nd + k] += v;
+    }
+  }
+}
+
+cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef *op, double *Jd, const int32_t *ids,
+                                int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
+  if (e1 <= e0) return cudaSuccess;
+  k_jacobi_elems<<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(e0, e1, ids, m.conn, m.geom, m.mat,
+                                                                                D, m.epad, op, Jd, atomic);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_faces(const DevMesh &m, const MatConst *mc, double cC, double *Jd, const int32_t *ids,
+                                int64_t f0, int64_t f1, bool atomic, cudaStream_t s) {
+  if (f1 <= f0) return cudaSuccess;
+  k_jacobi_faces<<<(unsigned)((f1 - f0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(f0, f1, ids, m.fpad, m.fnode,
+                                                                                m.fgeom, m.fmat, mc, cC, Jd, atomic);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ strains for the spring update
+
+__global__ void __launch_bounds__(kBlock) k_strain(int64_t e0, int64_t e1, const int32_t *__restrict__ conn,
+                                                   const double *__restrict__ geom, int64_t epad,
+                                                   const double *__restrict__ u, const double *__restrict__ du,
+                                                   double *out) {
+  const int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= e1) return;
+  int nd[10];
+#pragma unroll
+  for (int a = 0; a < 10; ++a) nd[a] = conn[a * epad + e];
+  double g[4][3], vol;
+  load_grads(geom, epad, e, g, vol);
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    const double *src = which ? du : u;
+    double x[10][3], P[4][3];
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) x[a][r] = src[3 * (int64_t)nd[a] + r];
+    compute_P(x, P);
+    double H[3][3], eps[6];
+    point_grad<double, 0>(x, P, g, H);
+    voigt_strain(H, eps);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[(e * 4 + 0) * 12 + 6 * which + k] = eps[k];
+    point_grad<double, 1>(x, P, g, H);
+    voigt_strain(H, eps);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[(e * 4 + 1) * 12 + 6 * which + k] = eps[k];
+    point_grad<double, 2>(x, P, g, H);
+    voigt_strain(H, eps);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[(e * 4 + 2) * 12 + 6 * which + k] = eps[k];
+    point_grad<double, 3>(x, P, g, H);
+    voigt_strain(H, eps);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[(e * 4 + 3) * 12 + 6 * which + k] = eps[k];
+  }
+}
+
+cudaError_t launch_strain(const DevMesh &m, const double *u, const double *du, double *out, int64_t e0, int64_t e1,
+                          cudaStream_t s) {
+  if (e1 <= e0) return cudaSuccess;
+  k_strain<<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(e0, e1, m.conn, m.geom, m.epad, u, du, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ns

@@ -1,0 +1,485 @@
+// Node-vector kernels: preconditioned CG (Sec. 2.2; 3x3 block Jacobi) with
+// warp-shuffle block reductions finished in a fixed order (deterministic),
+// the Newmark-beta updates below Eq. 1, surface gathers and conversions.
+#include "kern_common.cuh"
+
+namespace ns {
+
+int vec_blocks(int64_t n_nodes) {
+  int64_t nb = (n_nodes + kBlock - 1) / kBlock;
+  const int64_t cap = 152 * 8;
+  if (nb > cap) nb = cap;
+  if (nb < 1) nb = 1;
+  return (int)nb;
+}
+
+__global__ void k_fill(double *x, double v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+__global__ void k_negate_copy(double *dst, const double *src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = -src[i];
+}
+
+cudaError_t launch_fill(double *x, double v, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_fill<<<vec_blocks(n), kBlock, 0, s>>>(x, v, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_negate_copy(double *dst, const double *src, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_negate_copy<<<vec_blocks(n), kBlock, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+// packed symmetric 3x3: xx yy zz yz xz xy
+__device__ __forceinline__ void sym3_apply(const double *J, const double r[3], double z[3]) {
+  z[0] = J[0] * r[0] + J[5] * r[1] + J[4] * r[2];
+  z[1] = J[5] * r[0] + J[1] * r[1] + J[3] * r[2];
+  z[2] = J[4] * r[0] + J[3] * r[1] + J[2] * r[2];
+}
+
+__global__ void k_invert_blocks(const double *Jd, double *Jinv, float *Jinv32, int64_t N, int32_t *bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double *a = Jd + 6 * i;
+    const double xx = a[0], yy = a[1], zz = a[2], yz = a[3], xz = a[4], xy = a[5];
+    const double c00 = yy * zz - yz * yz, c11 = xx * zz - xz * xz, c22 = xx * yy - xy * xy;
+    const double c12 = xy * xz - xx * yz, c02 = xy * yz - yy * xz, c01 = xz * yz - xy * zz;
+    const double det = xx * c00 + xy * c01 + xz * c02;
+    if (!(det > 0.0)) {
+      atomicCAS(bad, 0, (int32_t)(i + 1));
+      continue;
+    }
+    const double inv[6] = {c00 / det, c11 / det, c22 / det, c12 / det, c02 / det, c01 / det};
+    for (int k = 0; k < 6; ++k) {
+      Jinv[6 * i + k] = inv[k];
+      if (Jinv32) Jinv32[6 * i + k] = (float)inv[k];
+    }
+  }
+}
+
+cudaError_t launch_invert_blocks(const double *Jd, double *Jinv, float *Jinv32, int64_t N, int32_t *bad,
+                                 cudaStream_t s) {
+  k_invert_blocks<<<vec_blocks(N), kBlock, 0, s>>>(Jd, Jinv, Jinv32, N, bad);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ CG
+
+__global__ void __launch_bounds__(kBlock) k_cg_init(const double *__restrict__ b, const double *__restrict__ Ap,
+                                                    const double *__restrict__ Jinv, double *r, double *z, double *p,
+                                                    int64_t N, double *part) {
+  double bb = 0.0, rr = 0.0, rz = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double rv[3], zv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double bv = b[3 * i + c];
+      rv[c] = bv - Ap[3 * i + c];
+      bb += bv * bv;
+      rr += rv[c] * rv[c];
+    }
+    sym3_apply(Jinv + 6 * i, rv, zv);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r[3 * i + c] = rv[c];
+      z[3 * i + c] = zv[c];
+      p[3 * i + c] = zv[c];
+      rz += rv[c] * zv[c];
+    }
+  }
+  const double s0 = block_sum(bb), s1 = block_sum(rr), s2 = block_sum(rz);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
+    part[2 * gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv, double *r, double *z, double *p,
+                           int64_t N, double *part, cudaStream_t s) {
+  k_cg_init<<<vec_blocks(N), kBlock, 0, s>>>(b, Ap, Jinv, r, z, p, N, part);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock) k_cg_final(const double *__restrict__ part, int n, int nvals,
+                                                     CgScalars *sc, int mode, double tol, int max_iter) {
+  if (mode != NS_FIN_INIT && sc->done) return;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < nvals; ++k) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[k * n + i];
+    v[k] = block_sum(acc);
+  }
+  if (threadIdx.x != 0) return;
+  if (mode == NS_FIN_INIT) {
+    sc->bb = v[0];
+    sc->rr = v[1];
+    sc->rr0 = v[1];
+    sc->rz = v[2];
+    sc->rz_old = v[2];
+    sc->iters = 0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->done = (v[0] == 0.0) ? 2 : (v[1] <= tol * tol * v[0] ? 1 : 0);
+  } else if (mode == NS_FIN_PAP) {
+    sc->pAp = v[0];
+    sc->alpha = sc->rz_old / v[0];
+  } else if (mode == NS_FIN_FCG_INIT) {
+    sc->bb = v[0];
+    sc->rr = v[1];
+    sc->rr0 = v[1];
+    sc->iters = 0;
+    sc->beta = 0.0;
+    sc->pAp = 1.0;
+    sc->done = (v[0] == 0.0) ? 2 : (v[1] <= tol * tol * v[0] ? 1 : 0);
+  } else if (mode == NS_FIN_FCG_BETA) {
+    sc->beta = (sc->iters == 0) ? 0.0 : -v[0] / sc->pAp;
+  } else if (mode == NS_FIN_FCG_UPDATE) {
+    sc->rr = v[0];
+    sc->iters += 1;
+    if (v[0] <= tol * tol * sc->bb)
+      sc->done = 1;
+    else if (sc->iters >= max_iter)
+      sc->done = 3;
+  } else {
+    sc->rr = v[0];
+    sc->rz = v[1];
+    sc->iters += 1;
+    if (v[0] <= tol * tol * sc->bb)
+      sc->done = 1;
+    else if (sc->iters >= max_iter)
+      sc->done = 3;
+    sc->beta = v[1] / sc->rz_old;
+    sc->rz_old = v[1];
+  }
+}
+
+cudaError_t launch_cg_final(const double *part, int n, int nvals, CgScalars *sc, int mode, double tol, int max_iter,
+                            cudaStream_t s) {
+  k_cg_final<<<1, kBlock, 0, s>>>(part, n, nvals, sc, mode, tol, max_iter);
+  return cudaGetLastError();
+}
+
+// alpha = (p.r) / (p.A p) of the flexible CG, from two partial arrays
+__global__ void __launch_bounds__(kBlock) k_fcg_alpha(const double *__restrict__ pr, int npr,
+                                                      const double *__restrict__ pap, int npap, CgScalars *sc) {
+  if (sc->done) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < npr; i += blockDim.x) a += pr[i];
+  for (int i = threadIdx.x; i < npap; i += blockDim.x) b += pap[i];
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0) {
+    sc->pAp = b;
+    sc->alpha = a / b;
+  }
+}
+
+cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int npap, CgScalars *sc, cudaStream_t s) {
+  k_fcg_alpha<<<1, kBlock, 0, s>>>(pr, npr, pap, npap, sc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ flexible outer CG (FP64)
+// Flexible CG with one-term orthogonalisation (Notay): z_k = B_k(r_k) (inner FP32 solve),
+// p_k = z_k - (z_k.A p_{k-1} / p_{k-1}.A p_{k-1}) p_{k-1}, alpha_k = p_k.r_k / p_k.A p_k.
+
+// z = ||r|| * x_in (undo the inner scaling); partial z . A p_{k-1}
+__global__ void __launch_bounds__(kBlock) k_fcg_gamma(const float *__restrict__ xin, double *z,
+                                                      const double *__restrict__ Ap, int64_t n3, double *part,
+                                                      const CgScalars *so) {
+  if (so->done) return;
+  const double nr = sqrt(so->rr);
+  double g = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)xin[i] * nr;
+    z[i] = zi;
+    g += zi * Ap[i];
+  }
+  g = block_sum(g);
+  if (threadIdx.x == 0) part[blockIdx.x] = g;
+}
+
+// p = z + beta p; partial p . r; Ap = 0
+__global__ void __launch_bounds__(kBlock) k_fcg_p(double *p, const double *__restrict__ z,
+                                                  const double *__restrict__ r, double *Ap, int64_t n3, double *part,
+                                                  const CgScalars *so) {
+  if (so->done) return;
+  const double beta = so->beta;
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double pi = z[i] + beta * p[i];
+    p[i] = pi;
+    a += pi * r[i];
+    Ap[i] = 0.0;
+  }
+  a = block_sum(a);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+// x += alpha p; r -= alpha A p; partial r . r
+__global__ void __launch_bounds__(kBlock) k_fcg_update(double *x, double *r, const double *__restrict__ p,
+                                                       const double *__restrict__ Ap, int64_t n3, double *part,
+                                                       const CgScalars *so) {
+  if (so->done) return;
+  const double alpha = so->alpha;
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * Ap[i];
+    r[i] = ri;
+    a += ri * ri;
+  }
+  a = block_sum(a);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+// r = b - Ap; partials b.b, r.r
+__global__ void __launch_bounds__(kBlock) k_fcg_init(const double *__restrict__ b, const double *__restrict__ Ap,
+                                                     double *r, int64_t n3, double *part) {
+  double bb = 0.0, rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bv = b[i], rv = bv - Ap[i];
+    r[i] = rv;
+    bb += bv * bv;
+    rr += rv * rv;
+  }
+  const double s0 = block_sum(bb), s1 = block_sum(rr);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_t N, double *part, cudaStream_t s) {
+  k_fcg_init<<<vec_blocks(N), kBlock, 0, s>>>(b, Ap, r, 3 * N, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_fcg_gamma(const float *xin, double *z, const double *Ap, int64_t N, double *part,
+                             const CgScalars *so, cudaStream_t s) {
+  k_fcg_gamma<<<vec_blocks(N), kBlock, 0, s>>>(xin, z, Ap, 3 * N, part, so);
+  return cudaGetLastError();
+}
+cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, int64_t N, double *part,
+                         const CgScalars *so, cudaStream_t s) {
+  k_fcg_p<<<vec_blocks(N), kBlock, 0, s>>>(p, z, r, Ap, 3 * N, part, so);
+  return cudaGetLastError();
+}
+cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, int64_t N, double *part,
+                              const CgScalars *so, cudaStream_t s) {
+  k_fcg_update<<<vec_blocks(N), kBlock, 0, s>>>(x, r, p, Ap, 3 * N, part, so);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ inner FP32 PCG (preconditioner)
+// Solves A x_in = r / ||r|| approximately in FP32 (FP64 reductions), block-Jacobi
+// preconditioned, from x_in = 0.  Skips when the outer CG is done.
+
+__device__ __forceinline__ void sym3_apply_f(const float *J, const float r[3], float z[3]) {
+  z[0] = J[0] * r[0] + J[5] * r[1] + J[4] * r[2];
+  z[1] = J[5] * r[0] + J[1] * r[1] + J[3] * r[2];
+  z[2] = J[4] * r[0] + J[3] * r[1] + J[2] * r[2];
+}
+
+__global__ void __launch_bounds__(kBlock) k_in_init(const double *__restrict__ r, const CgScalars *so,
+                                                    const float *__restrict__ J, float *rin, float *zin, float *pin,
+                                                    float *xin, float *Apin, int64_t N, double *part) {
+  if (so->done) return;
+  const double sc = 1.0 / sqrt(so->rr);
+  double rr = 0.0, rz = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    float rv[3], zv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rv[c] = (float)(r[3 * i + c] * sc);
+    sym3_apply_f(J + 6 * i, rv, zv);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rin[3 * i + c] = rv[c];
+      zin[3 * i + c] = zv[c];
+      pin[3 * i + c] = zv[c];
+      xin[3 * i + c] = 0.0f;
+      Apin[3 * i + c] = 0.0f;
+      rr += (double)rv[c] * rv[c];
+      rz += (double)rv[c] * zv[c];
+    }
+  }
+  const double s0 = block_sum(rr), s1 = block_sum(rz);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s0;
+    part[2 * gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_in_update(float *xin, float *rin, float *zin, const float *__restrict__ pin,
+                                                      const float *__restrict__ Apin, const float *__restrict__ J,
+                                                      int64_t N, double *part, const CgScalars *si,
+                                                      const CgScalars *so) {
+  if (so->done || si->done) return;
+  const float alpha = (float)si->alpha;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    float rv[3], zv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      xin[3 * i + c] += alpha * pin[3 * i + c];
+      rv[c] = rin[3 * i + c] - alpha * Apin[3 * i + c];
+      rin[3 * i + c] = rv[c];
+      rr += (double)rv[c] * rv[c];
+    }
+    sym3_apply_f(J + 6 * i, rv, zv);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      zin[3 * i + c] = zv[c];
+      rz += (double)rv[c] * zv[c];
+    }
+  }
+  const double s0 = block_sum(rr), s1 = block_sum(rz);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+__global__ void k_in_pupdate(float *pin, const float *__restrict__ zin, float *Apin, int64_t n3, const CgScalars *si,
+                             const CgScalars *so) {
+  if (so->done || si->done) return;
+  const float beta = (float)si->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    pin[i] = zin[i] + beta * pin[i];
+    Apin[i] = 0.0f;
+  }
+}
+
+cudaError_t launch_in_init(const double *r, const CgScalars *so, const float *J, float *rin, float *zin, float *pin,
+                           float *xin, float *Apin, int64_t N, double *part, cudaStream_t s) {
+  k_in_init<<<vec_blocks(N), kBlock, 0, s>>>(r, so, J, rin, zin, pin, xin, Apin, N, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_in_update(float *xin, float *rin, float *zin, const float *pin, const float *Apin, const float *J,
+                             int64_t N, double *part, const CgScalars *si, const CgScalars *so, cudaStream_t s) {
+  k_in_update<<<vec_blocks(N), kBlock, 0, s>>>(xin, rin, zin, pin, Apin, J, N, part, si, so);
+  return cudaGetLastError();
+}
+cudaError_t launch_in_pupdate(float *pin, const float *zin, float *Apin, int64_t N, const CgScalars *si,
+                              const CgScalars *so, cudaStream_t s) {
+  k_in_pupdate<<<vec_blocks(N), kBlock, 0, s>>>(pin, zin, Apin, 3 * N, si, so);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock) k_cg_update(double *x, double *r, double *z, const double *__restrict__ p,
+                                                      const double *__restrict__ Ap, const double *__restrict__ Jinv,
+                                                      int64_t N, double *part, const CgScalars *sc) {
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double rv[3], zv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x[3 * i + c] += alpha * p[3 * i + c];
+      rv[c] = r[3 * i + c] - alpha * Ap[3 * i + c];
+      r[3 * i + c] = rv[c];
+      rr += rv[c] * rv[c];
+    }
+    sym3_apply(Jinv + 6 * i, rv, zv);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      z[3 * i + c] = zv[c];
+      rz += rv[c] * zv[c];
+    }
+  }
+  const double s0 = block_sum(rr), s1 = block_sum(rz);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+cudaError_t launch_cg_update(double *x, double *r, double *z, const double *p, const double *Ap, const double *Jinv,
+                             int64_t N, double *part, const CgScalars *sc, cudaStream_t s) {
+  k_cg_update<<<vec_blocks(N), kBlock, 0, s>>>(x, r, z, p, Ap, Jinv, N, part, sc);
+  return cudaGetLastError();
+}
+
+__global__ void k_cg_pupdate(double *p, const double *__restrict__ z, double *Ap, int64_t n3, const CgScalars *sc) {
+  if (sc->done) return;
+  const double beta = sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = z[i] + beta * p[i];
+    Ap[i] = 0.0;
+  }
+}
+
+cudaError_t launch_cg_pupdate(double *p, const double *z, double *Ap, int64_t N, const CgScalars *sc, cudaStream_t s) {
+  k_cg_pupdate<<<vec_blocks(N), kBlock, 0, s>>>(p, z, Ap, 3 * N, sc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Newmark-beta updates (below Eq. 1)
+
+// du holds the increment; u += du; v <- -v + 2/dt du; a <- -a - 4/dt v_old + 4/dt^2 du.
+__global__ void k_newmark(double *u, double *v, double *a, const double *__restrict__ du, int64_t n3, double dt) {
+  const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = du[i], vo = v[i];
+    u[i] += d;
+    v[i] = -vo + c2 * d;
+    a[i] = -a[i] - c4 * vo + c44 * d;
+  }
+}
+
+cudaError_t launch_newmark(double *u, double *v, double *a, double *, const double *du, int64_t N, double dt,
+                           cudaStream_t s) {
+  k_newmark<<<vec_blocks(N), kBlock, 0, s>>>(u, v, a, du, 3 * N, dt);
+  return cudaGetLastError();
+}
+
+__global__ void k_surface_gather(const int32_t *__restrict__ surf, int64_t Ns, const double *__restrict__ u,
+                                 const double *__restrict__ v, const double *__restrict__ a, double *ou, double *ov,
+                                 double *oa) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * Ns; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / 3, c = i % 3;
+    const int64_t n = surf[s];
+    ou[i] = u[3 * n + c];
+    ov[i] = v[3 * n + c];
+    oa[i] = a[3 * n + c];
+  }
+}
+
+cudaError_t launch_surface_gather(const int32_t *surf, int64_t Ns, const double *u, const double *v, const double *a,
+                                  double *ou, double *ov, double *oa, cudaStream_t s) {
+  if (Ns <= 0) return cudaSuccess;
+  k_surface_gather<<<vec_blocks(Ns), kBlock, 0, s>>>(surf, Ns, u, v, a, ou, ov, oa);
+  return cudaGetLastError();
+}
+
+__global__ void k_d_to_f32(const double *src, float *dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+cudaError_t launch_d_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_d_to_f32<<<vec_blocks(n), kBlock, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_dot_partials(const double *x, const double *y, int64_t n, double *part) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += x[i] * y[i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *part, cudaStream_t s) {
+  k_dot_partials<<<vec_blocks(n), kBlock, 0, s>>>(x, y, n, part);
+  return cudaGetLastError();
+}
+
+}  // namespace ns

@@ -1,0 +1,165 @@
+// Device helpers shared by the library's kernels: quadratic-tetrahedron
+// element arithmetic (Sec. 2.1), reductions and atomics.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ns_internal.h"
+
+namespace ns {
+
+// Barycentric coordinates of the four integration points: (a, b, b, b) and
+// permutations, a = (5 + 3 sqrt5)/20, b = (5 - sqrt5)/20 (degree-2 rule).
+#define NS_QA 0.58541019662496845446
+#define NS_QB 0.13819660112501051518
+
+// local node index of the edge between vertices i and j (order (0,1) (1,2) (0,2) (0,3) (1,3) (2,3))
+__host__ __device__ __forceinline__ constexpr int edge_node(int i, int j) {
+  return (i < j ? i : j) == 0 ? ((i > j ? i : j) == 1 ? 4 : ((i > j ? i : j) == 2 ? 6 : 7))
+                              : ((i < j ? i : j) == 1 ? ((i > j ? i : j) == 2 ? 5 : 8) : 9);
+}
+
+// packed index of entry (i, j) of a symmetric 6x6 (upper triangle, row major)
+__host__ __device__ __forceinline__ constexpr int sym6(int i, int j) {
+  return (i < j ? i : j) * 6 - ((i < j ? i : j) * ((i < j ? i : j) - 1)) / 2 + ((i > j ? i : j) - (i < j ? i : j));
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) {
+  return __ldg(p);
+}
+
+__device__ __forceinline__ void atomic_add(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add(float *p, float v) { atomicAdd(p, v); }
+
+// Barycentric gradients of one element: g[0..3][3], from the stored grad L1..L3.
+template <typename T>
+__device__ __forceinline__ void load_grads(const T *__restrict__ geom, int64_t epad, int64_t e, T g[4][3], T &vol) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[k + 1][c] = ldg(geom + (3 * k + c) * epad + e);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+  vol = ldg(geom + 9 * epad + e);
+}
+
+// Displacement gradient at integration point q: grad u = sum_k G_k (x) grad L_k with
+// G_k = P_k + 4(a-b) (q == k ? x_k : x_kq), P_k = (4b-1) x_k + 4b sum_{j != k} x_kj.
+template <typename T, int q>
+__device__ __forceinline__ void point_grad(const T x[10][3], const T P[4][3], const T g[4][3], T H[3][3]) {
+  const T dab = (T)(4.0 * (NS_QA - NS_QB));
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) H[r][c] = (T)0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T Gk[3];
+    const int nk = (k == q) ? k : edge_node(k, q);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Gk[r] = P[k][r] + dab * x[nk][r];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) H[r][c] += Gk[r] * g[k][c];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void compute_P(const T x[10][3], T P[4][3]) {
+  const T c1 = (T)(4.0 * NS_QB - 1.0), c2 = (T)(4.0 * NS_QB);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T s[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j != k)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) s[r] += x[edge_node(k, j)][r];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) P[k][r] = c1 * x[k][r] + c2 * s[r];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void voigt_strain(const T H[3][3], T eps[6]) {
+  eps[0] = H[0][0];
+  eps[1] = H[1][1];
+  eps[2] = H[2][2];
+  eps[3] = H[1][2] + H[2][1];
+  eps[4] = H[0][2] + H[2][0];
+  eps[5] = H[0][1] + H[1][0];
+}
+
+// Adds the nodal forces of stress sig (Voigt) at point q: y_i += grad N_i(q) . S.
+template <typename T, int q>
+__device__ __forceinline__ void point_force(const T sig[6], const T g[4][3], T y[10][3]) {
+  T R[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    R[k][0] = sig[0] * g[k][0] + sig[5] * g[k][1] + sig[4] * g[k][2];
+    R[k][1] = sig[5] * g[k][0] + sig[1] * g[k][1] + sig[3] * g[k][2];
+    R[k][2] = sig[4] * g[k][0] + sig[3] * g[k][1] + sig[2] * g[k][2];
+  }
+  const T la = (T)NS_QA, lb = (T)NS_QB;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T ck = (k == q) ? (T)(4.0 * NS_QA - 1.0) : (T)(4.0 * NS_QB - 1.0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) y[k][r] += ck * R[k][r];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = k + 1; j < 4; ++j) {
+      const T lk = (k == q) ? la : lb, lj = (j == q) ? la : lb;
+      const int ne = edge_node(k, j);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) y[ne][r] += (T)4 * (lj * R[k][r] + lk * R[j][r]);
+    }
+}
+
+// Component r of y += c * 420 * M_ref w, with the exact consistent mass of a straight
+// quadratic tetrahedron, M_ref * 420 / V: vertex-vertex 6 (diagonal) / 1; vertex-edge
+// -4 (edge touches the vertex) / -6; edge-edge 32 (diagonal) / 16 (sharing a vertex) /
+// 8 (opposite).  c carries V / 420 and the coefficient.
+template <typename T>
+__device__ __forceinline__ void mass_apply_1(const T w[10], T c, T y[10][3], int r) {
+  const T sv = w[0] + w[1] + w[2] + w[3];
+  const T se = w[4] + w[5] + w[6] + w[7] + w[8] + w[9];
+  // vertex i: 5 w_i + sv - 6 se + 2 (sum of the three edges at i)
+  const T vb = sv - (T)6 * se;
+  y[0][r] += c * ((T)5 * w[0] + vb + (T)2 * (w[4] + w[6] + w[7]));
+  y[1][r] += c * ((T)5 * w[1] + vb + (T)2 * (w[4] + w[5] + w[8]));
+  y[2][r] += c * ((T)5 * w[2] + vb + (T)2 * (w[5] + w[6] + w[9]));
+  y[3][r] += c * ((T)5 * w[3] + vb + (T)2 * (w[7] + w[8] + w[9]));
+  // edge (a,b) with opposite edge o: -6 sv + 2 (w_a + w_b) + 16 se + 16 w_e - 8 w_o
+  const T eb = (T)16 * se - (T)6 * sv;
+  y[4][r] += c * (eb + (T)2 * (w[0] + w[1]) + (T)16 * w[4] - (T)8 * w[9]);
+  y[5][r] += c * (eb + (T)2 * (w[1] + w[2]) + (T)16 * w[5] - (T)8 * w[7]);
+  y[6][r] += c * (eb + (T)2 * (w[0] + w[2]) + (T)16 * w[6] - (T)8 * w[8]);
+  y[7][r] += c * (eb + (T)2 * (w[0] + w[3]) + (T)16 * w[7] - (T)8 * w[5]);
+  y[8][r] += c * (eb + (T)2 * (w[1] + w[3]) + (T)16 * w[8] - (T)8 * w[6]);
+  y[9][r] += c * (eb + (T)2 * (w[2] + w[3]) + (T)16 * w[9] - (T)8 * w[4]);
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+}  // namespace ns

@@ -1,0 +1,1376 @@
+// C ABI and runtime of the GB300 time stepper: context, uploads, the per-step
+// driver (right-hand side, block-Jacobi set-up, PCG, Newmark update, multi-spring
+// update with the host<->HBM state stream of Alg. 3), read-back and checkpoints.
+#include <math.h>
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kern_common.cuh"
+#include "ns_internal.h"
+
+using namespace ns;
+
+namespace {
+
+struct EventTimer {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, int>> pending;  // (kind, first event index)
+  size_t used = 0;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void reset() {
+    used = 0;
+    pending.clear();
+  }
+  ~EventTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+enum TimeKind { TK_RHS, TK_JAC, TK_SOLVE, TK_NEWMARK, TK_SPRINGS, TK_STEP, TK_EBE64, TK_EBE32, TK_SPRING, TK_N };
+
+}  // namespace
+
+struct ns_ctx {
+  ns_config cfg{};
+  std::string err;
+  cudaStream_t s_main = nullptr, s_h2d = nullptr, s_d2h = nullptr;
+  DevMesh m;
+  double *xyz_d = nullptr;
+  bool has_mesh = false, has_mat = false, has_bnd = false, has_motion = false;
+  int nmat = 0;
+  std::vector<MatConst> mats_h;
+  MatConst *mats_d = nullptr;
+  OpCoef *op_A = nullptr, *op_K = nullptr, *op_M = nullptr, *op_Cr = nullptr, *op_rhs = nullptr;
+  double *q_d = nullptr, *T_d = nullptr, *pow_d = nullptr;
+  SpringTables tab{};
+  double *D = nullptr;
+  float *D32 = nullptr;
+  // spring state: resident elements [0, E_res) on the device, [E_res, E) in pinned host memory
+  int64_t E_res = 0;
+  SpringSoA st;                      // device, resident part
+  SpringSoA hst;                     // pinned host, streamed part
+  std::vector<SpringSoA> ring;       // device chunk buffers
+  cudaEvent_t *ev_h2d = nullptr, *ev_comp = nullptr, *ev_d2h = nullptr;
+  cudaEvent_t ev_d2h_all = nullptr, ev_stream_t0 = nullptr, ev_stream_t1 = nullptr, ev_strain = nullptr;
+  bool prefetched = false;
+  // node vectors
+  double *u = nullptr, *v = nullptr, *a = nullptr, *q = nullptr, *du = nullptr, *b = nullptr, *r = nullptr,
+         *z = nullptr, *p = nullptr, *Ap = nullptr, *Jd = nullptr, *Jinv = nullptr;
+  float *Jinv32 = nullptr;
+  float *rin = nullptr, *zin = nullptr, *pin = nullptr, *xin = nullptr, *Apin = nullptr;  // inner FP32 PCG
+  CgScalars *sc_in = nullptr;
+  double *eps = nullptr;
+  double *part = nullptr;
+  int64_t part_pap_cap = 0;
+  CgScalars *sc = nullptr, *sc_h = nullptr;
+  int32_t *flag_d = nullptr, *flag_h = nullptr;
+  double *vin_d = nullptr;
+  int64_t n_vin = 0;
+  double *surf_u = nullptr, *surf_v = nullptr, *surf_a = nullptr;
+  int64_t ring_steps = 0;
+  int64_t step = 0;
+  cudaEvent_t ev_sync = nullptr, ev_adv0 = nullptr, ev_adv1 = nullptr, ev_join = nullptr;
+  ns_stats stats{};
+  EventTimer timer;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
+};
+
+#define NS_SET(ctx, code, msg) \
+  do {                         \
+    (ctx)->err = (msg);        \
+    return (code);             \
+  } while (0)
+
+#define CKC(ctx, call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      return (e_ == cudaErrorMemoryAllocation) ? NS_ERR_OOM_DEVICE : NS_ERR_CUDA;          \
+    }                                                                                      \
+  } while (0)
+
+#define LAUNCH(ctx, call)                                                    \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    (ctx)->stats.kernel_launches++;                                          \
+    if (e_ != cudaSuccess) {                                                 \
+      (ctx)->err = std::string("launch ") + #call + ": " + cudaGetErrorString(e_); \
+      return NS_ERR_CUDA;                                                    \
+    }                                                                        \
+  } while (0)
+
+namespace {
+
+template <typename T>
+int dalloc(ns_ctx *c, T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e);
+    return NS_ERR_OOM_DEVICE;
+  }
+  return NS_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+int halloc(ns_ctx *c, T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaHostAlloc((void **)p, n * sizeof(T), cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cudaHostAlloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e);
+    return NS_ERR_OOM_PINNED;
+  }
+  return NS_OK;
+}
+
+template <typename T>
+void hfree(T *&p) {
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+}
+
+int64_t pad64(int64_t n) { return ((n + 63) / 64) * 64; }
+
+// Bounded wait: poll the event until it completes or the deadline passes.
+int wait_event(ns_ctx *c, cudaEvent_t ev) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return NS_OK;
+    if (e != cudaErrorNotReady) {
+      c->err = std::string("device error: ") + cudaGetErrorString(e);
+      return NS_ERR_CUDA;
+    }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > c->cfg.wait_timeout_s) {
+      c->err = "timed out waiting for the device";
+      return NS_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+int sync_stream(ns_ctx *c, cudaStream_t s) {
+  CKC(c, cudaEventRecord(c->ev_sync, s));
+  return wait_event(c, c->ev_sync);
+}
+
+int sync_all(ns_ctx *c) {
+  int rc;
+  if ((rc = sync_stream(c, c->s_main)) != NS_OK) return rc;
+  if ((rc = sync_stream(c, c->s_h2d)) != NS_OK) return rc;
+  return sync_stream(c, c->s_d2h);
+}
+
+void tbegin(ns_ctx *c, int kind, cudaStream_t s, cudaEvent_t *out) {
+  if (!c->cfg.timing) return;
+  *out = c->timer.get();
+  cudaEventRecord(*out, s);
+}
+
+void tend(ns_ctx *c, int kind, cudaStream_t s, cudaEvent_t start) {
+  if (!c->cfg.timing) return;
+  cudaEvent_t e = c->timer.get();
+  cudaEventRecord(e, s);
+  c->tev.push_back({kind, {start, e}});
+}
+
+void flush_times(ns_ctx *c) {
+  for (auto &t : c->tev) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, t.second.first, t.second.second) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    switch (t.first) {
+      case TK_RHS: c->stats.ms_rhs += ms; break;
+      case TK_JAC: c->stats.ms_jacobi += ms; break;
+      case TK_SOLVE: c->stats.ms_solve += ms; break;
+      case TK_NEWMARK: c->stats.ms_newmark += ms; break;
+      case TK_SPRINGS: c->stats.ms_springs += ms; break;
+      case TK_STEP: c->stats.ms_step += ms; break;
+      case TK_EBE64: c->stats.ms_ebe64 += ms; c->stats.n_ebe64++; break;
+      case TK_EBE32: c->stats.ms_ebe32 += ms; c->stats.n_ebe32++; break;
+      case TK_SPRING: c->stats.ms_spring += ms; c->stats.n_spring++; break;
+      default: break;
+    }
+  }
+  c->tev.clear();
+}
+
+int nblk(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+
+// ---------------------------------------------------------------- operator application helpers
+
+// y += Op x over all elements (atomic) or colour by colour (plain adds). Returns the number
+// of dot partials written (if dot != nullptr).
+int apply_elems64(ns_ctx *c, const OpCoef *op, const double *xm, const double *xk, double *y, double *dot,
+                  const int32_t *skip, int *npart) {
+  const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
+  int off = 0;
+  if (atomic) {
+    LAUNCH(c, launch_ebe64(c->m, c->D, op, xm, xk, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main));
+    off = nblk(c->m.E);
+  } else {
+    for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k) {
+      const int64_t e0 = c->m.ecol_off[k], e1 = c->m.ecol_off[k + 1];
+      LAUNCH(c, launch_ebe64(c->m, c->D, op, xm, xk, y, c->m.ecol_ids, e0, e1, false, dot ? dot + off : nullptr, skip,
+                             c->s_main));
+      off += nblk(e1 - e0);
+    }
+  }
+  if (npart) *npart = off;
+  return NS_OK;
+}
+
+int apply_faces64(ns_ctx *c, double cC, const double *x, const double *vin, double *y, double *dot,
+                  const int32_t *skip, int *npart) {
+  const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
+  int off = 0;
+  if (c->m.F > 0) {
+    if (atomic) {
+      LAUNCH(c, launch_faces64(c->m, c->mats_d, cC, x, vin, y, nullptr, 0, c->m.F, true, dot, skip, c->s_main));
+      off = nblk(c->m.F);
+    } else {
+      for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k) {
+        const int64_t f0 = c->m.fcol_off[k], f1 = c->m.fcol_off[k + 1];
+        LAUNCH(c, launch_faces64(c->m, c->mats_d, cC, x, vin, y, c->m.fcol_ids, f0, f1, false,
+                                 dot ? dot + off : nullptr, skip, c->s_main));
+        off += nblk(f1 - f0);
+      }
+    }
+  }
+  if (npart) *npart = off;
+  return NS_OK;
+}
+
+// y = A x (the matrix of Eq. 1), with the element-energy partials of x.A x if dot != nullptr
+int apply_A(ns_ctx *c, const double *x, double *y, bool zero_y, double *dot, const int32_t *skip, int *npart,
+            bool timed) {
+  int rc;
+  if (zero_y) CKC(c, cudaMemsetAsync(y, 0, sizeof(double) * 3 * c->m.N, c->s_main));
+  cudaEvent_t t0 = nullptr;
+  if (timed) tbegin(c, TK_EBE64, c->s_main, &t0);
+  int ne = 0, nf = 0;
+  if ((rc = apply_elems64(c, c->op_A, nullptr, x, y, dot, skip, &ne)) != NS_OK) return rc;
+  if (timed) tend(c, TK_EBE64, c->s_main, t0);
+  if ((rc = apply_faces64(c, 2.0 / c->cfg.dt, x, nullptr, y, dot ? dot + ne : nullptr, skip, &nf)) != NS_OK) return rc;
+  if (npart) *npart = ne + nf;
+  return NS_OK;
+}
+
+// y = A x in FP32 (inner preconditioner solve), element-energy partials into dot
+int apply_A32(ns_ctx *c, const float *x, float *y, double *dot, const int32_t *skip, int *npart) {
+  const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
+  int off = 0;
+  cudaEvent_t t0 = nullptr;
+  tbegin(c, TK_EBE32, c->s_main, &t0);
+  if (atomic) {
+    LAUNCH(c, launch_ebe32(c->m, c->D32, c->op_A, x, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main));
+    off = nblk(c->m.E);
+  } else {
+    for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k) {
+      const int64_t e0 = c->m.ecol_off[k], e1 = c->m.ecol_off[k + 1];
+      LAUNCH(c, launch_ebe32(c->m, c->D32, c->op_A, x, y, c->m.ecol_ids, e0, e1, false, dot + off, skip, c->s_main));
+      off += nblk(e1 - e0);
+    }
+  }
+  tend(c, TK_EBE32, c->s_main, t0);
+  if (c->m.F > 0) {
+    const float cC = (float)(2.0 / c->cfg.dt);
+    if (atomic) {
+      LAUNCH(c, launch_faces32(c->m, c->mats_d, cC, x, y, nullptr, 0, c->m.F, true, dot + off, skip, c->s_main));
+      off += nblk(c->m.F);
+    } else {
+      for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k) {
+        const int64_t f0 = c->m.fcol_off[k], f1 = c->m.fcol_off[k + 1];
+        LAUNCH(c, launch_faces32(c->m, c->mats_d, cC, x, y, c->m.fcol_ids, f0, f1, false, dot + off, skip,
+                                 c->s_main));
+        off += nblk(f1 - f0);
+      }
+    }
+  }
+  *npart = off;
+  return NS_OK;
+}
+
+int fill_opcoefs(ns_ctx *c) {
+  const double dt = c->cfg.dt;
+  OpCoef A{}, K{}, M{}, Cr{}, R{};
+  for (int i = 0; i < c->nmat; ++i) {
+    const MatConst &m = c->mats_h[i];
+    A.mK[i] = m.rho * (4.0 / (dt * dt) + 2.0 * m.ray_a / dt);
+    A.kK[i] = 1.0 + 2.0 * m.ray_b / dt;
+    K.kK[i] = 1.0;
+    M.mK[i] = m.rho;
+    Cr.mK[i] = m.rho * m.ray_a;
+    Cr.kK[i] = m.ray_b;
+    R.mM[i] = m.rho;                          // M a
+    R.mK[i] = m.rho * (4.0 / dt + m.ray_a);   // M (4/dt + alpha) v
+    R.kK[i] = m.ray_b;                        // beta K v
+  }
+  CKC(c, cudaMemcpy(c->op_A, &A, sizeof(OpCoef), cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->op_K, &K, sizeof(OpCoef), cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->op_M, &M, sizeof(OpCoef), cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->op_Cr, &Cr, sizeof(OpCoef), cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->op_rhs, &R, sizeof(OpCoef), cudaMemcpyHostToDevice));
+  return NS_OK;
+}
+
+int alloc_soa(ns_ctx *c, SpringSoA &s, int64_t nspr, bool host) {
+  int rc;
+  if (host) {
+    if ((rc = halloc(c, &s.tau, nspr)) || (rc = halloc(c, &s.gR, nspr)) || (rc = halloc(c, &s.tR, nspr)) ||
+        (rc = halloc(c, &s.gmax, nspr)) || (rc = halloc(c, &s.dir, nspr)) || (rc = halloc(c, &s.mode, nspr)))
+      return rc;
+    memset(s.tau, 0, nspr * 8);
+    memset(s.gR, 0, nspr * 8);
+    memset(s.tR, 0, nspr * 8);
+    memset(s.gmax, 0, nspr * 8);
+    memset(s.dir, 0, nspr * 4);
+    memset(s.mode, 0, nspr * 4);
+  } else {
+    if ((rc = dalloc(c, &s.tau, nspr)) || (rc = dalloc(c, &s.gR, nspr)) || (rc = dalloc(c, &s.tR, nspr)) ||
+        (rc = dalloc(c, &s.gmax, nspr)) || (rc = dalloc(c, &s.dir, nspr)) || (rc = dalloc(c, &s.mode, nspr)))
+      return rc;
+    CKC(c, cudaMemset(s.tau, 0, nspr * 8));
+    CKC(c, cudaMemset(s.gR, 0, nspr * 8));
+    CKC(c, cudaMemset(s.tR, 0, nspr * 8));
+    CKC(c, cudaMemset(s.gmax, 0, nspr * 8));
+    CKC(c, cudaMemset(s.dir, 0, nspr * 4));
+    CKC(c, cudaMemset(s.mode, 0, nspr * 4));
+  }
+  return NS_OK;
+}
+
+void free_soa(SpringSoA &s, bool host) {
+  if (host) {
+    hfree(s.tau); hfree(s.gR); hfree(s.tR); hfree(s.gmax); hfree(s.dir); hfree(s.mode);
+  } else {
+    dfree(s.tau); dfree(s.gR); dfree(s.tR); dfree(s.gmax); dfree(s.dir); dfree(s.mode);
+  }
+}
+
+// copy springs [off, off + n) between two SoA sets
+int copy_soa(ns_ctx *c, const SpringSoA &dst, int64_t doff, const SpringSoA &src, int64_t soff, int64_t n,
+             cudaMemcpyKind kind, cudaStream_t s) {
+  CKC(c, cudaMemcpyAsync(dst.tau + doff, src.tau + soff, n * 8, kind, s));
+  CKC(c, cudaMemcpyAsync(dst.gR + doff, src.gR + soff, n * 8, kind, s));
+  CKC(c, cudaMemcpyAsync(dst.tR + doff, src.tR + soff, n * 8, kind, s));
+  CKC(c, cudaMemcpyAsync(dst.gmax + doff, src.gmax + soff, n * 8, kind, s));
+  CKC(c, cudaMemcpyAsync(dst.dir + doff, src.dir + soff, n * 4, kind, s));
+  CKC(c, cudaMemcpyAsync(dst.mode + doff, src.mode + soff, n * 4, kind, s));
+  return NS_OK;
+}
+
+int64_t n_chunks(const ns_ctx *c) {
+  const int64_t ns_el = c->m.E - c->E_res;
+  return ns_el <= 0 ? 0 : (ns_el + c->cfg.chunk_elems - 1) / c->cfg.chunk_elems;
+}
+
+// H2D of streamed chunk k into ring slot k % R
+int issue_h2d(ns_ctx *c, int64_t k) {
+  const int R = c->cfg.ring_depth;
+  const int slot = (int)(k % R);
+  const int64_t S4 = 4 * (int64_t)c->tab.S;
+  const int64_t e0 = c->E_res + k * c->cfg.chunk_elems;
+  const int64_t e1 = std::min(c->m.E, e0 + c->cfg.chunk_elems);
+  if (k >= R) CKC(c, cudaStreamWaitEvent(c->s_h2d, c->ev_d2h[slot], 0));
+  int rc = copy_soa(c, c->ring[slot], 0, c->hst, (e0 - c->E_res) * S4, (e1 - e0) * S4, cudaMemcpyHostToDevice,
+                    c->s_h2d);
+  if (rc) return rc;
+  c->stats.h2d_bytes += (e1 - e0) * S4 * 40;
+  CKC(c, cudaEventRecord(c->ev_h2d[slot], c->s_h2d));
+  return NS_OK;
+}
+
+// Start the first ring-depth chunk transfers of this step as early as possible (they only
+// depend on the previous step's write-back, not on this step's solve).
+int prefetch_state(ns_ctx *c) {
+  const int64_t nc = n_chunks(c);
+  if (nc == 0 || c->prefetched) return NS_OK;
+  CKC(c, cudaStreamWaitEvent(c->s_h2d, c->ev_d2h_all, 0));
+  if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t0, c->s_h2d));
+  for (int64_t k = 0; k < std::min<int64_t>(nc, c->cfg.ring_depth); ++k) {
+    int rc = issue_h2d(c, k);
+    if (rc) return rc;
+  }
+  c->prefetched = true;
+  return NS_OK;
+}
+
+// Multi-spring update (Alg. 3 pipeline for the streamed part): resident elements in one
+// launch, then per chunk: wait H2D -> compute -> D2H, refilling freed slots.
+int spring_phase(ns_ctx *c) {
+  int rc;
+  cudaEvent_t t0 = nullptr;
+  LAUNCH(c, launch_strain(c->m, c->u, c->du, c->eps, 0, c->m.E, c->s_main));
+  if (c->E_res > 0) {
+    tbegin(c, TK_SPRING, c->s_main, &t0);
+    LAUNCH(c, launch_springs(c->tab, c->mats_d, c->m.mat, nullptr, c->eps, c->st, 0, 0, 4 * c->E_res, c->D, c->m.epad,
+                             nullptr, c->s_main));
+    tend(c, TK_SPRING, c->s_main, t0);
+  }
+  const int64_t nc = n_chunks(c);
+  if (nc == 0) return NS_OK;
+  if ((rc = prefetch_state(c)) != NS_OK) return rc;
+  const int R = c->cfg.ring_depth;
+  for (int64_t k = 0; k < nc; ++k) {
+    const int slot = (int)(k % R);
+    const int64_t e0 = c->E_res + k * c->cfg.chunk_elems;
+    const int64_t e1 = std::min(c->m.E, e0 + c->cfg.chunk_elems);
+    const int64_t S4 = 4 * (int64_t)c->tab.S;
+    CKC(c, cudaStreamWaitEvent(c->s_main, c->ev_h2d[slot], 0));
+    tbegin(c, TK_SPRING, c->s_main, &t0);
+    LAUNCH(c, launch_springs(c->tab, c->mats_d, c->m.mat, nullptr, c->eps, c->ring[slot], 4 * e0, 4 * e0, 4 * e1,
+                             c->D, c->m.epad, nullptr, c->s_main));
+    tend(c, TK_SPRING, c->s_main, t0);
+    CKC(c, cudaEventRecord(c->ev_comp[slot], c->s_main));
+    CKC(c, cudaStreamWaitEvent(c->s_d2h, c->ev_comp[slot], 0));
+    if ((rc = copy_soa(c, c->hst, (e0 - c->E_res) * S4, c->ring[slot], 0, (e1 - e0) * S4, cudaMemcpyDeviceToHost,
+                       c->s_d2h)))
+      return rc;
+    c->stats.d2h_bytes += (e1 - e0) * S4 * 40;
+    CKC(c, cudaEventRecord(c->ev_d2h[slot], c->s_d2h));
+    if (k + R < nc && (rc = issue_h2d(c, k + R)) != NS_OK) return rc;
+  }
+  CKC(c, cudaEventRecord(c->ev_d2h_all, c->s_d2h));
+  if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t1, c->s_d2h));
+  c->prefetched = false;
+  return NS_OK;
+}
+
+int read_scalars(ns_ctx *c) {
+  CKC(c, cudaMemcpyAsync(c->sc_h, c->sc, 2 * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->s_main));
+  return sync_stream(c, c->s_main);
+}
+
+// Flexible FP64 CG whose preconditioner is an FP32 block-Jacobi PCG on the same operator
+// (the paper's precision policy: only the preconditioning is single precision).
+int solve_ir(ns_ctx *c) {
+  int rc;
+  const int64_t N = c->m.N;
+  const int nbv = vec_blocks(N);
+  double *pv = c->part + c->part_pap_cap;
+  LAUNCH(c, launch_D_to_f32(c->D, c->D32, c->m.epad, c->m.E, c->s_main));
+  if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+  if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
+  LAUNCH(c, launch_fcg_init(c->b, c->Ap, c->r, N, pv, c->s_main));
+  LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc, NS_FIN_FCG_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+  if ((rc = read_scalars(c)) != NS_OK) return rc;
+  if (c->sc_h[0].done == 2) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+  int inner_total = 0;
+  const int32_t *skip_in = &c->sc_in->done, *skip_out = &c->sc->done;
+  while (c->sc_h[0].done == 0) {
+    // inner solve A z ~= r in FP32 from zero
+    LAUNCH(c, launch_in_init(c->r, c->sc, c->Jinv32, c->rin, c->zin, c->pin, c->xin, c->Apin, N, pv, c->s_main));
+    LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc_in, NS_FIN_INIT, c->cfg.inner_tol, c->cfg.inner_max_iter, c->s_main));
+    for (int it = 0; it < c->cfg.inner_max_iter; ++it) {
+      int np = 0;
+      if ((rc = apply_A32(c, c->pin, c->Apin, c->part, skip_in, &np)) != NS_OK) return rc;
+      LAUNCH(c, launch_cg_final(c->part, np, 1, c->sc_in, NS_FIN_PAP, c->cfg.inner_tol, c->cfg.inner_max_iter,
+                                c->s_main));
+      LAUNCH(c, launch_in_update(c->xin, c->rin, c->zin, c->pin, c->Apin, c->Jinv32, N, pv, c->sc_in, c->sc,
+                                 c->s_main));
+      LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc_in, NS_FIN_UPDATE, c->cfg.inner_tol, c->cfg.inner_max_iter,
+                                c->s_main));
+      LAUNCH(c, launch_in_pupdate(c->pin, c->zin, c->Apin, N, c->sc_in, c->sc, c->s_main));
+    }
+    // outer flexible CG step
+    LAUNCH(c, launch_fcg_gamma(c->xin, c->z, c->Ap, N, pv, c->sc, c->s_main));
+    LAUNCH(c, launch_cg_final(pv, nbv, 1, c->sc, NS_FIN_FCG_BETA, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+    LAUNCH(c, launch_fcg_p(c->p, c->z, c->r, c->Ap, N, pv, c->sc, c->s_main));
+    int np = 0;
+    if ((rc = apply_A(c, c->p, c->Ap, false, c->part, skip_out, &np, true)) != NS_OK) return rc;
+    LAUNCH(c, launch_fcg_alpha(pv, nbv, c->part, np, c->sc, c->s_main));
+    LAUNCH(c, launch_fcg_update(c->du, c->r, c->p, c->Ap, N, pv, c->sc, c->s_main));
+    LAUNCH(c, launch_cg_final(pv, nbv, 1, c->sc, NS_FIN_FCG_UPDATE, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+    if ((rc = read_scalars(c)) != NS_OK) return rc;
+    inner_total += c->sc_h[1].iters;
+  }
+  c->stats.inner_iters_last = inner_total;
+  return NS_OK;
+}
+
+// One time step n = step + 1 (Eq. 1 and the updates below it, then the spring update).
+int one_step(ns_ctx *c) {
+  int rc;
+  const double dt = c->cfg.dt;
+  const int64_t N = c->m.N, n = c->step + 1;
+  const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
+  cudaEvent_t tstep = nullptr, t0 = nullptr;
+  tbegin(c, TK_STEP, c->s_main, &tstep);
+  if ((rc = prefetch_state(c)) != NS_OK) return rc;
+
+  // 3x3 block-Jacobi preconditioner from the diagonal node blocks of A^n
+  tbegin(c, TK_JAC, c->s_main, &t0);
+  CKC(c, cudaMemsetAsync(c->Jd, 0, sizeof(double) * 6 * N, c->s_main));
+  if (atomic) {
+    LAUNCH(c, launch_jacobi_elems(c->m, c->D, c->op_A, c->Jd, nullptr, 0, c->m.E, true, c->s_main));
+    LAUNCH(c, launch_jacobi_faces(c->m, c->mats_d, 2.0 / dt, c->Jd, nullptr, 0, c->m.F, true, c->s_main));
+  } else {
+    for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k)
+      LAUNCH(c, launch_jacobi_elems(c->m, c->D, c->op_A, c->Jd, c->m.ecol_ids, c->m.ecol_off[k], c->m.ecol_off[k + 1],
+                                    false, c->s_main));
+    for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k)
+      LAUNCH(c, launch_jacobi_faces(c->m, c->mats_d, 2.0 / dt, c->Jd, c->m.fcol_ids, c->m.fcol_off[k],
+                                    c->m.fcol_off[k + 1], false, c->s_main));
+  }
+  CKC(c, cudaMemsetAsync(c->flag_d, 0, sizeof(int32_t), c->s_main));
+  LAUNCH(c, launch_invert_blocks(c->Jd, c->Jinv, c->Jinv32, N, c->flag_d, c->s_main));
+  tend(c, TK_JAC, c->s_main, t0);
+
+  // right-hand side of Eq. 1: f^n - q^{n-1} + C^n v^{n-1} + M (a^{n-1} + 4/dt v^{n-1})
+  tbegin(c, TK_RHS, c->s_main, &t0);
+  LAUNCH(c, launch_negate_copy(c->b, c->q, 3 * N, c->s_main));
+  if ((rc = apply_elems64(c, c->op_rhs, c->a, c->v, c->b, nullptr, nullptr, nullptr)) != NS_OK) return rc;
+  const double *vin = c->vin_d + 3 * std::min<int64_t>(n, c->n_vin - 1);
+  if ((rc = apply_faces64(c, 1.0, c->v, vin, c->b, nullptr, nullptr, nullptr)) != NS_OK) return rc;
+  tend(c, TK_RHS, c->s_main, t0);
+
+  // PCG on A du = b, starting from the previous increment (or zero)
+  tbegin(c, TK_SOLVE, c->s_main, &t0);
+  CKC(c, cudaMemcpyAsync(c->flag_h, c->flag_d, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s_main));
+  if (c->cfg.precision == NS_PREC_FP64_IR) {
+    if ((rc = solve_ir(c)) != NS_OK) return rc;
+  } else {
+  if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+  if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
+  const int nbv = vec_blocks(N);
+  double *pv = c->part + c->part_pap_cap;
+  LAUNCH(c, launch_cg_init(c->b, c->Ap, c->Jinv, c->r, c->z, c->p, N, pv, c->s_main));
+  LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc, NS_FIN_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+  if ((rc = read_scalars(c)) != NS_OK) return rc;
+  if (c->sc_h->done == 2) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+  const int batch = 8;
+  const int32_t *skip = &c->sc->done;
+  if (c->sc_h->done == 0) {
+    CKC(c, cudaMemsetAsync(c->Ap, 0, sizeof(double) * 3 * N, c->s_main));
+    for (;;) {
+      for (int it = 0; it < batch; ++it) {
+        int np = 0;
+        if ((rc = apply_A(c, c->p, c->Ap, false, c->part, skip, &np, true)) != NS_OK) return rc;
+        LAUNCH(c, launch_cg_final(c->part, np, 1, c->sc, NS_FIN_PAP, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+        LAUNCH(c, launch_cg_update(c->du, c->r, c->z, c->p, c->Ap, c->Jinv, N, pv, c->sc, c->s_main));
+        LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc, NS_FIN_UPDATE, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+        LAUNCH(c, launch_cg_pupdate(c->p, c->z, c->Ap, N, c->sc, c->s_main));
+      }
+      if ((rc = read_scalars(c)) != NS_OK) return rc;
+      if (c->sc_h->done) break;
+    }
+  }
+  }
+  tend(c, TK_SOLVE, c->s_main, t0);
+  if (*c->flag_h) NS_SET(c, NS_ERR_STATE, "block-Jacobi preconditioner has a non-positive diagonal block");
+  if (c->sc_h->done == 3) {
+    c->stats.cg_iters_last = c->sc_h->iters;
+    NS_SET(c, NS_ERR_NOT_CONVERGED, "CG reached the iteration limit at step " + std::to_string(n));
+  }
+  c->stats.cg_iters_last = c->sc_h->iters;
+  c->stats.cg_iters_total += c->sc_h->iters;
+  c->stats.relres_last = c->sc_h->bb > 0 ? sqrt(c->sc_h->rr / c->sc_h->bb) : 0.0;
+
+  // q^n = q^{n-1} + K^n du; u, v, a updates; surface record
+  tbegin(c, TK_NEWMARK, c->s_main, &t0);
+  if ((rc = apply_elems64(c, c->op_K, nullptr, c->du, c->q, nullptr, nullptr, nullptr)) != NS_OK) return rc;
+  LAUNCH(c, launch_newmark(c->u, c->v, c->a, nullptr, c->du, N, dt, c->s_main));
+  if (c->m.Ns > 0) {
+    const int64_t slot = (n - 1) % c->ring_steps, off = slot * c->m.Ns * 3;
+    LAUNCH(c, launch_surface_gather(c->m.surf, c->m.Ns, c->u, c->v, c->a, c->surf_u + off, c->surf_v + off,
+                                    c->surf_a + off, c->s_main));
+  }
+  tend(c, TK_NEWMARK, c->s_main, t0);
+
+  // multi-spring update -> D^n for the next step (lagged tangent, Alg. 4)
+  tbegin(c, TK_SPRINGS, c->s_main, &t0);
+  if ((rc = spring_phase(c)) != NS_OK) return rc;
+  tend(c, TK_SPRINGS, c->s_main, t0);
+  tend(c, TK_STEP, c->s_main, tstep);
+  c->step = n;
+  c->stats.steps = n;
+  return NS_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+void ns_config_default(ns_config *cfg) {
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->n_springs = 10;
+  cfg->dt = 0.01;
+  cfg->cg_tol = 1e-8;
+  cfg->cg_max_iter = 10000;
+  cfg->x0_prev = 1;
+  cfg->precision = NS_PREC_FP64;
+  cfg->scatter = NS_SCATTER_ATOMIC;
+  cfg->chunk_elems = 100000;
+  cfg->ring_depth = 3;
+  cfg->device_state_budget = -1;
+  cfg->rayleigh_f1 = 0.1;
+  cfg->rayleigh_f2 = 2.5;
+  cfg->surface_ring_steps = 64;
+  cfg->device = 0;
+  cfg->timing = 0;
+  cfg->inner_max_iter = 30;
+  cfg->inner_tol = 1e-3;
+  cfg->wait_timeout_s = 120.0;
+}
+
+static thread_local std::string g_create_err;
+
+const char *ns_last_error(ns_ctx *ctx) {
+  if (!ctx) return g_create_err.c_str();
+  return ctx->err.c_str();
+}
+
+int ns_create(ns_ctx **out, const ns_config *cfg) {
+  if (!out || !cfg) {
+    g_create_err = "null argument";
+    return NS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (cfg->n_springs < 5 || !(cfg->dt > 0) || !(cfg->cg_tol > 0) || cfg->cg_max_iter < 1 || cfg->ring_depth < 2 ||
+      cfg->chunk_elems < 1 || cfg->surface_ring_steps < 1 ||
+      (cfg->precision != NS_PREC_FP64 && cfg->precision != NS_PREC_FP64_IR) ||
+      (cfg->scatter != NS_SCATTER_ATOMIC && cfg->scatter != NS_SCATTER_COLOUR) || !(cfg->wait_timeout_s > 0) ||
+      cfg->inner_max_iter < 1 || !(cfg->inner_tol > 0)) {
+    g_create_err = "invalid configuration value";
+    return NS_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    g_create_err = "no CUDA device " + std::to_string(cfg->device);
+    return NS_ERR_CUDA;
+  }
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    g_create_err = "cudaSetDevice failed";
+    return NS_ERR_CUDA;
+  }
+  ns_ctx *c = new ns_ctx();
+  c->cfg = *cfg;
+  if (cudaStreamCreateWithFlags(&c->s_main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking) != cudaSuccess) {
+    g_create_err = "stream creation failed";
+    ns_destroy(c);
+    return NS_ERR_CUDA;
+  }
+  cudaEventCreateWithFlags(&c->ev_d2h_all, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_sync, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  cudaEventCreate(&c->ev_adv0);
+  cudaEventCreate(&c->ev_adv1);
+  cudaEventCreate(&c->ev_stream_t0);
+  cudaEventCreate(&c->ev_stream_t1);
+  cudaEventCreateWithFlags(&c->ev_strain, cudaEventDisableTiming);
+  const int R = cfg->ring_depth;
+  c->ev_h2d = new cudaEvent_t[R];
+  c->ev_comp = new cudaEvent_t[R];
+  c->ev_d2h = new cudaEvent_t[R];
+  for (int i = 0; i < R; ++i) {
+    cudaEventCreateWithFlags(&c->ev_h2d[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_d2h[i], cudaEventDisableTiming);
+  }
+  if (halloc(c, &c->sc_h, 2) || halloc(c, &c->flag_h, 1) || dalloc(c, &c->sc, 2) || dalloc(c, &c->flag_d, 1) ||
+      dalloc(c, &c->op_A, 1) ||
+      dalloc(c, &c->op_K, 1) || dalloc(c, &c->op_M, 1) || dalloc(c, &c->op_Cr, 1) || dalloc(c, &c->op_rhs, 1) ||
+      dalloc(c, &c->mats_d, kMaxMat)) {
+    g_create_err = c->err;
+    ns_destroy(c);
+    return NS_ERR_OOM_DEVICE;
+  }
+  cudaMemset(c->sc, 0, 2 * sizeof(CgScalars));
+  c->sc_in = c->sc + 1;
+  *c->flag_h = 0;
+  *out = c;
+  return NS_OK;
+}
+
+int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int32_t *conn, const int32_t *mat) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (c->has_mesh) NS_SET(c, NS_ERR_INVALID_ARG, "mesh already uploaded");
+  if (N <= 0 || E <= 0 || !xyz || !conn || !mat || N > INT32_MAX || E > INT32_MAX)
+    NS_SET(c, NS_ERR_INVALID_ARG, "bad mesh sizes or null pointers");
+  for (int64_t i = 0; i < E * 10; ++i)
+    if (conn[i] < 0 || conn[i] >= N) NS_SET(c, NS_ERR_BAD_MESH, "connectivity index out of range");
+  for (int64_t e = 0; e < E; ++e)
+    if (mat[e] < 0 || mat[e] >= kMaxMat) NS_SET(c, NS_ERR_BAD_MESH, "material index out of range");
+  int rc;
+  cudaSetDevice(c->cfg.device);
+  DevMesh &m = c->m;
+  m.N = N;
+  m.E = E;
+  m.epad = pad64(E);
+  std::vector<int32_t> soa((size_t)10 * m.epad, 0);
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 10; ++a) soa[(size_t)a * m.epad + e] = conn[e * 10 + a];
+  if ((rc = dalloc(c, &m.conn, soa.size())) || (rc = dalloc(c, &m.geom, 10 * m.epad)) ||
+      (rc = dalloc(c, &m.geom32, 10 * m.epad)) || (rc = dalloc(c, &m.mat, m.epad)) ||
+      (rc = dalloc(c, &c->xyz_d, 3 * N)))
+    return rc;
+  CKC(c, cudaMemcpy(m.conn, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(m.mat, mat, E * 4, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->xyz_d, xyz, N * 24, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemset(m.geom, 0, 10 * m.epad * 8));
+  CKC(c, cudaMemset(m.geom32, 0, 10 * m.epad * 4));
+  CKC(c, cudaMemset(c->flag_d, 0, 4));
+  LAUNCH(c, launch_geometry(m, c->xyz_d, c->flag_d, c->s_main));
+  CKC(c, cudaStreamSynchronize(c->s_main));
+  int32_t bad = 0;
+  CKC(c, cudaMemcpy(&bad, c->flag_d, 4, cudaMemcpyDeviceToHost));
+  if (bad) NS_SET(c, NS_ERR_BAD_MESH, "element " + std::to_string(bad - 1) + " has a non-positive volume or a curved edge");
+  // node vectors
+  const size_t n3 = 3 * (size_t)N;
+  if ((rc = dalloc(c, &c->u, n3)) || (rc = dalloc(c, &c->v, n3)) || (rc = dalloc(c, &c->a, n3)) ||
+      (rc = dalloc(c, &c->q, n3)) || (rc = dalloc(c, &c->du, n3)) || (rc = dalloc(c, &c->b, n3)) ||
+      (rc = dalloc(c, &c->r, n3)) || (rc = dalloc(c, &c->z, n3)) || (rc = dalloc(c, &c->p, n3)) ||
+      (rc = dalloc(c, &c->Ap, n3)) || (rc = dalloc(c, &c->Jd, 6 * (size_t)N)) ||
+      (rc = dalloc(c, &c->Jinv, 6 * (size_t)N)) || (rc = dalloc(c, &c->Jinv32, 6 * (size_t)N)) ||
+      (rc = dalloc(c, &c->eps, 48 * (size_t)E)))
+    return rc;
+  if (c->cfg.precision == NS_PREC_FP64_IR &&
+      ((rc = dalloc(c, &c->rin, n3)) || (rc = dalloc(c, &c->zin, n3)) || (rc = dalloc(c, &c->pin, n3)) ||
+       (rc = dalloc(c, &c->xin, n3)) || (rc = dalloc(c, &c->Apin, n3))))
+    return rc;
+  for (double *x : {c->u, c->v, c->a, c->q, c->du}) CKC(c, cudaMemset(x, 0, n3 * 8));
+  // colouring for the deterministic scatter
+  int32_t nc = 0;
+  if (c->cfg.scatter == NS_SCATTER_COLOUR) {
+    std::vector<int32_t> col((size_t)E);
+    if (host_colouring(E, N, conn, col.data(), &nc) != 0) NS_SET(c, NS_ERR_BAD_MESH, "more than 64 element colours");
+    std::vector<int32_t> ids((size_t)E);
+    m.ecol_off.assign(nc + 1, 0);
+    for (int64_t e = 0; e < E; ++e) m.ecol_off[col[e] + 1]++;
+    for (int k = 0; k < nc; ++k) m.ecol_off[k + 1] += m.ecol_off[k];
+    std::vector<int64_t> fillp(m.ecol_off.begin(), m.ecol_off.end() - 1);
+    for (int64_t e = 0; e < E; ++e) ids[fillp[col[e]]++] = (int32_t)e;
+    if ((rc = dalloc(c, &m.ecol_ids, (size_t)E))) return rc;
+    CKC(c, cudaMemcpy(m.ecol_ids, ids.data(), E * 4, cudaMemcpyHostToDevice));
+  }
+  c->part_pap_cap = nblk(E) + (int64_t)nc + 64 + nblk(1) * 2;
+  c->has_mesh = true;
+  return NS_OK;
+}
+
+int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh) NS_SET(c, NS_ERR_STATE, "upload the mesh before the materials");
+  if (n < 1 || n > kMaxMat || !mats) NS_SET(c, NS_ERR_INVALID_ARG, "bad material count");
+  for (int i = 0; i < n; ++i) {
+    const ns_material &m = mats[i];
+    if (!(m.rho > 0) || !(m.vs > 0) || !(m.vp > m.vs * 1.1547005383792517) || !(m.gamma_ref > 0) || !(m.h_max > 0) ||
+        !(m.h_max < 0.6) || !(m.rayleigh_h >= 0))
+      NS_SET(c, NS_ERR_INVALID_ARG, "material " + std::to_string(i) + " has an invalid parameter");
+  }
+  std::vector<int32_t> mh((size_t)c->m.E);
+  CKC(c, cudaMemcpy(mh.data(), c->m.mat, c->m.E * 4, cudaMemcpyDeviceToHost));
+  for (int32_t x : mh)
+    if (x >= n) NS_SET(c, NS_ERR_INVALID_ARG, "an element uses a material index beyond the table");
+  c->nmat = n;
+  c->mats_h.resize(n);
+  for (int i = 0; i < n; ++i) host_material_constants(mats[i], c->cfg.rayleigh_f1, c->cfg.rayleigh_f2, &c->mats_h[i]);
+  CKC(c, cudaMemcpy(c->mats_d, c->mats_h.data(), sizeof(MatConst) * n, cudaMemcpyHostToDevice));
+  int rc;
+  if ((rc = fill_opcoefs(c))) return rc;
+  if (c->has_mat) return NS_OK;  // state already allocated: only the constants change
+  // spring tables: q [S][6], T [S+1][21] = w q q^T (last row: their sum)
+  const int S = c->cfg.n_springs;
+  std::vector<double> qh(6 * (size_t)S), Th(21 * (size_t)(S + 1), 0.0);
+  double w = 0;
+  if (host_spring_directions(S, qh.data(), &w) != 0) NS_SET(c, NS_ERR_INVALID_ARG, "need at least 5 springs");
+  for (int k = 0; k < S; ++k)
+    for (int i = 0; i < 6; ++i)
+      for (int j = i; j < 6; ++j) {
+        const double t = w * qh[6 * k + i] * qh[6 * k + j];
+        Th[21 * (size_t)k + sym6(i, j)] = t;
+        Th[21 * (size_t)S + sym6(i, j)] += t;
+      }
+  std::vector<double> ph(kPowTabLen);
+  host_pow_tables(ph.data());
+  if ((rc = dalloc(c, &c->q_d, qh.size())) || (rc = dalloc(c, &c->T_d, Th.size())) ||
+      (rc = dalloc(c, &c->pow_d, ph.size())))
+    return rc;
+  CKC(c, cudaMemcpy(c->q_d, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->T_d, Th.data(), Th.size() * 8, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->pow_d, ph.data(), ph.size() * 8, cudaMemcpyHostToDevice));
+  c->tab.q = c->q_d;
+  c->tab.T = c->T_d;
+  c->tab.pow = c->pow_d;
+  c->tab.S = S;
+  // tangent D (element SoA [84][epad]) and spring state placement
+  const int64_t E = c->m.E, epad = c->m.epad;
+  if ((rc = dalloc(c, &c->D, 84 * (size_t)epad)) || (rc = dalloc(c, &c->D32, 84 * (size_t)epad))) return rc;
+  CKC(c, cudaMemset(c->D, 0, 84 * epad * 8));
+  LAUNCH(c, launch_elastic_D(c->tab, c->mats_d, c->m.mat, c->D, epad, 0, E, c->s_main));
+  const int64_t per_elem = ns_state_bytes(1, S);
+  if (c->cfg.device_state_budget < 0)
+    c->E_res = E;
+  else
+    c->E_res = std::min<int64_t>(E, c->cfg.device_state_budget / per_elem);
+  const int64_t S4 = 4 * (int64_t)S;
+  if ((rc = alloc_soa(c, c->st, std::max<int64_t>(1, c->E_res * S4), false))) return rc;
+  if (c->E_res < E) {
+    if ((rc = alloc_soa(c, c->hst, (E - c->E_res) * S4, true))) return rc;
+    c->ring.resize(c->cfg.ring_depth);
+    for (auto &rb : c->ring)
+      if ((rc = alloc_soa(c, rb, std::min<int64_t>(c->cfg.chunk_elems, E - c->E_res) * S4, false))) return rc;
+  }
+  c->stats.resident_elems = c->E_res;
+  c->stats.streamed_elems = E - c->E_res;
+  CKC(c, cudaStreamSynchronize(c->s_main));
+  c->has_mat = true;
+  return NS_OK;
+}
+
+int ns_set_boundary(ns_ctx *c, int64_t F, const int32_t *faces, const int32_t *face_elem, const int32_t *face_kind,
+                    int64_t Ns, const int32_t *surf) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh) NS_SET(c, NS_ERR_STATE, "upload the mesh before the boundary");
+  if (c->has_bnd) NS_SET(c, NS_ERR_INVALID_ARG, "boundary already set");
+  if (F < 0 || Ns < 0 || (F > 0 && (!faces || !face_elem || !face_kind)) || (Ns > 0 && !surf))
+    NS_SET(c, NS_ERR_INVALID_ARG, "bad boundary sizes or null pointers");
+  DevMesh &m = c->m;
+  for (int64_t i = 0; i < F * 6; ++i)
+    if (faces[i] < 0 || faces[i] >= m.N) NS_SET(c, NS_ERR_BAD_MESH, "face node index out of range");
+  for (int64_t f = 0; f < F; ++f)
+    if (face_elem[f] < 0 || face_elem[f] >= m.E || (face_kind[f] != 0 && face_kind[f] != 1))
+      NS_SET(c, NS_ERR_BAD_MESH, "bad face element or kind");
+  for (int64_t i = 0; i < Ns; ++i)
+    if (surf[i] < 0 || surf[i] >= m.N) NS_SET(c, NS_ERR_BAD_MESH, "surface node index out of range");
+  int rc;
+  m.F = F;
+  m.fpad = pad64(std::max<int64_t>(F, 1));
+  m.Ns = Ns;
+  std::vector<int32_t> mh((size_t)m.E);
+  CKC(c, cudaMemcpy(mh.data(), m.mat, m.E * 4, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> soa((size_t)6 * m.fpad, 0), fm((size_t)std::max<int64_t>(F, 1), 0);
+  for (int64_t f = 0; f < F; ++f) {
+    for (int a = 0; a < 6; ++a) soa[(size_t)a * m.fpad + f] = faces[f * 6 + a];
+    fm[f] = mh[face_elem[f]];
+  }
+  if ((rc = dalloc(c, &m.fnode, soa.size())) || (rc = dalloc(c, &m.fgeom, 4 * (size_t)m.fpad)) ||
+      (rc = dalloc(c, &m.fmat, fm.size())) || (rc = dalloc(c, &m.fkind, fm.size())) ||
+      (rc = dalloc(c, &m.surf, (size_t)std::max<int64_t>(Ns, 1))))
+    return rc;
+  CKC(c, cudaMemcpy(m.fnode, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(m.fmat, fm.data(), fm.size() * 4, cudaMemcpyHostToDevice));
+  if (F > 0) CKC(c, cudaMemcpy(m.fkind, face_kind, F * 4, cudaMemcpyHostToDevice));
+  if (Ns > 0) CKC(c, cudaMemcpy(m.surf, surf, Ns * 4, cudaMemcpyHostToDevice));
+  LAUNCH(c, launch_face_geometry(m, c->xyz_d, c->s_main));
+  CKC(c, cudaStreamSynchronize(c->s_main));
+  if (c->cfg.scatter == NS_SCATTER_COLOUR && F > 0) {
+    // greedy colouring of the faces (6 nodes each) in face order
+    std::vector<uint64_t> used((size_t)m.N, 0);
+    std::vector<int32_t> col((size_t)F);
+    int nc = 0;
+    for (int64_t f = 0; f < F; ++f) {
+      uint64_t taken = 0;
+      for (int a = 0; a < 6; ++a) taken |= used[faces[f * 6 + a]];
+      if (~taken == 0) NS_SET(c, NS_ERR_BAD_MESH, "more than 64 face colours");
+      const int k = __builtin_ctzll(~taken);
+      col[f] = k;
+      nc = std::max(nc, k + 1);
+      for (int a = 0; a < 6; ++a) used[faces[f * 6 + a]] |= 1ull << k;
+    }
+    m.fcol_off.assign(nc + 1, 0);
+    for (int64_t f = 0; f < F; ++f) m.fcol_off[col[f] + 1]++;
+    for (int k = 0; k < nc; ++k) m.fcol_off[k + 1] += m.fcol_off[k];
+    std::vector<int64_t> fillp(m.fcol_off.begin(), m.fcol_off.end() - 1);
+    std::vector<int32_t> ids((size_t)F);
+    for (int64_t f = 0; f < F; ++f) ids[fillp[col[f]]++] = (int32_t)f;
+    if ((rc = dalloc(c, &m.fcol_ids, (size_t)F))) return rc;
+    CKC(c, cudaMemcpy(m.fcol_ids, ids.data(), F * 4, cudaMemcpyHostToDevice));
+    c->part_pap_cap += nblk(F) + nc;
+  } else {
+    c->part_pap_cap += nblk(std::max<int64_t>(F, 1));
+  }
+  c->ring_steps = c->cfg.surface_ring_steps;
+  const size_t rs = (size_t)c->ring_steps * 3 * (size_t)std::max<int64_t>(Ns, 1);
+  if ((rc = dalloc(c, &c->surf_u, rs)) || (rc = dalloc(c, &c->surf_v, rs)) || (rc = dalloc(c, &c->surf_a, rs)))
+    return rc;
+  if ((rc = dalloc(c, &c->part, (size_t)(c->part_pap_cap + 3 * vec_blocks(m.N))))) return rc;
+  c->has_bnd = true;
+  return NS_OK;
+}
+
+int ns_set_ground_motion(ns_ctx *c, int64_t ns_, double dt, const double *acc) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (ns_ < 1 || !acc) NS_SET(c, NS_ERR_INVALID_ARG, "need at least one acceleration sample");
+  if (!(fabs(dt - c->cfg.dt) <= 1e-12 * c->cfg.dt)) NS_SET(c, NS_ERR_INVALID_ARG, "record dt differs from the step dt");
+  // trapezoidal input velocity, v(0) = 0; one extra entry for the first step past the record
+  std::vector<double> vin(3 * (size_t)(ns_ + 1), 0.0);
+  for (int64_t k = 1; k <= ns_; ++k)
+    for (int cc = 0; cc < 3; ++cc) {
+      const double a0 = acc[3 * (k - 1) + cc], a1 = (k < ns_) ? acc[3 * k + cc] : 0.0;
+      vin[3 * k + cc] = vin[3 * (k - 1) + cc] + 0.5 * dt * (a0 + a1);
+    }
+  int rc;
+  dfree(c->vin_d);
+  if ((rc = dalloc(c, &c->vin_d, vin.size()))) return rc;
+  CKC(c, cudaMemcpy(c->vin_d, vin.data(), vin.size() * 8, cudaMemcpyHostToDevice));
+  c->n_vin = ns_ + 1;
+  c->has_motion = true;
+  return NS_OK;
+}
+
+int ns_advance(ns_ctx *c, int64_t nsteps) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh || !c->has_mat || !c->has_bnd || !c->has_motion)
+    NS_SET(c, NS_ERR_STATE, "mesh, materials, boundary and ground motion must be set before advancing");
+  if (nsteps < 0) NS_SET(c, NS_ERR_INVALID_ARG, "negative step count");
+  cudaSetDevice(c->cfg.device);
+  CKC(c, cudaEventRecord(c->ev_adv0, c->s_main));
+  for (int64_t k = 0; k < nsteps; ++k) {
+    c->timer.reset();
+    c->tev.clear();
+    int rc = one_step(c);
+    if (rc != NS_OK) {
+      sync_all(c);
+      return rc;
+    }
+    if ((rc = sync_all(c)) != NS_OK) return rc;
+    if (c->cfg.timing) {
+      flush_times(c);
+      if (n_chunks(c) > 0) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c->ev_stream_t0, c->ev_stream_t1) == cudaSuccess) c->stats.ms_stream_wall += ms;
+        cudaGetLastError();
+      }
+    }
+  }
+  // join the copy streams into the main stream so the end event covers all device work
+  CKC(c, cudaEventRecord(c->ev_join, c->s_h2d));
+  CKC(c, cudaStreamWaitEvent(c->s_main, c->ev_join, 0));
+  CKC(c, cudaEventRecord(c->ev_join, c->s_d2h));
+  CKC(c, cudaStreamWaitEvent(c->s_main, c->ev_join, 0));
+  CKC(c, cudaEventRecord(c->ev_adv1, c->s_main));
+  int rc2 = wait_event(c, c->ev_adv1);
+  if (rc2 != NS_OK) return rc2;
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, c->ev_adv0, c->ev_adv1) == cudaSuccess) c->stats.ms_advance += ms;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) NS_SET(c, NS_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+  return NS_OK;
+}
+
+int ns_read_surface(ns_ctx *c, int64_t step0, int64_t nsteps, double *u, double *v, double *a) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_bnd) NS_SET(c, NS_ERR_STATE, "no boundary set");
+  if (nsteps < 0 || step0 < 1 || step0 + nsteps - 1 > c->step || step0 <= c->step - c->ring_steps)
+    NS_SET(c, NS_ERR_INVALID_ARG, "requested steps are not in the surface ring");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  const int64_t blk = c->m.Ns * 3;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const int64_t slot = (step0 + k - 1) % c->ring_steps;
+    if (u) CKC(c, cudaMemcpy(u + k * blk, c->surf_u + slot * blk, blk * 8, cudaMemcpyDeviceToHost));
+    if (v) CKC(c, cudaMemcpy(v + k * blk, c->surf_v + slot * blk, blk * 8, cudaMemcpyDeviceToHost));
+    if (a) CKC(c, cudaMemcpy(a + k * blk, c->surf_a + slot * blk, blk * 8, cudaMemcpyDeviceToHost));
+  }
+  return NS_OK;
+}
+
+namespace {
+struct SpringRec {
+  double tau, gR, tR, gmax;
+  int32_t dir, mode;
+};
+static_assert(sizeof(SpringRec) == 40, "40-byte spring record");
+
+// gather springs [s0, s0 + n) of the global order into host SoA buffers
+int state_to_host(ns_ctx *c, int64_t s0, int64_t n, SpringSoA &h) {
+  const int64_t res_n = c->E_res * 4 * (int64_t)c->tab.S;
+  for (int64_t s = s0; s < s0 + n;) {
+    const int64_t off = s - s0;
+    if (s < res_n) {
+      const int64_t cnt = std::min(s0 + n, res_n) - s;
+      int rc = copy_soa(c, h, off, c->st, s, cnt, cudaMemcpyDeviceToHost, c->s_main);
+      if (rc) return rc;
+      s += cnt;
+    } else {
+      const int64_t cnt = s0 + n - s;
+      memcpy(h.tau + off, c->hst.tau + (s - res_n), cnt * 8);
+      memcpy(h.gR + off, c->hst.gR + (s - res_n), cnt * 8);
+      memcpy(h.tR + off, c->hst.tR + (s - res_n), cnt * 8);
+      memcpy(h.gmax + off, c->hst.gmax + (s - res_n), cnt * 8);
+      memcpy(h.dir + off, c->hst.dir + (s - res_n), cnt * 4);
+      memcpy(h.mode + off, c->hst.mode + (s - res_n), cnt * 4);
+      s += cnt;
+    }
+  }
+  return sync_stream(c, c->s_main);
+}
+
+int state_from_host(ns_ctx *c, int64_t s0, int64_t n, const SpringSoA &h) {
+  const int64_t res_n = c->E_res * 4 * (int64_t)c->tab.S;
+  for (int64_t s = s0; s < s0 + n;) {
+    const int64_t off = s - s0;
+    if (s < res_n) {
+      const int64_t cnt = std::min(s0 + n, res_n) - s;
+      int rc = copy_soa(c, c->st, s, h, off, cnt, cudaMemcpyHostToDevice, c->s_main);
+      if (rc) return rc;
+      s += cnt;
+    } else {
+      const int64_t cnt = s0 + n - s;
+      memcpy(c->hst.tau + (s - res_n), h.tau + off, cnt * 8);
+      memcpy(c->hst.gR + (s - res_n), h.gR + off, cnt * 8);
+      memcpy(c->hst.tR + (s - res_n), h.tR + off, cnt * 8);
+      memcpy(c->hst.gmax + (s - res_n), h.gmax + off, cnt * 8);
+      memcpy(c->hst.dir + (s - res_n), h.dir + off, cnt * 4);
+      memcpy(c->hst.mode + (s - res_n), h.mode + off, cnt * 4);
+      s += cnt;
+    }
+  }
+  return sync_stream(c, c->s_main);
+}
+
+struct HostSoA {
+  std::vector<double> tau, gR, tR, gmax;
+  std::vector<int32_t> dir, mode;
+  SpringSoA view;
+  explicit HostSoA(int64_t n) : tau(n), gR(n), tR(n), gmax(n), dir(n), mode(n) {
+    view.tau = tau.data(); view.gR = gR.data(); view.tR = tR.data(); view.gmax = gmax.data();
+    view.dir = dir.data(); view.mode = mode.data();
+  }
+};
+
+void unpack_D(const std::vector<double> &Dsoa, int64_t epad_src, int64_t e_local, int64_t e_src, double *out36x4) {
+  for (int q = 0; q < 4; ++q)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) out36x4[q * 36 + i * 6 + j] = Dsoa[(size_t)(q * 21 + sym6(i, j)) * epad_src + e_local];
+  (void)e_src;
+}
+}  // namespace
+
+int ns_read_state(ns_ctx *c, int64_t e0, int64_t n, void *theta, double *D) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mat) NS_SET(c, NS_ERR_STATE, "no state yet");
+  if (e0 < 0 || n < 0 || e0 + n > c->m.E) NS_SET(c, NS_ERR_INVALID_ARG, "element range out of bounds");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  const int64_t S4 = 4 * (int64_t)c->tab.S;
+  if (theta && n > 0) {
+    HostSoA h(n * S4);
+    if ((rc = state_to_host(c, e0 * S4, n * S4, h.view))) return rc;
+    SpringRec *out = (SpringRec *)theta;
+    for (int64_t i = 0; i < n * S4; ++i) out[i] = {h.tau[i], h.gR[i], h.tR[i], h.gmax[i], h.dir[i], h.mode[i]};
+  }
+  if (D && n > 0) {
+    std::vector<double> tmp((size_t)84 * n);
+    for (int k = 0; k < 84; ++k)
+      CKC(c, cudaMemcpy(tmp.data() + (size_t)k * n, c->D + (size_t)k * c->m.epad + e0, n * 8, cudaMemcpyDeviceToHost));
+    for (int64_t e = 0; e < n; ++e) unpack_D(tmp, n, e, e0 + e, D + e * 144);
+  }
+  return NS_OK;
+}
+
+int ns_write_state(ns_ctx *c, int64_t e0, int64_t n, const void *theta, const double *D) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mat) NS_SET(c, NS_ERR_STATE, "no state yet");
+  if (e0 < 0 || n < 0 || e0 + n > c->m.E) NS_SET(c, NS_ERR_INVALID_ARG, "element range out of bounds");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  const int64_t S4 = 4 * (int64_t)c->tab.S;
+  if (theta && n > 0) {
+    HostSoA h(n * S4);
+    const SpringRec *in = (const SpringRec *)theta;
+    for (int64_t i = 0; i < n * S4; ++i) {
+      h.tau[i] = in[i].tau; h.gR[i] = in[i].gR; h.tR[i] = in[i].tR; h.gmax[i] = in[i].gmax;
+      h.dir[i] = in[i].dir; h.mode[i] = in[i].mode;
+    }
+    if ((rc = state_from_host(c, e0 * S4, n * S4, h.view))) return rc;
+  }
+  if (D && n > 0) {
+    std::vector<double> tmp((size_t)84 * n);
+    for (int64_t e = 0; e < n; ++e)
+      for (int q = 0; q < 4; ++q)
+        for (int i = 0; i < 6; ++i)
+          for (int j = i; j < 6; ++j) tmp[(size_t)(q * 21 + sym6(i, j)) * n + e] = D[e * 144 + q * 36 + i * 6 + j];
+    for (int k = 0; k < 84; ++k)
+      CKC(c, cudaMemcpy(c->D + (size_t)k * c->m.epad + e0, tmp.data() + (size_t)k * n, n * 8, cudaMemcpyHostToDevice));
+  }
+  return NS_OK;
+}
+
+static double *field_ptr(ns_ctx *c, int32_t f) {
+  switch (f) {
+    case NS_FIELD_U: return c->u;
+    case NS_FIELD_V: return c->v;
+    case NS_FIELD_A: return c->a;
+    case NS_FIELD_Q: return c->q;
+    case NS_FIELD_DU: return c->du;
+    default: return nullptr;
+  }
+}
+
+int ns_read_nodal(ns_ctx *c, int32_t field, double *out) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh) NS_SET(c, NS_ERR_STATE, "no mesh");
+  double *src = field_ptr(c, field);
+  if (!src || !out) NS_SET(c, NS_ERR_INVALID_ARG, "bad field or null output");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  CKC(c, cudaMemcpy(out, src, 3 * c->m.N * 8, cudaMemcpyDeviceToHost));
+  return NS_OK;
+}
+
+int ns_write_nodal(ns_ctx *c, int32_t field, const double *in) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh) NS_SET(c, NS_ERR_STATE, "no mesh");
+  double *dst = field_ptr(c, field);
+  if (!dst || !in) NS_SET(c, NS_ERR_INVALID_ARG, "bad field or null input");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  CKC(c, cudaMemcpy(dst, in, 3 * c->m.N * 8, cudaMemcpyHostToDevice));
+  return NS_OK;
+}
+
+int ns_apply_operator(ns_ctx *c, int32_t op, const double *x, double *y) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh || !c->has_mat || !c->has_bnd) NS_SET(c, NS_ERR_STATE, "mesh, materials and boundary required");
+  if (!x || !y || op < 0 || op > 4) NS_SET(c, NS_ERR_INVALID_ARG, "bad operator or null buffer");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  const size_t n3 = 3 * (size_t)c->m.N;
+  CKC(c, cudaMemcpy(c->p, x, n3 * 8, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemset(c->Ap, 0, n3 * 8));
+  switch (op) {
+    case NS_OP_K: rc = apply_elems64(c, c->op_K, nullptr, c->p, c->Ap, nullptr, nullptr, nullptr); break;
+    case NS_OP_M: rc = apply_elems64(c, c->op_M, nullptr, c->p, c->Ap, nullptr, nullptr, nullptr); break;
+    case NS_OP_CB: rc = apply_faces64(c, 1.0, c->p, nullptr, c->Ap, nullptr, nullptr, nullptr); break;
+    case NS_OP_A: rc = apply_A(c, c->p, c->Ap, false, nullptr, nullptr, nullptr, false); break;
+    case NS_OP_CR: rc = apply_elems64(c, c->op_Cr, nullptr, c->p, c->Ap, nullptr, nullptr, nullptr); break;
+  }
+  if (rc) return rc;
+  if ((rc = sync_stream(c, c->s_main)) != NS_OK) return rc;
+  CKC(c, cudaMemcpy(y, c->Ap, n3 * 8, cudaMemcpyDeviceToHost));
+  return NS_OK;
+}
+
+int ns_spring_points(ns_ctx *c, int64_t npts, const int32_t *mat, const double *eps, const double *deps, void *theta,
+                     double *D) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mat) NS_SET(c, NS_ERR_STATE, "materials required");
+  if (npts < 0 || (npts > 0 && (!mat || !eps || !deps || !theta || !D))) NS_SET(c, NS_ERR_INVALID_ARG, "bad arguments");
+  if (npts == 0) return NS_OK;
+  for (int64_t i = 0; i < npts; ++i)
+    if (mat[i] < 0 || mat[i] >= c->nmat) NS_SET(c, NS_ERR_INVALID_ARG, "material index out of range");
+  const int S = c->tab.S;
+  const int64_t nspr = npts * S;
+  int rc;
+  std::vector<double> e12((size_t)npts * 12);
+  for (int64_t i = 0; i < npts; ++i)
+    for (int k = 0; k < 6; ++k) {
+      e12[i * 12 + k] = eps[i * 6 + k];
+      e12[i * 12 + 6 + k] = deps[i * 6 + k];
+    }
+  HostSoA h(nspr);
+  SpringRec *rec = (SpringRec *)theta;
+  for (int64_t i = 0; i < nspr; ++i) {
+    h.tau[i] = rec[i].tau; h.gR[i] = rec[i].gR; h.tR[i] = rec[i].tR; h.gmax[i] = rec[i].gmax;
+    h.dir[i] = rec[i].dir; h.mode[i] = rec[i].mode;
+  }
+  SpringSoA d;
+  double *eps_d = nullptr, *dp = nullptr;
+  int32_t *mat_d = nullptr;
+  rc = alloc_soa(c, d, nspr, false);
+  if (!rc) rc = dalloc(c, &eps_d, e12.size());
+  if (!rc) rc = dalloc(c, &dp, 21 * (size_t)npts);
+  if (!rc) rc = dalloc(c, &mat_d, (size_t)npts);
+  if (!rc) rc = copy_soa(c, d, 0, h.view, 0, nspr, cudaMemcpyHostToDevice, c->s_main);
+  if (!rc) {
+    cudaMemcpyAsync(eps_d, e12.data(), e12.size() * 8, cudaMemcpyHostToDevice, c->s_main);
+    cudaMemcpyAsync(mat_d, mat, npts * 4, cudaMemcpyHostToDevice, c->s_main);
+    cudaError_t e = launch_springs(c->tab, c->mats_d, nullptr, mat_d, eps_d, d, 0, 0, npts, nullptr, 0, dp, c->s_main);
+    c->stats.kernel_launches++;
+    if (e != cudaSuccess) {
+      c->err = std::string("spring kernel: ") + cudaGetErrorString(e);
+      rc = NS_ERR_CUDA;
+    }
+  }
+  if (!rc) rc = copy_soa(c, h.view, 0, d, 0, nspr, cudaMemcpyDeviceToHost, c->s_main);
+  std::vector<double> dh(21 * (size_t)npts);
+  if (!rc && cudaMemcpyAsync(dh.data(), dp, dh.size() * 8, cudaMemcpyDeviceToHost, c->s_main) != cudaSuccess)
+    rc = NS_ERR_CUDA;
+  if (!rc) rc = sync_stream(c, c->s_main);
+  free_soa(d, false);
+  dfree(eps_d);
+  dfree(dp);
+  dfree(mat_d);
+  if (rc) return rc;
+  for (int64_t i = 0; i < nspr; ++i) rec[i] = {h.tau[i], h.gR[i], h.tR[i], h.gmax[i], h.dir[i], h.mode[i]};
+  for (int64_t p = 0; p < npts; ++p)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) D[p * 36 + i * 6 + j] = dh[p * 21 + sym6(i, j)];
+  return NS_OK;
+}
+
+int ns_get_stats(ns_ctx *c, ns_stats *st) {
+  if (!c || !st) return NS_ERR_INVALID_ARG;
+  *st = c->stats;
+  return NS_OK;
+}
+
+int ns_reset_stats(ns_ctx *c) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  const int64_t steps = c->stats.steps, launches = c->stats.kernel_launches, re = c->stats.resident_elems,
+                se = c->stats.streamed_elems;
+  c->stats = ns_stats{};
+  c->stats.steps = steps;
+  c->stats.kernel_launches = launches;
+  c->stats.resident_elems = re;
+  c->stats.streamed_elems = se;
+  return NS_OK;
+}
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int64_t version, step, N, E, S;
+};
+}  // namespace
+
+int ns_checkpoint_size(ns_ctx *c, int64_t *bytes) {
+  if (!c || !bytes) return NS_ERR_INVALID_ARG;
+  if (!c->has_mat) NS_SET(c, NS_ERR_STATE, "no state yet");
+  *bytes = (int64_t)sizeof(CkptHeader) + 5 * 3 * c->m.N * 8 + c->m.E * 144 * 8 + ns_state_bytes(c->m.E, c->tab.S);
+  return NS_OK;
+}
+
+int ns_checkpoint(ns_ctx *c, void *buf, int64_t bytes) {
+  int64_t need = 0;
+  int rc = ns_checkpoint_size(c, &need);
+  if (rc) return rc;
+  if (!buf || bytes < need) NS_SET(c, NS_ERR_INVALID_ARG, "checkpoint buffer too small");
+  char *p = (char *)buf;
+  CkptHeader h{};
+  memcpy(h.magic, "NSCKPT01", 8);
+  h.version = 1;
+  h.step = c->step;
+  h.N = c->m.N;
+  h.E = c->m.E;
+  h.S = c->tab.S;
+  memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  for (int f = 0; f < 5; ++f) {
+    if ((rc = ns_read_nodal(c, f, (double *)p))) return rc;
+    p += 3 * c->m.N * 8;
+  }
+  if ((rc = ns_read_state(c, 0, c->m.E, p + c->m.E * 144 * 8, (double *)p))) return rc;
+  return NS_OK;
+}
+
+int ns_restore(ns_ctx *c, const void *buf, int64_t bytes) {
+  int64_t need = 0;
+  int rc = ns_checkpoint_size(c, &need);
+  if (rc) return rc;
+  if (!buf || bytes < need) NS_SET(c, NS_ERR_INVALID_ARG, "checkpoint buffer too small");
+  const char *p = (const char *)buf;
+  CkptHeader h;
+  memcpy(&h, p, sizeof(h));
+  if (memcmp(h.magic, "NSCKPT01", 8) != 0 || h.N != c->m.N || h.E != c->m.E || h.S != c->tab.S)
+    NS_SET(c, NS_ERR_INVALID_ARG, "checkpoint does not match this model");
+  p += sizeof(h);
+  for (int f = 0; f < 5; ++f) {
+    if ((rc = ns_write_nodal(c, f, (const double *)p))) return rc;
+    p += 3 * c->m.N * 8;
+  }
+  if ((rc = ns_write_state(c, 0, c->m.E, p + c->m.E * 144 * 8, (const double *)p))) return rc;
+  c->step = h.step;
+  c->stats.steps = h.step;
+  return NS_OK;
+}
+
+void ns_destroy(ns_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  if (c->s_main) cudaStreamSynchronize(c->s_main);
+  if (c->s_h2d) cudaStreamSynchronize(c->s_h2d);
+  if (c->s_d2h) cudaStreamSynchronize(c->s_d2h);
+  DevMesh &m = c->m;
+  dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
+  dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
+  dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
+  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->D); dfree(c->D32);
+  free_soa(c->st, false);
+  free_soa(c->hst, true);
+  for (auto &rb : c->ring) free_soa(rb, false);
+  dfree(c->u); dfree(c->v); dfree(c->a); dfree(c->q); dfree(c->du); dfree(c->b); dfree(c->r); dfree(c->z);
+  dfree(c->p); dfree(c->Ap); dfree(c->Jd); dfree(c->Jinv); dfree(c->eps); dfree(c->part); dfree(c->vin_d);
+  dfree(c->surf_u); dfree(c->surf_v); dfree(c->surf_a);
+  dfree(c->Jinv32);
+  dfree(c->rin); dfree(c->zin); dfree(c->pin); dfree(c->xin); dfree(c->Apin);
+  dfree(c->sc);
+  dfree(c->flag_d);
+  hfree(c->sc_h);
+  hfree(c->flag_h);
+  if (c->ev_h2d) {
+    for (int i = 0; i < c->cfg.ring_depth; ++i) {
+      cudaEventDestroy(c->ev_h2d[i]);
+      cudaEventDestroy(c->ev_comp[i]);
+      cudaEventDestroy(c->ev_d2h[i]);
+    }
+    delete[] c->ev_h2d;
+    delete[] c->ev_comp;
+    delete[] c->ev_d2h;
+  }
+  if (c->ev_d2h_all) cudaEventDestroy(c->ev_d2h_all);
+  if (c->ev_sync) cudaEventDestroy(c->ev_sync);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_adv0) cudaEventDestroy(c->ev_adv0);
+  if (c->ev_adv1) cudaEventDestroy(c->ev_adv1);
+  if (c->ev_stream_t0) cudaEventDestroy(c->ev_stream_t0);
+  if (c->ev_stream_t1) cudaEventDestroy(c->ev_stream_t1);
+  if (c->ev_strain) cudaEventDestroy(c->ev_strain);
+  if (c->s_main) cudaStreamDestroy(c->s_main);
+  if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+  if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+  delete c;
+}
+
+// ---------------------------------------------------------------- host-only helpers
+
+int ns_spring_directions(int32_t S, double *q, double *w) {
+  if (!q || !w) return NS_ERR_INVALID_ARG;
+  return host_spring_directions(S, q, w) == 0 ? NS_OK : NS_ERR_INVALID_ARG;
+}
+
+int ns_colour_elements(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, int32_t *nc) {
+  if (E < 0 || N <= 0 || !conn || !colour || !nc) return NS_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < 10 * E; ++i)
+    if (conn[i] < 0 || conn[i] >= N) return NS_ERR_BAD_MESH;
+  return host_colouring(E, N, conn, colour, nc) == 0 ? NS_OK : NS_ERR_BAD_MESH;
+}
+
+int64_t ns_state_bytes(int64_t E, int32_t S) { return E * 4 * (int64_t)S * 40; }
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Host-side set-up of the time stepper: multi-spring geometry, material
+// constants and greedy element colouring.  Runs once per context.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ns_internal.h"
+
+namespace ns {
+
+namespace {
+
+void matmul6(const double *A, const double *B, double *C) {
+  double T[36];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 6; ++k) s += A[i * 6 + k] * B[k * 6 + j];
+      T[i * 6 + j] = s;
+    }
+  memcpy(C, T, sizeof(T));
+}
+
+// Inverse square root of a symmetric positive definite 6x6 by the coupled
+// Newton-Schulz (Denman-Beavers type) iteration on A/c with c = ||A||_F:
+//   Y <- Y (3I - Z Y)/2,  Z <- (3I - Z Y) Z /2,   Y -> (A/c)^(1/2), Z -> (A/c)^(-1/2).
+void inv_sqrt6(const double *A, double *out) {
+  double c = 0.0;
+  for (int i = 0; i < 36; ++i) c += A[i] * A[i];
+  c = sqrt(c);
+  double Y[36], Z[36], M[36];
+  for (int i = 0; i < 36; ++i) {
+    Y[i] = A[i] / c;
+    Z[i] = (i % 7 == 0) ? 1.0 : 0.0;
+  }
+  for (int it = 0; it < 200; ++it) {
+    matmul6(Z, Y, M);
+    double dev = 0.0;
+    for (int i = 0; i < 36; ++i) {
+      const double id = (i % 7 == 0) ? 1.0 : 0.0;
+      dev += (M[i] - id) * (M[i] - id);
+      M[i] = 0.5 * (3.0 * id - M[i]);
+    }
+    matmul6(Y, M, Y);
+    matmul6(M, Z, Z);
+    if (dev < 1e-30) break;
+  }
+  const double sc = 1.0 / sqrt(c);
+  for (int i = 0; i < 36; ++i) out[i] = Z[i] * sc;
+}
+
+}  // namespace
+
+// Spring directions (Sec. 2.1 multi-spring model; geometry per the documented reading):
+// plane normal n_k on a hemispherical Fibonacci lattice (z = 1 - (k+1/2)/S, azimuth
+// k pi (3 - sqrt5)), slip s_k in the plane at angle 2 pi frac(k sqrt2) from
+// t1 = (-sin phi, cos phi, 0) towards t2 = n x t1, shear projection
+// p_k = (2 nx sx, 2 ny sy, 2 nz sz, ny sz + nz sy, nx sz + nz sx, nx sy + ny sx);
+// q_k = T p_k with T = (2S/5 Ddev)^(1/2) P^(+1/2), P = sum p p^T, so that
+// (5/(2S)) sum q q^T = Ddev = diag(2,2,2,1,1,1) - (2/3) m m^T exactly.
+int host_spring_directions(int S, double *q, double *w) {
+  if (S < 5) return -1;
+  std::vector<double> p(6 * (size_t)S);
+  double P[36] = {0};
+  const double golden = M_PI * (3.0 - sqrt(5.0));
+  for (int k = 0; k < S; ++k) {
+    const double z = 1.0 - (k + 0.5) / S, r = sqrt(1.0 - z * z), phi = golden * k;
+    const double n[3] = {r * cos(phi), r * sin(phi), z};
+    const double t1[3] = {-sin(phi), cos(phi), 0.0};
+    const double t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+    double f = sqrt(2.0) * k;
+    f -= floor(f);
+    const double cs = cos(2.0 * M_PI * f), sn = sin(2.0 * M_PI * f);
+    double sl[3];
+    for (int c = 0; c < 3; ++c) sl[c] = cs * t1[c] + sn * t2[c];
+    double *pk = &p[6 * (size_t)k];
+    pk[0] = 2.0 * n[0] * sl[0];
+    pk[1] = 2.0 * n[1] * sl[1];
+    pk[2] = 2.0 * n[2] * sl[2];
+    pk[3] = n[1] * sl[2] + n[2] * sl[1];
+    pk[4] = n[0] * sl[2] + n[2] * sl[0];
+    pk[5] = n[0] * sl[1] + n[1] * sl[0];
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) P[i * 6 + j] += pk[i] * pk[j];
+  }
+  // P has the volumetric direction m = (1,1,1,0,0,0) as its null vector; adding the
+  // projector m m^T / 3 makes it invertible without changing the other eigenpairs.
+  double Pm[36], Pih[36];
+  for (int i = 0; i < 36; ++i) Pm[i] = P[i] + ((i / 6 < 3 && i % 6 < 3) ? 1.0 / 3.0 : 0.0);
+  inv_sqrt6(Pm, Pih);
+  for (int i = 0; i < 36; ++i) Pih[i] -= (i / 6 < 3 && i % 6 < 3) ? 1.0 / 3.0 : 0.0;
+  // (Ddev)^(1/2) = sqrt2 (I - 11^T/3) on the normal block, I on the shear block
+  double Dh[36] = {0};
+  const double sc = sqrt(2.0 * S / 5.0);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Dh[i * 6 + j] = sc * sqrt(2.0) * ((i == j ? 1.0 : 0.0) - 1.0 / 3.0);
+  for (int i = 3; i < 6; ++i) Dh[i * 6 + i] = sc;
+  double T[36];
+  matmul6(Dh, Pih, T);
+  for (int k = 0; k < S; ++k)
+    for (int i = 0; i < 6; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < 6; ++j) s += T[i * 6 + j] * p[6 * (size_t)k + j];
+      q[6 * (size_t)k + i] = s;
+    }
+  *w = 5.0 / (2.0 * S);
+  return 0;
+}
+
+// Greedy first-fit colouring in element order.
+int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, int32_t *nc) {
+  std::vector<uint64_t> used((size_t)N, 0);
+  int32_t ncol = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    uint64_t taken = 0;
+    for (int a = 0; a < 10; ++a) taken |= used[(size_t)conn[e * 10 + a]];
+    if (~taken == 0) return -1;
+    const int c = __builtin_ctzll(~taken);
+    colour[e] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+    for (int a = 0; a < 10; ++a) used[(size_t)conn[e * 10 + a]] |= (1ull << c);
+  }
+  *nc = ncol;
+  return 0;
+}
+
+// Derived constants: G0 = rho Vs^2, bulk Kb = rho (Vp^2 - 4/3 Vs^2); RO exponent
+// beta = 2 pi h_max / (2 - pi h_max) (loop damping tends to h_max), alpha = 2^beta
+// (secant G0/2 at gamma_ref); Rayleigh a = 2 h w1 w2/(w1 + w2), b = 2 h/(w1 + w2).
+void host_material_constants(const ns_material &m, double f1, double f2, MatConst *o) {
+  o->rho = m.rho;
+  o->vs = m.vs;
+  o->vp = m.vp;
+  o->G0 = m.rho * m.vs * m.vs;
+  o->Kb = m.rho * (m.vp * m.vp - 4.0 / 3.0 * m.vs * m.vs);
+  o->gref = m.gamma_ref;
+  o->beta_ro = 2.0 * M_PI * m.h_max / (2.0 - M_PI * m.h_max);
+  o->alpha_ro = exp2(o->beta_ro);
+  const double w1 = 2.0 * M_PI * f1, w2 = 2.0 * M_PI * f2;
+  o->ray_a = 2.0 * m.rayleigh_h * w1 * w2 / (w1 + w2);
+  o->ray_b = 2.0 * m.rayleigh_h / (w1 + w2);
+}
+
+// Tables of the FP64 power used by the spring law (table-driven logarithm and exponential
+// after Tang): r_j = 1/(1 + (j + 1/2)/128) rounded to double, -ln r_j split in two
+// doubles, 2^(i/64), and ln2, ln2/64 split so that the high parts have trailing zero bits.
+void host_pow_tables(double *out) {
+  const long double LN2 = 0.693147180559945309417232121458176568L;
+  for (int j = 0; j < 128; ++j) {
+    const double r = (double)(1.0L / (1.0L + ((long double)j + 0.5L) / 128.0L));
+    const long double l = -logl((long double)r);
+    out[j] = r;
+    out[128 + j] = (double)l;
+    out[256 + j] = (double)(l - (long double)(double)l);
+  }
+  for (int i = 0; i < 64; ++i) out[384 + i] = (double)exp2l((long double)i / 64.0L);
+  auto trunc_bits = [](double x, int drop) {
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    b &= ~((1ull << drop) - 1ull);
+    memcpy(&x, &b, 8);
+    return x;
+  };
+  const double l2h = trunc_bits((double)LN2, 11);
+  out[448] = l2h;
+  out[449] = (double)(LN2 - (long double)l2h);
+  const double l64h = trunc_bits((double)(LN2 / 64.0L), 20);
+  out[450] = l64h;
+  out[451] = (double)(LN2 / 64.0L - (long double)l64h);
+}
+
+}  // namespace ns

@@ -1,0 +1,164 @@
+// Internal declarations of the GB300 time stepper (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ns.h"
+
+namespace ns {
+
+constexpr int kQ = 4;          // integration points per element
+constexpr int kDPack = 21;     // unique entries of a symmetric 6x6
+constexpr int kMaxMat = 64;
+constexpr int kBlock = 256;
+
+// Per-material constants derived on the host from ns_material and the config.
+struct MatConst {
+  double rho, vs, vp, G0, Kb, gref, alpha_ro, beta_ro, ray_a, ray_b;
+};
+
+// Coefficients of one element-by-element operator application, per material:
+//   y_e = mM[m] * M_e xm + mK[m] * M_e xk + kK[m] * K_e xk
+struct OpCoef {
+  double mM[kMaxMat];
+  double mK[kMaxMat];
+  double kK[kMaxMat];
+};
+
+// Device mesh in structure-of-arrays form (element arrays have stride epad).
+struct DevMesh {
+  int64_t N = 0, E = 0, epad = 0, F = 0, fpad = 0, Ns = 0;
+  int32_t *conn = nullptr;   // [10][epad]
+  double *geom = nullptr;    // [10][epad]: grad L1 (3), grad L2 (3), grad L3 (3), volume
+  float *geom32 = nullptr;   // [10][epad]
+  int32_t *mat = nullptr;    // [E]
+  int32_t *fnode = nullptr;  // [6][fpad]
+  double *fgeom = nullptr;   // [4][fpad]: area, unit normal
+  int32_t *fmat = nullptr;   // [F]
+  int32_t *fkind = nullptr;  // [F]
+  int32_t *surf = nullptr;   // [Ns]
+  // colour mode: element and face ids sorted by colour
+  int32_t *ecol_ids = nullptr, *fcol_ids = nullptr;
+  std::vector<int64_t> ecol_off, fcol_off;
+};
+
+// Spring state arrays (structure of arrays over springs ordered [elem][point][spring]).
+struct SpringSoA {
+  double *tau = nullptr, *gR = nullptr, *tR = nullptr, *gmax = nullptr;
+  int32_t *dir = nullptr, *mode = nullptr;
+};
+
+struct CgScalars {
+  double bb, rr, rz, rz_old, pAp, alpha, beta;
+  double rr0;
+  int32_t iters, done, status, pad;
+  unsigned int counter;
+  unsigned int counter2;
+};
+
+// ------------------------------------------------------------------ launchers (k_*.cu)
+// All return cudaGetLastError() of their launch.
+cudaError_t launch_geometry(const DevMesh &m, const double *xyz, int32_t *bad, cudaStream_t s);
+cudaError_t launch_face_geometry(const DevMesh &m, const double *xyz, cudaStream_t s);
+
+// y (+)= Op x over elements [e0, e1) or over the colour list ids[e0, e1) when ids != nullptr.
+// xm may be nullptr (then mM is ignored).  If dot != nullptr, block partial sums of x_e . y_e go
+// to dot[blockIdx.x] (the element-local energy of the application).
+cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
+                         double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
+                         const int32_t *skip, cudaStream_t s);
+cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
+                         const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
+                         cudaStream_t s);
+// Boundary faces: y (+)= cC * C_f (x + [kind 0] vin) (vin may be nullptr)
+cudaError_t launch_faces64(const DevMesh &m, const MatConst *mc, double cC, const double *x, const double *vin,
+                           double *y, const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
+                           const int32_t *skip, cudaStream_t s);
+cudaError_t launch_faces32(const DevMesh &m, const MatConst *mc, float cC, const float *x, float *y,
+                           const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot, const int32_t *skip,
+                           cudaStream_t s);
+// 3x3 diagonal blocks of A (packed xx yy zz yz xz xy) accumulated into Jd [N][6]
+cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef *op, double *Jd, const int32_t *ids,
+                                int64_t e0, int64_t e1, bool atomic, cudaStream_t s);
+cudaError_t launch_jacobi_faces(const DevMesh &m, const MatConst *mc, double cC, double *Jd, const int32_t *ids,
+                                int64_t f0, int64_t f1, bool atomic, cudaStream_t s);
+// strains eps, deps at the 4 points of elements [e0, e1): out [E][4][12] (eps 6, deps 6)
+cudaError_t launch_strain(const DevMesh &m, const double *u, const double *du, double *out, int64_t e0, int64_t e1,
+                          cudaStream_t s);
+
+// ------------------------------------------------------------------ k_vec.cu
+cudaError_t launch_fill(double *x, double v, int64_t n, cudaStream_t s);
+cudaError_t launch_negate_copy(double *dst, const double *src, int64_t n, cudaStream_t s);
+cudaError_t launch_invert_blocks(const double *Jd, double *Jinv, float *Jinv32, int64_t N, int32_t *bad,
+                                 cudaStream_t s);
+int vec_blocks(int64_t n_nodes);  // fixed grid of the node-vector kernels (partials per block)
+// r = b - Ap; z = Jinv r; p = z; block partials of b.b, r.r, r.z -> part[0..3*nb)
+cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv, double *r, double *z, double *p,
+                           int64_t N, double *part, cudaStream_t s);
+#define NS_FIN_INIT 0
+#define NS_FIN_PAP 1
+#define NS_FIN_UPDATE 2
+#define NS_FIN_FCG_INIT 3
+#define NS_FIN_FCG_BETA 4
+#define NS_FIN_FCG_UPDATE 6
+// One block sums part[v*n .. v*n+n) for v < nvals in a fixed order and updates the CG scalars:
+//  INIT: bb, rr, rz -> done (1 converged, 2 zero right-hand side); PAP: pAp, alpha = rz/pAp;
+//  UPDATE: rr, rz -> iters++, done (1 converged, 3 iteration limit), beta = rz/rz_old.
+cudaError_t launch_cg_final(const double *part, int n, int nvals, CgScalars *sc, int mode, double tol, int max_iter,
+                            cudaStream_t s);
+// x += alpha p; r -= alpha Ap; z = Jinv r; partials r.r, r.z -> part[0..2*nb)
+cudaError_t launch_cg_update(double *x, double *r, double *z, const double *p, const double *Ap, const double *Jinv,
+                             int64_t N, double *part, const CgScalars *sc, cudaStream_t s);
+// p = z + beta p; Ap = 0
+cudaError_t launch_cg_pupdate(double *p, const double *z, double *Ap, int64_t N, const CgScalars *sc, cudaStream_t s);
+// flexible outer CG (FP64) with the inner FP32 PCG as preconditioner
+cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_t N, double *part, cudaStream_t s);
+cudaError_t launch_fcg_gamma(const float *xin, double *z, const double *Ap, int64_t N, double *part,
+                             const CgScalars *so, cudaStream_t s);
+cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, int64_t N, double *part,
+                         const CgScalars *so, cudaStream_t s);
+cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int npap, CgScalars *sc, cudaStream_t s);
+cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, int64_t N, double *part,
+                              const CgScalars *so, cudaStream_t s);
+cudaError_t launch_in_init(const double *r, const CgScalars *so, const float *J, float *rin, float *zin, float *pin,
+                           float *xin, float *Apin, int64_t N, double *part, cudaStream_t s);
+cudaError_t launch_in_update(float *xin, float *rin, float *zin, const float *pin, const float *Apin, const float *J,
+                             int64_t N, double *part, const CgScalars *si, const CgScalars *so, cudaStream_t s);
+cudaError_t launch_in_pupdate(float *pin, const float *zin, float *Apin, int64_t N, const CgScalars *si,
+                              const CgScalars *so, cudaStream_t s);
+cudaError_t launch_newmark(double *u, double *v, double *a, double *du_prev, const double *du, int64_t N, double dt,
+                           cudaStream_t s);
+cudaError_t launch_surface_gather(const int32_t *surf, int64_t Ns, const double *u, const double *v, const double *a,
+                                  double *ou, double *ov, double *oa, cudaStream_t s);
+cudaError_t launch_d_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);
+cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *part, cudaStream_t s);
+
+// ------------------------------------------------------------------ k_spring.cu
+struct SpringTables {
+  const double *q;    // [S][6]
+  const double *T;    // [S][21] w q q^T packed upper triangle (+ one row with their sum)
+  const double *pow;  // power tables: r[128], -ln r hi[128], lo[128], 2^(i/64)[64], ln2 hi/lo, ln2/64 hi/lo
+  int S;
+};
+constexpr int kPowTabLen = 452;
+// Spring update of points [p0, p1) (point p = elem*4 + qp), strains from eps [P][12];
+// state arrays indexed relative to `base` point; D written to D[(qp*21 + k) * epad + elem]
+// (element layout) or, if dpts != nullptr, to dpts[p][21] (free points).
+cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const int32_t *mat_of_elem,
+                           const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
+                           int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s);
+// elastic tangent for elements [e0, e1)
+cudaError_t launch_elastic_D(const SpringTables &tab, const MatConst *mc, const int32_t *mat, double *D, int64_t epad,
+                             int64_t e0, int64_t e1, cudaStream_t s);
+cudaError_t launch_D_to_f32(const double *D, float *D32, int64_t epad, int64_t E, cudaStream_t s);
+
+// ------------------------------------------------------------------ ns_host.cpp
+int host_spring_directions(int S, double *q, double *w);
+int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, int32_t *nc);
+void host_material_constants(const ns_material &m, double f1, double f2, MatConst *out);
+void host_pow_tables(double *out);  // kPowTabLen entries
+
+}  // namespace ns

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads, exports every entry point include/ns.h
+declares, and its host-only helpers agree with the oracle's independent
+re-derivations (no device work)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_02755_gb300 import binding, build, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ns.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ns_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(binding.EXPORTED) == names
+
+
+def test_spring_directions_match_oracle():
+    for S in (5, 10, 50, 150):
+        qg, wg = binding.ns_spring_directions(S)
+        qo, wo = oracle.spring_dirs(S)
+        assert wg == wo
+        assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
+    with pytest.raises(binding.NsError):
+        binding.ns_spring_directions(4)
+
+
+def test_colouring_bit_exact_with_oracle():
+    m = synth.kuhn_box(6, 5, 4, 60.0, 50.0, 40.0, jitter=0.1, seed=3)
+    cg, ncg = binding.ns_colour_elements(m.conn, m.n_nodes)
+    co, nco = oracle.colouring(m.conn, m.n_nodes)
+    assert ncg == nco
+    assert np.array_equal(cg, co)
+
+
+def test_state_bytes_match_paper_sizing():
+    assert binding.ns_state_bytes(1, 150) == 24000
+    assert binding.ns_state_bytes(7987200, 150) == 7987200 * 24000
+
+
+def test_create_without_device_reports_an_error_code():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(binding.NsError) as ei:
+        binding.ns_create(binding.ns_config_default())
+    assert ei.value.code == -4
+
+
+def test_invalid_config_rejected_before_device_use():
+    with pytest.raises(binding.NsError) as ei:
+        binding.ns_create(binding.ns_config_default(n_springs=3))
+    assert ei.value.code == -1

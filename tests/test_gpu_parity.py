@@ -1,0 +1,289 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Tolerances:
+  * element operators, spring points: 1e-12 relative (both sides FP64; only the
+    summation order differs);
+  * whole steps: relative L2 of surface displacement and velocity <= 1e-6
+    (both sides stop CG at ||r|| <= 1e-8 ||b||; the solutions differ at the
+    level of that tolerance, never above it);
+  * index-valued state (spring direction and branch flags): bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_02755_gb300 import binding as B
+from paper_2604_02755_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+    B.lib()
+
+
+def small(dims=(3, 2, 2), S=10, nt=80, seed=5, jitter=0.1, peak=3.0):
+    m = synth.kuhn_box(*dims, 30.0 * dims[0] / 3, 20.0 * dims[1] / 2, 30.0, layer_depths=(15.0,), jitter=jitter,
+                       seed=seed)
+    w = synth.band_limited_wave(seed, nt + 1, 0.01, peak=peak)
+    return synth.Workload("small", m, synth.two_layer_materials(0.02), S, 0.01, nt, w)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+@pytest.mark.parametrize("scatter", [B.NS_SCATTER_ATOMIC, B.NS_SCATTER_COLOUR])
+def test_operators_match_oracle(scatter):
+    wl = small(dims=(4, 3, 2))
+    o = oracle.Oracle.from_workload(wl)
+    rng = np.random.default_rng(0)
+    with B.Simulation(wl, scatter=scatter) as sim:
+        # random symmetric positive definite tangents at every point
+        E = wl.mesh.n_elems
+        A = rng.normal(size=(E, 4, 6, 6)) * 1e7
+        D = np.einsum("epij,epkj->epik", A, A) + 1e8 * np.eye(6)
+        B.ns_write_state(sim.ctx, 0, D=D)
+        x = rng.normal(size=(wl.mesh.n_nodes, 3))
+        for op in ("K", "M", "Cb", "A", "Cr"):
+            yg = B.ns_apply_operator(sim.ctx, op, x)
+            yo = o.operator(op, x, D=D)
+            assert np.abs(yg - yo).max() <= 1e-12 * np.abs(yo).max(), op
+
+
+def test_spring_points_match_oracle():
+    wl = small()
+    S = 50
+    q, w = oracle.spring_dirs(S)
+    mats = wl.materials
+    rng = np.random.default_rng(3)
+    npts = 64
+    mat = (np.arange(npts) % 2).astype(np.int32)
+    th_g = np.zeros((npts, S), B.SPRING_DTYPE)
+    th_o = np.zeros((npts, S), oracle.SPRING_DTYPE)
+    eps = np.zeros((npts, 6))
+    wl2 = synth.Workload(wl.name, wl.mesh, mats, S, wl.dt, wl.n_steps, wl.wave)
+    with B.Simulation(wl2) as sim:
+        for it in range(40):
+            scale = 10 ** rng.uniform(-6, -3, size=(npts, 1))
+            deps = rng.normal(size=(npts, 6)) * scale
+            if it == 5:
+                deps[:4] = 0.0  # zero increments leave the state untouched
+            eps = eps + deps
+            th_g, Dg = B.ns_spring_points(sim.ctx, mat, eps, deps, th_g.reshape(-1))
+            th_g = th_g.reshape(npts, S)
+            for p in range(npts):
+                mm = mats[mat[p]]
+                ro = oracle.ro_params(mm["rho"], mm["vs"], mm["gamma_ref"], mm["h_max"])
+                Kb = mm["rho"] * (mm["vp"] ** 2 - 4.0 / 3.0 * mm["vs"] ** 2)
+                Do = oracle.point_update(q, w, Kb, ro, eps[p], deps[p], th_o[p])
+                assert np.abs(Dg[p] - Do).max() <= 1e-12 * np.abs(Do).max(), (it, p)
+            assert np.array_equal(th_g["dir"], th_o["dir"])
+            assert np.array_equal(th_g["mode"], th_o["mode"])
+            for f in ("tau", "tR"):
+                scale = np.abs(th_o[f]).max() + 1e-300
+                assert np.abs(th_g[f] - th_o[f]).max() <= 1e-12 * scale, f
+            for f in ("gR", "gmax"):
+                scale = np.abs(th_o[f]).max() + 1e-300
+                assert np.abs(th_g[f] - th_o[f]).max() <= 1e-13 * scale, f
+    assert (th_o["mode"] == 1).any() and (th_o["mode"] == 0).any()
+
+
+def run_both(wl, nsteps, **cfg):
+    o = oracle.Oracle.from_workload(wl)
+    with B.Simulation(wl, surface_ring_steps=max(nsteps, 1), **cfg) as sim:
+        for _ in range(nsteps):
+            o.step()
+        sim.advance(nsteps)
+        out = dict(u=sim.nodal("u"), v=sim.nodal("v"), a=sim.nodal("a"), q=sim.nodal("q"), du=sim.nodal("du"),
+                   surf=sim.surface(1, nsteps), state=sim.state(), stats=sim.stats())
+    return o, out
+
+
+def test_one_step_matches_oracle():
+    wl = small(dims=(4, 3, 2), nt=40)
+    o, g = run_both(wl, 1)
+    for f in ("u", "v", "a", "q", "du"):
+        assert rel(g[f], getattr(o, f)) <= 1e-7, f
+    th, D = g["state"]
+    assert rel(D, o.D) <= 1e-8
+    assert np.array_equal(th["dir"], o.th["dir"]) and np.array_equal(th["mode"], o.th["mode"])
+    assert abs(g["stats"]["cg_iters_last"] - o.iters) <= 2
+
+
+@pytest.mark.parametrize("scatter,precision", [(B.NS_SCATTER_ATOMIC, B.NS_PREC_FP64),
+                                               (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64),
+                                               (B.NS_SCATTER_ATOMIC, B.NS_PREC_FP64_IR),
+                                               (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64_IR)])
+def test_thirty_steps_surface_parity(scatter, precision):
+    wl = small(dims=(4, 3, 3), nt=60)
+    nsteps = 30
+    o = oracle.Oracle.from_workload(wl)
+    us, vs = [], []
+    with B.Simulation(wl, surface_ring_steps=nsteps, scatter=scatter, precision=precision) as sim:
+        for _ in range(nsteps):
+            o.step()
+            us.append(o.u[wl.mesh.surf].copy())
+            vs.append(o.v[wl.mesh.surf].copy())
+        sim.advance(nsteps)
+        s = sim.surface(1, nsteps)
+        th, _ = sim.state()
+    assert rel(s["u"], np.array(us)) <= 1e-6
+    assert rel(s["v"], np.array(vs)) <= 1e-6
+    # almost every spring ends in the same branch state
+    assert np.mean(th["mode"] == o.th["mode"]) > 0.999
+    assert (o.th["mode"] == 1).mean() > 0.01  # hysteresis happened
+
+
+def test_colour_scatter_is_deterministic_and_streaming_is_invisible():
+    wl = small(dims=(4, 3, 3), nt=60)
+    n = 12
+    S = wl.n_springs
+    per_elem = B.ns_state_bytes(1, S)
+    res = []
+    for budget, chunk, ring in ((-1, 100000, 3), (-1, 100000, 3), (per_elem * 37, 13, 3), (0, 29, 2)):
+        with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR, surface_ring_steps=n, device_state_budget=budget,
+                          chunk_elems=chunk, ring_depth=ring) as sim:
+            sim.advance(n)
+            st = sim.stats()
+            res.append((sim.nodal("u"), sim.nodal("v"), sim.state(), st))
+    u0, v0, (th0, D0), _ = res[0]
+    for u, v, (th, D), st in res[1:]:
+        assert np.array_equal(u, u0) and np.array_equal(v, v0)
+        assert np.array_equal(D, D0)
+        assert th.tobytes() == th0.tobytes()
+    assert res[2][3]["streamed_elems"] == wl.mesh.n_elems - 37
+    assert res[3][3]["streamed_elems"] == wl.mesh.n_elems
+    assert res[3][3]["h2d_bytes"] == n * wl.mesh.n_elems * per_elem
+
+
+def test_checkpoint_restore_bit_identical():
+    wl = small(dims=(3, 3, 2), nt=40)
+    with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR) as a:
+        a.advance(10)
+        ua = a.nodal("u")
+        tha, Da = a.state()
+    with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR) as b:
+        b.advance(4)
+        ck = B.ns_checkpoint(b.ctx)
+    with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR) as c:
+        B.ns_restore(c.ctx, ck)
+        assert c.stats()["steps"] == 4
+        c.advance(6)
+        assert np.array_equal(c.nodal("u"), ua)
+        th, D = c.state()
+        assert np.array_equal(D, Da) and th.tobytes() == tha.tobytes()
+
+
+def test_errors_are_reported():
+    wl = small()
+    with B.Simulation(wl) as sim:
+        with pytest.raises(B.NsError) as ei:
+            B.ns_set_ground_motion(sim.ctx, wl.wave, 0.02)
+        assert ei.value.code == -1
+        with pytest.raises(B.NsError):
+            sim.surface(1, 1)  # nothing advanced yet
+    bad = small()
+    bad.mesh.xyz[bad.mesh.conn[0, 4]] += 1.0  # curved edge
+    with pytest.raises(B.NsError) as ei:
+        B.Simulation(bad)
+    assert ei.value.code == -5
+    wl = small()
+    with B.Simulation(wl, cg_max_iter=2) as sim:
+        with pytest.raises(B.NsError) as ei:
+            sim.advance(1)
+        assert ei.value.code == -6
+
+
+@pytest.mark.parametrize("precision,nsteps", [(B.NS_PREC_FP64, 60), (B.NS_PREC_FP64_IR, 60)])
+def test_tiny_two_layer_case_parity(precision, nsteps):
+    """The plain FP64 tiny case (200x200x60 m, 10x10x6 hexahedra -> 3,600 quadratic
+    tetrahedra, 10 springs/point, dt 0.01 s) over its first steps."""
+    wl = synth.tiny_two_layer()
+    o = oracle.Oracle.from_workload(wl)
+    us, vs = [], []
+    with B.Simulation(wl, surface_ring_steps=nsteps, precision=precision) as sim:
+        for _ in range(nsteps):
+            o.step()
+            us.append(o.u[wl.mesh.surf].copy())
+            vs.append(o.v[wl.mesh.surf].copy())
+        sim.advance(nsteps)
+        s = sim.surface(1, nsteps)
+    assert rel(s["u"], np.array(us)) <= 1e-6
+    assert rel(s["v"], np.array(vs)) <= 1e-6
+
+
+def test_tiny_two_layer_full_record():
+    """All 300 steps of the tiny case in the paper's precision policy."""
+    wl = synth.tiny_two_layer()
+    nsteps = wl.n_steps
+    o = oracle.Oracle.from_workload(wl)
+    us, vs = [], []
+    for _ in range(nsteps):
+        o.step()
+        us.append(o.u[wl.mesh.surf].copy())
+        vs.append(o.v[wl.mesh.surf].copy())
+    with B.Simulation(wl, surface_ring_steps=nsteps, precision=B.NS_PREC_FP64_IR) as sim:
+        sim.advance(nsteps)
+        s = sim.surface(1, nsteps)
+        th, _ = sim.state()
+    assert rel(s["u"], np.array(us)) <= 1e-6
+    assert rel(s["v"], np.array(vs)) <= 1e-6
+    assert np.mean(th["mode"] == o.th["mode"]) > 0.999
+
+
+def incident(conn, node):
+    return np.nonzero((conn == node).any(axis=1))[0]
+
+
+def test_large_model_sampled_outputs():
+    """The single large model at full size (7,987,200 elements, 150 springs/point,
+    191.7 GB of spring state in HBM), one step in the benchmark's configuration,
+    checked on sampled outputs the oracle computes one by one: the operator A at
+    sampled nodes (through a sub-model of the incident elements and faces) and the
+    multi-spring update of sampled elements from the device's strains."""
+    wl = synth.large_single_model()
+    m = wl.mesh
+    rng = np.random.default_rng(11)
+    samp_e = np.sort(rng.choice(m.n_elems, 6, replace=False))
+    S = wl.n_springs
+    with B.Simulation(wl, precision=B.NS_PREC_FP64_IR, surface_ring_steps=2) as sim:
+        sim.advance(1)
+        before = [B.ns_read_state(sim.ctx, int(e), 1, S) for e in samp_e]
+        sim.advance(1)
+        st = sim.stats()
+        assert st["relres_last"] <= 1e-8
+        u, du = sim.nodal("u"), sim.nodal("du")
+        after = [B.ns_read_state(sim.ctx, int(e), 1, S) for e in samp_e]
+        # spring update of sampled elements
+        q, w = oracle.spring_dirs(S)
+        Lq, _ = oracle.quad_points()
+        for e, (thb, _), (tha, Da) in zip(samp_e, before, after):
+            X = m.xyz[m.conn[e]]
+            mm = wl.materials[m.mat[e]]
+            ro = oracle.ro_params(mm["rho"], mm["vs"], mm["gamma_ref"], mm["h_max"])
+            Kb = mm["rho"] * (mm["vp"] ** 2 - 4.0 / 3.0 * mm["vs"] ** 2)
+            th = thb[0].copy()
+            for qp in range(4):
+                G, _ = oracle.grad(X, Lq[qp])
+                Bm = oracle.bmatrix(G)
+                eps = Bm @ u[m.conn[e]].ravel()
+                deps = Bm @ du[m.conn[e]].ravel()
+                Do = oracle.point_update(q, w, Kb, ro, eps, deps, th[qp])
+                assert np.abs(Da[0, qp] - Do).max() <= 1e-11 * np.abs(Do).max()
+            assert np.array_equal(th["dir"], tha[0]["dir"]) and np.array_equal(th["mode"], tha[0]["mode"])
+            assert np.abs(th["tau"] - tha[0]["tau"]).max() <= 1e-11 * (np.abs(th["tau"]).max() + 1e-300)
+        # operator at sampled nodes through the oracle on the incident sub-model
+        x = rng.normal(size=(m.n_nodes, 3))
+        y = B.ns_apply_operator(sim.ctx, "A", x)
+        _, Dall = None, None
+        for node in rng.choice(m.n_nodes, 4, replace=False):
+            els = incident(m.conn, node)
+            fcs = np.nonzero((m.faces == node).any(axis=1))[0]
+            _, Dloc = zip(*[B.ns_read_state(sim.ctx, int(e), 1, S, theta=False) for e in els])
+            Dloc = np.concatenate(Dloc)
+            sub = oracle.Oracle(m.xyz, m.conn[els], m.mat[els], wl.materials, m.faces[fcs],
+                                np.searchsorted(els, m.face_elem[fcs]), m.face_kind[fcs], S, wl.dt, wl.wave)
+            yo = sub.operator("A", x, D=Dloc)
+            assert np.abs(y[node] - yo[node]).max() <= 1e-12 * np.abs(yo[node]).max()
