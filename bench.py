@@ -174,7 +174,10 @@ def main():
     ap.add_argument("--workload", default="large", choices=["large", "tiny"])
     ap.add_argument("--no-stream", action="store_true", help="skip the streamed-state measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--stream-gb", type=float, default=48.0, help="spring state kept in pinned host memory (GB)")
+    ap.add_argument("--stream-gb", type=float, default=96.0, help="spring state kept in pinned host memory (GB)")
+    ap.add_argument("--solver", default="fp64-ir", choices=["fp64-ir", "fp64-pcg"],
+                    help="fp64-ir: FP64 flexible CG with an FP32 PCG preconditioner (the paper's precision policy); "
+                         "fp64-pcg: plain FP64 block-Jacobi PCG")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -197,7 +200,8 @@ def main():
     n_total = args.warmup + 2 * args.steps + 2
     wave = synth.band_limited_wave(2, max(n_total + 1, 400), wl.dt)
     wl.wave = wave
-    sim = B.Simulation(wl, device=local, timing=1, surface_ring_steps=max(args.steps, 1))
+    prec = B.NS_PREC_FP64_IR if args.solver == "fp64-ir" else B.NS_PREC_FP64
+    sim = B.Simulation(wl, device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec)
     sim.advance(args.warmup)
     B.ns_reset_stats(sim.ctx)
     st0 = sim.stats()
@@ -242,6 +246,13 @@ def main():
     d2h = sum(a.nbytes for a in s.values()) / args.steps
     e2e = {"value": e2e_work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     phases = {k: st[k] / args.steps for k in ("ms_rhs", "ms_jacobi", "ms_solve", "ms_newmark", "ms_springs")}
+    kernels = {"ebe64": {"launches_per_step": st["n_ebe64"] / args.steps,
+                         "avg_ms": st["ms_ebe64"] / max(st["n_ebe64"], 1)},
+               "ebe32": {"launches_per_step": st["n_ebe32"] / args.steps,
+                         "avg_ms": st["ms_ebe32"] / max(st["n_ebe32"], 1)},
+               "springs": {"launches_per_step": st["n_spring"] / args.steps,
+                           "avg_ms": st["ms_spring"] / max(st["n_spring"], 1)}}
+    inner_iters = st["inner_iters_last"]
     cg_iters = st["cg_iters_total"] / args.steps
     sim.close()
     del sim
@@ -252,7 +263,8 @@ def main():
         per_elem = B.ns_state_bytes(1, wl.n_springs)
         stream_elems = int(args.stream_gb * 1e9 / per_elem)
         budget = (E - stream_elems) * per_elem
-        sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000, ring_depth=3)
+        sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000, ring_depth=3,
+                           precision=prec)
         sim.advance(1)
         B.ns_reset_stats(sim.ctx)
         sim.advance(2)
@@ -282,6 +294,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
+                "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver,
                 "state_stream": stream}
         print(json.dumps(line), flush=True)
     dist.finalize(dd)

@@ -6,9 +6,26 @@
 namespace ns {
 
 struct RoPar {
-  double G0, tref, alpha, beta;  // tref = G0 * gamma_ref
-  double iG0, itref;             // reciprocals
+  double G0, alpha, beta, iG0, itref;  // itref = 1 / (G0 gamma_ref)
+  double c2, c3;                       // series coefficients of (1 + d)^beta
+  float itref_f, iG0_f, alpha_f, beta_f;
 };
+
+__device__ __forceinline__ RoPar ro_par(const MatConst &m) {
+  RoPar r;
+  r.G0 = m.G0;
+  r.alpha = m.alpha_ro;
+  r.beta = m.beta_ro;
+  r.iG0 = 1.0 / m.G0;
+  r.itref = 1.0 / (m.G0 * m.gref);
+  r.c2 = m.beta_ro * (m.beta_ro - 1.0) * 0.5;
+  r.c3 = r.c2 * (m.beta_ro - 2.0) * (1.0 / 3.0);
+  r.itref_f = (float)r.itref;
+  r.iG0_f = (float)r.iG0;
+  r.alpha_f = (float)m.alpha_ro;
+  r.beta_f = (float)m.beta_ro;
+  return r;
+}
 
 // ---------------------------------------------------------------------------------------
 // FP64 power x^beta for x > 0 (normal), table-driven after Tang (ACM TOMS 1989, 1990):
@@ -66,42 +83,22 @@ __device__ __forceinline__ double pow_pos(double x, double beta, const PowTab &t
   return exp_tab(beta * ln_pos(x, tb), tb);
 }
 
-// Skeleton strain of a stress g(tau) = (tau/G0)(1 + alpha |tau/tref|^beta) and the root
-// tau = F(ga) for ga > 0 (g is odd, increasing, convex for tau > 0; tau <= G0 ga).
-//  1. FP32 Newton (from the guess when it lies in (0, G0 ga], else from G0 ga) to ~1e-7.
-//  2. FP64 safeguarded Newton from that seed; the power is evaluated once with pow_pos and
-//     carried to each new iterate by the series (1 + d)^beta (|d| <= 1e-4: error < 1e-19),
-//     re-evaluated whenever an iterate moves further.  Stops when a Newton step is below
-//     1e-12 tau (the remaining error then is below rounding).
-// *pw returns |F/tref|^beta at the returned root (for the tangent 1/g'(F)).
-__device__ double ro_F(double ga, double guess, const RoPar &p, const PowTab &tb, double *pw) {
-  if (ga == 0.0) {
-    *pw = 0.0;
-    return 0.0;
-  }
+// FP32 reciprocal refined once (relative error ~1e-14) or twice (~1e-28) in FP64.
+__device__ __forceinline__ double rcp1(double x) {
+  double r = (double)(1.0f / (float)x);
+  return r * fma(-x, r, 2.0);
+}
+__device__ __forceinline__ double rcp2(double x) {
+  double r = rcp1(x);
+  return r * fma(-x, r, 2.0);
+}
+
+// Safeguarded FP64 Newton on g(tau) = ga from tau in (0, hi]: bisection replaces steps that
+// leave the bracket; the power is re-evaluated at every iterate.  Used only when the
+// fast path below does not certify convergence.
+__device__ double ro_F_safe(double ga, double tau, const RoPar &p, const PowTab &tb, double *pw) {
   const double hi = p.G0 * ga;
-  const float itrf = (float)p.itref, af = (float)p.alpha, bf = (float)p.beta, gaf = (float)ga,
-              iG0f = (float)p.iG0, hif = (float)hi;
-  float t = (guess > 0.0 && guess < hi) ? (float)guess : hif;
-  if (!(t > 0.0f)) t = hif;
-  for (int it = 0; it < 40 && t > 0.0f; ++it) {
-    const float pwf = powf(t * itrf, bf);
-    const float step = (t * iG0f * (1.0f + af * pwf) - gaf) / ((1.0f + af * (1.0f + bf) * pwf) * iG0f);
-    float tn = t - step;
-    if (!(tn > 0.0f)) tn = 0.5f * t;
-    if (tn > hif) tn = hif;
-    const bool conv = fabsf(step) <= 2e-7f * t;
-    t = tn;
-    if (conv) break;
-  }
-  double tau = (double)t;
-  if (!(tau > 0.0) || !(tau <= hi)) tau = hi;
-  const double b = p.beta, c2 = b * (b - 1.0) * 0.5, c3 = c2 * (b - 2.0) * (1.0 / 3.0),
-               c4 = c3 * (b - 3.0) * 0.25;
-  double w = pow_pos(tau * p.itref, b, tb), tw = tau;
-  double itw = (double)(1.0f / (float)tw);
-  itw = itw * (2.0 - tw * itw);
-  double lo = 0.0, up = hi;
+  double lo = 0.0, up = hi, w = pow_pos(tau * p.itref, p.beta, tb);
   for (int it = 0; it < 200; ++it) {
     const double gval = tau * p.iG0 * (1.0 + p.alpha * w);
     if (gval == ga) break;
@@ -109,72 +106,127 @@ __device__ double ro_F(double ga, double guess, const RoPar &p, const PowTab &tb
       up = tau;
     else
       lo = tau;
-    const double step = (gval - ga) * p.G0 / (1.0 + p.alpha * (1.0 + b) * w);
+    const double step = (gval - ga) * p.G0 / (1.0 + p.alpha * (1.0 + p.beta) * w);
     double nt = tau - step;
     const bool newton = nt >= lo && nt <= up;
     if (!newton) nt = 0.5 * (lo + up);
     const double last = nt - tau;
     tau = nt;
-    const double d = (tau - tw) * itw;
-    if (fabs(d) <= 1e-4)
-      w *= fma(d, fma(d, fma(d, fma(d, c4, c3), c2), b), 1.0);  // w now belongs to tau
-    else
-      w = pow_pos(tau * p.itref, b, tb);
-    tw = tau;
-    itw = (double)(1.0f / (float)tw);
-    itw = itw * (2.0 - tw * itw);
-    if (newton && fabs(last) <= 1e-12 * tau) break;
+    w = pow_pos(tau * p.itref, p.beta, tb);
+    if (newton && fabs(last) <= 1e-15 * tau) break;
   }
   *pw = w;
   return tau;
 }
 
-__device__ __forceinline__ double ro_tangent_from_pw(double pw, const RoPar &p) {
-  return p.G0 / (1.0 + p.alpha * (1.0 + p.beta) * pw);
+// Root tau = F(ga) of the skeleton g(tau) = (tau/G0)(1 + alpha (tau/tref)^beta) = ga > 0
+// (g odd, increasing, convex for tau > 0, tau <= G0 ga), or -- when `solve` is false --
+// only the power at tau = ga.  Every lane evaluates exactly one FP64 power, so a warp
+// whose springs follow different Masing paths does not diverge around it:
+//  1. (solve) FP32 Newton from the guess if it lies in (0, G0 ga], else from G0 ga,
+//     to a relative step of 4e-6;
+//  2. w = (tau/tref)^beta in FP64 (table-driven power);
+//  3. (solve) two FP64 Newton steps (FP32 reciprocal of g', contraction ~1e-7 per step
+//     on top of the quadratic one) carrying w by the series (1 + d)^beta; a seed error
+//     of 4e-6 leaves < 1e-17 after them.  If the steps are not small enough the safe
+//     loop above takes over.
+// *pw returns (F/tref)^beta at the returned root.
+__device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, const RoPar &p, const PowTab &tb,
+                                           double *pw) {
+  double tau = ga;
+  if (solve) {
+    const double hi = p.G0 * ga;
+    const float gaf = (float)ga, hif = (float)hi;
+    float t = (guess > 0.0 && guess < hi) ? (float)guess : hif;
+    if (!(t > 0.0f)) t = hif;
+    for (int it = 0; it < 40; ++it) {
+      const float pwf = __powf(t * p.itref_f, p.beta_f);
+      const float gp = 1.0f + p.alpha_f * (1.0f + p.beta_f) * pwf;
+      const float step = (t * p.iG0_f * (1.0f + p.alpha_f * pwf) - gaf) * __fdividef((float)p.G0, gp);
+      float tn = t - step;
+      if (!(tn > 0.0f)) tn = 0.5f * t;
+      if (tn > hif) tn = hif;
+      const bool conv = fabsf(step) <= 4e-6f * t;
+      t = tn;
+      if (conv) break;
+    }
+    tau = (double)t;
+    if (!(tau > 0.0) || !(tau <= hi)) tau = hi;
+  }
+  if (!(tau > 0.0)) {  // zero strain (or zero stress): the power vanishes
+    *pw = 0.0;
+    return 0.0;
+  }
+  double w = pow_pos(tau * p.itref, p.beta, tb);
+  if (solve) {
+    const double it0 = rcp1(tau);
+    double dmax = 0.0;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const double gval = tau * p.iG0 * fma(p.alpha, w, 1.0);
+      const double gp = fma(p.alpha * (1.0 + p.beta), w, 1.0);
+      const double step = (gval - ga) * p.G0 * (double)(1.0f / (float)gp);
+      const double d = -step * it0;
+      tau -= step;
+      w *= fma(d, fma(d, fma(d, p.c3, p.c2), p.beta), 1.0);
+      dmax = (it == 0) ? fabs(d) : dmax;
+      if (it == 1 && !(fabs(d) <= 1e-9 && dmax <= 1e-4)) tau = ro_F_safe(ga, tau > 0.0 ? tau : 0.5 * ga * p.G0, p, tb, &w);
+    }
+  }
+  *pw = w;
+  return tau;
 }
 
-__device__ __forceinline__ double signed_F(double x, double guess_abs, const RoPar &p, const PowTab &tb, double *pw) {
-  const double f = ro_F(fabs(x), guess_abs, p, tb, pw);
-  return x < 0.0 ? -f : f;
+// G0 / g'(tau) with g' = 1 + alpha (1 + beta) pw.
+__device__ __forceinline__ double ro_tangent_from_pw(double pw, const RoPar &p) {
+  return p.G0 * rcp2(fma(p.alpha * (1.0 + p.beta), pw, 1.0));
 }
 
 // One spring (Masing bookkeeping of the documented reading): virgin -> skeleton in the
 // direction of motion; reversal stores (gamma_old, tau_old) and follows
-// tau = tR + 2 F((gamma - gR)/2); moving outward past gmax returns to the skeleton.
-// The previous value on the same curve seeds the root search.  Returns the tangent.
-__device__ double spring_update(double g, double dg, const RoPar &p, const PowTab &tb, double &tau, double &gR,
-                                double &tR, double &gmax, int &dir, int &mode) {
-  double pw;
-  if (dg != 0.0) {
+// tau = tR + 2 F((gamma - gR)/2); moving outward with |gamma| >= gmax returns to the
+// skeleton tau = F(gamma) (decided before the root solve, so each spring solves once).
+// With no increment the state is kept and only the tangent is evaluated.
+// Returns the tangent dtau/dgamma at the end state.
+__device__ __forceinline__ double spring_update(double g, double dg, const RoPar &p, const PowTab &tb, double &tau,
+                                                double &gR, double &tR, double &gmax, int &dir, int &mode) {
+  const bool active = dg != 0.0;
+  double x, guess = 0.0;
+  if (active) {
     const int sgn = dg > 0.0 ? 1 : -1;
-    bool same_curve = true;
+    bool same = true;
     if (dir == 0) {
       dir = sgn;
       mode = 0;
-      same_curve = false;
+      same = false;
     } else if (sgn != dir) {
       gR = g - dg;
       tR = tau;
       mode = 1;
       dir = sgn;
-      same_curve = false;
+      same = false;
     }
-    if (mode == 0) {
-      tau = signed_F(g, same_curve ? fabs(tau) : 0.0, p, tb, &pw);
-      if (fabs(g) > gmax) gmax = fabs(g);
-    } else {
-      const double f = signed_F(0.5 * (g - gR), same_curve ? 0.5 * fabs(tau - tR) : 0.0, p, tb, &pw);
-      tau = tR + 2.0 * f;
-      if (fabs(g) >= gmax && g * (double)dir > 0.0) {
-        mode = 0;
-        tau = signed_F(g, fabs(tau), p, tb, &pw);
-        gmax = fabs(g);
-      }
+    if (mode == 1 && fabs(g) >= gmax && g * (double)dir > 0.0) {
+      mode = 0;  // outward past the largest skeleton strain: back on the skeleton
+      guess = fabs(tau);
+    } else if (same) {
+      guess = (mode == 0) ? fabs(tau) : 0.5 * fabs(tau - tR);
     }
-    return ro_tangent_from_pw(pw, p);
+    x = (mode == 0) ? g : 0.5 * (g - gR);
+  } else {
+    x = (mode == 0) ? tau : 0.5 * (tau - tR);  // the power at the current state only
   }
-  const double te = (mode == 0) ? tau : 0.5 * (tau - tR);
-  pw = (te == 0.0) ? 0.0 : pow_pos(fabs(te) * p.itref, p.beta, tb);
+  double pw;
+  const double f = ro_solve(active, fabs(x), guess, p, tb, &pw);
+  if (active) {
+    const double fs = x < 0.0 ? -f : f;
+    if (mode == 0) {
+      tau = fs;
+      gmax = fmax(gmax, fabs(g));
+    } else {
+      tau = tR + 2.0 * fs;
+    }
+  }
   return ro_tangent_from_pw(pw, p);
 }
 
@@ -198,8 +250,7 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
     const int lp = g / S, k = g - lp * S;
     const int64_t p = pt + lp;
     const int mt = mat_p ? mat_p[p] : mat_e[p >> 2];
-    const MatConst &m = mc[mt];
-    const RoPar rp{m.G0, m.G0 * m.gref, m.alpha_ro, m.beta_ro, 1.0 / m.G0, 1.0 / (m.G0 * m.gref)};
+    const RoPar rp = ro_par(mc[mt]);
     const double *ep = eps + 12 * p;
     const double *qk = q + 6 * k;
     double gam = 0.0, dgam = 0.0;
@@ -230,9 +281,18 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
     const int64_t p = pt + lp;
     const int mt = mat_p ? mat_p[p] : mat_e[p >> 2];
     const bool nn = ij < 3 || ij == 6 || ij == 7 || ij == 11;  // (i,j) both < 3
-    double acc = nn ? mc[mt].Kb : 0.0;
     const double *Gp = Gs + lp * S;
-    for (int k = 0; k < S; ++k) acc += Gp[k] * __ldg(T + 21 * k + ij);
+    // four independent partial sums (latency hiding), combined in a fixed order
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = 0;
+    for (; k + 3 < S; k += 4) {
+      a0 = fma(Gp[k], __ldg(T + 21 * k + ij), a0);
+      a1 = fma(Gp[k + 1], __ldg(T + 21 * (k + 1) + ij), a1);
+      a2 = fma(Gp[k + 2], __ldg(T + 21 * (k + 2) + ij), a2);
+      a3 = fma(Gp[k + 3], __ldg(T + 21 * (k + 3) + ij), a3);
+    }
+    for (; k < S; ++k) a0 = fma(Gp[k], __ldg(T + 21 * k + ij), a0);
+    const double acc = (nn ? mc[mt].Kb : 0.0) + ((a0 + a1) + (a2 + a3));
     if (dpts)
       dpts[21 * p + ij] = acc;
     else

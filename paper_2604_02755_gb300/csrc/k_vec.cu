@@ -107,7 +107,7 @@ cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv
 
 __global__ void __launch_bounds__(kBlock) k_cg_final(const double *__restrict__ part, int n, int nvals,
                                                      CgScalars *sc, int mode, double tol, int max_iter) {
-  if (mode != NS_FIN_INIT && sc->done) return;
+  if (mode != NS_FIN_INIT && mode != NS_FIN_FCG_INIT && sc->done) return;
   double v[3] = {0.0, 0.0, 0.0};
   for (int k = 0; k < nvals; ++k) {
     double acc = 0.0;

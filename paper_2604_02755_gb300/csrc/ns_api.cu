@@ -357,12 +357,12 @@ int alloc_soa(ns_ctx *c, SpringSoA &s, int64_t nspr, bool host) {
     if ((rc = dalloc(c, &s.tau, nspr)) || (rc = dalloc(c, &s.gR, nspr)) || (rc = dalloc(c, &s.tR, nspr)) ||
         (rc = dalloc(c, &s.gmax, nspr)) || (rc = dalloc(c, &s.dir, nspr)) || (rc = dalloc(c, &s.mode, nspr)))
       return rc;
-    CKC(c, cudaMemset(s.tau, 0, nspr * 8));
-    CKC(c, cudaMemset(s.gR, 0, nspr * 8));
-    CKC(c, cudaMemset(s.tR, 0, nspr * 8));
-    CKC(c, cudaMemset(s.gmax, 0, nspr * 8));
-    CKC(c, cudaMemset(s.dir, 0, nspr * 4));
-    CKC(c, cudaMemset(s.mode, 0, nspr * 4));
+    CKC(c, cudaMemsetAsync(s.tau, 0, nspr * 8, c->s_main));
+    CKC(c, cudaMemsetAsync(s.gR, 0, nspr * 8, c->s_main));
+    CKC(c, cudaMemsetAsync(s.tR, 0, nspr * 8, c->s_main));
+    CKC(c, cudaMemsetAsync(s.gmax, 0, nspr * 8, c->s_main));
+    CKC(c, cudaMemsetAsync(s.dir, 0, nspr * 4, c->s_main));
+    CKC(c, cudaMemsetAsync(s.mode, 0, nspr * 4, c->s_main));
   }
   return NS_OK;
 }
@@ -423,32 +423,36 @@ int prefetch_state(ns_ctx *c) {
   return NS_OK;
 }
 
-// Multi-spring update (Alg. 3 pipeline for the streamed part): resident elements in one
-// launch, then per chunk: wait H2D -> compute -> D2H, refilling freed slots.
+// Multi-spring update (Alg. 3 pipeline for the streamed part).  Streamed chunk k goes
+// H2D (copy stream) -> compute (main stream) -> D2H (second copy stream) through a ring
+// of R device buffers; the resident elements are cut into slices that the main stream
+// computes between chunks, so the copy engines stay busy while a chunk is in flight.
+int spring_launch(ns_ctx *c, const SpringSoA &st, int64_t base_elem, int64_t e0, int64_t e1) {
+  if (e1 <= e0) return NS_OK;
+  cudaEvent_t t0 = nullptr;
+  tbegin(c, TK_SPRING, c->s_main, &t0);
+  LAUNCH(c, launch_springs(c->tab, c->mats_d, c->m.mat, nullptr, c->eps, st, 4 * base_elem, 4 * e0, 4 * e1, c->D,
+                           c->m.epad, nullptr, c->s_main));
+  tend(c, TK_SPRING, c->s_main, t0);
+  return NS_OK;
+}
+
 int spring_phase(ns_ctx *c) {
   int rc;
-  cudaEvent_t t0 = nullptr;
   LAUNCH(c, launch_strain(c->m, c->u, c->du, c->eps, 0, c->m.E, c->s_main));
-  if (c->E_res > 0) {
-    tbegin(c, TK_SPRING, c->s_main, &t0);
-    LAUNCH(c, launch_springs(c->tab, c->mats_d, c->m.mat, nullptr, c->eps, c->st, 0, 0, 4 * c->E_res, c->D, c->m.epad,
-                             nullptr, c->s_main));
-    tend(c, TK_SPRING, c->s_main, t0);
-  }
   const int64_t nc = n_chunks(c);
-  if (nc == 0) return NS_OK;
+  if (nc == 0) return spring_launch(c, c->st, 0, 0, c->E_res);
   if ((rc = prefetch_state(c)) != NS_OK) return rc;
   const int R = c->cfg.ring_depth;
+  const int64_t S4 = 4 * (int64_t)c->tab.S;
+  auto slice = [&](int64_t k) { return c->E_res * k / (nc + 1); };  // resident slice k = [slice(k), slice(k+1))
+  if ((rc = spring_launch(c, c->st, 0, slice(0), slice(1))) != NS_OK) return rc;
   for (int64_t k = 0; k < nc; ++k) {
     const int slot = (int)(k % R);
     const int64_t e0 = c->E_res + k * c->cfg.chunk_elems;
     const int64_t e1 = std::min(c->m.E, e0 + c->cfg.chunk_elems);
-    const int64_t S4 = 4 * (int64_t)c->tab.S;
     CKC(c, cudaStreamWaitEvent(c->s_main, c->ev_h2d[slot], 0));
-    tbegin(c, TK_SPRING, c->s_main, &t0);
-    LAUNCH(c, launch_springs(c->tab, c->mats_d, c->m.mat, nullptr, c->eps, c->ring[slot], 4 * e0, 4 * e0, 4 * e1,
-                             c->D, c->m.epad, nullptr, c->s_main));
-    tend(c, TK_SPRING, c->s_main, t0);
+    if ((rc = spring_launch(c, c->ring[slot], e0, e0, e1)) != NS_OK) return rc;
     CKC(c, cudaEventRecord(c->ev_comp[slot], c->s_main));
     CKC(c, cudaStreamWaitEvent(c->s_d2h, c->ev_comp[slot], 0));
     if ((rc = copy_soa(c, c->hst, (e0 - c->E_res) * S4, c->ring[slot], 0, (e1 - e0) * S4, cudaMemcpyDeviceToHost,
@@ -457,6 +461,7 @@ int spring_phase(ns_ctx *c) {
     c->stats.d2h_bytes += (e1 - e0) * S4 * 40;
     CKC(c, cudaEventRecord(c->ev_d2h[slot], c->s_d2h));
     if (k + R < nc && (rc = issue_h2d(c, k + R)) != NS_OK) return rc;
+    if ((rc = spring_launch(c, c->st, 0, slice(k + 1), slice(k + 2))) != NS_OK) return rc;
   }
   CKC(c, cudaEventRecord(c->ev_d2h_all, c->s_d2h));
   if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t1, c->s_d2h));
@@ -524,7 +529,6 @@ int one_step(ns_ctx *c) {
   const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
   cudaEvent_t tstep = nullptr, t0 = nullptr;
   tbegin(c, TK_STEP, c->s_main, &tstep);
-  if ((rc = prefetch_state(c)) != NS_OK) return rc;
 
   // 3x3 block-Jacobi preconditioner from the diagonal node blocks of A^n
   tbegin(c, TK_JAC, c->s_main, &t0);
@@ -708,7 +712,8 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
     ns_destroy(c);
     return NS_ERR_OOM_DEVICE;
   }
-  cudaMemset(c->sc, 0, 2 * sizeof(CgScalars));
+  cudaMemsetAsync(c->sc, 0, 2 * sizeof(CgScalars), c->s_main);
+  cudaStreamSynchronize(c->s_main);
   c->sc_in = c->sc + 1;
   *c->flag_h = 0;
   *out = c;
@@ -740,9 +745,9 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
   CKC(c, cudaMemcpy(m.conn, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(m.mat, mat, E * 4, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->xyz_d, xyz, N * 24, cudaMemcpyHostToDevice));
-  CKC(c, cudaMemset(m.geom, 0, 10 * m.epad * 8));
-  CKC(c, cudaMemset(m.geom32, 0, 10 * m.epad * 4));
-  CKC(c, cudaMemset(c->flag_d, 0, 4));
+  CKC(c, cudaMemsetAsync(m.geom, 0, 10 * m.epad * 8, c->s_main));
+  CKC(c, cudaMemsetAsync(m.geom32, 0, 10 * m.epad * 4, c->s_main));
+  CKC(c, cudaMemsetAsync(c->flag_d, 0, 4, c->s_main));
   LAUNCH(c, launch_geometry(m, c->xyz_d, c->flag_d, c->s_main));
   CKC(c, cudaStreamSynchronize(c->s_main));
   int32_t bad = 0;
@@ -761,7 +766,7 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
       ((rc = dalloc(c, &c->rin, n3)) || (rc = dalloc(c, &c->zin, n3)) || (rc = dalloc(c, &c->pin, n3)) ||
        (rc = dalloc(c, &c->xin, n3)) || (rc = dalloc(c, &c->Apin, n3))))
     return rc;
-  for (double *x : {c->u, c->v, c->a, c->q, c->du}) CKC(c, cudaMemset(x, 0, n3 * 8));
+  for (double *x : {c->u, c->v, c->a, c->q, c->du}) CKC(c, cudaMemsetAsync(x, 0, n3 * 8, c->s_main));
   // colouring for the deterministic scatter
   int32_t nc = 0;
   if (c->cfg.scatter == NS_SCATTER_COLOUR) {
@@ -829,7 +834,7 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   // tangent D (element SoA [84][epad]) and spring state placement
   const int64_t E = c->m.E, epad = c->m.epad;
   if ((rc = dalloc(c, &c->D, 84 * (size_t)epad)) || (rc = dalloc(c, &c->D32, 84 * (size_t)epad))) return rc;
-  CKC(c, cudaMemset(c->D, 0, 84 * epad * 8));
+  CKC(c, cudaMemsetAsync(c->D, 0, 84 * epad * 8, c->s_main));
   LAUNCH(c, launch_elastic_D(c->tab, c->mats_d, c->m.mat, c->D, epad, 0, E, c->s_main));
   const int64_t per_elem = ns_state_bytes(1, S);
   if (c->cfg.device_state_budget < 0)
@@ -1162,7 +1167,7 @@ int ns_apply_operator(ns_ctx *c, int32_t op, const double *x, double *y) {
   if ((rc = sync_all(c)) != NS_OK) return rc;
   const size_t n3 = 3 * (size_t)c->m.N;
   CKC(c, cudaMemcpy(c->p, x, n3 * 8, cudaMemcpyHostToDevice));
-  CKC(c, cudaMemset(c->Ap, 0, n3 * 8));
+  CKC(c, cudaMemsetAsync(c->Ap, 0, n3 * 8, c->s_main));
   switch (op) {
     case NS_OP_K: rc = apply_elems64(c, c->op_K, nullptr, c->p, c->Ap, nullptr, nullptr, nullptr); break;
     case NS_OP_M: rc = apply_elems64(c, c->op_M, nullptr, c->p, c->Ap, nullptr, nullptr, nullptr); break;
