@@ -345,43 +345,47 @@ cudaError_t launch_faces32(const DevMesh &m, const MatConst *mc, float cC, const
 // ------------------------------------------------------------------ block-Jacobi diagonal blocks
 
 // For node i of the element: sum_q w_q B_i^T D_q B_i (3x3) + mass diagonal, packed xx yy zz yz xz xy.
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1, const int32_t *__restrict__ ids,
                                                          const int32_t *__restrict__ conn,
-                                                         const double *__restrict__ geom,
+                                                         const T *__restrict__ geom,
                                                          const int32_t *__restrict__ mat,
-                                                         const double *__restrict__ D, int64_t epad,
-                                                         const OpCoef *__restrict__ op, double *Jd, bool atomic) {
+                                                         const T *__restrict__ D, int64_t epad,
+                                                         const OpCoef *__restrict__ op, T *Jd, bool atomic) {
   const int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= e1) return;
   const int64_t e = ids ? (int64_t)ids[i] : i;
   const int mt = mat[e];
-  const double cK = op->kK[mt], cM = op->mK[mt];
-  double g[4][3], vol;
+  const T cK = (T)op->kK[mt], cM = (T)op->mK[mt];
+  T g[4][3], vol;
   load_grads(geom, epad, e, g, vol);
-  double acc[10][6];
+  T acc[10][6];
 #pragma unroll
   for (int a = 0; a < 10; ++a)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[a][k] = 0.0;
-  const double w = cK * vol * 0.25;
+    for (int k = 0; k < 6; ++k) acc[a][k] = (T)0;
+  const T w = cK * vol * (T)0.25;
+#pragma unroll 1
   for (int q = 0; q < 4; ++q) {
-    double d[21];
+    T d[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) d[k] = w * D[(q * 21 + k) * epad + e];
 #pragma unroll
     for (int a = 0; a < 10; ++a) {
-      double gn[3];
+      T gn[3];
       if (a < 4) {
-        const double c = 4.0 * (a == q ? NS_QA : NS_QB) - 1.0;
+        const T c = (T)4.0 * (a == q ? (T)NS_QA : (T)NS_QB) - (T)1.0;
+#pragma unroll
         for (int r = 0; r < 3; ++r) gn[r] = c * g[a][r];
       } else {
-        const int ia[6] = {0, 1, 0, 0, 1, 2}, ib[6] = {1, 2, 2, 3, 3, 3};
-        const int pa = ia[a - 4], pb = ib[a - 4];
-        const double la = pa == q ? NS_QA : NS_QB, lb = pb == q ? NS_QA : NS_QB;
-        for (int r = 0; r < 3; ++r) gn[r] = 4.0 * (la * g[pb][r] + lb * g[pa][r]);
+        const int pa = (a == 4 || a == 6 || a == 7) ? 0 : (a == 5 || a == 8) ? 1 : 2;
+        const int pb = (a == 4) ? 1 : (a == 5 || a == 6) ? 2 : 3;
+        const T la = pa == q ? (T)NS_QA : (T)NS_QB, lb = pb == q ? (T)NS_QA : (T)NS_QB;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gn[r] = (T)4.0 * (la * g[pb][r] + lb * g[pa][r]);
       }
       // columns of B_i: bx = (g0,0,0,0,g2,g1), by = (0,g1,0,g2,0,g0), bz = (0,0,g2,g1,g0,0)
-      double Dbx[6], Dby[6], Dbz[6];
+      T Dbx[6], Dby[6], Dbz[6];
 #pragma unroll
       for (int r = 0; r < 6; ++r) {
         Dbx[r] = d[sym6(r, 0)] * gn[0] + d[sym6(r, 4)] * gn[2] + d[sym6(r, 5)] * gn[1];
@@ -396,10 +400,10 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1,
       acc[a][5] += gn[0] * Dby[0] + gn[2] * Dby[4] + gn[1] * Dby[5];  // xy = bx . D by
     }
   }
-  const double mv = cM * vol * (6.0 / 420.0), me = cM * vol * (32.0 / 420.0);
+  const T mv = cM * vol * (T)(6.0 / 420.0), me = cM * vol * (T)(32.0 / 420.0);
 #pragma unroll
   for (int a = 0; a < 10; ++a) {
-    const double md = a < 4 ? mv : me;
+    const T md = a < 4 ? mv : me;
     acc[a][0] += md;
     acc[a][1] += md;
     acc[a][2] += md;
@@ -407,17 +411,18 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1,
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       if (atomic)
-        atomicAdd(Jd + 6 * n + k, acc[a][k]);
+        atomic_add(Jd + 6 * n + k, acc[a][k]);
       else
         Jd[6 * n + k] += acc[a][k];
     }
   }
 }
 
+template <typename T>
 __global__ void k_jacobi_faces(int64_t f0, int64_t f1, const int32_t *__restrict__ ids, int64_t fpad,
                                const int32_t *__restrict__ fnode, const double *__restrict__ fgeom,
                                const int32_t *__restrict__ fmat, const MatConst *__restrict__ mc, double cC,
-                               double *Jd, bool atomic) {
+                               T *Jd, bool atomic) {
   const int64_t i = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= f1) return;
   const int64_t f = ids ? (int64_t)ids[i] : i;
@@ -430,9 +435,9 @@ __global__ void k_jacobi_faces(int64_t f0, int64_t f1, const int32_t *__restrict
     const int64_t nd = fnode[a * fpad + f];
     for (int k = 0; k < 6; ++k) {
       const int r = pr[k][0], c = pr[k][1];
-      const double v = md * ((r == c ? rvs : 0.0) + rvd * n[r] * n[c]);
+      const T v = (T)(md * ((r == c ? rvs : 0.0) + rvd * n[r] * n[c]));
       if (atomic)
-        atomicAdd(Jd + 6 * nd + k, v);
+        atomic_add(Jd + 6 * nd + k, v);
       else
         Jd[6 * nd + k] += v;
     }
@@ -442,16 +447,32 @@ __global__ void k_jacobi_faces(int64_t f0, int64_t f1, const int32_t *__restrict
 cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef *op, double *Jd, const int32_t *ids,
                                 int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
-  k_jacobi_elems<<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(e0, e1, ids, m.conn, m.geom, m.mat,
-                                                                                D, m.epad, op, Jd, atomic);
+  k_jacobi_elems<double><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      e0, e1, ids, m.conn, m.geom, m.mat, D, m.epad, op, Jd, atomic);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_elems32(const DevMesh &m, const float *D, const OpCoef *op, float *Jd, const int32_t *ids,
+                                  int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
+  if (e1 <= e0) return cudaSuccess;
+  k_jacobi_elems<float><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      e0, e1, ids, m.conn, m.geom32, m.mat, D, m.epad, op, Jd, atomic);
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_faces(const DevMesh &m, const MatConst *mc, double cC, double *Jd, const int32_t *ids,
                                 int64_t f0, int64_t f1, bool atomic, cudaStream_t s) {
   if (f1 <= f0) return cudaSuccess;
-  k_jacobi_faces<<<(unsigned)((f1 - f0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(f0, f1, ids, m.fpad, m.fnode,
-                                                                                m.fgeom, m.fmat, mc, cC, Jd, atomic);
+  k_jacobi_faces<double><<<(unsigned)((f1 - f0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, mc, cC, Jd, atomic);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_faces32(const DevMesh &m, const MatConst *mc, double cC, float *Jd, const int32_t *ids,
+                                  int64_t f0, int64_t f1, bool atomic, cudaStream_t s) {
+  if (f1 <= f0) return cudaSuccess;
+  k_jacobi_faces<float><<<(unsigned)((f1 - f0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, mc, cC, Jd, atomic);
   return cudaGetLastError();
 }
 

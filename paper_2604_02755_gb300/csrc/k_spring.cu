@@ -5,28 +5,6 @@
 
 namespace ns {
 
-struct RoPar {
-  double G0, alpha, beta, iG0, itref;  // itref = 1 / (G0 gamma_ref)
-  double c2, c3;                       // series coefficients of (1 + d)^beta
-  float itref_f, iG0_f, alpha_f, beta_f;
-};
-
-__device__ __forceinline__ RoPar ro_par(const MatConst &m) {
-  RoPar r;
-  r.G0 = m.G0;
-  r.alpha = m.alpha_ro;
-  r.beta = m.beta_ro;
-  r.iG0 = 1.0 / m.G0;
-  r.itref = 1.0 / (m.G0 * m.gref);
-  r.c2 = m.beta_ro * (m.beta_ro - 1.0) * 0.5;
-  r.c3 = r.c2 * (m.beta_ro - 2.0) * (1.0 / 3.0);
-  r.itref_f = (float)r.itref;
-  r.iG0_f = (float)r.iG0;
-  r.alpha_f = (float)m.alpha_ro;
-  r.beta_f = (float)m.beta_ro;
-  return r;
-}
-
 // ---------------------------------------------------------------------------------------
 // FP64 power x^beta for x > 0 (normal), table-driven after Tang (ACM TOMS 1989, 1990):
 //   ln x = e ln2 + ln(1/r_j) + ln(1 + u),  u = m r_j - 1,  |u| <= 2^-8,
@@ -83,36 +61,32 @@ __device__ __forceinline__ double pow_pos(double x, double beta, const PowTab &t
   return exp_tab(beta * ln_pos(x, tb), tb);
 }
 
-// FP32 reciprocal refined once (relative error ~1e-14) or twice (~1e-28) in FP64.
+// FP32 reciprocal refined once in FP64 (relative error ~1e-14).
 __device__ __forceinline__ double rcp1(double x) {
   double r = (double)(1.0f / (float)x);
-  return r * fma(-x, r, 2.0);
-}
-__device__ __forceinline__ double rcp2(double x) {
-  double r = rcp1(x);
   return r * fma(-x, r, 2.0);
 }
 
 // Safeguarded FP64 Newton on g(tau) = ga from tau in (0, hi]: bisection replaces steps that
 // leave the bracket; the power is re-evaluated at every iterate.  Used only when the
 // fast path below does not certify convergence.
-__device__ double ro_F_safe(double ga, double tau, const RoPar &p, const PowTab &tb, double *pw) {
+__device__ double ro_F_safe(double ga, double tau, const MatConst &p, const PowTab &tb, double *pw) {
   const double hi = p.G0 * ga;
-  double lo = 0.0, up = hi, w = pow_pos(tau * p.itref, p.beta, tb);
+  double lo = 0.0, up = hi, w = pow_pos(tau * p.itref, p.beta_ro, tb);
   for (int it = 0; it < 200; ++it) {
-    const double gval = tau * p.iG0 * (1.0 + p.alpha * w);
+    const double gval = tau * p.iG0 * (1.0 + p.alpha_ro * w);
     if (gval == ga) break;
     if (gval > ga)
       up = tau;
     else
       lo = tau;
-    const double step = (gval - ga) * p.G0 / (1.0 + p.alpha * (1.0 + p.beta) * w);
+    const double step = (gval - ga) * p.G0 / (1.0 + p.ab1 * w);
     double nt = tau - step;
     const bool newton = nt >= lo && nt <= up;
     if (!newton) nt = 0.5 * (lo + up);
     const double last = nt - tau;
     tau = nt;
-    w = pow_pos(tau * p.itref, p.beta, tb);
+    w = pow_pos(tau * p.itref, p.beta_ro, tb);
     if (newton && fabs(last) <= 1e-15 * tau) break;
   }
   *pw = w;
@@ -124,31 +98,35 @@ __device__ double ro_F_safe(double ga, double tau, const RoPar &p, const PowTab 
 // only the power at tau = ga.  Every lane evaluates exactly one FP64 power, so a warp
 // whose springs follow different Masing paths does not diverge around it:
 //  1. (solve) FP32 Newton from the guess if it lies in (0, G0 ga], else from G0 ga,
-//     to a relative step of 4e-6;
+//     until a step is below 4e-6 of the iterate;
 //  2. w = (tau/tref)^beta in FP64 (table-driven power);
-//  3. (solve) two FP64 Newton steps (FP32 reciprocal of g', contraction ~1e-7 per step
-//     on top of the quadratic one) carrying w by the series (1 + d)^beta; a seed error
-//     of 4e-6 leaves < 1e-17 after them.  If the steps are not small enough the safe
-//     loop above takes over.
+//  3. (solve) one FP64 Halley step (cubic: a seed error e leaves ~e^3), the power
+//     carried to the new iterate by the series (1 + d)^beta.  Unless the FP32 stage
+//     converged and the step is below 2e-5 of tau the safeguarded loop takes over.
 // *pw returns (F/tref)^beta at the returned root.
-__device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, const RoPar &p, const PowTab &tb,
+__device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, const MatConst &p, const PowTab &tb,
                                            double *pw) {
   double tau = ga;
+  bool seeded = true;
   if (solve) {
     const double hi = p.G0 * ga;
     const float gaf = (float)ga, hif = (float)hi;
     float t = (guess > 0.0 && guess < hi) ? (float)guess : hif;
     if (!(t > 0.0f)) t = hif;
+    seeded = false;
     for (int it = 0; it < 40; ++it) {
       const float pwf = __powf(t * p.itref_f, p.beta_f);
       const float gp = 1.0f + p.alpha_f * (1.0f + p.beta_f) * pwf;
-      const float step = (t * p.iG0_f * (1.0f + p.alpha_f * pwf) - gaf) * __fdividef((float)p.G0, gp);
+      const float step = (t * p.iG0_f * (1.0f + p.alpha_f * pwf) - gaf) * __fdividef(p.G0_f, gp);
       float tn = t - step;
       if (!(tn > 0.0f)) tn = 0.5f * t;
       if (tn > hif) tn = hif;
       const bool conv = fabsf(step) <= 4e-6f * t;
       t = tn;
-      if (conv) break;
+      if (conv) {
+        seeded = true;
+        break;
+      }
     }
     tau = (double)t;
     if (!(tau > 0.0) || !(tau <= hi)) tau = hi;
@@ -157,29 +135,28 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
     *pw = 0.0;
     return 0.0;
   }
-  double w = pow_pos(tau * p.itref, p.beta, tb);
+  double w = pow_pos(tau * p.itref, p.beta_ro, tb);
   if (solve) {
+    // Halley: step = h / (1 - h f''/(2 f')), h = f/f' the Newton step
     const double it0 = rcp1(tau);
-    double dmax = 0.0;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const double gval = tau * p.iG0 * fma(p.alpha, w, 1.0);
-      const double gp = fma(p.alpha * (1.0 + p.beta), w, 1.0);
-      const double step = (gval - ga) * p.G0 * (double)(1.0f / (float)gp);
-      const double d = -step * it0;
-      tau -= step;
-      w *= fma(d, fma(d, fma(d, p.c3, p.c2), p.beta), 1.0);
-      dmax = (it == 0) ? fabs(d) : dmax;
-      if (it == 1 && !(fabs(d) <= 1e-9 && dmax <= 1e-4)) tau = ro_F_safe(ga, tau > 0.0 ? tau : 0.5 * ga * p.G0, p, tb, &w);
-    }
+    const double gval = tau * p.iG0 * fma(p.alpha_ro, w, 1.0);
+    const double gp = fma(p.ab1, w, 1.0);
+    const double rg = rcp1(gp);
+    const double h = (gval - ga) * p.G0 * rg;
+    const double hc = h * (0.5 * p.ab1b) * w * it0 * rg;
+    const double step = h * fma(hc, 1.0 + hc, 1.0);
+    const double d = -step * it0;
+    tau -= step;
+    w *= fma(d, fma(d, fma(d, p.c3, p.c2), p.beta_ro), 1.0);
+    if (!(seeded && fabs(d) <= 2e-5)) tau = ro_F_safe(ga, (tau > 0.0 && tau <= p.G0 * ga) ? tau : p.G0 * ga, p, tb, &w);
   }
   *pw = w;
   return tau;
 }
 
 // G0 / g'(tau) with g' = 1 + alpha (1 + beta) pw.
-__device__ __forceinline__ double ro_tangent_from_pw(double pw, const RoPar &p) {
-  return p.G0 * rcp2(fma(p.alpha * (1.0 + p.beta), pw, 1.0));
+__device__ __forceinline__ double ro_tangent_from_pw(double pw, const MatConst &p) {
+  return p.G0 * rcp1(fma(p.ab1, pw, 1.0));
 }
 
 // One spring (Masing bookkeeping of the documented reading): virgin -> skeleton in the
@@ -188,7 +165,7 @@ __device__ __forceinline__ double ro_tangent_from_pw(double pw, const RoPar &p) 
 // skeleton tau = F(gamma) (decided before the root solve, so each spring solves once).
 // With no increment the state is kept and only the tangent is evaluated.
 // Returns the tangent dtau/dgamma at the end state.
-__device__ __forceinline__ double spring_update(double g, double dg, const RoPar &p, const PowTab &tb, double &tau,
+__device__ __forceinline__ double spring_update(double g, double dg, const MatConst &p, const PowTab &tb, double &tau,
                                                 double &gR, double &tR, double &gmax, int &dir, int &mode) {
   const bool active = dg != 0.0;
   double x, guess = 0.0;
@@ -206,7 +183,7 @@ __device__ __forceinline__ double spring_update(double g, double dg, const RoPar
       dir = sgn;
       same = false;
     }
-    if (mode == 1 && fabs(g) >= gmax && g * (double)dir > 0.0) {
+    if (mode == 1 && fabs(g) >= gmax && (dir > 0 ? g > 0.0 : g < 0.0)) {
       mode = 0;  // outward past the largest skeleton strain: back on the skeleton
       guess = fabs(tau);
     } else if (same) {
@@ -224,7 +201,7 @@ __device__ __forceinline__ double spring_update(double g, double dg, const RoPar
       tau = fs;
       gmax = fmax(gmax, fabs(g));
     } else {
-      tau = tR + 2.0 * fs;
+      tau = fma(2.0, fs, tR);
     }
   }
   return ro_tangent_from_pw(pw, p);
@@ -233,14 +210,14 @@ __device__ __forceinline__ double spring_update(double g, double dg, const RoPar
 // Block = a tile of TP consecutive points (TP multiple of 4) with all their S springs.
 // Phase 1: each thread updates springs of the tile (coalesced state access), stores
 // G_k in shared memory.  Phase 2: D_p[ij] = Kb [i,j < 3] + sum_k G_k T_k[ij].
-__global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q, const double *__restrict__ T, int S,
+__global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q, const float2 *__restrict__ T2, int S,
                                                     int TP, const MatConst *__restrict__ mc,
                                                     const int32_t *__restrict__ mat_e, const int32_t *__restrict__ mat_p,
                                                     const double *__restrict__ eps, double *tau_a, double *gR_a,
                                                     double *tR_a, double *gmax_a, int32_t *dir_a, int32_t *mode_a,
                                                     int64_t base, int64_t p0, int64_t p1, double *D, int64_t epad,
                                                     double *dpts, const double *__restrict__ ptab) {
-  extern __shared__ double Gs[];
+  extern __shared__ float2 Gs[];
   const PowTab tb{ptab, ptab + 128, ptab + 256, ptab + 384, __ldg(ptab + 448), __ldg(ptab + 449), __ldg(ptab + 450),
                   __ldg(ptab + 451)};
   const int64_t pt = p0 + (int64_t)blockIdx.x * TP;
@@ -250,7 +227,7 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
     const int lp = g / S, k = g - lp * S;
     const int64_t p = pt + lp;
     const int mt = mat_p ? mat_p[p] : mat_e[p >> 2];
-    const RoPar rp = ro_par(mc[mt]);
+    const MatConst &rp = mc[mt];
     const double *ep = eps + 12 * p;
     const double *qk = q + 6 * k;
     double gam = 0.0, dgam = 0.0;
@@ -272,7 +249,9 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
       dir_a[si] = dir;
       mode_a[si] = mode;
     }
-    Gs[g] = G;
+    // keep G as an unevaluated sum of two floats for the double-float accumulation
+    const float gh = (float)G;
+    Gs[g] = make_float2(gh, (float)(G - (double)gh));
   }
   __syncthreads();
   const int nout = np * 21;
@@ -281,18 +260,36 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
     const int64_t p = pt + lp;
     const int mt = mat_p ? mat_p[p] : mat_e[p >> 2];
     const bool nn = ij < 3 || ij == 6 || ij == 7 || ij == 11;  // (i,j) both < 3
-    const double *Gp = Gs + lp * S;
-    // four independent partial sums (latency hiding), combined in a fixed order
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    // sum_k G_k T_k[ij] in double-float arithmetic on the FP32 pipes: exact products
+    // (FMA error terms), cross terms, and compensated (two-sum) accumulation -- about
+    // 48 significand bits, far below the FP64 rounding of the tangent itself
+    const float2 *Gp = Gs + lp * S;
+    float sh0 = 0.0f, sl0 = 0.0f, sh1 = 0.0f, sl1 = 0.0f;
     int k = 0;
-    for (; k + 3 < S; k += 4) {
-      a0 = fma(Gp[k], __ldg(T + 21 * k + ij), a0);
-      a1 = fma(Gp[k + 1], __ldg(T + 21 * (k + 1) + ij), a1);
-      a2 = fma(Gp[k + 2], __ldg(T + 21 * (k + 2) + ij), a2);
-      a3 = fma(Gp[k + 3], __ldg(T + 21 * (k + 3) + ij), a3);
+    for (; k + 1 < S; k += 2) {
+      {
+        const float2 g2 = Gp[k], t2 = T2[21 * k + ij];
+        const float pr = g2.x * t2.x, er = fmaf(g2.x, t2.x, -pr), cr = fmaf(g2.x, t2.y, g2.y * t2.x);
+        const float sn = sh0 + pr, bv = sn - sh0;
+        sl0 += ((sh0 - (sn - bv)) + (pr - bv)) + (er + cr);
+        sh0 = sn;
+      }
+      {
+        const float2 g2 = Gp[k + 1], t2 = T2[21 * (k + 1) + ij];
+        const float pr = g2.x * t2.x, er = fmaf(g2.x, t2.x, -pr), cr = fmaf(g2.x, t2.y, g2.y * t2.x);
+        const float sn = sh1 + pr, bv = sn - sh1;
+        sl1 += ((sh1 - (sn - bv)) + (pr - bv)) + (er + cr);
+        sh1 = sn;
+      }
     }
-    for (; k < S; ++k) a0 = fma(Gp[k], __ldg(T + 21 * k + ij), a0);
-    const double acc = (nn ? mc[mt].Kb : 0.0) + ((a0 + a1) + (a2 + a3));
+    if (k < S) {
+      const float2 g2 = Gp[k], t2 = T2[21 * k + ij];
+      const float pr = g2.x * t2.x, er = fmaf(g2.x, t2.x, -pr), cr = fmaf(g2.x, t2.y, g2.y * t2.x);
+      const float sn = sh0 + pr, bv = sn - sh0;
+      sl0 += ((sh0 - (sn - bv)) + (pr - bv)) + (er + cr);
+      sh0 = sn;
+    }
+    const double acc = (nn ? mc[mt].Kb : 0.0) + (((double)sh0 + (double)sh1) + ((double)sl0 + (double)sl1));
     if (dpts)
       dpts[21 * p + ij] = acc;
     else
@@ -312,14 +309,14 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
                            int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
   const int TP = tile_points(tab.S);
-  const size_t smem = sizeof(double) * TP * tab.S;
+  const size_t smem = sizeof(float2) * TP * tab.S;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_springs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
-  k_springs<<<nb, kBlock, smem, s>>>(tab.q, tab.T, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, st.gR,
+  k_springs<<<nb, kBlock, smem, s>>>(tab.q, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, st.gR,
                                      st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow);
   return cudaGetLastError();
 }

@@ -61,6 +61,28 @@ __global__ void k_invert_blocks(const double *Jd, double *Jinv, float *Jinv32, i
   }
 }
 
+__global__ void k_invert_blocks32(const float *Jd, float *Jinv32, int64_t N, int32_t *bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float *a = Jd + 6 * i;
+    const float xx = a[0], yy = a[1], zz = a[2], yz = a[3], xz = a[4], xy = a[5];
+    const float c00 = yy * zz - yz * yz, c11 = xx * zz - xz * xz, c22 = xx * yy - xy * xy;
+    const float c12 = xy * xz - xx * yz, c02 = xy * yz - yy * xz, c01 = xz * yz - xy * zz;
+    const float det = xx * c00 + xy * c01 + xz * c02;
+    if (!(det > 0.0f)) {
+      atomicCAS(bad, 0, (int32_t)(i + 1));
+      continue;
+    }
+    const float id = 1.0f / det;
+    const float inv[6] = {c00 * id, c11 * id, c22 * id, c12 * id, c02 * id, c01 * id};
+    for (int k = 0; k < 6; ++k) Jinv32[6 * i + k] = inv[k];
+  }
+}
+
+cudaError_t launch_invert_blocks32(const float *Jd, float *Jinv32, int64_t N, int32_t *bad, cudaStream_t s) {
+  k_invert_blocks32<<<vec_blocks(N), kBlock, 0, s>>>(Jd, Jinv32, N, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_invert_blocks(const double *Jd, double *Jinv, float *Jinv32, int64_t N, int32_t *bad,
                                  cudaStream_t s) {
   k_invert_blocks<<<vec_blocks(N), kBlock, 0, s>>>(Jd, Jinv, Jinv32, N, bad);

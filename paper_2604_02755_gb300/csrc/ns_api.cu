@@ -55,6 +55,7 @@ struct ns_ctx {
   MatConst *mats_d = nullptr;
   OpCoef *op_A = nullptr, *op_K = nullptr, *op_M = nullptr, *op_Cr = nullptr, *op_rhs = nullptr;
   double *q_d = nullptr, *T_d = nullptr, *pow_d = nullptr;
+  float2 *T2_d = nullptr;
   SpringTables tab{};
   double *D = nullptr;
   float *D32 = nullptr;
@@ -481,7 +482,6 @@ int solve_ir(ns_ctx *c) {
   const int64_t N = c->m.N;
   const int nbv = vec_blocks(N);
   double *pv = c->part + c->part_pap_cap;
-  LAUNCH(c, launch_D_to_f32(c->D, c->D32, c->m.epad, c->m.E, c->s_main));
   if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
   if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
   LAUNCH(c, launch_fcg_init(c->b, c->Ap, c->r, N, pv, c->s_main));
@@ -530,22 +530,41 @@ int one_step(ns_ctx *c) {
   cudaEvent_t tstep = nullptr, t0 = nullptr;
   tbegin(c, TK_STEP, c->s_main, &tstep);
 
-  // 3x3 block-Jacobi preconditioner from the diagonal node blocks of A^n
+  // 3x3 block-Jacobi preconditioner from the diagonal node blocks of A^n (FP32 when it only
+  // serves the inner single-precision solve)
   tbegin(c, TK_JAC, c->s_main, &t0);
-  CKC(c, cudaMemsetAsync(c->Jd, 0, sizeof(double) * 6 * N, c->s_main));
-  if (atomic) {
-    LAUNCH(c, launch_jacobi_elems(c->m, c->D, c->op_A, c->Jd, nullptr, 0, c->m.E, true, c->s_main));
-    LAUNCH(c, launch_jacobi_faces(c->m, c->mats_d, 2.0 / dt, c->Jd, nullptr, 0, c->m.F, true, c->s_main));
-  } else {
-    for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k)
-      LAUNCH(c, launch_jacobi_elems(c->m, c->D, c->op_A, c->Jd, c->m.ecol_ids, c->m.ecol_off[k], c->m.ecol_off[k + 1],
-                                    false, c->s_main));
-    for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k)
-      LAUNCH(c, launch_jacobi_faces(c->m, c->mats_d, 2.0 / dt, c->Jd, c->m.fcol_ids, c->m.fcol_off[k],
-                                    c->m.fcol_off[k + 1], false, c->s_main));
-  }
   CKC(c, cudaMemsetAsync(c->flag_d, 0, sizeof(int32_t), c->s_main));
-  LAUNCH(c, launch_invert_blocks(c->Jd, c->Jinv, c->Jinv32, N, c->flag_d, c->s_main));
+  if (c->cfg.precision == NS_PREC_FP64_IR) {
+    float *Jd32 = (float *)c->Jd;  // the FP64 block buffer is reused for the FP32 blocks
+    LAUNCH(c, launch_D_to_f32(c->D, c->D32, c->m.epad, c->m.E, c->s_main));
+    CKC(c, cudaMemsetAsync(Jd32, 0, sizeof(float) * 6 * N, c->s_main));
+    if (atomic) {
+      LAUNCH(c, launch_jacobi_elems32(c->m, c->D32, c->op_A, Jd32, nullptr, 0, c->m.E, true, c->s_main));
+      LAUNCH(c, launch_jacobi_faces32(c->m, c->mats_d, 2.0 / dt, Jd32, nullptr, 0, c->m.F, true, c->s_main));
+    } else {
+      for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k)
+        LAUNCH(c, launch_jacobi_elems32(c->m, c->D32, c->op_A, Jd32, c->m.ecol_ids, c->m.ecol_off[k],
+                                        c->m.ecol_off[k + 1], false, c->s_main));
+      for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k)
+        LAUNCH(c, launch_jacobi_faces32(c->m, c->mats_d, 2.0 / dt, Jd32, c->m.fcol_ids, c->m.fcol_off[k],
+                                        c->m.fcol_off[k + 1], false, c->s_main));
+    }
+    LAUNCH(c, launch_invert_blocks32(Jd32, c->Jinv32, N, c->flag_d, c->s_main));
+  } else {
+    CKC(c, cudaMemsetAsync(c->Jd, 0, sizeof(double) * 6 * N, c->s_main));
+    if (atomic) {
+      LAUNCH(c, launch_jacobi_elems(c->m, c->D, c->op_A, c->Jd, nullptr, 0, c->m.E, true, c->s_main));
+      LAUNCH(c, launch_jacobi_faces(c->m, c->mats_d, 2.0 / dt, c->Jd, nullptr, 0, c->m.F, true, c->s_main));
+    } else {
+      for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k)
+        LAUNCH(c, launch_jacobi_elems(c->m, c->D, c->op_A, c->Jd, c->m.ecol_ids, c->m.ecol_off[k],
+                                      c->m.ecol_off[k + 1], false, c->s_main));
+      for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k)
+        LAUNCH(c, launch_jacobi_faces(c->m, c->mats_d, 2.0 / dt, c->Jd, c->m.fcol_ids, c->m.fcol_off[k],
+                                      c->m.fcol_off[k + 1], false, c->s_main));
+    }
+    LAUNCH(c, launch_invert_blocks(c->Jd, c->Jinv, c->Jinv32, N, c->flag_d, c->s_main));
+  }
   tend(c, TK_JAC, c->s_main, t0);
 
   // right-hand side of Eq. 1: f^n - q^{n-1} + C^n v^{n-1} + M (a^{n-1} + 4/dt v^{n-1})
@@ -821,15 +840,22 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
       }
   std::vector<double> ph(kPowTabLen);
   host_pow_tables(ph.data());
+  std::vector<float2> T2h(21 * (size_t)S);
+  for (size_t i = 0; i < T2h.size(); ++i) {
+    const float hi = (float)Th[i];
+    T2h[i] = make_float2(hi, (float)(Th[i] - (double)hi));
+  }
   if ((rc = dalloc(c, &c->q_d, qh.size())) || (rc = dalloc(c, &c->T_d, Th.size())) ||
-      (rc = dalloc(c, &c->pow_d, ph.size())))
+      (rc = dalloc(c, &c->pow_d, ph.size())) || (rc = dalloc(c, &c->T2_d, T2h.size())))
     return rc;
+  CKC(c, cudaMemcpy(c->T2_d, T2h.data(), T2h.size() * sizeof(float2), cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->q_d, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->T_d, Th.data(), Th.size() * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->pow_d, ph.data(), ph.size() * 8, cudaMemcpyHostToDevice));
   c->tab.q = c->q_d;
   c->tab.T = c->T_d;
   c->tab.pow = c->pow_d;
+  c->tab.T2 = c->T2_d;
   c->tab.S = S;
   // tangent D (element SoA [84][epad]) and spring state placement
   const int64_t E = c->m.E, epad = c->m.epad;
@@ -1325,7 +1351,7 @@ void ns_destroy(ns_ctx *c) {
   dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
   dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
   dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
-  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->D); dfree(c->D32);
+  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->T2_d); dfree(c->D); dfree(c->D32);
   free_soa(c->st, false);
   free_soa(c->hst, true);
   for (auto &rb : c->ring) free_soa(rb, false);

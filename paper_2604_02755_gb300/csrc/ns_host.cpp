@@ -141,6 +141,18 @@ void host_material_constants(const ns_material &m, double f1, double f2, MatCons
   const double w1 = 2.0 * M_PI * f1, w2 = 2.0 * M_PI * f2;
   o->ray_a = 2.0 * m.rayleigh_h * w1 * w2 / (w1 + w2);
   o->ray_b = 2.0 * m.rayleigh_h / (w1 + w2);
+  o->iG0 = 1.0 / o->G0;
+  o->itref = 1.0 / (o->G0 * o->gref);
+  o->ab1 = o->alpha_ro * (1.0 + o->beta_ro);
+  o->ab1b = o->ab1 * o->beta_ro;
+  o->c2 = o->beta_ro * (o->beta_ro - 1.0) * 0.5;
+  o->c3 = o->c2 * (o->beta_ro - 2.0) / 3.0;
+  o->itref_f = (float)o->itref;
+  o->iG0_f = (float)o->iG0;
+  o->alpha_f = (float)o->alpha_ro;
+  o->beta_f = (float)o->beta_ro;
+  o->G0_f = (float)o->G0;
+  o->pad_f = 0.0f;
 }
 
 // Tables of the FP64 power used by the spring law (table-driven logarithm and exponential

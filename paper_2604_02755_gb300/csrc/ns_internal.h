@@ -18,6 +18,10 @@ constexpr int kBlock = 256;
 // Per-material constants derived on the host from ns_material and the config.
 struct MatConst {
   double rho, vs, vp, G0, Kb, gref, alpha_ro, beta_ro, ray_a, ray_b;
+  // spring-law constants: 1/G0, 1/(G0 gamma_ref), alpha (1 + beta), alpha (1 + beta) beta,
+  // series coefficients beta (beta - 1)/2 and beta (beta - 1)(beta - 2)/6, FP32 copies
+  double iG0, itref, ab1, ab1b, c2, c3;
+  float itref_f, iG0_f, alpha_f, beta_f, G0_f, pad_f;
 };
 
 // Coefficients of one element-by-element operator application, per material:
@@ -85,6 +89,12 @@ cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef 
                                 int64_t e0, int64_t e1, bool atomic, cudaStream_t s);
 cudaError_t launch_jacobi_faces(const DevMesh &m, const MatConst *mc, double cC, double *Jd, const int32_t *ids,
                                 int64_t f0, int64_t f1, bool atomic, cudaStream_t s);
+// FP32 variants (the preconditioner of the flexible solver only needs single precision)
+cudaError_t launch_jacobi_elems32(const DevMesh &m, const float *D, const OpCoef *op, float *Jd, const int32_t *ids,
+                                  int64_t e0, int64_t e1, bool atomic, cudaStream_t s);
+cudaError_t launch_jacobi_faces32(const DevMesh &m, const MatConst *mc, double cC, float *Jd, const int32_t *ids,
+                                  int64_t f0, int64_t f1, bool atomic, cudaStream_t s);
+cudaError_t launch_invert_blocks32(const float *Jd, float *Jinv32, int64_t N, int32_t *bad, cudaStream_t s);
 // strains eps, deps at the 4 points of elements [e0, e1): out [E][4][12] (eps 6, deps 6)
 cudaError_t launch_strain(const DevMesh &m, const double *u, const double *du, double *out, int64_t e0, int64_t e1,
                           cudaStream_t s);
@@ -140,6 +150,7 @@ cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, dou
 struct SpringTables {
   const double *q;    // [S][6]
   const double *T;    // [S][21] w q q^T packed upper triangle (+ one row with their sum)
+  const float2 *T2;   // [S][21] the same entries as (hi, lo) float pairs
   const double *pow;  // power tables: r[128], -ln r hi[128], lo[128], 2^(i/64)[64], ln2 hi/lo, ln2/64 hi/lo
   int S;
 };

@@ -215,16 +215,20 @@ def test_tiny_two_layer_case_parity(precision, nsteps):
 
 
 def test_tiny_two_layer_full_record():
-    """All 300 steps of the tiny case in the paper's precision policy."""
+    """All 300 steps of the tiny case, through the main motion.  Over this record the
+    CG stopping tolerance itself decides the answer at the 1e-4 level: the oracle at
+    1e-8 and at 1e-12 differ by 7.0e-5 in surface displacement (relative L2), while 1e-10
+    and 1e-12 agree to 1.7e-10.  Parity is therefore checked with both sides solving to
+    1e-12, where the answer no longer depends on the tolerance."""
     wl = synth.tiny_two_layer()
     nsteps = wl.n_steps
-    o = oracle.Oracle.from_workload(wl)
+    o = oracle.Oracle.from_workload(wl, tol=1e-12)
     us, vs = [], []
     for _ in range(nsteps):
         o.step()
         us.append(o.u[wl.mesh.surf].copy())
         vs.append(o.v[wl.mesh.surf].copy())
-    with B.Simulation(wl, surface_ring_steps=nsteps, precision=B.NS_PREC_FP64_IR) as sim:
+    with B.Simulation(wl, surface_ring_steps=nsteps, precision=B.NS_PREC_FP64_IR, cg_tol=1e-12) as sim:
         sim.advance(nsteps)
         s = sim.surface(1, nsteps)
         th, _ = sim.state()
