@@ -179,6 +179,26 @@ int ns_apply_operator(ns_ctx *ctx, int32_t op, const double *x, double *y);
 int ns_spring_points(ns_ctx *ctx, int64_t npts, const int32_t *mat, const double *eps, const double *deps,
                      void *theta, double *D);
 
+/* Allocation-free ns_spring_points (no counterpart in the paper).  For callers that
+ * must not allocate device memory at the point of the call -- e.g. a host application
+ * that commits a fixed device-memory budget at start-up and forbids later allocation, or
+ * threads that must not take the CUDA allocator's locks -- the device staging buffers
+ * live in one file-scope device array of 8 MiB that the library reserves on every GPU
+ * that loads it (kept until the process exits).  Same arguments, layouts and results
+ * as ns_spring_points; no cudaMalloc/cudaFree or other allocating call is made.
+ *  - npts may be at most ns_spring_points_noalloc_capacity(n_springs) (more points:
+ *    NS_ERR_INVALID_ARG with a message giving the limit).
+ *  - The first call on a device resolves the array's device address (once per device,
+ *    with that device current); make that first call before any stream capture.
+ *  - All calls share the array; each call writes every byte it reads, so nothing of a
+ *    previous call is reused, but calls that overlap on the GPU (several host threads or
+ *    contexts on one device) race on it and must be serialised by the caller. */
+int ns_spring_points_noalloc(ns_ctx *ctx, int64_t npts, const int32_t *mat, const double *eps, const double *deps,
+                             void *theta, double *D);
+
+/* Largest npts ns_spring_points_noalloc accepts at S springs per point. */
+int64_t ns_spring_points_noalloc_capacity(int32_t S);
+
 int ns_get_stats(ns_ctx *ctx, ns_stats *st);
 int ns_reset_stats(ns_ctx *ctx);
 

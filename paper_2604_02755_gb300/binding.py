@@ -64,7 +64,8 @@ EXPORTED = ["ns_config_default", "ns_create", "ns_upload_mesh", "ns_set_material
             "ns_set_ground_motion", "ns_advance", "ns_read_surface", "ns_read_state", "ns_write_state",
             "ns_read_nodal", "ns_write_nodal", "ns_apply_operator", "ns_spring_points", "ns_get_stats",
             "ns_reset_stats", "ns_checkpoint_size", "ns_checkpoint", "ns_restore", "ns_destroy", "ns_last_error",
-            "ns_spring_directions", "ns_colour_elements", "ns_state_bytes"]
+            "ns_spring_directions", "ns_colour_elements", "ns_state_bytes", "ns_spring_points_noalloc",
+            "ns_spring_points_noalloc_capacity"]
 
 _lib = None
 
@@ -103,6 +104,8 @@ def lib():
             "ns_spring_directions": ([i32, vp, C.POINTER(d)], C.c_int),
             "ns_colour_elements": ([i64, i64, vp, vp, C.POINTER(i32)], C.c_int),
             "ns_state_bytes": ([i64, i32], i64),
+            "ns_spring_points_noalloc": ([vp, i64, vp, vp, vp, vp, vp], C.c_int),
+            "ns_spring_points_noalloc_capacity": ([i32], i64),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -218,6 +221,19 @@ def ns_spring_points(ctx, mat, eps, deps, theta):
     D = np.zeros((mat.shape[0], 6, 6))
     _check(ctx, lib().ns_spring_points(ctx, mat.shape[0], _p(mat), _p(eps), _p(deps), _p(theta), _p(D)))
     return theta, D
+
+
+def ns_spring_points_noalloc(ctx, mat, eps, deps, theta):
+    """Same as ns_spring_points, through the entry point that allocates no device memory."""
+    mat = _i32(mat); eps = _f64(eps); deps = _f64(deps)
+    theta = np.ascontiguousarray(theta, SPRING_DTYPE)
+    D = np.zeros((mat.shape[0], 6, 6))
+    _check(ctx, lib().ns_spring_points_noalloc(ctx, mat.shape[0], _p(mat), _p(eps), _p(deps), _p(theta), _p(D)))
+    return theta, D
+
+
+def ns_spring_points_noalloc_capacity(S):
+    return int(lib().ns_spring_points_noalloc_capacity(int(S)))
 
 
 def ns_get_stats(ctx) -> dict:

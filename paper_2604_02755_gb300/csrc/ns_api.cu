@@ -640,6 +640,23 @@ int one_step(ns_ctx *c) {
 
 }  // namespace
 
+// ============================================================================ context views
+
+namespace ns {
+int ctx_spring_view(ns_ctx *c, SpringCtxView *v) {
+  if (!c || !c->has_mat) return NS_ERR_STATE;
+  v->tab = c->tab;
+  v->mats = c->mats_d;
+  v->nmat = c->nmat;
+  v->stream = c->s_main;
+  v->device = c->cfg.device;
+  return NS_OK;
+}
+void ctx_set_error(ns_ctx *c, const char *msg) { c->err = msg; }
+void ctx_count_launches(ns_ctx *c, int n) { c->stats.kernel_launches += n; }
+int ctx_sync_main(ns_ctx *c) { return sync_stream(c, c->s_main); }
+}  // namespace ns
+
 // ============================================================================ C ABI
 
 extern "C" {

@@ -166,6 +166,20 @@ cudaError_t launch_elastic_D(const SpringTables &tab, const MatConst *mc, const 
                              int64_t e0, int64_t e1, cudaStream_t s);
 cudaError_t launch_D_to_f32(const double *D, float *D32, int64_t epad, int64_t E, cudaStream_t s);
 
+// ------------------------------------------------------------------ context views (ns_api.cu)
+// What the allocation-free spring entry point needs from a context.
+struct SpringCtxView {
+  SpringTables tab;
+  const MatConst *mats;
+  int nmat;
+  cudaStream_t stream;
+  int device;
+};
+int ctx_spring_view(ns_ctx *c, SpringCtxView *v);  // NS_OK once materials are set
+void ctx_set_error(ns_ctx *c, const char *msg);
+void ctx_count_launches(ns_ctx *c, int n);
+int ctx_sync_main(ns_ctx *c);                       // bounded wait for the context's main stream
+
 // ------------------------------------------------------------------ ns_host.cpp
 int host_spring_directions(int S, double *q, double *w);
 int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, int32_t *nc);
