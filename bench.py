@@ -44,7 +44,22 @@ UNIT = "elem-steps/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # algorithmic work per unit of the two candidate dominant kernels
 EBE_FLOP_PER_ELEM = 1800.0      # y_e = A_e x_e with a dense 30 x 30 element matrix
+# ncu summary holding the spring kernel's DRAM bytes per spring (traffic scales with springs)
+SPRING_PROFILE = "k_springs_large_model_cut_16x16x52.md"
 SPRING_FLOP_PER_SPRING = 66.0   # gamma and dgamma (12 FMA) + D accumulation (21 FMA), transcendental work excluded
+
+
+def profiled_bytes(name, key):
+    """DRAM bytes per unit that an ncu capture recorded for a kernel (a `key = value` line
+    of its summary under profiles/), or None when there is no such summary."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        for line in open(path):
+            if line.strip().startswith(key + " ="):
+                return float(line.split("=", 1)[1])
+    except OSError:
+        pass
+    return None
 
 
 def sample_clocks_start(path):
@@ -171,12 +186,19 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "precision", "tiny"],
+                    help="large: the single large model (default); precision: the 1M-element three-layer "
+                         "precision-form model; tiny: the 3,600-element two-layer case")
+    ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="hexahedra of a smaller cut of the large model (same spacing, interface and springs), "
+                         "used for profiling captures that must stay small")
     ap.add_argument("--no-stream", action="store_true", help="skip the streamed-state measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--stream-gb", type=float, default=96.0, help="spring state kept in pinned host memory (GB)")
-    ap.add_argument("--solver", default="fp64-ir", choices=["fp64-ir", "fp64-pcg"],
+    ap.add_argument("--stream-gb", type=float, default=128.0, help="spring state kept in pinned host memory (GB)")
+    ap.add_argument("--ring-depth", type=int, default=12, help="device chunk buffers of the streamed state")
+    ap.add_argument("--solver", default="fp64-ir", choices=["fp64-ir", "fp64-ir16", "fp64-pcg"],
                     help="fp64-ir: FP64 flexible CG with an FP32 PCG preconditioner (the paper's precision policy); "
+                         "fp64-ir16: the same with the inner operator reading D in FP16; "
                          "fp64-pcg: plain FP64 block-Jacobi PCG")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -195,12 +217,20 @@ def main():
     dist.barrier(dd)
     nsbuild.build()
 
-    wl = synth.large_single_model() if args.workload == "large" else synth.tiny_two_layer()
+    if args.workload == "tiny":
+        wl = synth.tiny_two_layer()
+    elif args.workload == "precision":
+        wl = synth.precision_form_model(dims=tuple(args.dims) if args.dims else (64, 64, 41))
+    elif args.dims:
+        wl = synth.large_single_model(dims=tuple(args.dims))
+        wl.name = "cut of the single large model: %dx%dx%d hexahedra at 5 m, 150 springs" % tuple(args.dims)
+    else:
+        wl = synth.large_single_model()
     E = wl.mesh.n_elems
     n_total = args.warmup + 2 * args.steps + 2
     wave = synth.band_limited_wave(2, max(n_total + 1, 400), wl.dt)
     wl.wave = wave
-    prec = B.NS_PREC_FP64_IR if args.solver == "fp64-ir" else B.NS_PREC_FP64
+    prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     sim = B.Simulation(wl, device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec)
     sim.advance(args.warmup)
     B.ns_reset_stats(sim.ctx)
@@ -219,6 +249,7 @@ def main():
     launches = st["kernel_launches"] - st0["kernel_launches"]
 
     # roofline of the dominant kernel (FP64 ALU bound)
+    traffic = None
     if st["ms_ebe64"] >= st["ms_spring"]:
         per = st["ms_ebe64"] / max(st["n_ebe64"], 1) / 1e3
         flops = EBE_FLOP_PER_ELEM * E
@@ -230,9 +261,11 @@ def main():
         flops = SPRING_FLOP_PER_SPRING * n_spr
         kern = "k_springs (multi-spring update, FP64)"
         unit_desc = "%g flop/spring x %d springs" % (SPRING_FLOP_PER_SPRING, n_spr)
+        bps = profiled_bytes(SPRING_PROFILE, "dram_bytes_per_spring")
+        traffic = bps * n_spr if bps else None
     achieved = flops / per / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kern, "work_per_launch": unit_desc,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kern, "work_per_launch": unit_desc,
             "avg_launch_ms": per * 1e3, "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)"}
 
     # end to end through the public API: input record from host, advance, surface read-back to host
@@ -258,24 +291,31 @@ def main():
     del sim
 
     stream = None
-    if ws == 1 and not args.no_stream and args.workload == "large":
+    if ws == 1 and not args.no_stream and args.workload == "large" and not args.dims:
         link = link_bandwidth()
         per_elem = B.ns_state_bytes(1, wl.n_springs)
         stream_elems = int(args.stream_gb * 1e9 / per_elem)
         budget = (E - stream_elems) * per_elem
-        sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000, ring_depth=3,
-                           precision=prec)
+        ring = args.ring_depth
+        sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
+                           ring_depth=ring, precision=prec)
         sim.advance(1)
         B.ns_reset_stats(sim.ctx)
+        h0 = sim.stats()
         sim.advance(2)
         st2 = sim.stats()
         sim.close()
         del sim
-        moved = st2["h2d_bytes"] + st2["d2h_bytes"]
-        gbs = moved / (st2["ms_stream_wall"] / 1e3) / 1e9
+        moved = (st2["h2d_bytes"] - h0["h2d_bytes"]) + (st2["d2h_bytes"] - h0["d2h_bytes"])
+        early = st2["h2d_bytes_early"] - h0["h2d_bytes_early"]
+        gbs = (moved - early) / (st2["ms_stream_wall"] / 1e3) / 1e9
         stream = {"streamed_elems": st2["streamed_elems"], "bytes_per_step": moved / 2,
+                  "early_h2d_bytes_per_step": early / 2,
                   "stream_GBps": gbs, "link_GBps_measured": link, "frac_of_link": gbs / link,
-                  "step_ms": st2["ms_advance"] / 2, "chunk_elems": 100000, "ring_depth": 3}
+                  "window": "multi-spring phase start to last D2H; H2D issued at step start (overlapping the "
+                            "solve) excluded from the bytes",
+                  "step_ms": st2["ms_advance"] / 2, "resident_step_ms": job_s / args.steps * 1e3,
+                  "chunk_elems": 100000, "ring_depth": ring}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -284,13 +324,16 @@ def main():
         v_cpu, desc = oracle_sample()
         cpu = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
+    state_gb = B.ns_state_bytes(E, wl.n_springs) / 1e9
+    l2_note = ("inputs larger than L2: %.1f GB of spring state read and written per step, no flush needed" % state_gb
+               if state_gb > 0.5 else "working set near L2 size (%.3f GB of spring state); no flush" % state_gb)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": job_s / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": wl.name, "elements": E, "nodes": wl.mesh.n_nodes,
                            "springs_per_point": wl.n_springs, "dt": wl.dt, "cg_tol": 1e-8,
-                           "state": "resident in HBM", "l2": "inputs larger than L2 (about 200 GB working set)",
+                           "state": "resident in HBM", "l2": l2_note,
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,

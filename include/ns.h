@@ -49,6 +49,8 @@ extern "C" {
 
 #define NS_PREC_FP64 0   /* FP64 PCG with FP64 3x3 block-Jacobi (plain method) */
 #define NS_PREC_FP64_IR 1 /* FP64 outer CG, FP32 inner CG as preconditioner (paper's precision policy) */
+#define NS_PREC_FP64_IR16 2 /* as NS_PREC_FP64_IR, the inner operator reading the tangent D in FP16
+                               (D / G0 of the element's material; FP32 arithmetic) */
 
 #define NS_SCATTER_ATOMIC 0 /* element results added with FP64/FP32 atomics (fast) */
 #define NS_SCATTER_COLOUR 1 /* greedy element colouring, plain stores (deterministic) */
@@ -98,8 +100,10 @@ typedef struct {
   double ms_rhs, ms_jacobi, ms_solve, ms_newmark, ms_springs, ms_step;
   int64_t n_ebe64, n_ebe32, n_spring;  /* launches of the FP64 operator, FP32 operator, spring kernel */
   double ms_ebe64, ms_ebe32, ms_spring; /* their summed durations */
-  double ms_stream_wall;      /* multi-spring phase of the streamed part (first H2D to last D2H) */
+  double ms_stream_wall;      /* multi-spring phase with a streamed part: its start to the last D2H */
   double ms_advance;          /* CUDA-event time of ns_advance calls, all streams joined (always valid) */
+  int64_t h2d_bytes_early;    /* of h2d_bytes: chunks loaded at the start of a step, before its
+                                 multi-spring phase (they overlap the solve) */
 } ns_stats;
 
 /* Fill cfg with defaults: 10 springs, dt 0.01, tol 1e-8, 10000 iterations,

@@ -17,7 +17,7 @@ from . import build as _build
 NS_OK = 0
 NS_ERR = {-1: "NS_ERR_INVALID_ARG", -2: "NS_ERR_OOM_DEVICE", -3: "NS_ERR_OOM_PINNED", -4: "NS_ERR_CUDA",
           -5: "NS_ERR_BAD_MESH", -6: "NS_ERR_NOT_CONVERGED", -7: "NS_ERR_TIMEOUT", -8: "NS_ERR_STATE"}
-NS_PREC_FP64, NS_PREC_FP64_IR = 0, 1
+NS_PREC_FP64, NS_PREC_FP64_IR, NS_PREC_FP64_IR16 = 0, 1, 2
 NS_SCATTER_ATOMIC, NS_SCATTER_COLOUR = 0, 1
 NS_FIELD = {"u": 0, "v": 1, "a": 2, "q": 3, "du": 4}
 NS_OP = {"K": 0, "M": 1, "Cb": 2, "A": 3, "Cr": 4}
@@ -54,7 +54,8 @@ class ns_stats(C.Structure):
                 ("ms_solve", C.c_double), ("ms_newmark", C.c_double), ("ms_springs", C.c_double),
                 ("ms_step", C.c_double), ("n_ebe64", C.c_int64), ("n_ebe32", C.c_int64), ("n_spring", C.c_int64),
                 ("ms_ebe64", C.c_double), ("ms_ebe32", C.c_double), ("ms_spring", C.c_double),
-                ("ms_stream_wall", C.c_double), ("ms_advance", C.c_double)]
+                ("ms_stream_wall", C.c_double), ("ms_advance", C.c_double),
+                ("h2d_bytes_early", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -105,15 +105,28 @@ cudaError_t launch_face_geometry(const DevMesh &m, const double *xyz, cudaStream
 
 // ------------------------------------------------------------------ operator
 
+// Entry m of the [84][epad] point-major tangent of element e: FP64 or FP32 as stored, or
+// from FP16 pairs [42][epad] (entries 2j and 2j+1 in one 4-byte word).
+__device__ __forceinline__ double dload(const double *__restrict__ D, int64_t epad, int64_t e, int m) {
+  return __ldg(D + m * epad + e);
+}
+__device__ __forceinline__ float dload(const float *__restrict__ D, int64_t epad, int64_t e, int m) {
+  return __ldg(D + m * epad + e);
+}
+__device__ __forceinline__ float dload(const __half2 *__restrict__ D, int64_t epad, int64_t e, int m) {
+  const __half2 h = __ldg(D + (m >> 1) * epad + e);
+  return (m & 1) ? __high2float(h) : __low2float(h);
+}
+
 // Stress of integration point Q: sig = w D_Q eps_Q(x).
-template <typename T, int Q>
+template <typename T, int Q, typename TD>
 __device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], const T g[4][3],
-                                             const T *__restrict__ D, int64_t epad, int64_t e, T w, T sig[6]) {
+                                             const TD *__restrict__ D, int64_t epad, int64_t e, T w, T sig[6]) {
   T H[3][3], eps[6], d[21];
   point_grad<T, Q>(x, P, g, H);
   voigt_strain(H, eps);
 #pragma unroll
-  for (int k = 0; k < 21; ++k) d[k] = ldg(D + (Q * 21 + k) * epad + e);
+  for (int k = 0; k < 21; ++k) d[k] = dload(D, epad, e, Q * 21 + k);
   sig[0] = w * (d[0] * eps[0] + d[1] * eps[1] + d[2] * eps[2] + d[3] * eps[3] + d[4] * eps[4] + d[5] * eps[5]);
   sig[1] = w * (d[1] * eps[0] + d[6] * eps[1] + d[7] * eps[2] + d[8] * eps[3] + d[9] * eps[4] + d[10] * eps[5]);
   sig[2] = w * (d[2] * eps[0] + d[7] * eps[1] + d[11] * eps[2] + d[12] * eps[3] + d[13] * eps[4] + d[14] * eps[5]);
@@ -125,10 +138,10 @@ __device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], 
 // Operator kernel, one thread per element.  Phases keep the register footprint small:
 // (1) gather x, stresses at the four points; (2) nodal forces B^T sig; (3) consistent mass
 // one displacement component at a time (re-gathered from cache); (4) scatter.
-template <typename T, bool HAS_XM, bool ATOMIC, bool DOT>
+template <typename T, typename TD, int VS, bool HAS_XM, bool ATOMIC, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_ebe(int64_t e0, int64_t e1, const int32_t *__restrict__ ids,
                                                 const int32_t *__restrict__ conn, const T *__restrict__ geom,
-                                                const int32_t *__restrict__ mat, const T *__restrict__ D,
+                                                const int32_t *__restrict__ mat, const TD *__restrict__ D,
                                                 int64_t epad, const OpCoef *__restrict__ op,
                                                 const T *__restrict__ xm, const T *__restrict__ xk, T *y,
                                                 double *dot, const int32_t *skip) {
@@ -156,9 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_ebe(int64_t e0, int64_t e1, const in
       {
         T x[10][3], P[4][3];
 #pragma unroll
-        for (int a = 0; a < 10; ++a)
-#pragma unroll
-          for (int r = 0; r < 3; ++r) x[a][r] = ldg(xk + 3 * (int64_t)nd[a] + r);
+        for (int a = 0; a < 10; ++a) load_node<VS>(xk, nd[a], x[a]);
         compute_P(x, P);
         const T w = cK * vol * (T)0.25;
         point_stress<T, 0>(x, P, g, D, epad, e, w, sig[0]);
@@ -178,28 +189,26 @@ __global__ void __launch_bounds__(kBlock) k_ebe(int64_t e0, int64_t e1, const in
         T w[10];
 #pragma unroll
         for (int a = 0; a < 10; ++a) {
-          w[a] = cMk * ldg(xk + 3 * (int64_t)nd[a] + r);
-          if (HAS_XM) w[a] += cMm * ldg(xm + 3 * (int64_t)nd[a] + r);
+          w[a] = cMk * ldg(xk + VS * (int64_t)nd[a] + r);
+          if (HAS_XM) w[a] += cMm * ldg(xm + VS * (int64_t)nd[a] + r);
         }
         mass_apply_1(w, c, ye, r);
       }
     }
     if (DOT) {
+      // element-local x_e . y_e in the operator's precision; block sums in FP64
+      T ld = (T)0;
 #pragma unroll
-      for (int a = 0; a < 10; ++a)
+      for (int a = 0; a < 10; ++a) {
+        T xa[3];
+        load_node<VS>(xk, nd[a], xa);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) mydot += (double)ldg(xk + 3 * (int64_t)nd[a] + r) * (double)ye[a][r];
+        for (int r = 0; r < 3; ++r) ld += xa[r] * ye[a][r];
+      }
+      mydot = (double)ld;
     }
 #pragma unroll
-    for (int a = 0; a < 10; ++a)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        T *dst = y + 3 * (int64_t)nd[a] + r;
-        if (ATOMIC)
-          atomic_add(dst, ye[a][r]);
-        else
-          *dst += ye[a][r];
-      }
+    for (int a = 0; a < 10; ++a) add_node<VS, ATOMIC>(y, nd[a], ye[a]);
   }
   if (DOT) {
     double s = block_sum(mydot);
@@ -207,15 +216,15 @@ __global__ void __launch_bounds__(kBlock) k_ebe(int64_t e0, int64_t e1, const in
   }
 }
 
-template <typename T, bool HAS_XM>
-static cudaError_t ebe_dispatch(const DevMesh &m, const T *D, const T *geom, const OpCoef *op, const T *xm,
+template <typename T, typename TD, int VS, bool HAS_XM>
+static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, const OpCoef *op, const T *xm,
                                 const T *xk, T *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic,
                                 double *dot, const int32_t *skip, cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
   unsigned nb = (unsigned)((e1 - e0 + kBlock - 1) / kBlock);
-#define NS_EBE_LAUNCH(A, DT)                                                                              \
-  k_ebe<T, HAS_XM, A, DT><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, \
-                                                 dot, skip)
+#define NS_EBE_LAUNCH(A, DT)                                                                                  \
+  k_ebe<T, TD, VS, HAS_XM, A, DT><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, \
+                                                     dot, skip)
   if (atomic) {
     if (dot)
       NS_EBE_LAUNCH(true, true);
@@ -234,21 +243,29 @@ static cudaError_t ebe_dispatch(const DevMesh &m, const T *D, const T *geom, con
 cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
                          const int32_t *skip, cudaStream_t s) {
-  if (xm) return ebe_dispatch<double, true>(m, D, m.geom, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s);
-  return ebe_dispatch<double, false>(m, D, m.geom, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
+  if (xm) return ebe_dispatch<double, double, 3, true>(m, D, m.geom, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s);
+  return ebe_dispatch<double, double, 3, false>(m, D, m.geom, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
 }
 
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
                          cudaStream_t s) {
-  return ebe_dispatch<float, false>(m, D, m.geom32, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
+  // inner-solve vectors are [N][4]
+  return ebe_dispatch<float, float, 4, false>(m, D, m.geom32, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
+}
+
+cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, const float *xk, float *y,
+                         const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
+                         cudaStream_t s) {
+  return ebe_dispatch<float, __half2, 4, false>(m, static_cast<const __half2 *>(D16), m.geom32, op, nullptr, xk, y,
+                                                ids, e0, e1, atomic, dot, skip, s);
 }
 
 // ------------------------------------------------------------------ dashpot faces
 
 // C_f = (A/180) Mtri (x) rho [Vs I + (Vp - Vs) n n^T]; Mtri*180/A: vertex 6 / -1, vertex vs
 // opposite edge -4 (else 0), edge 32 / 16.  Face nodes: v0 v1 v2 e01 e12 e02.
-template <typename T, bool ATOMIC, bool DOT>
+template <typename T, int VS, bool ATOMIC, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const int32_t *__restrict__ ids,
                                                   int64_t fpad, const int32_t *__restrict__ fnode,
                                                   const double *__restrict__ fgeom, const int32_t *__restrict__ fmat,
@@ -272,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) w[a][r] = x[3 * (int64_t)nd[a] + r] + (inp ? (T)vin[r] : (T)0);
+      for (int r = 0; r < 3; ++r) w[a][r] = x[VS * (int64_t)nd[a] + r] + (inp ? (T)vin[r] : (T)0);
     T m[6][3];  // Mtri applied per component
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -291,8 +308,8 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const T v = sc * (rvs * m[a][r] + rvd * n[r] * nm);
-        if (DOT) mydot += (double)x[3 * (int64_t)nd[a] + r] * (double)v;
-        T *dst = y + 3 * (int64_t)nd[a] + r;
+        if (DOT) mydot += (double)x[VS * (int64_t)nd[a] + r] * (double)v;
+        T *dst = y + VS * (int64_t)nd[a] + r;
         if (ATOMIC)
           atomic_add(dst, v);
         else
@@ -306,14 +323,14 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
   }
 }
 
-template <typename T>
+template <typename T, int VS>
 static cudaError_t faces_dispatch(const DevMesh &m, const MatConst *mc, T cC, const T *x, const double *vin, T *y,
                                   const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
                                   const int32_t *skip, cudaStream_t s) {
   if (f1 <= f0) return cudaSuccess;
   unsigned nb = (unsigned)((f1 - f0 + kBlock - 1) / kBlock);
 #define NS_F_LAUNCH(A, DT) \
-  k_faces<T, A, DT><<<nb, kBlock, 0, s>>>(f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, m.fkind, mc, cC, x, vin, y, \
+  k_faces<T, VS, A, DT><<<nb, kBlock, 0, s>>>(f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, m.fkind, mc, cC, x, vin, y, \
                                           dot, skip)
   if (atomic) {
     if (dot)
@@ -333,13 +350,13 @@ static cudaError_t faces_dispatch(const DevMesh &m, const MatConst *mc, T cC, co
 cudaError_t launch_faces64(const DevMesh &m, const MatConst *mc, double cC, const double *x, const double *vin,
                            double *y, const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
                            const int32_t *skip, cudaStream_t s) {
-  return faces_dispatch<double>(m, mc, cC, x, vin, y, ids, f0, f1, atomic, dot, skip, s);
+  return faces_dispatch<double, 3>(m, mc, cC, x, vin, y, ids, f0, f1, atomic, dot, skip, s);
 }
 
 cudaError_t launch_faces32(const DevMesh &m, const MatConst *mc, float cC, const float *x, float *y,
                            const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot, const int32_t *skip,
                            cudaStream_t s) {
-  return faces_dispatch<float>(m, mc, cC, x, nullptr, y, ids, f0, f1, atomic, dot, skip, s);
+  return faces_dispatch<float, 4>(m, mc, cC, x, nullptr, y, ids, f0, f1, atomic, dot, skip, s);
 }
 
 // ------------------------------------------------------------------ block-Jacobi diagonal blocks

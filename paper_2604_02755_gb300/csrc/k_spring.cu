@@ -1,6 +1,8 @@
 // Multi-spring constitutive update at every integration point (Sec. 2.1, Eq. 2):
 // spring strains gamma_k = q_k . eps, modified Ramberg-Osgood skeleton with the
 // Masing rule per spring (40-byte state), tangent D = Kb m m^T + w sum_k G_k q_k q_k^T.
+#include <algorithm>
+
 #include "kern_common.cuh"
 
 namespace ns {
@@ -38,8 +40,6 @@ __device__ __forceinline__ double ln_pos(double x, const PowTab &tb) {
 }
 
 __device__ __forceinline__ double exp_tab(double y, const PowTab &tb) {
-  if (y < -700.0) return 0.0;
-  if (y > 700.0) return __longlong_as_double(0x7FF0000000000000LL);
   const double kd = rint(y * (64.0 / 0.6931471805599453));
   const int k = (int)kd;
   double f = fma(-kd, tb.l64hi, y);
@@ -53,12 +53,25 @@ __device__ __forceinline__ double exp_tab(double y, const PowTab &tb) {
   q *= f;
   const double t = __ldg(tb.t64 + (k & 63));
   const double r = fma(t, q, t);
-  const int sh = k >> 6;  // floor(k / 64)
+  // 2^floor(k/64) built in the exponent field; the clamp turns underflow into 0 and
+  // keeps overflow finite (neither occurs for the strains of the spring law)
+  const int sh = max(-1023, min(1023, k >> 6));
   return r * __longlong_as_double((long long)(sh + 1023) << 52);
 }
 
 __device__ __forceinline__ double pow_pos(double x, double beta, const PowTab &tb) {
   return exp_tab(beta * ln_pos(x, tb), tb);
+}
+
+// Sign, zero and magnitude tests on the IEEE bit pattern (integer pipes; the FP64 pipe
+// is the scarce resource of this kernel).  For non-negative doubles the bit patterns
+// order like the values.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool d_is_zero(double x) { return (dbits(x) << 1) == 0; }
+__device__ __forceinline__ bool d_sign(double x) { return dbits(x) < 0; }
+__device__ __forceinline__ double d_abs(double x) { return __longlong_as_double(dbits(x) & 0x7FFFFFFFFFFFFFFFLL); }
+__device__ __forceinline__ double d_copysign(double m, double s) {
+  return __longlong_as_double((dbits(m) & 0x7FFFFFFFFFFFFFFFLL) | (dbits(s) & (long long)0x8000000000000000ULL));
 }
 
 // FP32 reciprocal refined once in FP64 (relative error ~1e-14).
@@ -109,12 +122,10 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
   double tau = ga;
   bool seeded = true;
   if (solve) {
-    const double hi = p.G0 * ga;
-    const float gaf = (float)ga, hif = (float)hi;
-    float t = (guess > 0.0 && guess < hi) ? (float)guess : hif;
-    if (!(t > 0.0f)) t = hif;
+    const float gaf = (float)ga, hif = p.G0_f * gaf, gs = (float)guess;
+    float t = (gs > 0.0f && gs < hif) ? gs : hif;
     seeded = false;
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0; it < 40 && t > 0.0f; ++it) {
       const float pwf = __powf(t * p.itref_f, p.beta_f);
       const float gp = 1.0f + p.alpha_f * (1.0f + p.beta_f) * pwf;
       const float step = (t * p.iG0_f * (1.0f + p.alpha_f * pwf) - gaf) * __fdividef(p.G0_f, gp);
@@ -128,27 +139,29 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
         break;
       }
     }
-    tau = (double)t;
-    if (!(tau > 0.0) || !(tau <= hi)) tau = hi;
+    tau = (t > 0.0f) ? (double)t : p.G0 * ga;  // FP32 underflow: start from the linear bound
   }
-  if (!(tau > 0.0)) {  // zero strain (or zero stress): the power vanishes
+  if (d_is_zero(tau)) {  // zero strain (or zero stress): the power vanishes
     *pw = 0.0;
     return 0.0;
   }
   double w = pow_pos(tau * p.itref, p.beta_ro, tb);
   if (solve) {
-    // Halley: step = h / (1 - h f''/(2 f')), h = f/f' the Newton step
+    // Halley: step = h / (1 - h f''/(2 f')) with h = f/f' the Newton step; |h f''/(2 f')|
+    // is ~ the seed error (<= 4e-6), so 1/(1 - c) = 1 + c to far below rounding
     const double it0 = rcp1(tau);
     const double gval = tau * p.iG0 * fma(p.alpha_ro, w, 1.0);
-    const double gp = fma(p.ab1, w, 1.0);
-    const double rg = rcp1(gp);
+    const double rg = rcp1(fma(p.ab1, w, 1.0));
     const double h = (gval - ga) * p.G0 * rg;
-    const double hc = h * (0.5 * p.ab1b) * w * it0 * rg;
-    const double step = h * fma(hc, 1.0 + hc, 1.0);
+    const double hc = h * p.hab1b * w * it0 * rg;
+    const double step = fma(h, hc, h);
     const double d = -step * it0;
     tau -= step;
     w *= fma(d, fma(d, fma(d, p.c3, p.c2), p.beta_ro), 1.0);
-    if (!(seeded && fabs(d) <= 2e-5)) tau = ro_F_safe(ga, (tau > 0.0 && tau <= p.G0 * ga) ? tau : p.G0 * ga, p, tb, &w);
+    if (!(seeded && fabs(d) <= 2e-5)) {
+      const double hi = p.G0 * ga;
+      tau = ro_F_safe(ga, (tau > 0.0 && tau <= hi) ? tau : hi, p, tb, &w);
+    }
   }
   *pw = w;
   return tau;
@@ -167,10 +180,10 @@ __device__ __forceinline__ double ro_tangent_from_pw(double pw, const MatConst &
 // Returns the tangent dtau/dgamma at the end state.
 __device__ __forceinline__ double spring_update(double g, double dg, const MatConst &p, const PowTab &tb, double &tau,
                                                 double &gR, double &tR, double &gmax, int &dir, int &mode) {
-  const bool active = dg != 0.0;
+  const bool active = !d_is_zero(dg);
   double x, guess = 0.0;
   if (active) {
-    const int sgn = dg > 0.0 ? 1 : -1;
+    const int sgn = d_sign(dg) ? -1 : 1;
     bool same = true;
     if (dir == 0) {
       dir = sgn;
@@ -183,23 +196,26 @@ __device__ __forceinline__ double spring_update(double g, double dg, const MatCo
       dir = sgn;
       same = false;
     }
-    if (mode == 1 && fabs(g) >= gmax && (dir > 0 ? g > 0.0 : g < 0.0)) {
-      mode = 0;  // outward past the largest skeleton strain: back on the skeleton
-      guess = fabs(tau);
+    // outward (g on the side of dir, nonzero) with |g| >= gmax: back on the skeleton
+    const bool outward = !d_is_zero(g) && (d_sign(g) == (dir < 0));
+    if (mode == 1 && outward && dbits(d_abs(g)) >= dbits(gmax)) {
+      mode = 0;
+      guess = d_abs(tau);
     } else if (same) {
-      guess = (mode == 0) ? fabs(tau) : 0.5 * fabs(tau - tR);
+      guess = (mode == 0) ? d_abs(tau) : 0.5 * d_abs(tau - tR);
     }
     x = (mode == 0) ? g : 0.5 * (g - gR);
   } else {
     x = (mode == 0) ? tau : 0.5 * (tau - tR);  // the power at the current state only
   }
   double pw;
-  const double f = ro_solve(active, fabs(x), guess, p, tb, &pw);
+  const double f = ro_solve(active, d_abs(x), guess, p, tb, &pw);
   if (active) {
-    const double fs = x < 0.0 ? -f : f;
+    const double fs = d_copysign(f, x);
     if (mode == 0) {
       tau = fs;
-      gmax = fmax(gmax, fabs(g));
+      const double ag = d_abs(g);
+      if (dbits(ag) > dbits(gmax)) gmax = ag;
     } else {
       tau = fma(2.0, fs, tR);
     }
@@ -351,6 +367,26 @@ __global__ void k_D_to_f32(const double *D, float *D32, int64_t n) {
 cudaError_t launch_D_to_f32(const double *D, float *D32, int64_t epad, int64_t, cudaStream_t s) {
   const int64_t n = 84 * epad;
   k_D_to_f32<<<152 * 8, kBlock, 0, s>>>(D, D32, n);
+  return cudaGetLastError();
+}
+
+// FP16 copy of the tangent for the inner operator, scaled by 1/G0 of the element's material
+// so that the entries (Kb/G0 + 4/3 at most, ~6 for Poisson's ratio 0.4) sit well inside the
+// FP16 range; blockIdx.y = pair j of entries (2j, 2j+1).
+__global__ void k_D_to_f16(const double *__restrict__ D, const int32_t *__restrict__ mat,
+                           const MatConst *__restrict__ mc, __half2 *D16, int64_t epad, int64_t E) {
+  const int64_t j = blockIdx.y;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double s = mc[mat[e]].iG0;
+    D16[j * epad + e] = __floats2half2_rn((float)(D[2 * j * epad + e] * s), (float)(D[(2 * j + 1) * epad + e] * s));
+  }
+}
+
+cudaError_t launch_D_to_f16(const double *D, const int32_t *mat, const MatConst *mc, void *D16, int64_t epad,
+                            int64_t E, cudaStream_t s) {
+  if (E <= 0) return cudaSuccess;
+  const unsigned nx = (unsigned)std::min<int64_t>((E + kBlock - 1) / kBlock, 152 * 2);
+  k_D_to_f16<<<dim3(nx, 42), kBlock, 0, s>>>(D, mat, mc, static_cast<__half2 *>(D16), epad, E);
   return cudaGetLastError();
 }
 

@@ -210,17 +210,20 @@ cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int n
 // Flexible CG with one-term orthogonalisation (Notay): z_k = B_k(r_k) (inner FP32 solve),
 // p_k = z_k - (z_k.A p_{k-1} / p_{k-1}.A p_{k-1}) p_{k-1}, alpha_k = p_k.r_k / p_k.A p_k.
 
-// z = ||r|| * x_in (undo the inner scaling); partial z . A p_{k-1}
-__global__ void __launch_bounds__(kBlock) k_fcg_gamma(const float *__restrict__ xin, double *z,
-                                                      const double *__restrict__ Ap, int64_t n3, double *part,
+// z = ||r|| * x_in (undo the inner scaling; x_in is [N][4]); partial z . A p_{k-1}
+__global__ void __launch_bounds__(kBlock) k_fcg_gamma(const float4 *__restrict__ xin, double *z,
+                                                      const double *__restrict__ Ap, int64_t N, double *part,
                                                       const CgScalars *so) {
   if (so->done) return;
   const double nr = sqrt(so->rr);
   double g = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = (double)xin[i] * nr;
-    z[i] = zi;
-    g += zi * Ap[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 xv = xin[i];
+    const double z0 = (double)xv.x * nr, z1 = (double)xv.y * nr, z2 = (double)xv.z * nr;
+    z[3 * i] = z0;
+    z[3 * i + 1] = z1;
+    z[3 * i + 2] = z2;
+    g += z0 * Ap[3 * i] + z1 * Ap[3 * i + 1] + z2 * Ap[3 * i + 2];
   }
   g = block_sum(g);
   if (threadIdx.x == 0) part[blockIdx.x] = g;
@@ -283,7 +286,7 @@ cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_
 }
 cudaError_t launch_fcg_gamma(const float *xin, double *z, const double *Ap, int64_t N, double *part,
                              const CgScalars *so, cudaStream_t s) {
-  k_fcg_gamma<<<vec_blocks(N), kBlock, 0, s>>>(xin, z, Ap, 3 * N, part, so);
+  k_fcg_gamma<<<vec_blocks(N), kBlock, 0, s>>>(reinterpret_cast<const float4 *>(xin), z, Ap, N, part, so);
   return cudaGetLastError();
 }
 cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, int64_t N, double *part,
@@ -299,37 +302,34 @@ cudaError_t launch_fcg_update(double *x, double *r, const double *p, const doubl
 
 // ------------------------------------------------------------------ inner FP32 PCG (preconditioner)
 // Solves A x_in = r / ||r|| approximately in FP32 (FP64 reductions), block-Jacobi
-// preconditioned, from x_in = 0.  Skips when the outer CG is done.
+// preconditioned, from x_in = 0.  Skips when the outer CG is done.  Its vectors are
+// [N][4] (x y z and a zero pad) so that the operator gathers and scatters one 16-byte
+// row per node.
 
-__device__ __forceinline__ void sym3_apply_f(const float *J, const float r[3], float z[3]) {
-  z[0] = J[0] * r[0] + J[5] * r[1] + J[4] * r[2];
-  z[1] = J[5] * r[0] + J[1] * r[1] + J[3] * r[2];
-  z[2] = J[4] * r[0] + J[3] * r[1] + J[2] * r[2];
+__device__ __forceinline__ float4 sym3_apply_f(const float *J, const float4 r) {
+  return make_float4(J[0] * r.x + J[5] * r.y + J[4] * r.z, J[5] * r.x + J[1] * r.y + J[3] * r.z,
+                     J[4] * r.x + J[3] * r.y + J[2] * r.z, 0.0f);
 }
 
 __global__ void __launch_bounds__(kBlock) k_in_init(const double *__restrict__ r, const CgScalars *so,
-                                                    const float *__restrict__ J, float *rin, float *zin, float *pin,
-                                                    float *xin, float *Apin, int64_t N, double *part) {
+                                                    const float *__restrict__ J, float4 *rin, float4 *zin, float4 *pin,
+                                                    float4 *xin, float4 *Apin, int64_t N, double *part) {
   if (so->done) return;
   const double sc = 1.0 / sqrt(so->rr);
-  double rr = 0.0, rz = 0.0;
+  float rr = 0.0f, rz = 0.0f;  // per-thread partials (a few dozen terms) in FP32
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    float rv[3], zv[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) rv[c] = (float)(r[3 * i + c] * sc);
-    sym3_apply_f(J + 6 * i, rv, zv);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      rin[3 * i + c] = rv[c];
-      zin[3 * i + c] = zv[c];
-      pin[3 * i + c] = zv[c];
-      xin[3 * i + c] = 0.0f;
-      Apin[3 * i + c] = 0.0f;
-      rr += (double)rv[c] * rv[c];
-      rz += (double)rv[c] * zv[c];
-    }
+    const float4 rv = make_float4((float)(r[3 * i] * sc), (float)(r[3 * i + 1] * sc), (float)(r[3 * i + 2] * sc), 0.0f);
+    const float4 zv = sym3_apply_f(J + 6 * i, rv);
+    rin[i] = rv;
+    zin[i] = zv;
+    pin[i] = zv;
+    xin[i] = zero;
+    Apin[i] = zero;
+    rr = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rr)));
+    rz = fmaf(rv.x, zv.x, fmaf(rv.y, zv.y, fmaf(rv.z, zv.z, rz)));
   }
-  const double s0 = block_sum(rr), s1 = block_sum(rz);
+  const double s0 = block_sum((double)rr), s1 = block_sum((double)rz);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = s0;
     part[gridDim.x + blockIdx.x] = s0;
@@ -337,59 +337,68 @@ __global__ void __launch_bounds__(kBlock) k_in_init(const double *__restrict__ r
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_in_update(float *xin, float *rin, float *zin, const float *__restrict__ pin,
-                                                      const float *__restrict__ Apin, const float *__restrict__ J,
-                                                      int64_t N, double *part, const CgScalars *si,
-                                                      const CgScalars *so) {
+__global__ void __launch_bounds__(kBlock) k_in_update(float4 *xin, float4 *rin, float4 *zin,
+                                                      const float4 *__restrict__ pin, const float4 *__restrict__ Apin,
+                                                      const float *__restrict__ J, int64_t N, double *part,
+                                                      const CgScalars *si, const CgScalars *so) {
   if (so->done || si->done) return;
   const float alpha = (float)si->alpha;
-  double rr = 0.0, rz = 0.0;
+  float rr = 0.0f, rz = 0.0f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    float rv[3], zv[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      xin[3 * i + c] += alpha * pin[3 * i + c];
-      rv[c] = rin[3 * i + c] - alpha * Apin[3 * i + c];
-      rin[3 * i + c] = rv[c];
-      rr += (double)rv[c] * rv[c];
-    }
-    sym3_apply_f(J + 6 * i, rv, zv);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      zin[3 * i + c] = zv[c];
-      rz += (double)rv[c] * zv[c];
-    }
+    const float4 pv = pin[i], av = Apin[i];
+    float4 xv = xin[i], rv = rin[i];
+    xv.x = fmaf(alpha, pv.x, xv.x);
+    xv.y = fmaf(alpha, pv.y, xv.y);
+    xv.z = fmaf(alpha, pv.z, xv.z);
+    rv.x = fmaf(-alpha, av.x, rv.x);
+    rv.y = fmaf(-alpha, av.y, rv.y);
+    rv.z = fmaf(-alpha, av.z, rv.z);
+    xin[i] = xv;
+    rin[i] = rv;
+    const float4 zv = sym3_apply_f(J + 6 * i, rv);
+    zin[i] = zv;
+    rr = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rr)));
+    rz = fmaf(rv.x, zv.x, fmaf(rv.y, zv.y, fmaf(rv.z, zv.z, rz)));
   }
-  const double s0 = block_sum(rr), s1 = block_sum(rz);
+  const double s0 = block_sum((double)rr), s1 = block_sum((double)rz);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = s0;
     part[gridDim.x + blockIdx.x] = s1;
   }
 }
 
-__global__ void k_in_pupdate(float *pin, const float *__restrict__ zin, float *Apin, int64_t n3, const CgScalars *si,
+__global__ void k_in_pupdate(float4 *pin, const float4 *__restrict__ zin, float4 *Apin, int64_t N, const CgScalars *si,
                              const CgScalars *so) {
   if (so->done || si->done) return;
   const float beta = (float)si->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    pin[i] = zin[i] + beta * pin[i];
-    Apin[i] = 0.0f;
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 zv = zin[i];
+    float4 pv = pin[i];
+    pv.x = fmaf(beta, pv.x, zv.x);
+    pv.y = fmaf(beta, pv.y, zv.y);
+    pv.z = fmaf(beta, pv.z, zv.z);
+    pin[i] = pv;
+    Apin[i] = zero;
   }
 }
 
+static float4 *f4(float *p) { return reinterpret_cast<float4 *>(p); }
+static const float4 *f4(const float *p) { return reinterpret_cast<const float4 *>(p); }
+
 cudaError_t launch_in_init(const double *r, const CgScalars *so, const float *J, float *rin, float *zin, float *pin,
                            float *xin, float *Apin, int64_t N, double *part, cudaStream_t s) {
-  k_in_init<<<vec_blocks(N), kBlock, 0, s>>>(r, so, J, rin, zin, pin, xin, Apin, N, part);
+  k_in_init<<<vec_blocks(N), kBlock, 0, s>>>(r, so, J, f4(rin), f4(zin), f4(pin), f4(xin), f4(Apin), N, part);
   return cudaGetLastError();
 }
 cudaError_t launch_in_update(float *xin, float *rin, float *zin, const float *pin, const float *Apin, const float *J,
                              int64_t N, double *part, const CgScalars *si, const CgScalars *so, cudaStream_t s) {
-  k_in_update<<<vec_blocks(N), kBlock, 0, s>>>(xin, rin, zin, pin, Apin, J, N, part, si, so);
+  k_in_update<<<vec_blocks(N), kBlock, 0, s>>>(f4(xin), f4(rin), f4(zin), f4(pin), f4(Apin), J, N, part, si, so);
   return cudaGetLastError();
 }
 cudaError_t launch_in_pupdate(float *pin, const float *zin, float *Apin, int64_t N, const CgScalars *si,
                               const CgScalars *so, cudaStream_t s) {
-  k_in_pupdate<<<vec_blocks(N), kBlock, 0, s>>>(pin, zin, Apin, 3 * N, si, so);
+  k_in_pupdate<<<vec_blocks(N), kBlock, 0, s>>>(f4(pin), f4(zin), f4(Apin), N, si, so);
   return cudaGetLastError();
 }
 

@@ -1,8 +1,11 @@
 // Device helpers shared by the library's kernels: quadratic-tetrahedron
 // element arithmetic (Sec. 2.1), reductions and atomics.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "ns_internal.h"
 
@@ -31,6 +34,46 @@ __device__ __forceinline__ T ldg(const T *p) {
 
 __device__ __forceinline__ void atomic_add(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add(float *p, float v) { atomicAdd(p, v); }
+
+// Node vectors are [N][VS]: VS = 3 (packed x y z) or, for the FP32 inner solve, VS = 4
+// (x y z and a zero pad, one 16-byte row per node: one vector load per node gather and
+// one vector atomic per node scatter).
+template <int VS, typename T>
+__device__ __forceinline__ void load_node(const T *__restrict__ x, int64_t n, T v[3]) {
+  if constexpr (VS == 4 && std::is_same<T, float>::value) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(x) + n);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[r] = __ldg(x + VS * n + r);
+  }
+}
+
+template <int VS, bool ATOMIC, typename T>
+__device__ __forceinline__ void add_node(T *y, int64_t n, const T v[3]) {
+  if constexpr (VS == 4 && std::is_same<T, float>::value) {
+    float4 *d = reinterpret_cast<float4 *>(y) + n;
+    if (ATOMIC) {
+      atomicAdd(d, make_float4(v[0], v[1], v[2], 0.0f));
+    } else {
+      float4 o = *d;
+      o.x += v[0];
+      o.y += v[1];
+      o.z += v[2];
+      *d = o;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (ATOMIC)
+        atomic_add(y + VS * n + r, v[r]);
+      else
+        y[VS * n + r] += v[r];
+    }
+  }
+}
 
 // Barycentric gradients of one element: g[0..3][3], from the stored grad L1..L3.
 template <typename T>

@@ -58,7 +58,9 @@ struct ns_ctx {
   float2 *T2_d = nullptr;
   SpringTables tab{};
   double *D = nullptr;
-  float *D32 = nullptr;
+  float *D32 = nullptr;   // NS_PREC_FP64_IR: FP32 copy of D for the inner operator
+  __half *D16 = nullptr;  // NS_PREC_FP64_IR16: FP16 pairs of D / G0
+  OpCoef *op_A16 = nullptr;  // op_A with kK scaled by G0 (reads D16)
   // spring state: resident elements [0, E_res) on the device, [E_res, E) in pinned host memory
   int64_t E_res = 0;
   SpringSoA st;                      // device, resident part
@@ -290,13 +292,18 @@ int apply_A32(ns_ctx *c, const float *x, float *y, double *dot, const int32_t *s
   int off = 0;
   cudaEvent_t t0 = nullptr;
   tbegin(c, TK_EBE32, c->s_main, &t0);
+  const bool h16 = c->cfg.precision == NS_PREC_FP64_IR16;
+  auto elems = [&](const int32_t *ids, int64_t e0, int64_t e1, bool at, double *d) {
+    return h16 ? launch_ebe16(c->m, c->D16, c->op_A16, x, y, ids, e0, e1, at, d, skip, c->s_main)
+               : launch_ebe32(c->m, c->D32, c->op_A, x, y, ids, e0, e1, at, d, skip, c->s_main);
+  };
   if (atomic) {
-    LAUNCH(c, launch_ebe32(c->m, c->D32, c->op_A, x, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main));
+    LAUNCH(c, elems(nullptr, 0, c->m.E, true, dot));
     off = nblk(c->m.E);
   } else {
     for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k) {
       const int64_t e0 = c->m.ecol_off[k], e1 = c->m.ecol_off[k + 1];
-      LAUNCH(c, launch_ebe32(c->m, c->D32, c->op_A, x, y, c->m.ecol_ids, e0, e1, false, dot + off, skip, c->s_main));
+      LAUNCH(c, elems(c->m.ecol_ids, e0, e1, false, dot + off));
       off += nblk(e1 - e0);
     }
   }
@@ -335,6 +342,9 @@ int fill_opcoefs(ns_ctx *c) {
     R.kK[i] = m.ray_b;                        // beta K v
   }
   CKC(c, cudaMemcpy(c->op_A, &A, sizeof(OpCoef), cudaMemcpyHostToDevice));
+  OpCoef A16 = A;
+  for (int i = 0; i < c->nmat; ++i) A16.kK[i] = A.kK[i] * c->mats_h[i].G0;
+  CKC(c, cudaMemcpy(c->op_A16, &A16, sizeof(OpCoef), cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->op_K, &K, sizeof(OpCoef), cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->op_M, &M, sizeof(OpCoef), cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->op_Cr, &Cr, sizeof(OpCoef), cudaMemcpyHostToDevice));
@@ -409,17 +419,21 @@ int issue_h2d(ns_ctx *c, int64_t k) {
   return NS_OK;
 }
 
-// Start the first ring-depth chunk transfers of this step as early as possible (they only
-// depend on the previous step's write-back, not on this step's solve).
+// Start the first ring-depth chunk transfers of a step at its beginning: they depend only
+// on the previous step's write-back of the same ring slot, so they overlap this step's
+// right-hand side, preconditioner set-up and solve.
 int prefetch_state(ns_ctx *c) {
   const int64_t nc = n_chunks(c);
   if (nc == 0 || c->prefetched) return NS_OK;
-  CKC(c, cudaStreamWaitEvent(c->s_h2d, c->ev_d2h_all, 0));
-  if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t0, c->s_h2d));
+  const int64_t h0 = c->stats.h2d_bytes;
   for (int64_t k = 0; k < std::min<int64_t>(nc, c->cfg.ring_depth); ++k) {
+    // slot k was last drained by the previous step's D2H of the last chunk it held,
+    // which the copy stream orders after the D2H of chunk k itself
+    CKC(c, cudaStreamWaitEvent(c->s_h2d, c->ev_d2h[k], 0));
     int rc = issue_h2d(c, k);
     if (rc) return rc;
   }
+  c->stats.h2d_bytes_early += c->stats.h2d_bytes - h0;
   c->prefetched = true;
   return NS_OK;
 }
@@ -443,6 +457,7 @@ int spring_phase(ns_ctx *c) {
   LAUNCH(c, launch_strain(c->m, c->u, c->du, c->eps, 0, c->m.E, c->s_main));
   const int64_t nc = n_chunks(c);
   if (nc == 0) return spring_launch(c, c->st, 0, 0, c->E_res);
+  if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t0, c->s_main));
   if ((rc = prefetch_state(c)) != NS_OK) return rc;
   const int R = c->cfg.ring_depth;
   const int64_t S4 = 4 * (int64_t)c->tab.S;
@@ -529,6 +544,7 @@ int one_step(ns_ctx *c) {
   const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
   cudaEvent_t tstep = nullptr, t0 = nullptr;
   tbegin(c, TK_STEP, c->s_main, &tstep);
+  if ((rc = prefetch_state(c)) != NS_OK) return rc;
 
   // 3x3 block-Jacobi preconditioner from the diagonal node blocks of A^n (FP32 when it only
   // serves the inner single-precision solve)
@@ -564,6 +580,8 @@ int one_step(ns_ctx *c) {
                                       c->m.fcol_off[k + 1], false, c->s_main));
     }
     LAUNCH(c, launch_invert_blocks(c->Jd, c->Jinv, c->Jinv32, N, c->flag_d, c->s_main));
+    if (c->cfg.precision == NS_PREC_FP64_IR16)
+      LAUNCH(c, launch_D_to_f16(c->D, c->m.mat, c->mats_d, c->D16, c->m.epad, c->m.E, c->s_main));
   }
   tend(c, TK_JAC, c->s_main, t0);
 
@@ -578,7 +596,7 @@ int one_step(ns_ctx *c) {
   // PCG on A du = b, starting from the previous increment (or zero)
   tbegin(c, TK_SOLVE, c->s_main, &t0);
   CKC(c, cudaMemcpyAsync(c->flag_h, c->flag_d, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s_main));
-  if (c->cfg.precision == NS_PREC_FP64_IR) {
+  if (c->cfg.precision != NS_PREC_FP64) {
     if ((rc = solve_ir(c)) != NS_OK) return rc;
   } else {
   if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
@@ -698,7 +716,8 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
   *out = nullptr;
   if (cfg->n_springs < 5 || !(cfg->dt > 0) || !(cfg->cg_tol > 0) || cfg->cg_max_iter < 1 || cfg->ring_depth < 2 ||
       cfg->chunk_elems < 1 || cfg->surface_ring_steps < 1 ||
-      (cfg->precision != NS_PREC_FP64 && cfg->precision != NS_PREC_FP64_IR) ||
+      (cfg->precision != NS_PREC_FP64 && cfg->precision != NS_PREC_FP64_IR &&
+       cfg->precision != NS_PREC_FP64_IR16) ||
       (cfg->scatter != NS_SCATTER_ATOMIC && cfg->scatter != NS_SCATTER_COLOUR) || !(cfg->wait_timeout_s > 0) ||
       cfg->inner_max_iter < 1 || !(cfg->inner_tol > 0)) {
     g_create_err = "invalid configuration value";
@@ -741,7 +760,7 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
     cudaEventCreateWithFlags(&c->ev_d2h[i], cudaEventDisableTiming);
   }
   if (halloc(c, &c->sc_h, 2) || halloc(c, &c->flag_h, 1) || dalloc(c, &c->sc, 2) || dalloc(c, &c->flag_d, 1) ||
-      dalloc(c, &c->op_A, 1) ||
+      dalloc(c, &c->op_A, 1) || dalloc(c, &c->op_A16, 1) ||
       dalloc(c, &c->op_K, 1) || dalloc(c, &c->op_M, 1) || dalloc(c, &c->op_Cr, 1) || dalloc(c, &c->op_rhs, 1) ||
       dalloc(c, &c->mats_d, kMaxMat)) {
     g_create_err = c->err;
@@ -798,9 +817,10 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
       (rc = dalloc(c, &c->Jinv, 6 * (size_t)N)) || (rc = dalloc(c, &c->Jinv32, 6 * (size_t)N)) ||
       (rc = dalloc(c, &c->eps, 48 * (size_t)E)))
     return rc;
-  if (c->cfg.precision == NS_PREC_FP64_IR &&
-      ((rc = dalloc(c, &c->rin, n3)) || (rc = dalloc(c, &c->zin, n3)) || (rc = dalloc(c, &c->pin, n3)) ||
-       (rc = dalloc(c, &c->xin, n3)) || (rc = dalloc(c, &c->Apin, n3))))
+  const size_t n4 = 4 * (size_t)N;  // inner FP32 vectors: [N][4] rows of 16 bytes
+  if (c->cfg.precision != NS_PREC_FP64 &&
+      ((rc = dalloc(c, &c->rin, n4)) || (rc = dalloc(c, &c->zin, n4)) || (rc = dalloc(c, &c->pin, n4)) ||
+       (rc = dalloc(c, &c->xin, n4)) || (rc = dalloc(c, &c->Apin, n4))))
     return rc;
   for (double *x : {c->u, c->v, c->a, c->q, c->du}) CKC(c, cudaMemsetAsync(x, 0, n3 * 8, c->s_main));
   // colouring for the deterministic scatter
@@ -876,7 +896,9 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   c->tab.S = S;
   // tangent D (element SoA [84][epad]) and spring state placement
   const int64_t E = c->m.E, epad = c->m.epad;
-  if ((rc = dalloc(c, &c->D, 84 * (size_t)epad)) || (rc = dalloc(c, &c->D32, 84 * (size_t)epad))) return rc;
+  if ((rc = dalloc(c, &c->D, 84 * (size_t)epad))) return rc;
+  if (c->cfg.precision == NS_PREC_FP64_IR && (rc = dalloc(c, &c->D32, 84 * (size_t)epad))) return rc;
+  if (c->cfg.precision == NS_PREC_FP64_IR16 && (rc = dalloc(c, &c->D16, 84 * (size_t)epad))) return rc;
   CKC(c, cudaMemsetAsync(c->D, 0, 84 * epad * 8, c->s_main));
   LAUNCH(c, launch_elastic_D(c->tab, c->mats_d, c->m.mat, c->D, epad, 0, E, c->s_main));
   const int64_t per_elem = ns_state_bytes(1, S);
@@ -1003,6 +1025,7 @@ int ns_advance(ns_ctx *c, int64_t nsteps) {
     int rc = one_step(c);
     if (rc != NS_OK) {
       sync_all(c);
+      c->prefetched = false;  // chunks loaded for the failed step are loaded again
       return rc;
     }
     if ((rc = sync_all(c)) != NS_OK) return rc;
@@ -1369,6 +1392,7 @@ void ns_destroy(ns_ctx *c) {
   dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
   dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
   dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->T2_d); dfree(c->D); dfree(c->D32);
+  dfree(c->D16); dfree(c->op_A16);
   free_soa(c->st, false);
   free_soa(c->hst, true);
   for (auto &rb : c->ring) free_soa(rb, false);

@@ -147,6 +147,7 @@ void host_material_constants(const ns_material &m, double f1, double f2, MatCons
   o->ab1b = o->ab1 * o->beta_ro;
   o->c2 = o->beta_ro * (o->beta_ro - 1.0) * 0.5;
   o->c3 = o->c2 * (o->beta_ro - 2.0) / 3.0;
+  o->hab1b = 0.5 * o->ab1b;
   o->itref_f = (float)o->itref;
   o->iG0_f = (float)o->iG0;
   o->alpha_f = (float)o->alpha_ro;

@@ -20,7 +20,7 @@ struct MatConst {
   double rho, vs, vp, G0, Kb, gref, alpha_ro, beta_ro, ray_a, ray_b;
   // spring-law constants: 1/G0, 1/(G0 gamma_ref), alpha (1 + beta), alpha (1 + beta) beta,
   // series coefficients beta (beta - 1)/2 and beta (beta - 1)(beta - 2)/6, FP32 copies
-  double iG0, itref, ab1, ab1b, c2, c3;
+  double iG0, itref, ab1, ab1b, c2, c3, hab1b;
   float itref_f, iG0_f, alpha_f, beta_f, G0_f, pad_f;
 };
 
@@ -75,6 +75,11 @@ cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, co
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
                          const int32_t *skip, cudaStream_t s);
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
+                         const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
+                         cudaStream_t s);
+// As launch_ebe32 with D stored as FP16 pairs [42][epad] (entries 2j, 2j+1 of the [84] point-major
+// order) holding D / G0 of the element's material; op->kK carries the factor G0.
+cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
                          cudaStream_t s);
 // Boundary faces: y (+)= cC * C_f (x + [kind 0] vin) (vin may be nullptr)
@@ -165,6 +170,9 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
 cudaError_t launch_elastic_D(const SpringTables &tab, const MatConst *mc, const int32_t *mat, double *D, int64_t epad,
                              int64_t e0, int64_t e1, cudaStream_t s);
 cudaError_t launch_D_to_f32(const double *D, float *D32, int64_t epad, int64_t E, cudaStream_t s);
+// D16[j][e] = half2(D[2j][e], D[2j+1][e]) / G0[mat[e]] for the FP16 inner operator
+cudaError_t launch_D_to_f16(const double *D, const int32_t *mat, const MatConst *mc, void *D16, int64_t epad,
+                            int64_t E, cudaStream_t s);
 
 // ------------------------------------------------------------------ context views (ns_api.cu)
 // What the allocation-free spring entry point needs from a context.

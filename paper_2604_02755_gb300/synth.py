@@ -326,3 +326,60 @@ def large_single_model(nt: int = 2000, seed: int = 2, n_springs: int = 150, dims
     w = band_limited_wave(seed, nt + 1, 0.005)
     return Workload("single large model 800x800x260 m, 5 m hex, 150 springs", m, two_layer_materials(0.02),
                     n_springs, 0.005, nt, w)
+
+
+def precision_form_model(nt: int = 3000, seed: int = 4, n_springs: int = 50, dims=(64, 64, 41),
+                         column=None) -> Workload:
+    """Precision-form model: 320x320x205 m at 5 m hexahedra (64x64x41 -> 1,007,616
+    quadratic tetrahedra, 1,381,203 nodes), three layers (0-20 m Vs 150, 20-60 m Vs 300,
+    bedrock Vs 600), vertices jittered by up to 10% of h, 50 springs per point,
+    dt = 0.005 s.  column=(i0, j0, ni, nj) cuts an ni x nj hexahedron column out of it."""
+    nx, ny, nz = dims
+    h = 5.0
+    lz = nz * h
+    if column is None:
+        m = kuhn_box(nx, ny, nz, nx * h, ny * h, lz, layer_depths=(20.0, 60.0), jitter=0.1, seed=seed)
+    else:
+        i0, j0, ni, nj = column
+        m = kuhn_box(ni, nj, nz, ni * h, nj * h, lz, layer_depths=(20.0, 60.0), jitter=0.1, seed=seed,
+                     x0=i0 * h, y0=j0 * h)
+    w = band_limited_wave(seed, nt + 1, 0.005)
+    return Workload("precision-form model 320x320x205 m, 5 m hex, three layers, 50 springs", m,
+                    three_layer_materials(0.02), n_springs, 0.005, nt, w)
+
+
+@dataclass
+class Ensemble:
+    """Members sharing one mesh: member m has its own materials (same layering) and input."""
+    name: str
+    mesh: Mesh
+    members: list            # [M] lists of material rows
+    waves: list              # [M] arrays [n_steps + 1, 3]
+    n_springs: int
+    dt: float
+    n_steps: int
+
+    def member(self, m: int) -> Workload:
+        return Workload("%s, member %d" % (self.name, m), self.mesh, self.members[m], self.n_springs, self.dt,
+                        self.n_steps, self.waves[m])
+
+
+def ensemble_members(M: int = 64, nt: int = 4000, seed: int = 3, n_springs: int = 50, dims=(40, 40, 21),
+                     h: float = 4.0, interface_depth: float = 40.0) -> Ensemble:
+    """Batched ensemble: M members on one shared mesh -- 160x160x84 m at 4 m hexahedra
+    (40x40x21 -> 201,600 quadratic tetrahedra, 282,123 nodes), soil over bedrock with a
+    planar interface 40 m deep, vertices jittered by up to 10% of h, 50 springs per point,
+    dt = 0.005 s.  Per member (seeded): soil Vs ~ U(100, 300) m/s, reference strain
+    ~ logU(1e-4, 1e-3), damping ratio ~ U(1, 5)% (Rayleigh, both layers), and an
+    independent band-limited input wave."""
+    nx, ny, nz = dims
+    m = kuhn_box(nx, ny, nz, nx * h, ny * h, nz * h, layer_depths=(interface_depth,), jitter=0.1, seed=seed)
+    u = uniform01(seed, 3 * M, stream=40).reshape(3, M)
+    vs = 100.0 + 200.0 * u[0]
+    gref = 10.0 ** (-4.0 + u[1])
+    hr = 0.01 + 0.04 * u[2]
+    members = [[soil(1700.0, float(vs[k]), float(gref[k]), 0.20, float(hr[k])),
+                soil(2000.0, 600.0, 1e-2, 0.20, float(hr[k]))] for k in range(M)]
+    waves = [band_limited_wave(seed * 1000 + 17 + k, nt + 1, 0.005) for k in range(M)]
+    return Ensemble("batched ensemble, %d members on 160x160x84 m at 4 m, 50 springs" % M, m, members, waves,
+                    n_springs, 0.005, nt)

@@ -115,7 +115,9 @@ def test_one_step_matches_oracle():
 @pytest.mark.parametrize("scatter,precision", [(B.NS_SCATTER_ATOMIC, B.NS_PREC_FP64),
                                                (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64),
                                                (B.NS_SCATTER_ATOMIC, B.NS_PREC_FP64_IR),
-                                               (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64_IR)])
+                                               (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64_IR),
+                                               (B.NS_SCATTER_ATOMIC, B.NS_PREC_FP64_IR16),
+                                               (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64_IR16)])
 def test_thirty_steps_surface_parity(scatter, precision):
     wl = small(dims=(4, 3, 3), nt=60)
     nsteps = 30
