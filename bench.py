@@ -180,15 +180,82 @@ def reference_arm(args):
     return 0
 
 
+def served(args, dd, rank, ws, local):
+    """Served ensemble: a Poisson trace of requests of uneven size submitted at their
+    arrival times to the serving runtime; value = all requests' element-steps over the
+    makespan (first arrival to last completion), with p50/p99 time to solution."""
+    from paper_2604_02755_gb300 import binding as B
+    trace = synth.served_trace(R=args.requests, step_scale=args.step_scale, seed=5 + rank)
+    prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
+    clk_path = os.path.join(tempfile.gettempdir(), "ns_clocks_%d.csv" % rank)
+    srv = B.Server(device=local, pinned_budget=int(args.pinned_gb * 1e9), max_active=args.max_active,
+                   quantum_steps=16)
+    dist.barrier(dd)
+    proc, fh = sample_clocks_start(clk_path)
+    t0 = time.perf_counter()
+    ids = []
+    for r in trace:
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(r.workload, r.n_steps, precision=prec, graphs=1))
+    st = [srv.wait(i, 3600.0) for i in ids]
+    res_bytes = 0
+    for i in ids:
+        res_bytes += sum(a.nbytes for a in srv.result(i).values())
+    wall = time.perf_counter() - t0
+    clocks = sample_clocks_stop(proc, fh, clk_path, local)
+    srv.close()
+    failed = [s_ for s_ in st if s_["state"] != B.NS_CASE_DONE]
+    work = float(sum(s_["elem_steps"] for s_ in st))
+    job_s, work_all = dist.reduce_time_and_work(dd, wall, work, device="cuda")
+    tts = np.array([s_["t_done"] - s_["t_submit"] for s_ in st])
+    wait = np.array([s_["t_admit"] - s_["t_submit"] for s_ in st])
+    if rank == 0:
+        sizes = [r.workload.mesh.n_elems for r in trace]
+        line = {"metric": "served elem-steps/s; time to solution p50/p99", "value": work_all / job_s,
+                "unit": "elem-steps/s", "n_gpus": ws, "steps": len(trace), "warmup": 0,
+                "ms_per_step": job_s / max(1, len(trace)) * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "served ensemble: %d requests, Poisson arrivals 4/s, %d-%d elements, "
+                                       "20-150 springs, steps U[1000,4000] x %g" %
+                                       (len(trace), min(sizes), max(sizes), args.step_scale),
+                           "max_active": args.max_active, "solver": args.solver, "graphs": 1,
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "time_to_solution_s": {"p50": float(np.percentile(tts, 50)), "p99": float(np.percentile(tts, 99)),
+                                       "max": float(tts.max())},
+                "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "max": float(wait.max())},
+                "streamed_requests": int(sum(s_["streamed"] for s_ in st)), "failed": len(failed),
+                "e2e": {"value": work_all / job_s, "unit": "elem-steps/s",
+                        "h2d_bytes_per_step": int(sum(r.workload.mesh.xyz.nbytes + r.workload.mesh.conn.nbytes +
+                                                      r.workload.wave.nbytes for r in trace) / len(trace)),
+                        "d2h_bytes_per_step": int(res_bytes / len(trace))},
+                "gpu_launches": int(sum(s_["kernel_launches"] for s_ in st)), "clocks": clocks,
+                "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    dist.finalize(dd)
+    return 0 if not failed else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "precision", "tiny"],
+    ap.add_argument("--workload", default="large", choices=["large", "precision", "ensemble", "served", "tiny"],
                     help="large: the single large model (default); precision: the 1M-element three-layer "
-                         "precision-form model; tiny: the 3,600-element two-layer case")
+                         "precision-form model; ensemble: --members cases on a shared 201,600-element mesh "
+                         "advanced together; tiny: the 3,600-element two-layer case")
+    ap.add_argument("--members", type=int, default=64, help="members of the ensemble workload")
+    ap.add_argument("--requests", type=int, default=12, help="requests of the served trace")
+    ap.add_argument("--step-scale", type=float, default=0.01,
+                    help="served trace: fraction of the 1000-4000 steps each request runs")
+    ap.add_argument("--max-active", type=int, default=4, help="served: requests in flight together")
+    ap.add_argument("--pinned-gb", type=float, default=32.0, help="served: pinned host budget for streamed state")
+    ap.add_argument("--graphs", type=int, default=-1, choices=[-1, 0, 1],
+                    help="replay solver iterations as captured CUDA graphs (1) or launch them one by one (0, "
+                         "keeps per-kernel times); default: 1 for the launch-bound tiny case, else 0")
     ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                     help="hexahedra of a smaller cut of the large model (same spacing, interface and springs), "
                          "used for profiling captures that must stay small")
@@ -216,8 +283,17 @@ def main():
         nsbuild.build()
     dist.barrier(dd)
     nsbuild.build()
+    if args.workload == "served":
+        return served(args, dd, rank, ws, local)
 
-    if args.workload == "tiny":
+    n_total = args.warmup + 2 * args.steps + 2
+    ens = None
+    if args.workload == "ensemble":
+        ens = synth.ensemble_members(M=args.members, nt=max(n_total, 400),
+                                     dims=tuple(args.dims) if args.dims else (40, 40, 21))
+        wl = ens.member(0)
+        wl.name = ens.name
+    elif args.workload == "tiny":
         wl = synth.tiny_two_layer()
     elif args.workload == "precision":
         wl = synth.precision_form_model(dims=tuple(args.dims) if args.dims else (64, 64, 41))
@@ -226,12 +302,15 @@ def main():
         wl.name = "cut of the single large model: %dx%dx%d hexahedra at 5 m, 150 springs" % tuple(args.dims)
     else:
         wl = synth.large_single_model()
-    E = wl.mesh.n_elems
-    n_total = args.warmup + 2 * args.steps + 2
-    wave = synth.band_limited_wave(2, max(n_total + 1, 400), wl.dt)
-    wl.wave = wave
+    M = len(ens.members) if ens else 1
+    E = wl.mesh.n_elems * M
+    if ens is None:
+        wave = synth.band_limited_wave(2, max(n_total + 1, 400), wl.dt)
+        wl.wave = wave
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
-    sim = B.Simulation(wl, device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec)
+    graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
+    kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs)
+    sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
     B.ns_reset_stats(sim.ctx)
     st0 = sim.stats()
@@ -270,12 +349,17 @@ def main():
 
     # end to end through the public API: input record from host, advance, surface read-back to host
     t0 = time.perf_counter()
-    B.ns_set_ground_motion(sim.ctx, wave, wl.dt)
+    if ens:
+        for m in range(M):
+            B.ns_set_member_ground_motion(sim.ctx, m, ens.waves[m], wl.dt)
+        h2d = sum(w.nbytes for w in ens.waves) / args.steps
+    else:
+        B.ns_set_ground_motion(sim.ctx, wave, wl.dt)
+        h2d = wave.nbytes / args.steps
     sim.advance(args.steps)
     s = sim.surface(st["steps"] + 1, args.steps)
     e2e_s = time.perf_counter() - t0
     e2e_s, e2e_work = dist.reduce_time_and_work(dd, e2e_s, float(E * args.steps), device="cuda")
-    h2d = wave.nbytes / args.steps
     d2h = sum(a.nbytes for a in s.values()) / args.steps
     e2e = {"value": e2e_work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     phases = {k: st[k] / args.steps for k in ("ms_rhs", "ms_jacobi", "ms_solve", "ms_newmark", "ms_springs")}
@@ -298,7 +382,7 @@ def main():
         budget = (E - stream_elems) * per_elem
         ring = args.ring_depth
         sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
-                           ring_depth=ring, precision=prec)
+                           ring_depth=ring, precision=prec, graphs=graphs)
         sim.advance(1)
         B.ns_reset_stats(sim.ctx)
         h0 = sim.stats()
@@ -331,13 +415,13 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": job_s / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl.name, "elements": E, "nodes": wl.mesh.n_nodes,
+                "config": {"workload": wl.name, "elements": E, "nodes": wl.mesh.n_nodes * M, "members": M,
                            "springs_per_point": wl.n_springs, "dt": wl.dt, "cg_tol": 1e-8,
                            "state": "resident in HBM", "l2": l2_note,
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
-                "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver,
+                "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
                 "state_stream": stream}
         print(json.dumps(line), flush=True)
     dist.finalize(dd)

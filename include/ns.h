@@ -78,6 +78,13 @@ typedef struct {
   int32_t inner_max_iter;      /* NS_PREC_FP64_IR: inner FP32 CG iterations per preconditioner call */
   double inner_tol;            /* NS_PREC_FP64_IR: inner relative residual target */
   double wait_timeout_s;       /* bound on each host wait for the device */
+  int32_t graphs;              /* 1: each outer iteration of the flexible solver (inner FP32 solve
+                                  included) and each batch of plain CG iterations is captured once
+                                  as a CUDA graph and replayed; per-kernel times of the operators
+                                  inside are then not recorded (ns_stats ms_ebe32 stays 0) */
+  int32_t stage_elements;      /* 1: the FP32 inner operator stages each 256-element tile of element
+                                  data in shared memory with bulk copies (atomic scatter, one member);
+                                  0: per-thread loads */
 } ns_config;
 
 /* Material of one element group (Sec. 2.1; parameters of the readings):
@@ -140,6 +147,27 @@ int ns_set_boundary(ns_ctx *ctx, int64_t n_faces, const int32_t *faces, const in
  * integral from zero; beyond the last sample the acceleration is zero.
  * May be called again to replace the record (steps already taken stay). */
 int ns_set_ground_motion(ns_ctx *ctx, int64_t n_samples, double dt, const double *acc);
+
+/* Batched ensemble (many cases of the method advanced together; Sec. 2.3 runs many
+ * cases, and Table 1's throughput is per case).  Declares that the uploaded mesh is the
+ * disjoint union of M independent members: member m owns elements
+ * [elem_off[m], elem_off[m+1]) and nodes [node_off[m], node_off[m+1]) (elem_off[0] =
+ * node_off[0] = 0, elem_off[M] = n_elems, node_off[M] = n_nodes, every range non-empty);
+ * no element may use a node of another member (NS_ERR_BAD_MESH) and the boundary faces
+ * must be ordered by member.  Members take their materials through their elements'
+ * material ids (one table for all), their input from ns_set_member_ground_motion, and
+ * each solves its own CG (own scalars, converged against its own ||b||); every kernel
+ * launch of a step covers all members.  Call after ns_upload_mesh and ns_set_boundary and
+ * before ns_set_ground_motion, once; needs NS_SCATTER_ATOMIC.  Arrays are copied. */
+int ns_set_members(ns_ctx *ctx, int32_t M, const int64_t *elem_off, const int64_t *node_off);
+
+/* Input acceleration of one member (same layout, dt and number of samples as the
+ * record given to ns_set_ground_motion, which every member starts with). */
+int ns_set_member_ground_motion(ns_ctx *ctx, int32_t member, int64_t n_samples, double dt, const double *acc);
+
+/* Outer CG iterations of each member at the last step into iters[M] (M = the context's
+ * member count, 1 without ns_set_members). */
+int ns_get_member_iters(ns_ctx *ctx, int32_t M, int32_t *iters);
 
 /* Advance nsteps time steps.  Returns after the device work of all steps is
  * complete.  On NS_ERR_NOT_CONVERGED the failing step is not applied and

@@ -38,7 +38,7 @@ class ns_config(C.Structure):
                 ("ring_depth", C.c_int32), ("device_state_budget", C.c_int64), ("rayleigh_f1", C.c_double),
                 ("rayleigh_f2", C.c_double), ("surface_ring_steps", C.c_int64), ("device", C.c_int32),
                 ("timing", C.c_int32), ("inner_max_iter", C.c_int32), ("inner_tol", C.c_double),
-                ("wait_timeout_s", C.c_double)]
+                ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32)]
 
 
 class ns_material(C.Structure):
@@ -61,12 +61,39 @@ class ns_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ns_server_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("device_budget", C.c_int64), ("pinned_budget", C.c_int64),
+                ("max_active", C.c_int32), ("quantum_steps", C.c_int32)]
+
+
+class ns_case(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("xyz", C.c_void_p), ("n_elems", C.c_int64), ("conn", C.c_void_p),
+                ("mat", C.c_void_p), ("n_mat", C.c_int32), ("mats", C.c_void_p), ("n_faces", C.c_int64),
+                ("faces", C.c_void_p), ("face_elem", C.c_void_p), ("face_kind", C.c_void_p), ("n_surf", C.c_int64),
+                ("surf", C.c_void_p), ("n_samples", C.c_int64), ("acc", C.c_void_p), ("cfg", ns_config),
+                ("n_steps", C.c_int64)]
+
+
+class ns_case_stats(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("streamed", C.c_int32), ("pad", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("device_bytes", C.c_int64), ("state_bytes", C.c_int64), ("elem_steps", C.c_int64),
+                ("ms_device", C.c_double), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+NS_CASE_QUEUED, NS_CASE_RUNNING, NS_CASE_DONE, NS_CASE_FAILED = 0, 1, 2, 3
+
 EXPORTED = ["ns_config_default", "ns_create", "ns_upload_mesh", "ns_set_materials", "ns_set_boundary",
             "ns_set_ground_motion", "ns_advance", "ns_read_surface", "ns_read_state", "ns_write_state",
             "ns_read_nodal", "ns_write_nodal", "ns_apply_operator", "ns_spring_points", "ns_get_stats",
             "ns_reset_stats", "ns_checkpoint_size", "ns_checkpoint", "ns_restore", "ns_destroy", "ns_last_error",
             "ns_spring_directions", "ns_colour_elements", "ns_state_bytes", "ns_spring_points_noalloc",
-            "ns_spring_points_noalloc_capacity"]
+            "ns_spring_points_noalloc_capacity", "ns_set_members", "ns_set_member_ground_motion",
+            "ns_get_member_iters", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
+            "ns_server_wait", "ns_server_result", "ns_server_release", "ns_server_destroy"]
 
 _lib = None
 
@@ -107,6 +134,17 @@ def lib():
             "ns_state_bytes": ([i64, i32], i64),
             "ns_spring_points_noalloc": ([vp, i64, vp, vp, vp, vp, vp], C.c_int),
             "ns_spring_points_noalloc_capacity": ([i32], i64),
+            "ns_set_members": ([vp, i32, vp, vp], C.c_int),
+            "ns_set_member_ground_motion": ([vp, i32, i64, d, vp], C.c_int),
+            "ns_get_member_iters": ([vp, i32, vp], C.c_int),
+            "ns_case_bytes": ([C.POINTER(ns_case), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
+            "ns_server_create": ([C.POINTER(vp), C.POINTER(ns_server_config)], C.c_int),
+            "ns_server_submit": ([vp, C.POINTER(ns_case), C.POINTER(i64)], C.c_int),
+            "ns_server_status": ([vp, i64, C.POINTER(ns_case_stats)], C.c_int),
+            "ns_server_wait": ([vp, i64, d], C.c_int),
+            "ns_server_result": ([vp, i64, vp, vp, vp], C.c_int),
+            "ns_server_release": ([vp, i64], C.c_int),
+            "ns_server_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -171,6 +209,22 @@ def ns_set_boundary(ctx, faces, face_elem, face_kind, surf):
 def ns_set_ground_motion(ctx, acc, dt):
     acc = _f64(acc).reshape(-1, 3)
     _check(ctx, lib().ns_set_ground_motion(ctx, acc.shape[0], float(dt), _p(acc)))
+
+
+def ns_set_members(ctx, elem_off, node_off):
+    eo = np.ascontiguousarray(elem_off, np.int64); no = np.ascontiguousarray(node_off, np.int64)
+    _check(ctx, lib().ns_set_members(ctx, eo.shape[0] - 1, _p(eo), _p(no)))
+
+
+def ns_set_member_ground_motion(ctx, member, acc, dt):
+    acc = _f64(acc).reshape(-1, 3)
+    _check(ctx, lib().ns_set_member_ground_motion(ctx, int(member), acc.shape[0], float(dt), _p(acc)))
+
+
+def ns_get_member_iters(ctx, M):
+    out = np.zeros(M, np.int32)
+    _check(ctx, lib().ns_get_member_iters(ctx, int(M), _p(out)))
+    return out
 
 
 def ns_advance(ctx, nsteps):
@@ -349,3 +403,142 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class BatchSimulation(Simulation):
+    """Members advanced together in one context (synth.Ensemble-like: one mesh shared by
+    all members, per-member materials and waves).  The context holds the disjoint union
+    of M copies of the mesh (synth.union_of_copies); member m's surface response is
+    rows [m * n_surf, (m + 1) * n_surf) of the context's surface record."""
+
+    def __init__(self, ens, **cfg_overrides):
+        from . import synth
+        M = len(ens.members)
+        cfg = dict(n_springs=ens.n_springs, dt=ens.dt)
+        cfg.update(cfg_overrides)
+        self.cfg = ns_config_default(**cfg)
+        self.ctx = ns_create(self.cfg)
+        self.M = M
+        U = synth.union_of_copies(ens.mesh, M, n_materials=len(ens.members[0]))
+        self.n_nodes, self.n_elems, self.n_surf = U.mesh.n_nodes, U.mesh.n_elems, int(U.mesh.surf.shape[0])
+        self.member_surf = int(ens.mesh.surf.shape[0])
+        self.S = ens.n_springs
+        try:
+            ns_upload_mesh(self.ctx, U.mesh.xyz, U.mesh.conn, U.mesh.mat)
+            ns_set_materials(self.ctx, [row for mats in ens.members for row in mats])
+            ns_set_boundary(self.ctx, U.mesh.faces, U.mesh.face_elem, U.mesh.face_kind, U.mesh.surf)
+            ns_set_members(self.ctx, U.elem_off, U.node_off)
+            ns_set_ground_motion(self.ctx, ens.waves[0], ens.dt)
+            for m in range(M):
+                ns_set_member_ground_motion(self.ctx, m, ens.waves[m], ens.dt)
+        except Exception:
+            self.close()
+            raise
+
+    def member_surface(self, m, step0, n, fields=("u", "v", "a")):
+        s = self.surface(step0, n, fields)
+        k = self.member_surf
+        return {f: a[:, m * k:(m + 1) * k] for f, a in s.items()}
+
+    def member_iters(self):
+        return ns_get_member_iters(self.ctx, self.M)
+
+
+# ------------------------------------------------------------------ served ensemble (include/ns_server.h)
+
+def _case(wl, n_steps, keep, **cfg_overrides):
+    """ns_case for a workload (synth.Workload-like); `keep` collects the arrays it points to."""
+    m = wl.mesh
+    arrs = dict(xyz=_f64(m.xyz), conn=_i32(m.conn), mat=_i32(m.mat), faces=_i32(m.faces).reshape(-1, 6),
+                face_elem=_i32(m.face_elem), face_kind=_i32(m.face_kind), surf=_i32(m.surf),
+                acc=_f64(wl.wave).reshape(-1, 3))
+    mats = (ns_material * len(wl.materials))()
+    for i, r in enumerate(wl.materials):
+        mats[i] = ns_material(r["rho"], r["vs"], r["vp"], r["gamma_ref"], r["h_max"], r["rayleigh_h"])
+    keep.append((arrs, mats))
+    cfg = dict(n_springs=wl.n_springs, dt=wl.dt)
+    cfg.update(cfg_overrides)
+    return ns_case(n_nodes=arrs["xyz"].shape[0], xyz=_p(arrs["xyz"]), n_elems=arrs["conn"].shape[0],
+                   conn=_p(arrs["conn"]), mat=_p(arrs["mat"]), n_mat=len(wl.materials),
+                   mats=C.cast(mats, C.c_void_p), n_faces=arrs["faces"].shape[0], faces=_p(arrs["faces"]),
+                   face_elem=_p(arrs["face_elem"]), face_kind=_p(arrs["face_kind"]), n_surf=arrs["surf"].shape[0],
+                   surf=_p(arrs["surf"]), n_samples=arrs["acc"].shape[0], acc=_p(arrs["acc"]),
+                   cfg=ns_config_default(**cfg), n_steps=int(n_steps))
+
+
+def ns_case_bytes(wl, n_steps, **cfg_overrides):
+    keep = []
+    c = _case(wl, n_steps, keep, **cfg_overrides)
+    dev, st, dstr = C.c_int64(), C.c_int64(), C.c_int64()
+    rc = lib().ns_case_bytes(C.byref(c), C.byref(dev), C.byref(st), C.byref(dstr))
+    if rc != NS_OK:
+        raise NsError(rc, "invalid case")
+    return dev.value, st.value, dstr.value
+
+
+class Server:
+    """Served ensemble: cases queued first come first served and admitted into concurrent
+    slots as device / pinned-host memory allows (include/ns_server.h)."""
+
+    def __init__(self, device=0, device_budget=None, pinned_budget=0, max_active=4, quantum_steps=16):
+        if device_budget is None:
+            import torch
+            free, _ = torch.cuda.mem_get_info(device)
+            device_budget = int(free * 0.85)
+        cfg = ns_server_config(device=device, device_budget=int(device_budget), pinned_budget=int(pinned_budget),
+                               max_active=int(max_active), quantum_steps=int(quantum_steps))
+        h = C.c_void_p()
+        rc = lib().ns_server_create(C.byref(h), C.byref(cfg))
+        if rc != NS_OK:
+            raise NsError(rc, "server creation failed")
+        self.h = h
+        self.n_surf = {}
+        self.n_steps = {}
+
+    def submit(self, wl, n_steps, **cfg_overrides):
+        keep = []
+        c = _case(wl, n_steps, keep, **cfg_overrides)
+        i = C.c_int64()
+        rc = lib().ns_server_submit(self.h, C.byref(c), C.byref(i))
+        if rc != NS_OK:
+            raise NsError(rc, "submission refused")
+        self.n_surf[i.value] = int(wl.mesh.surf.shape[0])
+        self.n_steps[i.value] = int(n_steps)
+        return i.value
+
+    def status(self, i):
+        st = ns_case_stats()
+        rc = lib().ns_server_status(self.h, int(i), C.byref(st))
+        if rc != NS_OK:
+            raise NsError(rc, "unknown case")
+        return st.as_dict()
+
+    def wait(self, i, timeout_s=3600.0):
+        rc = lib().ns_server_wait(self.h, int(i), float(timeout_s))
+        if rc != NS_OK:
+            raise NsError(rc, "wait failed")
+        return self.status(i)
+
+    def result(self, i, fields=("u", "v", "a")):
+        shape = (self.n_steps[i], self.n_surf[i], 3)
+        out = {k: np.zeros(shape) for k in fields}
+        rc = lib().ns_server_result(self.h, int(i), _p(out.get("u")), _p(out.get("v")), _p(out.get("a")))
+        if rc != NS_OK:
+            raise NsError(rc, "case %d has no result" % i)
+        return out
+
+    def release(self, i):
+        rc = lib().ns_server_release(self.h, int(i))
+        if rc != NS_OK:
+            raise NsError(rc, "release failed")
+
+    def close(self):
+        if self.h:
+            lib().ns_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libns.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 CU_SOURCES = ["k_ebe.cu", "k_vec.cu", "k_spring.cu", "ns_api.cu", "ns_noalloc.cu"]
-CPP_SOURCES = ["ns_host.cpp"]
+CPP_SOURCES = ["ns_host.cpp", "ns_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +31,8 @@ def _nvcc() -> str:
 
 
 def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "ns.h"), __file__]
+    files = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+             + [__file__])
     return max(os.path.getmtime(f) for f in files if os.path.isfile(f))
 
 
@@ -47,7 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         out = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc] + ARCH + common + ["-c", os.path.join(CSRC, src), "-o", out]
         if src.endswith(".cpp"):
-            cmd = [nvcc] + common + ["-x", "c++", "-c", os.path.join(CSRC, src), "-o", out]
+            cmd = [nvcc] + common + ["-Xcompiler", "-pthread", "-x", "c++", "-c", os.path.join(CSRC, src), "-o", out]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("compilation of %s failed:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
@@ -59,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-Xcompiler", "-pthread", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link of libns.so failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

@@ -2,6 +2,8 @@
 // geometry set-up, the operator y = mM M xm + mK M xk + kK K xk applied on the fly
 // (K_e = sum_q w_q B^T D_q B, Eq. 2), Lysmer dashpot faces, block-Jacobi diagonal
 // blocks and integration-point strains for the multi-spring update.
+#include <atomic>
+
 #include "kern_common.cuh"
 
 namespace ns {
@@ -118,15 +120,16 @@ __device__ __forceinline__ float dload(const __half2 *__restrict__ D, int64_t ep
   return (m & 1) ? __high2float(h) : __low2float(h);
 }
 
-// Stress of integration point Q: sig = w D_Q eps_Q(x).
-template <typename T, int Q, typename TD>
-__device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], const T g[4][3],
-                                             const TD *__restrict__ D, int64_t epad, int64_t e, T w, T sig[6]) {
+// Stress of integration point Q: sig = w D_Q eps_Q(x); dl(m) gives entry m of the
+// element's [84] point-major tangent.
+template <typename T, int Q, typename DL>
+__device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], const T g[4][3], const DL &dl, T w,
+                                             T sig[6]) {
   T H[3][3], eps[6], d[21];
   point_grad<T, Q>(x, P, g, H);
   voigt_strain(H, eps);
 #pragma unroll
-  for (int k = 0; k < 21; ++k) d[k] = dload(D, epad, e, Q * 21 + k);
+  for (int k = 0; k < 21; ++k) d[k] = (T)dl(Q * 21 + k);
   sig[0] = w * (d[0] * eps[0] + d[1] * eps[1] + d[2] * eps[2] + d[3] * eps[3] + d[4] * eps[4] + d[5] * eps[5]);
   sig[1] = w * (d[1] * eps[0] + d[6] * eps[1] + d[7] * eps[2] + d[8] * eps[3] + d[9] * eps[4] + d[10] * eps[5]);
   sig[2] = w * (d[2] * eps[0] + d[7] * eps[1] + d[11] * eps[2] + d[12] * eps[3] + d[13] * eps[4] + d[14] * eps[5]);
@@ -138,77 +141,100 @@ __device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], 
 // Operator kernel, one thread per element.  Phases keep the register footprint small:
 // (1) gather x, stresses at the four points; (2) nodal forces B^T sig; (3) consistent mass
 // one displacement component at a time (re-gathered from cache); (4) scatter.
+// One element of the operator: y_e = (kK K_e + mK M_e) x_e + mM M_e xm_e scattered into y
+// (nodes nd, material mt, barycentric gradients g, volume vol, tangent entries dl(m));
+// returns x_e . y_e when DOT.
+template <typename T, int VS, bool HAS_XM, bool ATOMIC, bool DOT, typename DL>
+__device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][3], T vol, const DL &dl,
+                                         const OpCoef *__restrict__ op, const T *__restrict__ xm,
+                                         const T *__restrict__ xk, T *y) {
+  const T cK = (T)op->kK[mt], cMk = (T)op->mK[mt];
+  const T cMm = HAS_XM ? (T)op->mM[mt] : (T)0;
+  T ye[10][3];
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ye[a][r] = (T)0;
+  if (cK != (T)0) {
+    T sig[4][6];
+    {
+      T x[10][3], P[4][3];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) load_node<VS>(xk, nd[a], x[a]);
+      compute_P(x, P);
+      const T w = cK * vol * (T)0.25;
+      point_stress<T, 0>(x, P, g, dl, w, sig[0]);
+      point_stress<T, 1>(x, P, g, dl, w, sig[1]);
+      point_stress<T, 2>(x, P, g, dl, w, sig[2]);
+      point_stress<T, 3>(x, P, g, dl, w, sig[3]);
+    }
+    point_force<T, 0>(sig[0], g, ye);
+    point_force<T, 1>(sig[1], g, ye);
+    point_force<T, 2>(sig[2], g, ye);
+    point_force<T, 3>(sig[3], g, ye);
+  }
+  if (cMk != (T)0 || cMm != (T)0) {
+    const T c = vol * (T)(1.0 / 420.0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      T w[10];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) {
+        w[a] = cMk * ldg(xk + VS * (int64_t)nd[a] + r);
+        if (HAS_XM) w[a] += cMm * ldg(xm + VS * (int64_t)nd[a] + r);
+      }
+      mass_apply_1(w, c, ye, r);
+    }
+  }
+  T ld = (T)0;
+  if (DOT) {
+    // element-local x_e . y_e in the operator's precision (block sums in FP64)
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+      T xa[3];
+      load_node<VS>(xk, nd[a], xa);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) ld += xa[r] * ye[a][r];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 10; ++a) add_node<VS, ATOMIC>(y, nd[a], ye[a]);
+  return ld;
+}
+
+// Operator kernel, one thread per element.  Phases keep the register footprint small:
+// (1) gather x, stresses at the four points; (2) nodal forces B^T sig; (3) consistent mass
+// one displacement component at a time (re-gathered from cache); (4) scatter.
+// FP32 variants are held to two resident blocks per SM (128 registers): the gathers and
+// the tangent loads of more warps in flight outweigh the few spilled registers.
 template <typename T, typename TD, int VS, bool HAS_XM, bool ATOMIC, bool DOT>
-__global__ void __launch_bounds__(kBlock) k_ebe(int64_t e0, int64_t e1, const int32_t *__restrict__ ids,
-                                                const int32_t *__restrict__ conn, const T *__restrict__ geom,
-                                                const int32_t *__restrict__ mat, const TD *__restrict__ D,
-                                                int64_t epad, const OpCoef *__restrict__ op,
-                                                const T *__restrict__ xm, const T *__restrict__ xk, T *y,
-                                                double *dot, const int32_t *skip) {
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
+    k_ebe(int64_t e0, int64_t e1, const int32_t *__restrict__ ids, const int32_t *__restrict__ conn,
+          const T *__restrict__ geom, const int32_t *__restrict__ mat, const TD *__restrict__ D, int64_t epad,
+          const OpCoef *__restrict__ op, const T *__restrict__ xm, const T *__restrict__ xk, T *y, double *dot,
+          const int32_t *skip, const Seg *seg) {
+  int64_t i, end;
+  if (seg) {  // members: this block's slice of one member's elements, that member's skip flag
+    const Seg sg = seg[blockIdx.x];
+    i = sg.a0 + threadIdx.x;
+    end = sg.a1;
+    if (skip) skip += (int64_t)sg.m * kScStride;
+  } else {
+    i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    end = e1;
+  }
   if (skip && *skip) return;
-  const int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool active = i < e1;
   double mydot = 0.0;
-  if (active) {
+  if (i < end) {
     const int64_t e = ids ? (int64_t)ids[i] : i;
     int nd[10];
 #pragma unroll
     for (int a = 0; a < 10; ++a) nd[a] = ldg(conn + a * epad + e);
     const int mt = ldg(mat + e);
-    const T cK = (T)op->kK[mt], cMk = (T)op->mK[mt];
-    const T cMm = HAS_XM ? (T)op->mM[mt] : (T)0;
     T g[4][3], vol;
     load_grads(geom, epad, e, g, vol);
-    T ye[10][3];
-#pragma unroll
-    for (int a = 0; a < 10; ++a)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) ye[a][r] = (T)0;
-    if (cK != (T)0) {
-      T sig[4][6];
-      {
-        T x[10][3], P[4][3];
-#pragma unroll
-        for (int a = 0; a < 10; ++a) load_node<VS>(xk, nd[a], x[a]);
-        compute_P(x, P);
-        const T w = cK * vol * (T)0.25;
-        point_stress<T, 0>(x, P, g, D, epad, e, w, sig[0]);
-        point_stress<T, 1>(x, P, g, D, epad, e, w, sig[1]);
-        point_stress<T, 2>(x, P, g, D, epad, e, w, sig[2]);
-        point_stress<T, 3>(x, P, g, D, epad, e, w, sig[3]);
-      }
-      point_force<T, 0>(sig[0], g, ye);
-      point_force<T, 1>(sig[1], g, ye);
-      point_force<T, 2>(sig[2], g, ye);
-      point_force<T, 3>(sig[3], g, ye);
-    }
-    if (cMk != (T)0 || cMm != (T)0) {
-      const T c = vol * (T)(1.0 / 420.0);
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        T w[10];
-#pragma unroll
-        for (int a = 0; a < 10; ++a) {
-          w[a] = cMk * ldg(xk + VS * (int64_t)nd[a] + r);
-          if (HAS_XM) w[a] += cMm * ldg(xm + VS * (int64_t)nd[a] + r);
-        }
-        mass_apply_1(w, c, ye, r);
-      }
-    }
-    if (DOT) {
-      // element-local x_e . y_e in the operator's precision; block sums in FP64
-      T ld = (T)0;
-#pragma unroll
-      for (int a = 0; a < 10; ++a) {
-        T xa[3];
-        load_node<VS>(xk, nd[a], xa);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) ld += xa[r] * ye[a][r];
-      }
-      mydot = (double)ld;
-    }
-#pragma unroll
-    for (int a = 0; a < 10; ++a) add_node<VS, ATOMIC>(y, nd[a], ye[a]);
+    const auto dl = [&](int k) { return dload(D, epad, e, k); };
+    mydot = (double)ebe_element<T, VS, HAS_XM, ATOMIC, DOT>(nd, mt, g, vol, dl, op, xm, xk, y);
   }
   if (DOT) {
     double s = block_sum(mydot);
@@ -216,15 +242,131 @@ __global__ void __launch_bounds__(kBlock) k_ebe(int64_t e0, int64_t e1, const in
   }
 }
 
+// ------------------------------------------------------------------ staged FP32 operator
+// One block = one tile of kTile consecutive elements.  One thread issues bulk copies
+// (cp.async.bulk: the TMA engine's linear form) of the tile's slice of every element row
+// -- tangent D (84 rows of FP32, or 42 rows of FP16 pairs), FP32 geometry (10 rows),
+// connectivity (10 rows), material (1 row) -- into shared memory, all completing on one
+// mbarrier; the threads then compute from shared memory.  The whole tile (~107 KB for
+// FP32 D) is in flight at once, where the direct kernel keeps only the loads its
+// registers can hold.  Rows start at 256-byte boundaries (epad is a multiple of 64 and
+// tiles are 1 KB), and a row copy never reaches past epad.
+constexpr int kTile = kBlock;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase 0 (~ a second at most); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, 0)) return true;
+  return false;
+}
+
+template <typename TD>
+__host__ __device__ constexpr int staged_d_rows() {
+  return std::is_same<TD, float>::value ? 84 : 42;
+}
+template <typename TD>
+__host__ __device__ constexpr size_t staged_smem() {
+  return (size_t)(staged_d_rows<TD>() + 21) * kTile * 4 + 16;
+}
+
+__device__ __forceinline__ float dload_s(const float *Ds, int t, int m) { return Ds[m * kTile + t]; }
+__device__ __forceinline__ float dload_s(const __half2 *Ds, int t, int m) {
+  const __half2 h = Ds[(m >> 1) * kTile + t];
+  return (m & 1) ? __high2float(h) : __low2float(h);
+}
+
+template <typename TD, bool DOT>
+__global__ void __launch_bounds__(kTile, 2)
+    k_ebe32_staged(int64_t E, int64_t epad, const int32_t *__restrict__ conn, const float *__restrict__ geom,
+                   const int32_t *__restrict__ mat, const TD *__restrict__ D, const OpCoef *__restrict__ op,
+                   const float *__restrict__ xk, float *y, double *dot, const int32_t *skip, int32_t *err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int DR = staged_d_rows<TD>();
+  TD *Ds = reinterpret_cast<TD *>(smem);                     // [DR][kTile]
+  float *Gs = reinterpret_cast<float *>(smem + (size_t)DR * kTile * 4);  // [10][kTile]
+  int32_t *Cs = reinterpret_cast<int32_t *>(Gs + 10 * kTile);          // [10][kTile]
+  int32_t *Ms = Cs + 10 * kTile;                                       // [kTile]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(Ms + kTile);
+  if (skip && *skip) return;
+  const int t = threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * kTile;
+  const int64_t rowlen = (epad - e0) < kTile ? (epad - e0) : kTile;  // a multiple of 64 elements
+  const uint32_t rb = (uint32_t)(rowlen * 4);
+  if (t == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (t == 0) {
+    mbar_expect_tx(bar, rb * (uint32_t)(DR + 21));
+    for (int r = 0; r < DR; ++r) bulk_g2s(Ds + r * kTile, D + r * epad + e0, rb, bar);
+    for (int r = 0; r < 10; ++r) bulk_g2s(Gs + r * kTile, geom + r * epad + e0, rb, bar);
+    for (int r = 0; r < 10; ++r) bulk_g2s(Cs + r * kTile, conn + r * epad + e0, rb, bar);
+    bulk_g2s(Ms, mat + e0, rb, bar);
+  }
+  if (!mbar_wait_bounded(bar)) {
+    // the copies did not complete: report, wait (bounded) for them once more, leave
+    if (t == 0) atomicExch(err, 1);
+    mbar_wait_bounded(bar);
+    return;
+  }
+  double mydot = 0.0;
+  const int64_t e = e0 + t;
+  if (e < E) {
+    int nd[10];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) nd[a] = Cs[a * kTile + t];
+    const int mt = Ms[t];
+    float g[4][3], vol;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[k + 1][c] = Gs[(3 * k + c) * kTile + t];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+    vol = Gs[9 * kTile + t];
+    const auto dl = [&](int k) { return dload_s(Ds, t, k); };
+    mydot = (double)ebe_element<float, 4, false, true, DOT>(nd, mt, g, vol, dl, op, nullptr, xk, y);
+  }
+  if (DOT) {
+    double s = block_sum(mydot);
+    if (t == 0) dot[blockIdx.x] = s;
+  }
+}
+
 template <typename T, typename TD, int VS, bool HAS_XM>
 static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, const OpCoef *op, const T *xm,
                                 const T *xk, T *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic,
-                                double *dot, const int32_t *skip, cudaStream_t s) {
-  if (e1 <= e0) return cudaSuccess;
-  unsigned nb = (unsigned)((e1 - e0 + kBlock - 1) / kBlock);
+                                double *dot, const int32_t *skip, cudaStream_t s, const SegList &sg) {
+  if (!sg.seg && e1 <= e0) return cudaSuccess;
+  const unsigned nb = sg.seg ? (unsigned)sg.n : (unsigned)((e1 - e0 + kBlock - 1) / kBlock);
 #define NS_EBE_LAUNCH(A, DT)                                                                                  \
   k_ebe<T, TD, VS, HAS_XM, A, DT><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, \
-                                                     dot, skip)
+                                                     dot, skip, sg.seg)
   if (atomic) {
     if (dot)
       NS_EBE_LAUNCH(true, true);
@@ -242,23 +384,54 @@ static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, co
 
 cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
-                         const int32_t *skip, cudaStream_t s) {
-  if (xm) return ebe_dispatch<double, double, 3, true>(m, D, m.geom, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s);
-  return ebe_dispatch<double, double, 3, false>(m, D, m.geom, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
+                         const int32_t *skip, cudaStream_t s, SegList sg) {
+  if (xm)
+    return ebe_dispatch<double, double, 3, true>(m, D, m.geom, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s, sg);
+  return ebe_dispatch<double, double, 3, false>(m, D, m.geom, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s,
+                                                sg);
+}
+
+template <typename TD>
+static cudaError_t staged_dispatch(const DevMesh &m, const TD *D, const OpCoef *op, const float *xk, float *y,
+                                   double *dot, const int32_t *skip, cudaStream_t s) {
+  constexpr size_t smem = staged_smem<TD>();
+  // the shared-memory opt-in is a per-device attribute of each instantiation
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load() & bit)) {
+    cudaFuncSetAttribute(k_ebe32_staged<TD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_ebe32_staged<TD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done.fetch_or(bit);
+  }
+  const unsigned nb = (unsigned)((m.E + kTile - 1) / kTile);
+  if (dot)
+    k_ebe32_staged<TD, true><<<nb, kTile, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip,
+                                                    m.kerr);
+  else
+    k_ebe32_staged<TD, false><<<nb, kTile, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip,
+                                                     m.kerr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s) {
+                         cudaStream_t s, SegList sg, bool staged) {
+  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr)
+    return staged_dispatch<float>(m, D, op, xk, y, dot, skip, s);
   // inner-solve vectors are [N][4]
-  return ebe_dispatch<float, float, 4, false>(m, D, m.geom32, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s);
+  return ebe_dispatch<float, float, 4, false>(m, D, m.geom32, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s,
+                                              sg);
 }
 
 cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s) {
+                         cudaStream_t s, SegList sg, bool staged) {
+  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr)
+    return staged_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
   return ebe_dispatch<float, __half2, 4, false>(m, static_cast<const __half2 *>(D16), m.geom32, op, nullptr, xk, y,
-                                                ids, e0, e1, atomic, dot, skip, s);
+                                                ids, e0, e1, atomic, dot, skip, s, sg);
 }
 
 // ------------------------------------------------------------------ dashpot faces
@@ -271,11 +444,21 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
                                                   const double *__restrict__ fgeom, const int32_t *__restrict__ fmat,
                                                   const int32_t *__restrict__ fkind, const MatConst *__restrict__ mc,
                                                   T cC, const T *__restrict__ x, const double *__restrict__ vin,
-                                                  T *y, double *dot, const int32_t *skip) {
+                                                  T *y, double *dot, const int32_t *skip, const Seg *seg,
+                                                  const int32_t *__restrict__ fmem, int64_t vin_stride) {
+  int64_t i, end;
+  if (seg) {
+    const Seg sg = seg[blockIdx.x];
+    i = sg.a0 + threadIdx.x;
+    end = sg.a1;
+    if (skip) skip += (int64_t)sg.m * kScStride;
+  } else {
+    i = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    end = f1;
+  }
   if (skip && *skip) return;
-  const int64_t i = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double mydot = 0.0;
-  if (i < f1) {
+  if (i < end) {
     const int64_t f = ids ? (int64_t)ids[i] : i;
     int nd[6];
 #pragma unroll
@@ -285,11 +468,12 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
     const MatConst &mm = mc[fmat[f]];
     const T rvs = (T)(mm.rho * mm.vs), rvd = (T)(mm.rho * (mm.vp - mm.vs));
     const bool inp = vin && fkind[f] == 0;
+    const double *vf = (vin && fmem) ? vin + fmem[f] * vin_stride : vin;  // the face's member's input
     T w[6][3];
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) w[a][r] = x[VS * (int64_t)nd[a] + r] + (inp ? (T)vin[r] : (T)0);
+      for (int r = 0; r < 3; ++r) w[a][r] = x[VS * (int64_t)nd[a] + r] + (inp ? (T)vf[r] : (T)0);
     T m[6][3];  // Mtri applied per component
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -326,12 +510,14 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
 template <typename T, int VS>
 static cudaError_t faces_dispatch(const DevMesh &m, const MatConst *mc, T cC, const T *x, const double *vin, T *y,
                                   const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
-                                  const int32_t *skip, cudaStream_t s) {
-  if (f1 <= f0) return cudaSuccess;
-  unsigned nb = (unsigned)((f1 - f0 + kBlock - 1) / kBlock);
+                                  const int32_t *skip, cudaStream_t s, const SegList &sg, const int32_t *fmem,
+                                  int64_t vin_stride) {
+  if (!sg.seg && f1 <= f0) return cudaSuccess;
+  if (sg.seg && sg.n == 0) return cudaSuccess;
+  const unsigned nb = sg.seg ? (unsigned)sg.n : (unsigned)((f1 - f0 + kBlock - 1) / kBlock);
 #define NS_F_LAUNCH(A, DT) \
   k_faces<T, VS, A, DT><<<nb, kBlock, 0, s>>>(f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, m.fkind, mc, cC, x, vin, y, \
-                                          dot, skip)
+                                              dot, skip, sg.seg, fmem, vin_stride)
   if (atomic) {
     if (dot)
       NS_F_LAUNCH(true, true);
@@ -349,25 +535,25 @@ static cudaError_t faces_dispatch(const DevMesh &m, const MatConst *mc, T cC, co
 
 cudaError_t launch_faces64(const DevMesh &m, const MatConst *mc, double cC, const double *x, const double *vin,
                            double *y, const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
-                           const int32_t *skip, cudaStream_t s) {
-  return faces_dispatch<double, 3>(m, mc, cC, x, vin, y, ids, f0, f1, atomic, dot, skip, s);
+                           const int32_t *skip, cudaStream_t s, SegList sg, const int32_t *fmem, int64_t vin_stride) {
+  return faces_dispatch<double, 3>(m, mc, cC, x, vin, y, ids, f0, f1, atomic, dot, skip, s, sg, fmem, vin_stride);
 }
 
 cudaError_t launch_faces32(const DevMesh &m, const MatConst *mc, float cC, const float *x, float *y,
                            const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot, const int32_t *skip,
-                           cudaStream_t s) {
-  return faces_dispatch<float, 4>(m, mc, cC, x, nullptr, y, ids, f0, f1, atomic, dot, skip, s);
+                           cudaStream_t s, SegList sg) {
+  return faces_dispatch<float, 4>(m, mc, cC, x, nullptr, y, ids, f0, f1, atomic, dot, skip, s, sg, nullptr, 0);
 }
 
 // ------------------------------------------------------------------ block-Jacobi diagonal blocks
 
 // For node i of the element: sum_q w_q B_i^T D_q B_i (3x3) + mass diagonal, packed xx yy zz yz xz xy.
-template <typename T>
+template <typename T, typename TD>
 __global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1, const int32_t *__restrict__ ids,
                                                          const int32_t *__restrict__ conn,
                                                          const T *__restrict__ geom,
                                                          const int32_t *__restrict__ mat,
-                                                         const T *__restrict__ D, int64_t epad,
+                                                         const TD *__restrict__ D, int64_t epad,
                                                          const OpCoef *__restrict__ op, T *Jd, bool atomic) {
   const int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= e1) return;
@@ -386,7 +572,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1,
   for (int q = 0; q < 4; ++q) {
     T d[21];
 #pragma unroll
-    for (int k = 0; k < 21; ++k) d[k] = w * D[(q * 21 + k) * epad + e];
+    for (int k = 0; k < 21; ++k) d[k] = w * dload(D, epad, e, q * 21 + k);
 #pragma unroll
     for (int a = 0; a < 10; ++a) {
       T gn[3];
@@ -464,7 +650,7 @@ __global__ void k_jacobi_faces(int64_t f0, int64_t f1, const int32_t *__restrict
 cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef *op, double *Jd, const int32_t *ids,
                                 int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
-  k_jacobi_elems<double><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+  k_jacobi_elems<double, double><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
       e0, e1, ids, m.conn, m.geom, m.mat, D, m.epad, op, Jd, atomic);
   return cudaGetLastError();
 }
@@ -472,8 +658,16 @@ cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef 
 cudaError_t launch_jacobi_elems32(const DevMesh &m, const float *D, const OpCoef *op, float *Jd, const int32_t *ids,
                                   int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
-  k_jacobi_elems<float><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+  k_jacobi_elems<float, float><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
       e0, e1, ids, m.conn, m.geom32, m.mat, D, m.epad, op, Jd, atomic);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_elems16(const DevMesh &m, const void *D16, const OpCoef *op, float *Jd, const int32_t *ids,
+                                  int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
+  if (e1 <= e0) return cudaSuccess;
+  k_jacobi_elems<float, __half2><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      e0, e1, ids, m.conn, m.geom32, m.mat, static_cast<const __half2 *>(D16), m.epad, op, Jd, atomic);
   return cudaGetLastError();
 }
 

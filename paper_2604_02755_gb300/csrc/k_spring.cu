@@ -2,6 +2,7 @@
 // spring strains gamma_k = q_k . eps, modified Ramberg-Osgood skeleton with the
 // Masing rule per spring (40-byte state), tangent D = Kb m m^T + w sum_k G_k q_k q_k^T.
 #include <algorithm>
+#include <atomic>
 
 #include "kern_common.cuh"
 
@@ -326,10 +327,14 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
   if (p1 <= p0) return cudaSuccess;
   const int TP = tile_points(tab.S);
   const size_t smem = sizeof(float2) * TP * tab.S;
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the shared-memory opt-in is a per-device attribute, set once per device (any thread)
+  static std::atomic<unsigned long long> attr_done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_done.load() & bit)) {
     cudaFuncSetAttribute(k_springs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
+    attr_done.fetch_or(bit);
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
   k_springs<<<nb, kBlock, smem, s>>>(tab.q, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, st.gR,

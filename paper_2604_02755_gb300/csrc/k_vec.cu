@@ -13,6 +13,35 @@ int vec_blocks(int64_t n_nodes) {
   return (int)nb;
 }
 
+// Loop bounds of one block of a node-vector kernel: its member's slice [a0, a1) (w entries
+// per node) when the launch is cut by members, else a grid-stride loop over [0, n).
+struct VRange {
+  int64_t i, end, step;
+  int m;
+};
+__device__ __forceinline__ VRange vrange(const Seg *seg, int64_t n, int w) {
+  if (seg) {
+    const Seg sg = seg[blockIdx.x];
+    return {sg.a0 * w + threadIdx.x, sg.a1 * w, (int64_t)blockDim.x, sg.m};
+  }
+  return {blockIdx.x * (int64_t)blockDim.x + threadIdx.x, n, (int64_t)gridDim.x * blockDim.x, 0};
+}
+static int vgrid(int64_t N, const SegList &sg) { return sg.seg ? sg.n : vec_blocks(N); }
+
+// Block sum of the partial slots of value k that belong to member m (all n slots without members).
+__device__ double part_sum(const double *__restrict__ part, int n, int k, const PartMap &pm, int m) {
+  double acc = 0.0;
+  const double *pk = part + (int64_t)k * n;
+  if (!pm.off1) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += pk[i];
+  } else {
+    for (int i = pm.off1[m] + threadIdx.x; i < pm.off1[m + 1]; i += blockDim.x) acc += pk[i];
+    if (pm.off2)
+      for (int i = pm.base2 + pm.off2[m] + threadIdx.x; i < pm.base2 + pm.off2[m + 1]; i += blockDim.x) acc += pk[i];
+  }
+  return block_sum(acc);
+}
+
 __global__ void k_fill(double *x, double v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = v;
@@ -93,9 +122,10 @@ cudaError_t launch_invert_blocks(const double *Jd, double *Jinv, float *Jinv32, 
 
 __global__ void __launch_bounds__(kBlock) k_cg_init(const double *__restrict__ b, const double *__restrict__ Ap,
                                                     const double *__restrict__ Jinv, double *r, double *z, double *p,
-                                                    int64_t N, double *part) {
+                                                    int64_t N, double *part, const Seg *seg) {
+  const VRange R = vrange(seg, N, 1);
   double bb = 0.0, rr = 0.0, rz = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     double rv[3], zv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -122,20 +152,22 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(const double *__restrict__ b
 }
 
 cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv, double *r, double *z, double *p,
-                           int64_t N, double *part, cudaStream_t s) {
-  k_cg_init<<<vec_blocks(N), kBlock, 0, s>>>(b, Ap, Jinv, r, z, p, N, part);
+                           int64_t N, double *part, cudaStream_t s, SegList sg) {
+  k_cg_init<<<vgrid(N, sg), kBlock, 0, s>>>(b, Ap, Jinv, r, z, p, N, part, sg.seg);
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kBlock) k_cg_final(const double *__restrict__ part, int n, int nvals,
-                                                     CgScalars *sc, int mode, double tol, int max_iter) {
+                                                     CgScalars *scs, int mode, double tol, int max_iter, PartMap pm,
+                                                     const CgScalars *gate) {
+  CgScalars *sc = scs + blockIdx.x;  // one block per member
+  if (gate && gate[blockIdx.x].done) {  // (inner INIT) the member's outer solve has converged
+    if (threadIdx.x == 0) sc->done = 1;
+    return;
+  }
   if (mode != NS_FIN_INIT && mode != NS_FIN_FCG_INIT && sc->done) return;
   double v[3] = {0.0, 0.0, 0.0};
-  for (int k = 0; k < nvals; ++k) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[k * n + i];
-    v[k] = block_sum(acc);
-  }
+  for (int k = 0; k < nvals; ++k) v[k] = part_sum(part, n, k, pm, blockIdx.x);
   if (threadIdx.x != 0) return;
   if (mode == NS_FIN_INIT) {
     sc->bb = v[0];
@@ -181,28 +213,28 @@ __global__ void __launch_bounds__(kBlock) k_cg_final(const double *__restrict__ 
 }
 
 cudaError_t launch_cg_final(const double *part, int n, int nvals, CgScalars *sc, int mode, double tol, int max_iter,
-                            cudaStream_t s) {
-  k_cg_final<<<1, kBlock, 0, s>>>(part, n, nvals, sc, mode, tol, max_iter);
+                            cudaStream_t s, int M, PartMap pm, const CgScalars *gate) {
+  k_cg_final<<<M, kBlock, 0, s>>>(part, n, nvals, sc, mode, tol, max_iter, pm, gate);
   return cudaGetLastError();
 }
 
-// alpha = (p.r) / (p.A p) of the flexible CG, from two partial arrays
+// alpha = (p.r) / (p.A p) of the flexible CG, from two partial arrays (one block per member)
 __global__ void __launch_bounds__(kBlock) k_fcg_alpha(const double *__restrict__ pr, int npr,
-                                                      const double *__restrict__ pap, int npap, CgScalars *sc) {
+                                                      const double *__restrict__ pap, int npap, CgScalars *scs,
+                                                      PartMap pmr, PartMap pma) {
+  CgScalars *sc = scs + blockIdx.x;
   if (sc->done) return;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < npr; i += blockDim.x) a += pr[i];
-  for (int i = threadIdx.x; i < npap; i += blockDim.x) b += pap[i];
-  a = block_sum(a);
-  b = block_sum(b);
+  const double a = part_sum(pr, npr, 0, pmr, blockIdx.x);
+  const double b = part_sum(pap, npap, 0, pma, blockIdx.x);
   if (threadIdx.x == 0) {
     sc->pAp = b;
     sc->alpha = a / b;
   }
 }
 
-cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int npap, CgScalars *sc, cudaStream_t s) {
-  k_fcg_alpha<<<1, kBlock, 0, s>>>(pr, npr, pap, npap, sc);
+cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int npap, CgScalars *sc, cudaStream_t s,
+                             int M, PartMap pmr, PartMap pma) {
+  k_fcg_alpha<<<M, kBlock, 0, s>>>(pr, npr, pap, npap, sc, pmr, pma);
   return cudaGetLastError();
 }
 
@@ -213,11 +245,12 @@ cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int n
 // z = ||r|| * x_in (undo the inner scaling; x_in is [N][4]); partial z . A p_{k-1}
 __global__ void __launch_bounds__(kBlock) k_fcg_gamma(const float4 *__restrict__ xin, double *z,
                                                       const double *__restrict__ Ap, int64_t N, double *part,
-                                                      const CgScalars *so) {
-  if (so->done) return;
-  const double nr = sqrt(so->rr);
+                                                      const CgScalars *so, const Seg *seg) {
+  const VRange R = vrange(seg, N, 1);
+  if (so[R.m].done) return;
+  const double nr = sqrt(so[R.m].rr);
   double g = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     const float4 xv = xin[i];
     const double z0 = (double)xv.x * nr, z1 = (double)xv.y * nr, z2 = (double)xv.z * nr;
     z[3 * i] = z0;
@@ -232,11 +265,12 @@ __global__ void __launch_bounds__(kBlock) k_fcg_gamma(const float4 *__restrict__
 // p = z + beta p; partial p . r; Ap = 0
 __global__ void __launch_bounds__(kBlock) k_fcg_p(double *p, const double *__restrict__ z,
                                                   const double *__restrict__ r, double *Ap, int64_t n3, double *part,
-                                                  const CgScalars *so) {
-  if (so->done) return;
-  const double beta = so->beta;
+                                                  const CgScalars *so, const Seg *seg) {
+  const VRange R = vrange(seg, n3, 3);
+  if (so[R.m].done) return;
+  const double beta = so[R.m].beta;
   double a = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     const double pi = z[i] + beta * p[i];
     p[i] = pi;
     a += pi * r[i];
@@ -249,11 +283,12 @@ __global__ void __launch_bounds__(kBlock) k_fcg_p(double *p, const double *__res
 // x += alpha p; r -= alpha A p; partial r . r
 __global__ void __launch_bounds__(kBlock) k_fcg_update(double *x, double *r, const double *__restrict__ p,
                                                        const double *__restrict__ Ap, int64_t n3, double *part,
-                                                       const CgScalars *so) {
-  if (so->done) return;
-  const double alpha = so->alpha;
+                                                       const CgScalars *so, const Seg *seg) {
+  const VRange R = vrange(seg, n3, 3);
+  if (so[R.m].done) return;
+  const double alpha = so[R.m].alpha;
   double a = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * Ap[i];
     r[i] = ri;
@@ -265,9 +300,10 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(double *x, double *r, con
 
 // r = b - Ap; partials b.b, r.r
 __global__ void __launch_bounds__(kBlock) k_fcg_init(const double *__restrict__ b, const double *__restrict__ Ap,
-                                                     double *r, int64_t n3, double *part) {
+                                                     double *r, int64_t n3, double *part, const Seg *seg) {
+  const VRange R = vrange(seg, n3, 3);
   double bb = 0.0, rr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     const double bv = b[i], rv = bv - Ap[i];
     r[i] = rv;
     bb += bv * bv;
@@ -280,23 +316,23 @@ __global__ void __launch_bounds__(kBlock) k_fcg_init(const double *__restrict__ 
   }
 }
 
-cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_t N, double *part, cudaStream_t s) {
-  k_fcg_init<<<vec_blocks(N), kBlock, 0, s>>>(b, Ap, r, 3 * N, part);
+cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_t N, double *part, cudaStream_t s, SegList sg) {
+  k_fcg_init<<<vgrid(N, sg), kBlock, 0, s>>>(b, Ap, r, 3 * N, part, sg.seg);
   return cudaGetLastError();
 }
 cudaError_t launch_fcg_gamma(const float *xin, double *z, const double *Ap, int64_t N, double *part,
-                             const CgScalars *so, cudaStream_t s) {
-  k_fcg_gamma<<<vec_blocks(N), kBlock, 0, s>>>(reinterpret_cast<const float4 *>(xin), z, Ap, N, part, so);
+                             const CgScalars *so, cudaStream_t s, SegList sg) {
+  k_fcg_gamma<<<vgrid(N, sg), kBlock, 0, s>>>(reinterpret_cast<const float4 *>(xin), z, Ap, N, part, so, sg.seg);
   return cudaGetLastError();
 }
 cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, int64_t N, double *part,
-                         const CgScalars *so, cudaStream_t s) {
-  k_fcg_p<<<vec_blocks(N), kBlock, 0, s>>>(p, z, r, Ap, 3 * N, part, so);
+                         const CgScalars *so, cudaStream_t s, SegList sg) {
+  k_fcg_p<<<vgrid(N, sg), kBlock, 0, s>>>(p, z, r, Ap, 3 * N, part, so, sg.seg);
   return cudaGetLastError();
 }
 cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, int64_t N, double *part,
-                              const CgScalars *so, cudaStream_t s) {
-  k_fcg_update<<<vec_blocks(N), kBlock, 0, s>>>(x, r, p, Ap, 3 * N, part, so);
+                              const CgScalars *so, cudaStream_t s, SegList sg) {
+  k_fcg_update<<<vgrid(N, sg), kBlock, 0, s>>>(x, r, p, Ap, 3 * N, part, so, sg.seg);
   return cudaGetLastError();
 }
 
@@ -313,12 +349,13 @@ __device__ __forceinline__ float4 sym3_apply_f(const float *J, const float4 r) {
 
 __global__ void __launch_bounds__(kBlock) k_in_init(const double *__restrict__ r, const CgScalars *so,
                                                     const float *__restrict__ J, float4 *rin, float4 *zin, float4 *pin,
-                                                    float4 *xin, float4 *Apin, int64_t N, double *part) {
-  if (so->done) return;
-  const double sc = 1.0 / sqrt(so->rr);
+                                                    float4 *xin, float4 *Apin, int64_t N, double *part, const Seg *seg) {
+  const VRange R = vrange(seg, N, 1);
+  if (so[R.m].done) return;
+  const double sc = 1.0 / sqrt(so[R.m].rr);
   float rr = 0.0f, rz = 0.0f;  // per-thread partials (a few dozen terms) in FP32
   const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     const float4 rv = make_float4((float)(r[3 * i] * sc), (float)(r[3 * i + 1] * sc), (float)(r[3 * i + 2] * sc), 0.0f);
     const float4 zv = sym3_apply_f(J + 6 * i, rv);
     rin[i] = rv;
@@ -340,11 +377,12 @@ __global__ void __launch_bounds__(kBlock) k_in_init(const double *__restrict__ r
 __global__ void __launch_bounds__(kBlock) k_in_update(float4 *xin, float4 *rin, float4 *zin,
                                                       const float4 *__restrict__ pin, const float4 *__restrict__ Apin,
                                                       const float *__restrict__ J, int64_t N, double *part,
-                                                      const CgScalars *si, const CgScalars *so) {
-  if (so->done || si->done) return;
-  const float alpha = (float)si->alpha;
+                                                      const CgScalars *si, const CgScalars *so, const Seg *seg) {
+  const VRange R = vrange(seg, N, 1);
+  if (so[R.m].done || si[R.m].done) return;
+  const float alpha = (float)si[R.m].alpha;
   float rr = 0.0f, rz = 0.0f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     const float4 pv = pin[i], av = Apin[i];
     float4 xv = xin[i], rv = rin[i];
     xv.x = fmaf(alpha, pv.x, xv.x);
@@ -368,11 +406,12 @@ __global__ void __launch_bounds__(kBlock) k_in_update(float4 *xin, float4 *rin, 
 }
 
 __global__ void k_in_pupdate(float4 *pin, const float4 *__restrict__ zin, float4 *Apin, int64_t N, const CgScalars *si,
-                             const CgScalars *so) {
-  if (so->done || si->done) return;
-  const float beta = (float)si->beta;
+                             const CgScalars *so, const Seg *seg) {
+  const VRange R = vrange(seg, N, 1);
+  if (so[R.m].done || si[R.m].done) return;
+  const float beta = (float)si[R.m].beta;
   const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     const float4 zv = zin[i];
     float4 pv = pin[i];
     pv.x = fmaf(beta, pv.x, zv.x);
@@ -387,28 +426,29 @@ static float4 *f4(float *p) { return reinterpret_cast<float4 *>(p); }
 static const float4 *f4(const float *p) { return reinterpret_cast<const float4 *>(p); }
 
 cudaError_t launch_in_init(const double *r, const CgScalars *so, const float *J, float *rin, float *zin, float *pin,
-                           float *xin, float *Apin, int64_t N, double *part, cudaStream_t s) {
-  k_in_init<<<vec_blocks(N), kBlock, 0, s>>>(r, so, J, f4(rin), f4(zin), f4(pin), f4(xin), f4(Apin), N, part);
+                           float *xin, float *Apin, int64_t N, double *part, cudaStream_t s, SegList sg) {
+  k_in_init<<<vgrid(N, sg), kBlock, 0, s>>>(r, so, J, f4(rin), f4(zin), f4(pin), f4(xin), f4(Apin), N, part, sg.seg);
   return cudaGetLastError();
 }
 cudaError_t launch_in_update(float *xin, float *rin, float *zin, const float *pin, const float *Apin, const float *J,
-                             int64_t N, double *part, const CgScalars *si, const CgScalars *so, cudaStream_t s) {
-  k_in_update<<<vec_blocks(N), kBlock, 0, s>>>(f4(xin), f4(rin), f4(zin), f4(pin), f4(Apin), J, N, part, si, so);
+                             int64_t N, double *part, const CgScalars *si, const CgScalars *so, cudaStream_t s, SegList sg) {
+  k_in_update<<<vgrid(N, sg), kBlock, 0, s>>>(f4(xin), f4(rin), f4(zin), f4(pin), f4(Apin), J, N, part, si, so, sg.seg);
   return cudaGetLastError();
 }
 cudaError_t launch_in_pupdate(float *pin, const float *zin, float *Apin, int64_t N, const CgScalars *si,
-                              const CgScalars *so, cudaStream_t s) {
-  k_in_pupdate<<<vec_blocks(N), kBlock, 0, s>>>(f4(pin), f4(zin), f4(Apin), N, si, so);
+                              const CgScalars *so, cudaStream_t s, SegList sg) {
+  k_in_pupdate<<<vgrid(N, sg), kBlock, 0, s>>>(f4(pin), f4(zin), f4(Apin), N, si, so, sg.seg);
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kBlock) k_cg_update(double *x, double *r, double *z, const double *__restrict__ p,
                                                       const double *__restrict__ Ap, const double *__restrict__ Jinv,
-                                                      int64_t N, double *part, const CgScalars *sc) {
-  if (sc->done) return;
-  const double alpha = sc->alpha;
+                                                      int64_t N, double *part, const CgScalars *sc, const Seg *seg) {
+  const VRange R = vrange(seg, N, 1);
+  if (sc[R.m].done) return;
+  const double alpha = sc[R.m].alpha;
   double rr = 0.0, rz = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     double rv[3], zv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -432,22 +472,23 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(double *x, double *r, doub
 }
 
 cudaError_t launch_cg_update(double *x, double *r, double *z, const double *p, const double *Ap, const double *Jinv,
-                             int64_t N, double *part, const CgScalars *sc, cudaStream_t s) {
-  k_cg_update<<<vec_blocks(N), kBlock, 0, s>>>(x, r, z, p, Ap, Jinv, N, part, sc);
+                             int64_t N, double *part, const CgScalars *sc, cudaStream_t s, SegList sg) {
+  k_cg_update<<<vgrid(N, sg), kBlock, 0, s>>>(x, r, z, p, Ap, Jinv, N, part, sc, sg.seg);
   return cudaGetLastError();
 }
 
-__global__ void k_cg_pupdate(double *p, const double *__restrict__ z, double *Ap, int64_t n3, const CgScalars *sc) {
-  if (sc->done) return;
-  const double beta = sc->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_cg_pupdate(double *p, const double *__restrict__ z, double *Ap, int64_t n3, const CgScalars *sc, const Seg *seg) {
+  const VRange R = vrange(seg, n3, 3);
+  if (sc[R.m].done) return;
+  const double beta = sc[R.m].beta;
+  for (int64_t i = R.i; i < R.end; i += R.step) {
     p[i] = z[i] + beta * p[i];
     Ap[i] = 0.0;
   }
 }
 
-cudaError_t launch_cg_pupdate(double *p, const double *z, double *Ap, int64_t N, const CgScalars *sc, cudaStream_t s) {
-  k_cg_pupdate<<<vec_blocks(N), kBlock, 0, s>>>(p, z, Ap, 3 * N, sc);
+cudaError_t launch_cg_pupdate(double *p, const double *z, double *Ap, int64_t N, const CgScalars *sc, cudaStream_t s, SegList sg) {
+  k_cg_pupdate<<<vgrid(N, sg), kBlock, 0, s>>>(p, z, Ap, 3 * N, sc, sg.seg);
   return cudaGetLastError();
 }
 

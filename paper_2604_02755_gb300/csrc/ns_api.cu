@@ -86,6 +86,20 @@ struct ns_ctx {
   int64_t ring_steps = 0;
   int64_t step = 0;
   cudaEvent_t ev_sync = nullptr, ev_adv0 = nullptr, ev_adv1 = nullptr, ev_join = nullptr;
+  // batched members (ns_set_members): M independent sub-models of the uploaded mesh
+  int32_t M = 1;
+  std::vector<int64_t> moff_e, moff_n, moff_f;  // [M + 1] element / node / face ranges
+  Seg *vseg_d = nullptr, *eseg_d = nullptr, *fseg_d = nullptr;
+  int32_t *voff_d = nullptr, *eoff_d = nullptr, *foff_d = nullptr, *fmem_d = nullptr;
+  int nvseg = 0, neseg = 0, nfseg = 0;
+  std::vector<int32_t> member_iters;  // outer CG iterations of each member at the last step
+  std::vector<int32_t> face_elem_h;   // element of each boundary face (host copy)
+  // captured launch sequences (cfg.graphs): one outer flexible-CG iteration, one batch of
+  // plain CG iterations; with the launches and FP32 operator applications each contains
+  bool capturing = false;
+  cudaGraphExec_t g_outer = nullptr, g_batch = nullptr;
+  int64_t g_outer_cnt[3] = {0, 0, 0}, g_batch_cnt[3] = {0, 0, 0};
+  int64_t cap_ebe32 = 0, cap_ebe64 = 0;
   ns_stats stats{};
   EventTimer timer;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
@@ -190,13 +204,15 @@ int sync_all(ns_ctx *c) {
 }
 
 void tbegin(ns_ctx *c, int kind, cudaStream_t s, cudaEvent_t *out) {
-  if (!c->cfg.timing) return;
+  if (kind == TK_EBE32 && c->capturing) c->cap_ebe32++;
+  if (kind == TK_EBE64 && c->capturing) c->cap_ebe64++;
+  if (!c->cfg.timing || c->capturing) return;
   *out = c->timer.get();
   cudaEventRecord(*out, s);
 }
 
 void tend(ns_ctx *c, int kind, cudaStream_t s, cudaEvent_t start) {
-  if (!c->cfg.timing) return;
+  if (!c->cfg.timing || c->capturing) return;
   cudaEvent_t e = c->timer.get();
   cudaEventRecord(e, s);
   c->tev.push_back({kind, {start, e}});
@@ -227,6 +243,15 @@ void flush_times(ns_ctx *c) {
 
 int nblk(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
+// Launch cuts by member (empty lists with one member: the flat launches)
+SegList vsegs(const ns_ctx *c) { return c->M > 1 ? SegList{c->vseg_d, c->nvseg, c->voff_d} : SegList{}; }
+SegList esegs(const ns_ctx *c) { return c->M > 1 ? SegList{c->eseg_d, c->neseg, c->eoff_d} : SegList{}; }
+SegList fsegs(const ns_ctx *c) { return c->M > 1 ? SegList{c->fseg_d, c->nfseg, c->foff_d} : SegList{}; }
+int nvparts(const ns_ctx *c) { return c->M > 1 ? c->nvseg : vec_blocks(c->m.N); }
+PartMap vmap(const ns_ctx *c) { return c->M > 1 ? PartMap{c->voff_d, nullptr, 0} : PartMap{}; }
+// operator partials: element blocks first, then face blocks
+PartMap opmap(const ns_ctx *c) { return c->M > 1 ? PartMap{c->eoff_d, c->foff_d, c->neseg} : PartMap{}; }
+
 // ---------------------------------------------------------------- operator application helpers
 
 // y += Op x over all elements (atomic) or colour by colour (plain adds). Returns the number
@@ -236,8 +261,8 @@ int apply_elems64(ns_ctx *c, const OpCoef *op, const double *xm, const double *x
   const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
   int off = 0;
   if (atomic) {
-    LAUNCH(c, launch_ebe64(c->m, c->D, op, xm, xk, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main));
-    off = nblk(c->m.E);
+    LAUNCH(c, launch_ebe64(c->m, c->D, op, xm, xk, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main, esegs(c)));
+    off = c->M > 1 ? c->neseg : nblk(c->m.E);
   } else {
     for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k) {
       const int64_t e0 = c->m.ecol_off[k], e1 = c->m.ecol_off[k + 1];
@@ -256,8 +281,9 @@ int apply_faces64(ns_ctx *c, double cC, const double *x, const double *vin, doub
   int off = 0;
   if (c->m.F > 0) {
     if (atomic) {
-      LAUNCH(c, launch_faces64(c->m, c->mats_d, cC, x, vin, y, nullptr, 0, c->m.F, true, dot, skip, c->s_main));
-      off = nblk(c->m.F);
+      LAUNCH(c, launch_faces64(c->m, c->mats_d, cC, x, vin, y, nullptr, 0, c->m.F, true, dot, skip, c->s_main,
+                               fsegs(c), c->M > 1 ? c->fmem_d : nullptr, 3 * c->n_vin));
+      off = c->M > 1 ? c->nfseg : nblk(c->m.F);
     } else {
       for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k) {
         const int64_t f0 = c->m.fcol_off[k], f1 = c->m.fcol_off[k + 1];
@@ -293,17 +319,18 @@ int apply_A32(ns_ctx *c, const float *x, float *y, double *dot, const int32_t *s
   cudaEvent_t t0 = nullptr;
   tbegin(c, TK_EBE32, c->s_main, &t0);
   const bool h16 = c->cfg.precision == NS_PREC_FP64_IR16;
-  auto elems = [&](const int32_t *ids, int64_t e0, int64_t e1, bool at, double *d) {
-    return h16 ? launch_ebe16(c->m, c->D16, c->op_A16, x, y, ids, e0, e1, at, d, skip, c->s_main)
-               : launch_ebe32(c->m, c->D32, c->op_A, x, y, ids, e0, e1, at, d, skip, c->s_main);
+  auto elems = [&](const int32_t *ids, int64_t e0, int64_t e1, bool at, double *d, SegList sg) {
+    const bool st = c->cfg.stage_elements != 0;
+    return h16 ? launch_ebe16(c->m, c->D16, c->op_A16, x, y, ids, e0, e1, at, d, skip, c->s_main, sg, st)
+               : launch_ebe32(c->m, c->D32, c->op_A, x, y, ids, e0, e1, at, d, skip, c->s_main, sg, st);
   };
   if (atomic) {
-    LAUNCH(c, elems(nullptr, 0, c->m.E, true, dot));
-    off = nblk(c->m.E);
+    LAUNCH(c, elems(nullptr, 0, c->m.E, true, dot, esegs(c)));
+    off = c->M > 1 ? c->neseg : nblk(c->m.E);
   } else {
     for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k) {
       const int64_t e0 = c->m.ecol_off[k], e1 = c->m.ecol_off[k + 1];
-      LAUNCH(c, elems(c->m.ecol_ids, e0, e1, false, dot + off));
+      LAUNCH(c, elems(c->m.ecol_ids, e0, e1, false, dot + off, SegList{}));
       off += nblk(e1 - e0);
     }
   }
@@ -311,8 +338,9 @@ int apply_A32(ns_ctx *c, const float *x, float *y, double *dot, const int32_t *s
   if (c->m.F > 0) {
     const float cC = (float)(2.0 / c->cfg.dt);
     if (atomic) {
-      LAUNCH(c, launch_faces32(c->m, c->mats_d, cC, x, y, nullptr, 0, c->m.F, true, dot + off, skip, c->s_main));
-      off += nblk(c->m.F);
+      LAUNCH(c, launch_faces32(c->m, c->mats_d, cC, x, y, nullptr, 0, c->m.F, true, dot + off, skip, c->s_main,
+                               fsegs(c)));
+      off += c->M > 1 ? c->nfseg : nblk(c->m.F);
     } else {
       for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k) {
         const int64_t f0 = c->m.fcol_off[k], f1 = c->m.fcol_off[k + 1];
@@ -486,53 +514,175 @@ int spring_phase(ns_ctx *c) {
 }
 
 int read_scalars(ns_ctx *c) {
-  CKC(c, cudaMemcpyAsync(c->sc_h, c->sc, 2 * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->s_main));
+  CKC(c, cudaMemcpyAsync(c->sc_h, c->sc, 2 * (size_t)c->M * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->s_main));
   return sync_stream(c, c->s_main);
 }
 
+// outer solve finished for every member (scalars read back)
+bool outer_done(const ns_ctx *c) {
+  for (int m = 0; m < c->M; ++m)
+    if (c->sc_h[m].done == 0) return false;
+  return true;
+}
+
+// members with a zero right-hand side take du = 0 (done == 2 after the initial reduction)
+int zero_rhs_members(ns_ctx *c) {
+  for (int m = 0; m < c->M; ++m)
+    if (c->sc_h[m].done == 2) {
+      const int64_t n0 = c->M > 1 ? c->moff_n[m] : 0, n1 = c->M > 1 ? c->moff_n[m + 1] : c->m.N;
+      CKC(c, cudaMemsetAsync(c->du + 3 * n0, 0, sizeof(double) * 3 * (n1 - n0), c->s_main));
+    }
+  return NS_OK;
+}
+
+// Issue a fixed launch sequence on the main stream: directly, or (cfg.graphs) captured into
+// a CUDA graph on first use and replayed afterwards.  Every pointer and launch shape in the
+// sequence is fixed for the context's life; what varies (converged members, iteration
+// counts) lives in device memory that the kernels read.
+template <typename F>
+int issue_fixed(ns_ctx *c, cudaGraphExec_t *ge, int64_t cnt[3], F &&issue) {
+  if (!c->cfg.graphs) return issue();
+  if (!*ge) {
+    const int64_t k0 = c->stats.kernel_launches;
+    c->cap_ebe32 = c->cap_ebe64 = 0;
+    CKC(c, cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    int rc = issue();
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->s_main, &g);
+    if (rc == NS_OK && e != cudaSuccess) {
+      c->err = std::string("stream capture: ") + cudaGetErrorString(e);
+      rc = NS_ERR_CUDA;
+    }
+    if (rc == NS_OK) {
+      const cudaError_t e2 = cudaGraphInstantiate(ge, g, 0);
+      if (e2 != cudaSuccess) {
+        c->err = std::string("graph instantiation: ") + cudaGetErrorString(e2);
+        *ge = nullptr;
+        rc = NS_ERR_CUDA;
+      }
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    cnt[0] = c->stats.kernel_launches - k0;  // kernels, FP32 and FP64 operator launches of one replay
+    cnt[1] = c->cap_ebe32;
+    cnt[2] = c->cap_ebe64;
+    c->stats.kernel_launches = k0;
+    if (rc != NS_OK) return rc;
+  }
+  CKC(c, cudaGraphLaunch(*ge, c->s_main));
+  c->stats.kernel_launches += cnt[0];
+  c->stats.n_ebe32 += cnt[1];
+  c->stats.n_ebe64 += cnt[2];
+  return NS_OK;
+}
+
+void destroy_graphs(ns_ctx *c) {
+  if (c->g_outer) cudaGraphExecDestroy(c->g_outer);
+  if (c->g_batch) cudaGraphExecDestroy(c->g_batch);
+  c->g_outer = c->g_batch = nullptr;
+}
+
 // Flexible FP64 CG whose preconditioner is an FP32 block-Jacobi PCG on the same operator
-// (the paper's precision policy: only the preconditioning is single precision).
+// (the paper's precision policy: only the preconditioning is single precision).  With
+// members every launch covers all of them and each member iterates on its own scalars.
 int solve_ir(ns_ctx *c) {
   int rc;
   const int64_t N = c->m.N;
-  const int nbv = vec_blocks(N);
+  const int nbv = nvparts(c), M = c->M;
+  const SegList vs = vsegs(c);
+  const PartMap vm = vmap(c), om = opmap(c);
   double *pv = c->part + c->part_pap_cap;
   if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
   if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
-  LAUNCH(c, launch_fcg_init(c->b, c->Ap, c->r, N, pv, c->s_main));
-  LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc, NS_FIN_FCG_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+  LAUNCH(c, launch_fcg_init(c->b, c->Ap, c->r, N, pv, c->s_main, vs));
+  LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc, NS_FIN_FCG_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M, vm));
   if ((rc = read_scalars(c)) != NS_OK) return rc;
-  if (c->sc_h[0].done == 2) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+  if ((rc = zero_rhs_members(c)) != NS_OK) return rc;
   int inner_total = 0;
   const int32_t *skip_in = &c->sc_in->done, *skip_out = &c->sc->done;
-  while (c->sc_h[0].done == 0) {
-    // inner solve A z ~= r in FP32 from zero
-    LAUNCH(c, launch_in_init(c->r, c->sc, c->Jinv32, c->rin, c->zin, c->pin, c->xin, c->Apin, N, pv, c->s_main));
-    LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc_in, NS_FIN_INIT, c->cfg.inner_tol, c->cfg.inner_max_iter, c->s_main));
+  // one outer iteration: inner FP32 solve A z ~= r from zero, then the flexible CG update
+  auto outer_iteration = [&]() -> int {
+    int rc;
+    LAUNCH(c, launch_in_init(c->r, c->sc, c->Jinv32, c->rin, c->zin, c->pin, c->xin, c->Apin, N, pv, c->s_main, vs));
+    LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc_in, NS_FIN_INIT, c->cfg.inner_tol, c->cfg.inner_max_iter, c->s_main,
+                              M, vm, c->sc));
     for (int it = 0; it < c->cfg.inner_max_iter; ++it) {
       int np = 0;
       if ((rc = apply_A32(c, c->pin, c->Apin, c->part, skip_in, &np)) != NS_OK) return rc;
       LAUNCH(c, launch_cg_final(c->part, np, 1, c->sc_in, NS_FIN_PAP, c->cfg.inner_tol, c->cfg.inner_max_iter,
-                                c->s_main));
+                                c->s_main, M, om));
       LAUNCH(c, launch_in_update(c->xin, c->rin, c->zin, c->pin, c->Apin, c->Jinv32, N, pv, c->sc_in, c->sc,
-                                 c->s_main));
+                                 c->s_main, vs));
       LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc_in, NS_FIN_UPDATE, c->cfg.inner_tol, c->cfg.inner_max_iter,
-                                c->s_main));
-      LAUNCH(c, launch_in_pupdate(c->pin, c->zin, c->Apin, N, c->sc_in, c->sc, c->s_main));
+                                c->s_main, M, vm));
+      LAUNCH(c, launch_in_pupdate(c->pin, c->zin, c->Apin, N, c->sc_in, c->sc, c->s_main, vs));
     }
     // outer flexible CG step
-    LAUNCH(c, launch_fcg_gamma(c->xin, c->z, c->Ap, N, pv, c->sc, c->s_main));
-    LAUNCH(c, launch_cg_final(pv, nbv, 1, c->sc, NS_FIN_FCG_BETA, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
-    LAUNCH(c, launch_fcg_p(c->p, c->z, c->r, c->Ap, N, pv, c->sc, c->s_main));
+    LAUNCH(c, launch_fcg_gamma(c->xin, c->z, c->Ap, N, pv, c->sc, c->s_main, vs));
+    LAUNCH(c, launch_cg_final(pv, nbv, 1, c->sc, NS_FIN_FCG_BETA, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M, vm));
+    LAUNCH(c, launch_fcg_p(c->p, c->z, c->r, c->Ap, N, pv, c->sc, c->s_main, vs));
     int np = 0;
     if ((rc = apply_A(c, c->p, c->Ap, false, c->part, skip_out, &np, true)) != NS_OK) return rc;
-    LAUNCH(c, launch_fcg_alpha(pv, nbv, c->part, np, c->sc, c->s_main));
-    LAUNCH(c, launch_fcg_update(c->du, c->r, c->p, c->Ap, N, pv, c->sc, c->s_main));
-    LAUNCH(c, launch_cg_final(pv, nbv, 1, c->sc, NS_FIN_FCG_UPDATE, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
+    LAUNCH(c, launch_fcg_alpha(pv, nbv, c->part, np, c->sc, c->s_main, M, vm, om));
+    LAUNCH(c, launch_fcg_update(c->du, c->r, c->p, c->Ap, N, pv, c->sc, c->s_main, vs));
+    LAUNCH(c, launch_cg_final(pv, nbv, 1, c->sc, NS_FIN_FCG_UPDATE, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M,
+                              vm));
+    return NS_OK;
+  };
+  while (!outer_done(c)) {
+    if ((rc = issue_fixed(c, &c->g_outer, c->g_outer_cnt, outer_iteration)) != NS_OK)
+      return rc;
     if ((rc = read_scalars(c)) != NS_OK) return rc;
-    inner_total += c->sc_h[1].iters;
+    int most = 0;
+    for (int m = 0; m < M; ++m) most = std::max(most, c->sc_h[M + m].iters);
+    inner_total += most;
   }
   c->stats.inner_iters_last = inner_total;
+  return NS_OK;
+}
+
+// Plain FP64 block-Jacobi PCG; convergence read back every `batch` iterations (kernels of
+// a converged member skip themselves in between).
+int solve_pcg(ns_ctx *c) {
+  int rc;
+  const int64_t N = c->m.N;
+  const int nbv = nvparts(c), M = c->M;
+  const SegList vs = vsegs(c);
+  const PartMap vm = vmap(c), om = opmap(c);
+  double *pv = c->part + c->part_pap_cap;
+  if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+  if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
+  LAUNCH(c, launch_cg_init(c->b, c->Ap, c->Jinv, c->r, c->z, c->p, N, pv, c->s_main, vs));
+  LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc, NS_FIN_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M, vm));
+  if ((rc = read_scalars(c)) != NS_OK) return rc;
+  if ((rc = zero_rhs_members(c)) != NS_OK) return rc;
+  const int batch = 8;
+  const int32_t *skip = &c->sc->done;
+  if (!outer_done(c)) {
+    CKC(c, cudaMemsetAsync(c->Ap, 0, sizeof(double) * 3 * N, c->s_main));
+    auto iterations = [&]() -> int {
+      int rc;
+      for (int it = 0; it < batch; ++it) {
+        int np = 0;
+        if ((rc = apply_A(c, c->p, c->Ap, false, c->part, skip, &np, true)) != NS_OK) return rc;
+        LAUNCH(c, launch_cg_final(c->part, np, 1, c->sc, NS_FIN_PAP, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M,
+                                  om));
+        LAUNCH(c, launch_cg_update(c->du, c->r, c->z, c->p, c->Ap, c->Jinv, N, pv, c->sc, c->s_main, vs));
+        LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc, NS_FIN_UPDATE, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M,
+                                  vm));
+        LAUNCH(c, launch_cg_pupdate(c->p, c->z, c->Ap, N, c->sc, c->s_main, vs));
+      }
+      return NS_OK;
+    };
+    for (;;) {
+      if ((rc = issue_fixed(c, &c->g_batch, c->g_batch_cnt, iterations)) != NS_OK)
+        return rc;
+      if ((rc = read_scalars(c)) != NS_OK) return rc;
+      if (outer_done(c)) break;
+    }
+  }
   return NS_OK;
 }
 
@@ -550,17 +700,25 @@ int one_step(ns_ctx *c) {
   // serves the inner single-precision solve)
   tbegin(c, TK_JAC, c->s_main, &t0);
   CKC(c, cudaMemsetAsync(c->flag_d, 0, sizeof(int32_t), c->s_main));
-  if (c->cfg.precision == NS_PREC_FP64_IR) {
+  if (c->cfg.precision != NS_PREC_FP64) {
+    // FP32 blocks from the inner operator's own copy of the tangent (FP32, or FP16 / G0)
+    const bool h16 = c->cfg.precision == NS_PREC_FP64_IR16;
     float *Jd32 = (float *)c->Jd;  // the FP64 block buffer is reused for the FP32 blocks
-    LAUNCH(c, launch_D_to_f32(c->D, c->D32, c->m.epad, c->m.E, c->s_main));
+    if (h16)
+      LAUNCH(c, launch_D_to_f16(c->D, c->m.mat, c->mats_d, c->D16, c->m.epad, c->m.E, c->s_main));
+    else
+      LAUNCH(c, launch_D_to_f32(c->D, c->D32, c->m.epad, c->m.E, c->s_main));
     CKC(c, cudaMemsetAsync(Jd32, 0, sizeof(float) * 6 * N, c->s_main));
+    auto jel = [&](const int32_t *ids, int64_t e0, int64_t e1, bool at) {
+      return h16 ? launch_jacobi_elems16(c->m, c->D16, c->op_A16, Jd32, ids, e0, e1, at, c->s_main)
+                 : launch_jacobi_elems32(c->m, c->D32, c->op_A, Jd32, ids, e0, e1, at, c->s_main);
+    };
     if (atomic) {
-      LAUNCH(c, launch_jacobi_elems32(c->m, c->D32, c->op_A, Jd32, nullptr, 0, c->m.E, true, c->s_main));
+      LAUNCH(c, jel(nullptr, 0, c->m.E, true));
       LAUNCH(c, launch_jacobi_faces32(c->m, c->mats_d, 2.0 / dt, Jd32, nullptr, 0, c->m.F, true, c->s_main));
     } else {
       for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k)
-        LAUNCH(c, launch_jacobi_elems32(c->m, c->D32, c->op_A, Jd32, c->m.ecol_ids, c->m.ecol_off[k],
-                                        c->m.ecol_off[k + 1], false, c->s_main));
+        LAUNCH(c, jel(c->m.ecol_ids, c->m.ecol_off[k], c->m.ecol_off[k + 1], false));
       for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k)
         LAUNCH(c, launch_jacobi_faces32(c->m, c->mats_d, 2.0 / dt, Jd32, c->m.fcol_ids, c->m.fcol_off[k],
                                         c->m.fcol_off[k + 1], false, c->s_main));
@@ -580,8 +738,6 @@ int one_step(ns_ctx *c) {
                                       c->m.fcol_off[k + 1], false, c->s_main));
     }
     LAUNCH(c, launch_invert_blocks(c->Jd, c->Jinv, c->Jinv32, N, c->flag_d, c->s_main));
-    if (c->cfg.precision == NS_PREC_FP64_IR16)
-      LAUNCH(c, launch_D_to_f16(c->D, c->m.mat, c->mats_d, c->D16, c->m.epad, c->m.E, c->s_main));
   }
   tend(c, TK_JAC, c->s_main, t0);
 
@@ -596,44 +752,26 @@ int one_step(ns_ctx *c) {
   // PCG on A du = b, starting from the previous increment (or zero)
   tbegin(c, TK_SOLVE, c->s_main, &t0);
   CKC(c, cudaMemcpyAsync(c->flag_h, c->flag_d, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s_main));
-  if (c->cfg.precision != NS_PREC_FP64) {
-    if ((rc = solve_ir(c)) != NS_OK) return rc;
-  } else {
-  if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
-  if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
-  const int nbv = vec_blocks(N);
-  double *pv = c->part + c->part_pap_cap;
-  LAUNCH(c, launch_cg_init(c->b, c->Ap, c->Jinv, c->r, c->z, c->p, N, pv, c->s_main));
-  LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc, NS_FIN_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
-  if ((rc = read_scalars(c)) != NS_OK) return rc;
-  if (c->sc_h->done == 2) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
-  const int batch = 8;
-  const int32_t *skip = &c->sc->done;
-  if (c->sc_h->done == 0) {
-    CKC(c, cudaMemsetAsync(c->Ap, 0, sizeof(double) * 3 * N, c->s_main));
-    for (;;) {
-      for (int it = 0; it < batch; ++it) {
-        int np = 0;
-        if ((rc = apply_A(c, c->p, c->Ap, false, c->part, skip, &np, true)) != NS_OK) return rc;
-        LAUNCH(c, launch_cg_final(c->part, np, 1, c->sc, NS_FIN_PAP, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
-        LAUNCH(c, launch_cg_update(c->du, c->r, c->z, c->p, c->Ap, c->Jinv, N, pv, c->sc, c->s_main));
-        LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc, NS_FIN_UPDATE, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main));
-        LAUNCH(c, launch_cg_pupdate(c->p, c->z, c->Ap, N, c->sc, c->s_main));
-      }
-      if ((rc = read_scalars(c)) != NS_OK) return rc;
-      if (c->sc_h->done) break;
-    }
-  }
-  }
+  if ((rc = (c->cfg.precision != NS_PREC_FP64) ? solve_ir(c) : solve_pcg(c)) != NS_OK) return rc;
   tend(c, TK_SOLVE, c->s_main, t0);
   if (*c->flag_h) NS_SET(c, NS_ERR_STATE, "block-Jacobi preconditioner has a non-positive diagonal block");
-  if (c->sc_h->done == 3) {
-    c->stats.cg_iters_last = c->sc_h->iters;
-    NS_SET(c, NS_ERR_NOT_CONVERGED, "CG reached the iteration limit at step " + std::to_string(n));
+  int most = 0, lim = -1;
+  double relres = 0.0;
+  c->member_iters.assign(c->M, 0);
+  for (int m = 0; m < c->M; ++m) {
+    const CgScalars &sh = c->sc_h[m];
+    c->member_iters[m] = sh.iters;
+    most = std::max(most, sh.iters);
+    if (sh.done == 3 && lim < 0) lim = m;
+    if (sh.bb > 0) relres = std::max(relres, sqrt(sh.rr / sh.bb));
   }
-  c->stats.cg_iters_last = c->sc_h->iters;
-  c->stats.cg_iters_total += c->sc_h->iters;
-  c->stats.relres_last = c->sc_h->bb > 0 ? sqrt(c->sc_h->rr / c->sc_h->bb) : 0.0;
+  c->stats.cg_iters_last = most;
+  if (lim >= 0)
+    NS_SET(c, NS_ERR_NOT_CONVERGED,
+           "CG reached the iteration limit at step " + std::to_string(n) +
+               (c->M > 1 ? " (member " + std::to_string(lim) + ")" : std::string()));
+  c->stats.cg_iters_total += most;
+  c->stats.relres_last = relres;
 
   // q^n = q^{n-1} + K^n du; u, v, a updates; surface record
   tbegin(c, TK_NEWMARK, c->s_main, &t0);
@@ -699,6 +837,8 @@ void ns_config_default(ns_config *cfg) {
   cfg->inner_max_iter = 30;
   cfg->inner_tol = 1e-3;
   cfg->wait_timeout_s = 120.0;
+  cfg->graphs = 1;
+  cfg->stage_elements = 1;
 }
 
 static thread_local std::string g_create_err;
@@ -794,7 +934,7 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
   for (int64_t e = 0; e < E; ++e)
     for (int a = 0; a < 10; ++a) soa[(size_t)a * m.epad + e] = conn[e * 10 + a];
   if ((rc = dalloc(c, &m.conn, soa.size())) || (rc = dalloc(c, &m.geom, 10 * m.epad)) ||
-      (rc = dalloc(c, &m.geom32, 10 * m.epad)) || (rc = dalloc(c, &m.mat, m.epad)) ||
+      (rc = dalloc(c, &m.geom32, 10 * m.epad)) || (rc = dalloc(c, &m.mat, m.epad)) || (rc = dalloc(c, &m.kerr, 1)) ||
       (rc = dalloc(c, &c->xyz_d, 3 * N)))
     return rc;
   CKC(c, cudaMemcpy(m.conn, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice));
@@ -802,6 +942,8 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
   CKC(c, cudaMemcpy(c->xyz_d, xyz, N * 24, cudaMemcpyHostToDevice));
   CKC(c, cudaMemsetAsync(m.geom, 0, 10 * m.epad * 8, c->s_main));
   CKC(c, cudaMemsetAsync(m.geom32, 0, 10 * m.epad * 4, c->s_main));
+  if (m.epad > E) CKC(c, cudaMemsetAsync(m.mat + E, 0, (m.epad - E) * 4, c->s_main));  // read by tile copies
+  CKC(c, cudaMemsetAsync(m.kerr, 0, 4, c->s_main));
   CKC(c, cudaMemsetAsync(c->flag_d, 0, 4, c->s_main));
   LAUNCH(c, launch_geometry(m, c->xyz_d, c->flag_d, c->s_main));
   CKC(c, cudaStreamSynchronize(c->s_main));
@@ -898,7 +1040,10 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   const int64_t E = c->m.E, epad = c->m.epad;
   if ((rc = dalloc(c, &c->D, 84 * (size_t)epad))) return rc;
   if (c->cfg.precision == NS_PREC_FP64_IR && (rc = dalloc(c, &c->D32, 84 * (size_t)epad))) return rc;
-  if (c->cfg.precision == NS_PREC_FP64_IR16 && (rc = dalloc(c, &c->D16, 84 * (size_t)epad))) return rc;
+  if (c->cfg.precision == NS_PREC_FP64_IR16) {
+    if ((rc = dalloc(c, &c->D16, 84 * (size_t)epad))) return rc;
+    CKC(c, cudaMemsetAsync(c->D16, 0, 84 * epad * 2, c->s_main));
+  }
   CKC(c, cudaMemsetAsync(c->D, 0, 84 * epad * 8, c->s_main));
   LAUNCH(c, launch_elastic_D(c->tab, c->mats_d, c->m.mat, c->D, epad, 0, E, c->s_main));
   const int64_t per_elem = ns_state_bytes(1, S);
@@ -947,6 +1092,7 @@ int ns_set_boundary(ns_ctx *c, int64_t F, const int32_t *faces, const int32_t *f
     for (int a = 0; a < 6; ++a) soa[(size_t)a * m.fpad + f] = faces[f * 6 + a];
     fm[f] = mh[face_elem[f]];
   }
+  c->face_elem_h.assign(face_elem, face_elem + F);
   if ((rc = dalloc(c, &m.fnode, soa.size())) || (rc = dalloc(c, &m.fgeom, 4 * (size_t)m.fpad)) ||
       (rc = dalloc(c, &m.fmat, fm.size())) || (rc = dalloc(c, &m.fkind, fm.size())) ||
       (rc = dalloc(c, &m.surf, (size_t)std::max<int64_t>(Ns, 1))))
@@ -1005,10 +1151,126 @@ int ns_set_ground_motion(ns_ctx *c, int64_t ns_, double dt, const double *acc) {
     }
   int rc;
   dfree(c->vin_d);
-  if ((rc = dalloc(c, &c->vin_d, vin.size()))) return rc;
-  CKC(c, cudaMemcpy(c->vin_d, vin.data(), vin.size() * 8, cudaMemcpyHostToDevice));
+  // [M][n_vin][3]: every member starts with this record
+  if ((rc = dalloc(c, &c->vin_d, vin.size() * (size_t)c->M))) return rc;
+  for (int m = 0; m < c->M; ++m)
+    CKC(c, cudaMemcpy(c->vin_d + (size_t)m * vin.size(), vin.data(), vin.size() * 8, cudaMemcpyHostToDevice));
   c->n_vin = ns_ + 1;
   c->has_motion = true;
+  return NS_OK;
+}
+
+int ns_set_member_ground_motion(ns_ctx *c, int32_t member, int64_t ns_, double dt, const double *acc) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_motion) NS_SET(c, NS_ERR_STATE, "set the common record (ns_set_ground_motion) first");
+  if (member < 0 || member >= c->M) NS_SET(c, NS_ERR_INVALID_ARG, "member index out of range");
+  if (ns_ + 1 != c->n_vin || !acc) NS_SET(c, NS_ERR_INVALID_ARG, "member records must have the common record's length");
+  if (!(fabs(dt - c->cfg.dt) <= 1e-12 * c->cfg.dt)) NS_SET(c, NS_ERR_INVALID_ARG, "record dt differs from the step dt");
+  std::vector<double> vin(3 * (size_t)(ns_ + 1), 0.0);
+  for (int64_t k = 1; k <= ns_; ++k)
+    for (int cc = 0; cc < 3; ++cc) {
+      const double a0 = acc[3 * (k - 1) + cc], a1 = (k < ns_) ? acc[3 * k + cc] : 0.0;
+      vin[3 * k + cc] = vin[3 * (k - 1) + cc] + 0.5 * dt * (a0 + a1);
+    }
+  CKC(c, cudaMemcpy(c->vin_d + (size_t)member * vin.size(), vin.data(), vin.size() * 8, cudaMemcpyHostToDevice));
+  return NS_OK;
+}
+
+int ns_set_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t *node_off) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh || !c->has_bnd) NS_SET(c, NS_ERR_STATE, "upload the mesh and the boundary before the members");
+  if (c->has_motion || c->step > 0 || c->M > 1) NS_SET(c, NS_ERR_STATE, "members must be set before the ground motion");
+  if (c->cfg.scatter != NS_SCATTER_ATOMIC) NS_SET(c, NS_ERR_INVALID_ARG, "members need the atomic scatter");
+  if (M < 1 || M > 65536 || !elem_off || !node_off) NS_SET(c, NS_ERR_INVALID_ARG, "bad member count");
+  const DevMesh &m = c->m;
+  if (elem_off[0] != 0 || elem_off[M] != m.E || node_off[0] != 0 || node_off[M] != m.N)
+    NS_SET(c, NS_ERR_INVALID_ARG, "member ranges must cover all elements and nodes");
+  for (int k = 0; k < M; ++k)
+    if (elem_off[k + 1] <= elem_off[k] || node_off[k + 1] <= node_off[k])
+      NS_SET(c, NS_ERR_INVALID_ARG, "every member needs elements and nodes");
+  // every element's nodes in its member's node range
+  std::vector<int32_t> conn((size_t)10 * m.epad);
+  CKC(c, cudaMemcpy(conn.data(), m.conn, conn.size() * 4, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < M; ++k)
+    for (int64_t e = elem_off[k]; e < elem_off[k + 1]; ++e)
+      for (int a = 0; a < 10; ++a) {
+        const int64_t nd = conn[(size_t)a * m.epad + e];
+        if (nd < node_off[k] || nd >= node_off[k + 1])
+          NS_SET(c, NS_ERR_BAD_MESH, "element " + std::to_string(e) + " uses a node of another member");
+      }
+  // faces ordered by member
+  std::vector<int32_t> fmem((size_t)std::max<int64_t>(m.F, 1), 0);
+  std::vector<int64_t> foff(M + 1, 0);
+  for (int64_t f = 0; f < m.F; ++f) {
+    const int64_t e = c->face_elem_h[f];
+    const int k = (int)(std::upper_bound(elem_off, elem_off + M + 1, e) - elem_off) - 1;
+    if (f > 0 && k < fmem[f - 1]) NS_SET(c, NS_ERR_INVALID_ARG, "boundary faces must be ordered by member");
+    fmem[f] = k;
+    foff[k + 1]++;
+  }
+  for (int k = 0; k < M; ++k) foff[k + 1] += foff[k];
+  c->moff_e.assign(elem_off, elem_off + M + 1);
+  c->moff_n.assign(node_off, node_off + M + 1);
+  c->moff_f = foff;
+  // launch cuts: element and face blocks of kBlock, node-vector blocks in proportion to size
+  std::vector<Seg> es, fs, vs;
+  std::vector<int32_t> eo(M + 1, 0), fo(M + 1, 0), vo(M + 1, 0);
+  const int vcap = 152 * 8;
+  for (int k = 0; k < M; ++k) {
+    for (int64_t a = elem_off[k]; a < elem_off[k + 1]; a += kBlock)
+      es.push_back(Seg{a, std::min<int64_t>(a + kBlock, elem_off[k + 1]), k, 0});
+    for (int64_t a = foff[k]; a < foff[k + 1]; a += kBlock)
+      fs.push_back(Seg{a, std::min<int64_t>(a + kBlock, foff[k + 1]), k, 0});
+    const int64_t nk = node_off[k + 1] - node_off[k];
+    int64_t bk = std::min<int64_t>((nk + kBlock - 1) / kBlock, 1 + (int64_t)((double)vcap * nk / m.N));
+    bk = std::max<int64_t>(bk, 1);
+    for (int64_t b = 0; b < bk; ++b)
+      vs.push_back(Seg{node_off[k] + nk * b / bk, node_off[k] + nk * (b + 1) / bk, k, 0});
+    eo[k + 1] = (int32_t)es.size();
+    fo[k + 1] = (int32_t)fs.size();
+    vo[k + 1] = (int32_t)vs.size();
+  }
+  int rc;
+  auto up = [&](auto **dst, const auto &src) -> int {
+    dfree(*dst);
+    int r = dalloc(c, dst, std::max<size_t>(src.size(), 1));
+    if (r) return r;
+    if (!src.empty()) {
+      cudaError_t e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(src[0]), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        c->err = cudaGetErrorString(e);
+        return NS_ERR_CUDA;
+      }
+    }
+    return NS_OK;
+  };
+  if ((rc = up(&c->eseg_d, es)) || (rc = up(&c->fseg_d, fs)) || (rc = up(&c->vseg_d, vs)) ||
+      (rc = up(&c->eoff_d, eo)) || (rc = up(&c->foff_d, fo)) || (rc = up(&c->voff_d, vo)) ||
+      (rc = up(&c->fmem_d, fmem)))
+    return rc;
+  c->neseg = (int)es.size();
+  c->nfseg = (int)fs.size();
+  c->nvseg = (int)vs.size();
+  // per-member CG scalars (outer [0, M), inner [M, 2M)) and partial-sum space
+  destroy_graphs(c);
+  dfree(c->sc);
+  hfree(c->sc_h);
+  if ((rc = dalloc(c, &c->sc, 2 * (size_t)M)) || (rc = halloc(c, &c->sc_h, 2 * (size_t)M))) return rc;
+  CKC(c, cudaMemsetAsync(c->sc, 0, 2 * M * sizeof(CgScalars), c->s_main));
+  c->sc_in = c->sc + M;
+  c->part_pap_cap = std::max<int64_t>(c->part_pap_cap, (int64_t)c->neseg + c->nfseg + 64);
+  dfree(c->part);
+  if ((rc = dalloc(c, &c->part, (size_t)(c->part_pap_cap + 3 * std::max(c->nvseg, vec_blocks(m.N)))))) return rc;
+  CKC(c, cudaStreamSynchronize(c->s_main));
+  c->M = M;
+  c->member_iters.assign(M, 0);
+  return NS_OK;
+}
+
+int ns_get_member_iters(ns_ctx *c, int32_t M, int32_t *iters) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (M != c->M || !iters) NS_SET(c, NS_ERR_INVALID_ARG, "member count differs from the context's");
+  for (int k = 0; k < M; ++k) iters[k] = k < (int)c->member_iters.size() ? c->member_iters[k] : 0;
   return NS_OK;
 }
 
@@ -1050,6 +1312,9 @@ int ns_advance(ns_ctx *c, int64_t nsteps) {
   if (cudaEventElapsedTime(&ms, c->ev_adv0, c->ev_adv1) == cudaSuccess) c->stats.ms_advance += ms;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) NS_SET(c, NS_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+  int32_t kerr = 0;
+  CKC(c, cudaMemcpy(&kerr, c->m.kerr, 4, cudaMemcpyDeviceToHost));
+  if (kerr) NS_SET(c, NS_ERR_TIMEOUT, "a kernel's bounded wait for its shared-memory copies gave up");
   return NS_OK;
 }
 
@@ -1388,11 +1653,14 @@ void ns_destroy(ns_ctx *c) {
   if (c->s_h2d) cudaStreamSynchronize(c->s_h2d);
   if (c->s_d2h) cudaStreamSynchronize(c->s_d2h);
   DevMesh &m = c->m;
-  dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
+  dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.kerr); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
   dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
   dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
   dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->T2_d); dfree(c->D); dfree(c->D32);
   dfree(c->D16); dfree(c->op_A16);
+  destroy_graphs(c);
+  dfree(c->vseg_d); dfree(c->eseg_d); dfree(c->fseg_d); dfree(c->voff_d); dfree(c->eoff_d); dfree(c->foff_d);
+  dfree(c->fmem_d);
   free_soa(c->st, false);
   free_soa(c->hst, true);
   for (auto &rb : c->ring) free_soa(rb, false);

@@ -12,7 +12,7 @@ namespace ns {
 
 constexpr int kQ = 4;          // integration points per element
 constexpr int kDPack = 21;     // unique entries of a symmetric 6x6
-constexpr int kMaxMat = 64;
+constexpr int kMaxMat = 1024;  // material table entries (members of a batch each bring their own)
 constexpr int kBlock = 256;
 
 // Per-material constants derived on the host from ns_material and the config.
@@ -47,6 +47,7 @@ struct DevMesh {
   // colour mode: element and face ids sorted by colour
   int32_t *ecol_ids = nullptr, *fcol_ids = nullptr;
   std::vector<int64_t> ecol_off, fcol_off;
+  int32_t *kerr = nullptr;  // device flag: a bounded wait inside a kernel gave up
 };
 
 // Spring state arrays (structure of arrays over springs ordered [elem][point][spring]).
@@ -62,6 +63,30 @@ struct CgScalars {
   unsigned int counter;
   unsigned int counter2;
 };
+// int32 stride between the `done` flags of consecutive members' scalars
+constexpr int kScStride = (int)(sizeof(CgScalars) / sizeof(int32_t));
+static_assert(sizeof(CgScalars) % sizeof(int32_t) == 0, "CgScalars must be a whole number of int32");
+
+// Batched members (independent sub-models of one disjoint-union mesh): a launch over
+// elements, faces or nodes is cut into blocks that never straddle two members.  Block b
+// covers indices [a0, a1) of member m; its partial sums land in slot b, and the
+// partial sums of member m are the slots [off[m], off[m+1]) of that launch.
+struct Seg {
+  int64_t a0, a1;
+  int32_t m, pad;
+};
+struct SegList {
+  const Seg *seg = nullptr;  // nullptr: one member, the historical flat launch
+  int n = 0;                 // blocks
+  const int32_t *off = nullptr;  // [M + 1] block offsets per member (device)
+};
+// Which partial sums make up member m's value: slots [off1[m], off1[m+1]) and, when off2
+// is set, base2 + [off2[m], off2[m+1]).  off1 == nullptr: one member, all n slots.
+struct PartMap {
+  const int32_t *off1 = nullptr;
+  const int32_t *off2 = nullptr;
+  int32_t base2 = 0;
+};
 
 // ------------------------------------------------------------------ launchers (k_*.cu)
 // All return cudaGetLastError() of their launch.
@@ -71,24 +96,30 @@ cudaError_t launch_face_geometry(const DevMesh &m, const double *xyz, cudaStream
 // y (+)= Op x over elements [e0, e1) or over the colour list ids[e0, e1) when ids != nullptr.
 // xm may be nullptr (then mM is ignored).  If dot != nullptr, block partial sums of x_e . y_e go
 // to dot[blockIdx.x] (the element-local energy of the application).
+// With sg.seg set (members, atomic scatter) the launch covers sg's blocks instead of
+// [e0, e1), and the skip flag of each block is that of its member (skip + m * kScStride).
 cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
-                         const int32_t *skip, cudaStream_t s);
+                         const int32_t *skip, cudaStream_t s, SegList sg = {});
+// staged: whole-mesh atomic launches stage each tile of elements in shared memory with
+// bulk copies (cp.async.bulk) instead of per-thread loads.
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s);
+                         cudaStream_t s, SegList sg = {}, bool staged = false);
 // As launch_ebe32 with D stored as FP16 pairs [42][epad] (entries 2j, 2j+1 of the [84] point-major
 // order) holding D / G0 of the element's material; op->kK carries the factor G0.
 cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s);
-// Boundary faces: y (+)= cC * C_f (x + [kind 0] vin) (vin may be nullptr)
+                         cudaStream_t s, SegList sg = {}, bool staged = false);
+// Boundary faces: y (+)= cC * C_f (x + [kind 0] vin) (vin may be nullptr); with members the
+// input of face f is vin + fmem[f] * vin_stride.
 cudaError_t launch_faces64(const DevMesh &m, const MatConst *mc, double cC, const double *x, const double *vin,
                            double *y, const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot,
-                           const int32_t *skip, cudaStream_t s);
+                           const int32_t *skip, cudaStream_t s, SegList sg = {}, const int32_t *fmem = nullptr,
+                           int64_t vin_stride = 0);
 cudaError_t launch_faces32(const DevMesh &m, const MatConst *mc, float cC, const float *x, float *y,
                            const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot, const int32_t *skip,
-                           cudaStream_t s);
+                           cudaStream_t s, SegList sg = {});
 // 3x3 diagonal blocks of A (packed xx yy zz yz xz xy) accumulated into Jd [N][6]
 cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef *op, double *Jd, const int32_t *ids,
                                 int64_t e0, int64_t e1, bool atomic, cudaStream_t s);
@@ -96,6 +127,9 @@ cudaError_t launch_jacobi_faces(const DevMesh &m, const MatConst *mc, double cC,
                                 int64_t f0, int64_t f1, bool atomic, cudaStream_t s);
 // FP32 variants (the preconditioner of the flexible solver only needs single precision)
 cudaError_t launch_jacobi_elems32(const DevMesh &m, const float *D, const OpCoef *op, float *Jd, const int32_t *ids,
+                                  int64_t e0, int64_t e1, bool atomic, cudaStream_t s);
+// from the FP16 tangent pairs (op->kK carries G0, as for launch_ebe16)
+cudaError_t launch_jacobi_elems16(const DevMesh &m, const void *D16, const OpCoef *op, float *Jd, const int32_t *ids,
                                   int64_t e0, int64_t e1, bool atomic, cudaStream_t s);
 cudaError_t launch_jacobi_faces32(const DevMesh &m, const MatConst *mc, double cC, float *Jd, const int32_t *ids,
                                   int64_t f0, int64_t f1, bool atomic, cudaStream_t s);
@@ -112,7 +146,7 @@ cudaError_t launch_invert_blocks(const double *Jd, double *Jinv, float *Jinv32, 
 int vec_blocks(int64_t n_nodes);  // fixed grid of the node-vector kernels (partials per block)
 // r = b - Ap; z = Jinv r; p = z; block partials of b.b, r.r, r.z -> part[0..3*nb)
 cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv, double *r, double *z, double *p,
-                           int64_t N, double *part, cudaStream_t s);
+                           int64_t N, double *part, cudaStream_t s, SegList sg = {});
 #define NS_FIN_INIT 0
 #define NS_FIN_PAP 1
 #define NS_FIN_UPDATE 2
@@ -122,28 +156,36 @@ cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv
 // One block sums part[v*n .. v*n+n) for v < nvals in a fixed order and updates the CG scalars:
 //  INIT: bb, rr, rz -> done (1 converged, 2 zero right-hand side); PAP: pAp, alpha = rz/pAp;
 //  UPDATE: rr, rz -> iters++, done (1 converged, 3 iteration limit), beta = rz/rz_old.
+// With members (M > 1) one block per member, summing the slots that pm assigns to it, each
+// member updating its own scalars sc[m].  A member whose gate[m].done is set is marked done
+// without reading its partials (the inner solve of a member whose outer solve converged).
 cudaError_t launch_cg_final(const double *part, int n, int nvals, CgScalars *sc, int mode, double tol, int max_iter,
-                            cudaStream_t s);
+                            cudaStream_t s, int M = 1, PartMap pm = {}, const CgScalars *gate = nullptr);
 // x += alpha p; r -= alpha Ap; z = Jinv r; partials r.r, r.z -> part[0..2*nb)
 cudaError_t launch_cg_update(double *x, double *r, double *z, const double *p, const double *Ap, const double *Jinv,
-                             int64_t N, double *part, const CgScalars *sc, cudaStream_t s);
+                             int64_t N, double *part, const CgScalars *sc, cudaStream_t s, SegList sg = {});
 // p = z + beta p; Ap = 0
-cudaError_t launch_cg_pupdate(double *p, const double *z, double *Ap, int64_t N, const CgScalars *sc, cudaStream_t s);
+cudaError_t launch_cg_pupdate(double *p, const double *z, double *Ap, int64_t N, const CgScalars *sc, cudaStream_t s,
+                              SegList sg = {});
 // flexible outer CG (FP64) with the inner FP32 PCG as preconditioner
-cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_t N, double *part, cudaStream_t s);
+cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_t N, double *part, cudaStream_t s,
+                            SegList sg = {});
 cudaError_t launch_fcg_gamma(const float *xin, double *z, const double *Ap, int64_t N, double *part,
-                             const CgScalars *so, cudaStream_t s);
+                             const CgScalars *so, cudaStream_t s, SegList sg = {});
 cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, int64_t N, double *part,
-                         const CgScalars *so, cudaStream_t s);
-cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int npap, CgScalars *sc, cudaStream_t s);
+                         const CgScalars *so, cudaStream_t s, SegList sg = {});
+// alpha = (p.r)/(p.Ap): pr holds vector partials (member m: pmr), pap operator partials (pma)
+cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int npap, CgScalars *sc, cudaStream_t s,
+                             int M = 1, PartMap pmr = {}, PartMap pma = {});
 cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, int64_t N, double *part,
-                              const CgScalars *so, cudaStream_t s);
+                              const CgScalars *so, cudaStream_t s, SegList sg = {});
 cudaError_t launch_in_init(const double *r, const CgScalars *so, const float *J, float *rin, float *zin, float *pin,
-                           float *xin, float *Apin, int64_t N, double *part, cudaStream_t s);
+                           float *xin, float *Apin, int64_t N, double *part, cudaStream_t s, SegList sg = {});
 cudaError_t launch_in_update(float *xin, float *rin, float *zin, const float *pin, const float *Apin, const float *J,
-                             int64_t N, double *part, const CgScalars *si, const CgScalars *so, cudaStream_t s);
+                             int64_t N, double *part, const CgScalars *si, const CgScalars *so, cudaStream_t s,
+                             SegList sg = {});
 cudaError_t launch_in_pupdate(float *pin, const float *zin, float *Apin, int64_t N, const CgScalars *si,
-                              const CgScalars *so, cudaStream_t s);
+                              const CgScalars *so, cudaStream_t s, SegList sg = {});
 cudaError_t launch_newmark(double *u, double *v, double *a, double *du_prev, const double *du, int64_t N, double dt,
                            cudaStream_t s);
 cudaError_t launch_surface_gather(const int32_t *surf, int64_t Ns, const double *u, const double *v, const double *a,

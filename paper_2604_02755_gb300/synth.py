@@ -383,3 +383,60 @@ def ensemble_members(M: int = 64, nt: int = 4000, seed: int = 3, n_springs: int 
     waves = [band_limited_wave(seed * 1000 + 17 + k, nt + 1, 0.005) for k in range(M)]
     return Ensemble("batched ensemble, %d members on 160x160x84 m at 4 m, 50 springs" % M, m, members, waves,
                     n_springs, 0.005, nt)
+
+
+@dataclass
+class Union:
+    mesh: Mesh
+    elem_off: np.ndarray  # [M + 1]
+    node_off: np.ndarray  # [M + 1]
+
+
+def union_of_copies(mesh: Mesh, M: int, n_materials: int) -> Union:
+    """Disjoint union of M copies of a mesh (copy m: nodes shifted by m * N, elements by
+    m * E, material ids by m * n_materials, faces and surface nodes in copy order)."""
+    N, E, F = mesh.n_nodes, mesh.n_elems, mesh.faces.shape[0]
+    k = np.arange(M)
+    xyz = np.tile(mesh.xyz, (M, 1))
+    conn = (mesh.conn[None, :, :] + (k * N)[:, None, None]).reshape(M * E, 10).astype(np.int32)
+    mat = (mesh.mat[None, :] + (k * n_materials)[:, None]).reshape(-1).astype(np.int32)
+    faces = (mesh.faces[None, :, :] + (k * N)[:, None, None]).reshape(M * F, 6).astype(np.int32)
+    face_elem = (mesh.face_elem[None, :] + (k * E)[:, None]).reshape(-1).astype(np.int32)
+    face_kind = np.tile(mesh.face_kind, M).astype(np.int32)
+    surf = (mesh.surf[None, :] + (k * N)[:, None]).reshape(-1).astype(np.int32)
+    u = Mesh(xyz=xyz, conn=conn, mat=mat, faces=faces, face_elem=face_elem, face_kind=face_kind, surf=surf,
+             dims=mesh.dims)
+    return Union(u, np.arange(M + 1, dtype=np.int64) * E, np.arange(M + 1, dtype=np.int64) * N)
+
+
+@dataclass
+class Request:
+    arrival_s: float
+    workload: Workload
+    n_steps: int
+
+
+def served_trace(R: int = 12, rate_per_s: float = 4.0, seed: int = 5, step_scale: float = 0.01,
+                 e_lo: float = 5e4, e_hi: float = 2e6, nz: int = 21, h: float = 4.0) -> list:
+    """Served ensemble: R requests with Poisson arrivals (rate_per_s), meshes of
+    log-uniform size in [e_lo, e_hi] elements (nx = ny hexahedra of h metres, nz deep,
+    soil over bedrock at 40 m, jitter 10%), springs ~ U{20..150}, steps ~ U[1000, 4000]
+    times step_scale, soil Vs ~ U(100, 300) m/s, reference strain ~ logU(1e-4, 1e-3),
+    damping ~ U(1, 5)%, independent input waves, dt 0.005 s."""
+    u = uniform01(seed, 8 * R, stream=60).reshape(8, R)
+    t = np.cumsum(-np.log1p(-u[0]) / rate_per_s)
+    out = []
+    for k in range(R):
+        E = math.exp(math.log(e_lo) + (math.log(e_hi) - math.log(e_lo)) * u[1, k])
+        n = max(2, int(round(math.sqrt(E / (6.0 * nz)))))
+        S = 20 + int(u[2, k] * 131) if u[2, k] < 1.0 else 150
+        steps = max(1, int(round((1000 + 3000 * u[3, k]) * step_scale)))
+        vs = 100.0 + 200.0 * u[4, k]
+        gref = 10.0 ** (-4.0 + u[5, k])
+        hr = 0.01 + 0.04 * u[6, k]
+        m = kuhn_box(n, n, nz, n * h, n * h, nz * h, layer_depths=(40.0,), jitter=0.1, seed=seed * 100 + k)
+        mats = [soil(1700.0, vs, gref, 0.20, hr), soil(2000.0, 600.0, 1e-2, 0.20, hr)]
+        w = band_limited_wave(seed * 1000 + k, max(steps + 1, 400), 0.005)
+        wl = Workload("request %d: %dx%dx%d hexahedra, %d springs" % (k, n, n, nz, S), m, mats, S, 0.005, steps, w)
+        out.append(Request(float(t[k]), wl, steps))
+    return out
