@@ -248,6 +248,11 @@ def main():
                          "precision-form model; ensemble: --members cases on a shared 201,600-element mesh "
                          "advanced together; tiny: the 3,600-element two-layer case")
     ap.add_argument("--members", type=int, default=64, help="members of the ensemble workload")
+    ap.add_argument("--stage", type=int, default=0, choices=[0, 1],
+                    help="FP32 inner operator: stage element tiles in shared memory with bulk copies (1) or "
+                         "per-thread loads (0)")
+    ap.add_argument("--inner-iters", type=int, default=30,
+                    help="FP32 inner CG iterations per outer iteration of the flexible solver")
     ap.add_argument("--requests", type=int, default=12, help="requests of the served trace")
     ap.add_argument("--step-scale", type=float, default=0.01,
                     help="served trace: fraction of the 1000-4000 steps each request runs")
@@ -263,6 +268,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--stream-gb", type=float, default=128.0, help="spring state kept in pinned host memory (GB)")
     ap.add_argument("--ring-depth", type=int, default=12, help="device chunk buffers of the streamed state")
+    ap.add_argument("--zero-copy", action="store_true",
+                    help="also measure the streamed state updated in place in pinned host memory (no ring)")
     ap.add_argument("--solver", default="fp64-ir", choices=["fp64-ir", "fp64-ir16", "fp64-pcg"],
                     help="fp64-ir: FP64 flexible CG with an FP32 PCG preconditioner (the paper's precision policy); "
                          "fp64-ir16: the same with the inner operator reading D in FP16; "
@@ -309,7 +316,8 @@ def main():
         wl.wave = wave
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
-    kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs)
+    kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
+              stage_elements=args.stage, inner_max_iter=args.inner_iters)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
     B.ns_reset_stats(sim.ctx)
@@ -381,25 +389,33 @@ def main():
         stream_elems = int(args.stream_gb * 1e9 / per_elem)
         budget = (E - stream_elems) * per_elem
         ring = args.ring_depth
-        sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
-                           ring_depth=ring, precision=prec, graphs=graphs)
-        sim.advance(1)
-        B.ns_reset_stats(sim.ctx)
-        h0 = sim.stats()
-        sim.advance(2)
-        st2 = sim.stats()
-        sim.close()
-        del sim
-        moved = (st2["h2d_bytes"] - h0["h2d_bytes"]) + (st2["d2h_bytes"] - h0["d2h_bytes"])
-        early = st2["h2d_bytes_early"] - h0["h2d_bytes_early"]
-        gbs = (moved - early) / (st2["ms_stream_wall"] / 1e3) / 1e9
-        stream = {"streamed_elems": st2["streamed_elems"], "bytes_per_step": moved / 2,
-                  "early_h2d_bytes_per_step": early / 2,
-                  "stream_GBps": gbs, "link_GBps_measured": link, "frac_of_link": gbs / link,
-                  "window": "multi-spring phase start to last D2H; H2D issued at step start (overlapping the "
-                            "solve) excluded from the bytes",
-                  "step_ms": st2["ms_advance"] / 2, "resident_step_ms": job_s / args.steps * 1e3,
-                  "chunk_elems": 100000, "ring_depth": ring}
+
+        def streamed_run(mode):
+            sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
+                               ring_depth=ring, precision=prec, graphs=graphs, stage_elements=args.stage,
+                               inner_max_iter=args.inner_iters, stream_mode=mode)
+            sim.advance(1)
+            B.ns_reset_stats(sim.ctx)
+            h0 = sim.stats()
+            sim.advance(2)
+            st2 = sim.stats()
+            sim.close()
+            moved = (st2["h2d_bytes"] - h0["h2d_bytes"]) + (st2["d2h_bytes"] - h0["d2h_bytes"])
+            early = st2["h2d_bytes_early"] - h0["h2d_bytes_early"]
+            gbs = (moved - early) / (st2["ms_stream_wall"] / 1e3) / 1e9
+            return {"streamed_elems": st2["streamed_elems"], "bytes_per_step": moved / 2,
+                    "early_h2d_bytes_per_step": early / 2,
+                    "stream_GBps": gbs, "link_GBps_measured": link, "frac_of_link": gbs / link,
+                    "step_ms": st2["ms_advance"] / 2, "resident_step_ms": job_s / args.steps * 1e3}
+
+        stream = streamed_run(B.NS_STREAM_RING)
+        stream.update({"window": "multi-spring phase start to last D2H; H2D issued at step start (overlapping the "
+                                 "solve) excluded from the bytes", "chunk_elems": 100000, "ring_depth": ring})
+        if args.zero_copy:
+            zc = streamed_run(B.NS_STREAM_ZERO_COPY)
+            zc["window"] = ("multi-spring phase (the kernel reads and writes the pinned host state in place); "
+                            "bytes = 40 B read + 40 B written per streamed spring")
+            stream["zero_copy"] = zc
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -422,6 +438,7 @@ def main():
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
                 "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
+                "staged_operator": args.stage, "inner_iters": args.inner_iters,
                 "state_stream": stream}
         print(json.dumps(line), flush=True)
     dist.finalize(dd)

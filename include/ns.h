@@ -84,8 +84,15 @@ typedef struct {
                                   inside are then not recorded (ns_stats ms_ebe32 stays 0) */
   int32_t stage_elements;      /* 1: the FP32 inner operator stages each 256-element tile of element
                                   data in shared memory with bulk copies (atomic scatter, one member);
-                                  0: per-thread loads */
+                                  0 (default): per-thread loads, which measured faster on GB300 */
+  int32_t stream_mode;         /* spring state beyond device_state_budget: NS_STREAM_RING (chunks
+                                  copied through device buffers, Alg. 3) or NS_STREAM_ZERO_COPY
+                                  (the spring kernel reads and writes the pinned host arrays in
+                                  place over the host link) */
 } ns_config;
+
+#define NS_STREAM_RING 0
+#define NS_STREAM_ZERO_COPY 1
 
 /* Material of one element group (Sec. 2.1; parameters of the readings):
  * density, S/P wave speeds, spring reference strain (secant modulus G0/2),

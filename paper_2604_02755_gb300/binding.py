@@ -19,6 +19,7 @@ NS_ERR = {-1: "NS_ERR_INVALID_ARG", -2: "NS_ERR_OOM_DEVICE", -3: "NS_ERR_OOM_PIN
           -5: "NS_ERR_BAD_MESH", -6: "NS_ERR_NOT_CONVERGED", -7: "NS_ERR_TIMEOUT", -8: "NS_ERR_STATE"}
 NS_PREC_FP64, NS_PREC_FP64_IR, NS_PREC_FP64_IR16 = 0, 1, 2
 NS_SCATTER_ATOMIC, NS_SCATTER_COLOUR = 0, 1
+NS_STREAM_RING, NS_STREAM_ZERO_COPY = 0, 1
 NS_FIELD = {"u": 0, "v": 1, "a": 2, "q": 3, "du": 4}
 NS_OP = {"K": 0, "M": 1, "Cb": 2, "A": 3, "Cr": 4}
 
@@ -38,7 +39,8 @@ class ns_config(C.Structure):
                 ("ring_depth", C.c_int32), ("device_state_budget", C.c_int64), ("rayleigh_f1", C.c_double),
                 ("rayleigh_f2", C.c_double), ("surface_ring_steps", C.c_int64), ("device", C.c_int32),
                 ("timing", C.c_int32), ("inner_max_iter", C.c_int32), ("inner_tol", C.c_double),
-                ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32)]
+                ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32),
+                ("stream_mode", C.c_int32)]
 
 
 class ns_material(C.Structure):

@@ -1,0 +1,173 @@
+// Power x^beta in double-float arithmetic (pairs of FP32 numbers, ~48 significand bits)
+// for the spring law's root solve.  GB300 issues FP32 arithmetic at 64 times its FP64
+// rate, so evaluating the power on the FP32 pipes leaves the scarce FP64 pipe to the
+// parts of the update that need FP64 state.
+//
+// Method (table-driven logarithm and exponential after Tang, ACM TOMS 1989/1990, with
+// the error-free transformations of Dekker and Knuth for the pairs):
+//   x = 2^e m (1 + eps),   m in [1, 2),   j = top 7 bits of m's fraction,
+//   A = ln(m (1 + eps)) = -ln r_j + ln(1 + u) + eps - eps^2/2,   u = m r_j - 1 (|u| < 2^-7.9),
+//   beta e = nb + phi (nb an integer, 0 <= phi < 1),   y = phi ln2 + beta A   (|y| < 2.5),
+//   k = round(64 y / ln2),   f = y - k ln2/64   (|f| <= ln2/128),
+//   x^beta = 2^(nb + floor(k/64)) 2^((k mod 64)/64) exp(f).
+// Taking the integer part of beta e out before the exponential keeps its argument small,
+// so the pair's ~48 bits give a relative error near 2^-47 for any x; ln2/64 is split into
+// three floats whose leading two carry few significant bits, so that k times them is
+// exact; r_j, -ln r_j and 2^(i/64) are tables built on the host in extended precision.
+// The series keep the pair precision only where the terms are large enough to need it.
+//
+// Written for both the device and the host (the host build must not contract
+// multiply-adds: -ffp-contract=off), so that the same arithmetic can be checked on a CPU.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#if defined(__CUDACC__)
+#define NS_HD __host__ __device__ __forceinline__
+#else
+#define NS_HD inline
+#endif
+
+namespace ns {
+
+// floats of the power tables (device array of kPowFLen floats)
+//   [0, 128)   r_j                   [128, 256) -ln r_j, high     [256, 384) -ln r_j, low
+//   [384, 448) 2^(i/64), high        [448, 512) 2^(i/64), low
+//   [512, 520) ln2 as a pair, ln2/64 in three parts (d0 d1 d2, the first two with few
+//              significant bits), 64/ln2, 0, 0
+constexpr int kPowFLen = 520;
+
+#if defined(__CUDA_ARCH__)
+NS_HD float df_add(float a, float b) { return __fadd_rn(a, b); }
+NS_HD float df_sub(float a, float b) { return __fsub_rn(a, b); }
+NS_HD float df_mul(float a, float b) { return __fmul_rn(a, b); }
+NS_HD float df_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+NS_HD uint32_t df_bits(float x) { return __float_as_uint(x); }
+NS_HD float df_from_bits(uint32_t b) { return __uint_as_float(b); }
+NS_HD float df_rint(float x) { return rintf(x); }
+NS_HD float df_rcp(float x) { return __frcp_rn(x); }
+#else
+NS_HD float df_add(float a, float b) { return a + b; }
+NS_HD float df_sub(float a, float b) { return a - b; }
+NS_HD float df_mul(float a, float b) { return a * b; }
+NS_HD float df_fma(float a, float b, float c) { return fmaf(a, b, c); }
+NS_HD uint32_t df_bits(float x) {
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  return b;
+}
+NS_HD float df_from_bits(uint32_t b) {
+  float x;
+  memcpy(&x, &b, 4);
+  return x;
+}
+NS_HD float df_rint(float x) { return rintf(x); }
+NS_HD float df_rcp(float x) { return 1.0f / x; }
+#endif
+
+// a + b = s + e exactly (any order of magnitudes)
+NS_HD void two_sum(float a, float b, float &s, float &e) {
+  s = df_add(a, b);
+  const float bb = df_sub(s, a);
+  e = df_add(df_sub(a, df_sub(s, bb)), df_sub(b, bb));
+}
+// a * b = p + e exactly
+NS_HD void two_prod(float a, float b, float &p, float &e) {
+  p = df_mul(a, b);
+  e = df_fma(a, b, -p);
+}
+
+// Exponent beta in the forms the power needs: a pair (bh + bl, ~48 bits) for beta times the
+// small log A, and three parts for beta times the binary exponent e, which must stay exact
+// to ~2^-56 |e| (an error in beta enters x^beta multiplied by ln x): b0 a multiple of 2^-15,
+// b1 a multiple of 2^-31 (both with at most 16 significant bits, so b0 e and b1 e are
+// exact for |e| < 256), b2 the float rest.
+struct PowBeta {
+  float bh, bl, b0, b1, b2;
+};
+
+// (xh + xl)^beta for a pair with xh a normal float in [2^-100, 2^100] (else false);
+// result (wh, wl).
+NS_HD bool df64_pow(float xh, float xl, const PowBeta &B, const float *__restrict__ tab, float &wh, float &wl) {
+  const float bh = B.bh, bl = B.bl;
+  const uint32_t xb = df_bits(xh);
+  const int ef = (int)((xb >> 23) & 0xff);
+  if ((xb >> 31) || ef < 27 || ef > 227) return false;  // outside [2^-100, 2^100]: caller falls back
+  const float fe = (float)(ef - 127);
+  const int j = (int)((xb >> 16) & 127);
+  const float m = df_from_bits((xb & 0x007fffffu) | 0x3f800000u);
+  const float eps = df_mul(xl, df_rcp(xh));  // |eps| ~ 2^-24; only its leading bits matter
+  const float *c = tab + 512;
+  // beta e = nb + phi, nb an integer, phi in [0, 1) as a pair: the whole exponent
+  // 2^(beta e) is split off, so the argument left for exp stays within |y| < 2.5
+  const float s0 = df_mul(B.b0, fe);  // exact, a multiple of b0's last bit
+  const float nb = floorf(s0);
+  float ph, pl;
+  two_sum(df_sub(s0, nb), df_mul(B.b1, fe), ph, pl);  // s0 - nb and b1 e exact
+  pl = df_fma(B.b2, fe, pl);
+  // u = m r_j - 1 as a pair: the product's rounding error is exact, p - 1 is exact (Sterbenz)
+  float p, pe;
+  two_prod(m, tab[j], p, pe);
+  float u1, u2;
+  two_sum(df_sub(p, 1.0f), pe, u1, u2);  // |u2| <= ulp(u1)/2
+  // ln(1 + u) = u - u^2/2 + u^3/3 - u^4/4 + u^5/5 - u^6/6 (+ O(2^-55)); u1 u2 ~ 2^-40 kept
+  float sq, sqe;
+  two_prod(u1, u1, sq, sqe);
+  float P = df_fma(u1, -1.0f / 6.0f, 0.2f);
+  P = df_fma(u1, P, -0.25f);
+  P = df_fma(u1, P, 1.0f / 3.0f);
+  P = df_mul(df_mul(df_mul(u1, u1), u1), P);
+  float l1h, l1l;
+  two_sum(u1, df_mul(-0.5f, sq), l1h, l1l);
+  l1l = df_add(l1l, df_add(df_add(u2, df_mul(-u1, u2)), df_add(df_mul(-0.5f, sqe), P)));
+  // A = ln m (1 + eps) = -ln r_j + ln(1 + u) + eps - eps^2/2,  |A| < ln2
+  float a1, a2;
+  two_sum(tab[128 + j], l1h, a1, a2);
+  a2 = df_add(df_add(a2, tab[256 + j]), df_add(l1l, df_fma(-0.5f * eps, eps, eps)));
+  // y = phi ln2 + beta A
+  float q1, q2;
+  two_prod(bh, a1, q1, q2);
+  q2 = df_add(q2, df_fma(bh, a2, df_mul(bl, a1)));
+  float r1, r2;
+  two_prod(ph, c[0], r1, r2);
+  r2 = df_add(r2, df_fma(ph, c[1], df_mul(pl, c[0])));
+  float yh, yl;
+  two_sum(r1, q1, yh, yl);
+  yl = df_add(yl, df_add(r2, q2));
+  // exp(y): k = round(64 y / ln2), f = y - k ln2/64 (the first subtraction is exact)
+  const float kf = df_rint(df_mul(yh, c[5]));
+  const int k = (int)kf;
+  const float fh0 = df_sub(yh, df_mul(kf, c[2]));
+  float gh, gl;
+  two_sum(fh0, -df_mul(kf, c[3]), gh, gl);
+  gl = df_add(gl, df_sub(yl, df_mul(kf, c[4])));
+  float g1, g2;
+  two_sum(gh, gl, g1, g2);  // |f| <= ln2/128 + tiny
+  // exp(f) - 1 = f + f^2/2 + f^3/6 + f^4/24 + f^5/120 (+ O(2^-54))
+  float fs, fse;
+  two_prod(g1, g1, fs, fse);
+  float Q = df_fma(g1, 1.0f / 120.0f, 1.0f / 24.0f);
+  Q = df_fma(g1, Q, 1.0f / 6.0f);
+  Q = df_mul(df_mul(df_mul(g1, g1), g1), Q);
+  float E1, E2;
+  two_sum(g1, df_mul(0.5f, fs), E1, E2);
+  E2 = df_add(df_add(E2, g2), df_add(df_fma(0.5f, fse, df_mul(g1, g2)), Q));
+  // 2^(i/64) (1 + E)
+  const int i = k & 63;
+  const float Th = tab[384 + i], Tl = tab[448 + i];
+  float th, tl;
+  two_prod(Th, E1, th, tl);
+  float s1, s2;
+  two_sum(Th, th, s1, s2);
+  s2 = df_add(df_add(s2, Tl), df_add(tl, df_fma(Th, E2, df_mul(Tl, E1))));
+  // times 2^(nb + floor(k/64)), a normal float for the accepted range of x
+  const int n = (int)nb + (k >> 6);
+  if (n < -120 || n > 120) return false;
+  const float sc = df_from_bits((uint32_t)(n + 127) << 23);
+  wh = df_mul(s1, sc);
+  wl = df_mul(s2, sc);
+  return true;
+}
+
+}  // namespace ns

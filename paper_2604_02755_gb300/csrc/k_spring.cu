@@ -119,12 +119,13 @@ __device__ double ro_F_safe(double ga, double tau, const MatConst &p, const PowT
 //     converged and the step is below 2e-5 of tau the safeguarded loop takes over.
 // *pw returns (F/tref)^beta at the returned root.
 __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, const MatConst &p, const PowTab &tb,
-                                           double *pw) {
+                                           const float *__restrict__ tabf, double *pw) {
   double tau = ga;
   bool seeded = true;
+  float t = 0.0f;  // the FP32 seed (tau == t exactly when t > 0)
   if (solve) {
     const float gaf = (float)ga, hif = p.G0_f * gaf, gs = (float)guess;
-    float t = (gs > 0.0f && gs < hif) ? gs : hif;
+    t = (gs > 0.0f && gs < hif) ? gs : hif;
     seeded = false;
     for (int it = 0; it < 40 && t > 0.0f; ++it) {
       const float pwf = __powf(t * p.itref_f, p.beta_f);
@@ -146,7 +147,20 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
     *pw = 0.0;
     return 0.0;
   }
-  double w = pow_pos(tau * p.itref, p.beta_ro, tb);
+  // the power at the seed: on the FP32 pipes in double-float arithmetic when the seed is an
+  // FP32 number in range (x = t itref as a float pair), else the FP64 table-driven power
+  double w;
+  bool have = false;
+  if (solve && t > 0.0f) {
+    float xh, xl, wh, wl;
+    two_prod(t, p.itref_f, xh, xl);
+    xl = df_fma(t, p.itref_lo, xl);
+    if (df64_pow(xh, xl, p.pbeta, tabf, wh, wl)) {
+      w = (double)wh + (double)wl;
+      have = true;
+    }
+  }
+  if (!have) w = pow_pos(tau * p.itref, p.beta_ro, tb);
   if (solve) {
     // Halley: step = h / (1 - h f''/(2 f')) with h = f/f' the Newton step; |h f''/(2 f')|
     // is ~ the seed error (<= 4e-6), so 1/(1 - c) = 1 + c to far below rounding
@@ -179,8 +193,9 @@ __device__ __forceinline__ double ro_tangent_from_pw(double pw, const MatConst &
 // skeleton tau = F(gamma) (decided before the root solve, so each spring solves once).
 // With no increment the state is kept and only the tangent is evaluated.
 // Returns the tangent dtau/dgamma at the end state.
-__device__ __forceinline__ double spring_update(double g, double dg, const MatConst &p, const PowTab &tb, double &tau,
-                                                double &gR, double &tR, double &gmax, int &dir, int &mode) {
+__device__ __forceinline__ double spring_update(double g, double dg, const MatConst &p, const PowTab &tb,
+                                                const float *__restrict__ tabf, double &tau, double &gR, double &tR,
+                                                double &gmax, int &dir, int &mode) {
   const bool active = !d_is_zero(dg);
   double x, guess = 0.0;
   if (active) {
@@ -210,7 +225,7 @@ __device__ __forceinline__ double spring_update(double g, double dg, const MatCo
     x = (mode == 0) ? tau : 0.5 * (tau - tR);  // the power at the current state only
   }
   double pw;
-  const double f = ro_solve(active, d_abs(x), guess, p, tb, &pw);
+  const double f = ro_solve(active, d_abs(x), guess, p, tb, tabf, &pw);
   if (active) {
     const double fs = d_copysign(f, x);
     if (mode == 0) {
@@ -233,7 +248,8 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
                                                     const double *__restrict__ eps, double *tau_a, double *gR_a,
                                                     double *tR_a, double *gmax_a, int32_t *dir_a, int32_t *mode_a,
                                                     int64_t base, int64_t p0, int64_t p1, double *D, int64_t epad,
-                                                    double *dpts, const double *__restrict__ ptab) {
+                                                    double *dpts, const double *__restrict__ ptab,
+                                                    const float *__restrict__ ptabf) {
   extern __shared__ float2 Gs[];
   const PowTab tb{ptab, ptab + 128, ptab + 256, ptab + 384, __ldg(ptab + 448), __ldg(ptab + 449), __ldg(ptab + 450),
                   __ldg(ptab + 451)};
@@ -257,7 +273,7 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
     const int64_t si = (p - base) * S + k;
     double tau = tau_a[si], gR = gR_a[si], tR = tR_a[si], gmax = gmax_a[si];
     int dir = dir_a[si], mode = mode_a[si];
-    const double G = spring_update(gam, dgam, rp, tb, tau, gR, tR, gmax, dir, mode);
+    const double G = spring_update(gam, dgam, rp, tb, ptabf, tau, gR, tR, gmax, dir, mode);
     if (dgam != 0.0) {
       tau_a[si] = tau;
       gR_a[si] = gR;
@@ -266,9 +282,13 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
       dir_a[si] = dir;
       mode_a[si] = mode;
     }
-    // keep G as an unevaluated sum of two floats for the double-float accumulation
-    const float gh = (float)G;
-    Gs[g] = make_float2(gh, (float)(G - (double)gh));
+    // G as an unevaluated sum of two floats for the double-float accumulation: the high
+    // part is G with its low 29 significand bits cleared, built as a float from the bit
+    // pattern on the integer pipes (G is a positive modulus in the normal float range)
+    const long long gb = __double_as_longlong(G);
+    const double Ghi = __longlong_as_double(gb & ~0x1FFFFFFFLL);
+    const unsigned int fb = (unsigned int)((((gb >> 52) & 0x7FF) - 896) << 23) | (unsigned int)((gb >> 29) & 0x7FFFFF);
+    Gs[g] = make_float2(__uint_as_float(fb), (float)(G - Ghi));
   }
   __syncthreads();
   const int nout = np * 21;
@@ -338,7 +358,7 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
   k_springs<<<nb, kBlock, smem, s>>>(tab.q, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, st.gR,
-                                     st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow);
+                                     st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow, tab.powf);
   return cudaGetLastError();
 }
 

@@ -55,6 +55,7 @@ struct ns_ctx {
   MatConst *mats_d = nullptr;
   OpCoef *op_A = nullptr, *op_K = nullptr, *op_M = nullptr, *op_Cr = nullptr, *op_rhs = nullptr;
   double *q_d = nullptr, *T_d = nullptr, *pow_d = nullptr;
+  float *powf_d = nullptr;
   float2 *T2_d = nullptr;
   SpringTables tab{};
   double *D = nullptr;
@@ -65,6 +66,7 @@ struct ns_ctx {
   int64_t E_res = 0;
   SpringSoA st;                      // device, resident part
   SpringSoA hst;                     // pinned host, streamed part
+  SpringSoA hst_dev;                 // the same arrays' device addresses (zero-copy mode)
   std::vector<SpringSoA> ring;       // device chunk buffers
   cudaEvent_t *ev_h2d = nullptr, *ev_comp = nullptr, *ev_d2h = nullptr;
   cudaEvent_t ev_d2h_all = nullptr, ev_stream_t0 = nullptr, ev_stream_t1 = nullptr, ev_strain = nullptr;
@@ -452,7 +454,7 @@ int issue_h2d(ns_ctx *c, int64_t k) {
 // right-hand side, preconditioner set-up and solve.
 int prefetch_state(ns_ctx *c) {
   const int64_t nc = n_chunks(c);
-  if (nc == 0 || c->prefetched) return NS_OK;
+  if (nc == 0 || c->prefetched || c->cfg.stream_mode == NS_STREAM_ZERO_COPY) return NS_OK;
   const int64_t h0 = c->stats.h2d_bytes;
   for (int64_t k = 0; k < std::min<int64_t>(nc, c->cfg.ring_depth); ++k) {
     // slot k was last drained by the previous step's D2H of the last chunk it held,
@@ -486,6 +488,16 @@ int spring_phase(ns_ctx *c) {
   const int64_t nc = n_chunks(c);
   if (nc == 0) return spring_launch(c, c->st, 0, 0, c->E_res);
   if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t0, c->s_main));
+  if (c->cfg.stream_mode == NS_STREAM_ZERO_COPY) {
+    // the streamed elements' springs are read and written in pinned host memory in place
+    if ((rc = spring_launch(c, c->st, 0, 0, c->E_res)) != NS_OK) return rc;
+    if ((rc = spring_launch(c, c->hst_dev, c->E_res, c->E_res, c->m.E)) != NS_OK) return rc;
+    const int64_t b = (c->m.E - c->E_res) * 4 * (int64_t)c->tab.S * 40;
+    c->stats.h2d_bytes += b;
+    c->stats.d2h_bytes += b;
+    if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t1, c->s_main));
+    return NS_OK;
+  }
   if ((rc = prefetch_state(c)) != NS_OK) return rc;
   const int R = c->cfg.ring_depth;
   const int64_t S4 = 4 * (int64_t)c->tab.S;
@@ -838,7 +850,8 @@ void ns_config_default(ns_config *cfg) {
   cfg->inner_tol = 1e-3;
   cfg->wait_timeout_s = 120.0;
   cfg->graphs = 1;
-  cfg->stage_elements = 1;
+  cfg->stage_elements = 0;
+  cfg->stream_mode = NS_STREAM_RING;
 }
 
 static thread_local std::string g_create_err;
@@ -859,7 +872,8 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
       (cfg->precision != NS_PREC_FP64 && cfg->precision != NS_PREC_FP64_IR &&
        cfg->precision != NS_PREC_FP64_IR16) ||
       (cfg->scatter != NS_SCATTER_ATOMIC && cfg->scatter != NS_SCATTER_COLOUR) || !(cfg->wait_timeout_s > 0) ||
-      cfg->inner_max_iter < 1 || !(cfg->inner_tol > 0)) {
+      cfg->inner_max_iter < 1 || !(cfg->inner_tol > 0) ||
+      (cfg->stream_mode != NS_STREAM_RING && cfg->stream_mode != NS_STREAM_ZERO_COPY)) {
     g_create_err = "invalid configuration value";
     return NS_ERR_INVALID_ARG;
   }
@@ -1019,21 +1033,26 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
       }
   std::vector<double> ph(kPowTabLen);
   host_pow_tables(ph.data());
+  std::vector<float> pfh(kPowFLen);
+  host_powf_tables(pfh.data());
   std::vector<float2> T2h(21 * (size_t)S);
   for (size_t i = 0; i < T2h.size(); ++i) {
     const float hi = (float)Th[i];
     T2h[i] = make_float2(hi, (float)(Th[i] - (double)hi));
   }
   if ((rc = dalloc(c, &c->q_d, qh.size())) || (rc = dalloc(c, &c->T_d, Th.size())) ||
-      (rc = dalloc(c, &c->pow_d, ph.size())) || (rc = dalloc(c, &c->T2_d, T2h.size())))
+      (rc = dalloc(c, &c->pow_d, ph.size())) || (rc = dalloc(c, &c->T2_d, T2h.size())) ||
+      (rc = dalloc(c, &c->powf_d, pfh.size())))
     return rc;
   CKC(c, cudaMemcpy(c->T2_d, T2h.data(), T2h.size() * sizeof(float2), cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->q_d, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->T_d, Th.data(), Th.size() * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->pow_d, ph.data(), ph.size() * 8, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->powf_d, pfh.data(), pfh.size() * 4, cudaMemcpyHostToDevice));
   c->tab.q = c->q_d;
   c->tab.T = c->T_d;
   c->tab.pow = c->pow_d;
+  c->tab.powf = c->powf_d;
   c->tab.T2 = c->T2_d;
   c->tab.S = S;
   // tangent D (element SoA [84][epad]) and spring state placement
@@ -1055,9 +1074,28 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   if ((rc = alloc_soa(c, c->st, std::max<int64_t>(1, c->E_res * S4), false))) return rc;
   if (c->E_res < E) {
     if ((rc = alloc_soa(c, c->hst, (E - c->E_res) * S4, true))) return rc;
-    c->ring.resize(c->cfg.ring_depth);
-    for (auto &rb : c->ring)
-      if ((rc = alloc_soa(c, rb, std::min<int64_t>(c->cfg.chunk_elems, E - c->E_res) * S4, false))) return rc;
+    if (c->cfg.stream_mode == NS_STREAM_ZERO_COPY) {
+      void *d = nullptr;
+      auto dev_of = [&](void *h) -> void * {
+        d = nullptr;
+        return cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess ? d : nullptr;
+      };
+      c->hst_dev.tau = (double *)dev_of(c->hst.tau);
+      c->hst_dev.gR = (double *)dev_of(c->hst.gR);
+      c->hst_dev.tR = (double *)dev_of(c->hst.tR);
+      c->hst_dev.gmax = (double *)dev_of(c->hst.gmax);
+      c->hst_dev.dir = (int32_t *)dev_of(c->hst.dir);
+      c->hst_dev.mode = (int32_t *)dev_of(c->hst.mode);
+      if (!c->hst_dev.tau || !c->hst_dev.gR || !c->hst_dev.tR || !c->hst_dev.gmax || !c->hst_dev.dir ||
+          !c->hst_dev.mode) {
+        cudaGetLastError();
+        NS_SET(c, NS_ERR_CUDA, "pinned state has no device address (zero-copy unavailable)");
+      }
+    } else {
+      c->ring.resize(c->cfg.ring_depth);
+      for (auto &rb : c->ring)
+        if ((rc = alloc_soa(c, rb, std::min<int64_t>(c->cfg.chunk_elems, E - c->E_res) * S4, false))) return rc;
+    }
   }
   c->stats.resident_elems = c->E_res;
   c->stats.streamed_elems = E - c->E_res;
@@ -1656,7 +1694,7 @@ void ns_destroy(ns_ctx *c) {
   dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.kerr); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
   dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
   dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
-  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->T2_d); dfree(c->D); dfree(c->D32);
+  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->powf_d); dfree(c->T2_d); dfree(c->D); dfree(c->D32);
   dfree(c->D16); dfree(c->op_A16);
   destroy_graphs(c);
   dfree(c->vseg_d); dfree(c->eseg_d); dfree(c->fseg_d); dfree(c->voff_d); dfree(c->eoff_d); dfree(c->foff_d);

@@ -153,7 +153,47 @@ void host_material_constants(const ns_material &m, double f1, double f2, MatCons
   o->alpha_f = (float)o->alpha_ro;
   o->beta_f = (float)o->beta_ro;
   o->G0_f = (float)o->G0;
+  o->itref_lo = (float)(o->itref - (double)o->itref_f);
+  // beta as a float pair, and as b0 (multiple of 2^-15) + b1 (multiple of 2^-31) + b2
+  const long double b = (long double)o->beta_ro;
+  o->pbeta.bh = (float)b;
+  o->pbeta.bl = (float)(b - (long double)o->pbeta.bh);
+  const long double b0 = roundl(b * 32768.0L) / 32768.0L;
+  const long double b1 = roundl((b - b0) * 2147483648.0L) / 2147483648.0L;
+  o->pbeta.b0 = (float)b0;
+  o->pbeta.b1 = (float)b1;
+  o->pbeta.b2 = (float)(b - b0 - b1);
   o->pad_f = 0.0f;
+}
+
+// Tables of the double-float power (df64.cuh), in extended precision: r_j = 1/(1 + (j +
+// 1/2)/128) rounded to float, -ln r_j of that float as a float pair, 2^(i/64) as a pair,
+// ln2 as a pair, ln2/64 as d0 (multiple of 2^-18) + d1 (multiple of 2^-30) + d2, 64/ln2.
+void host_powf_tables(float *out) {
+  const long double LN2 = 0.693147180559945309417232121458176568L;
+  for (int j = 0; j < 128; ++j) {
+    const float r = (float)(1.0L / (1.0L + ((long double)j + 0.5L) / 128.0L));
+    const long double l = -logl((long double)r);
+    out[j] = r;
+    out[128 + j] = (float)l;
+    out[256 + j] = (float)(l - (long double)(float)l);
+  }
+  for (int i = 0; i < 64; ++i) {
+    const long double t = exp2l((long double)i / 64.0L);
+    out[384 + i] = (float)t;
+    out[448 + i] = (float)(t - (long double)(float)t);
+  }
+  out[512] = (float)LN2;
+  out[513] = (float)(LN2 - (long double)(float)LN2);
+  const long double L64 = LN2 / 64.0L;
+  const long double d0 = roundl(L64 * 262144.0L) / 262144.0L;
+  const long double d1 = roundl((L64 - d0) * 1073741824.0L) / 1073741824.0L;
+  out[514] = (float)d0;
+  out[515] = (float)d1;
+  out[516] = (float)(L64 - d0 - d1);
+  out[517] = (float)(64.0L / LN2);
+  out[518] = 0.0f;
+  out[519] = 0.0f;
 }
 
 // Tables of the FP64 power used by the spring law (table-driven logarithm and exponential

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/ns.h"
+#include "df64.cuh"
 
 namespace ns {
 
@@ -21,7 +22,10 @@ struct MatConst {
   // spring-law constants: 1/G0, 1/(G0 gamma_ref), alpha (1 + beta), alpha (1 + beta) beta,
   // series coefficients beta (beta - 1)/2 and beta (beta - 1)(beta - 2)/6, FP32 copies
   double iG0, itref, ab1, ab1b, c2, c3, hab1b;
-  float itref_f, iG0_f, alpha_f, beta_f, G0_f, pad_f;
+  float itref_f, iG0_f, alpha_f, beta_f, G0_f;
+  float itref_lo;   // itref = itref_f + itref_lo (a float pair)
+  PowBeta pbeta;    // beta_ro for the double-float power
+  float pad_f;
 };
 
 // Coefficients of one element-by-element operator application, per material:
@@ -199,6 +203,7 @@ struct SpringTables {
   const double *T;    // [S][21] w q q^T packed upper triangle (+ one row with their sum)
   const float2 *T2;   // [S][21] the same entries as (hi, lo) float pairs
   const double *pow;  // power tables: r[128], -ln r hi[128], lo[128], 2^(i/64)[64], ln2 hi/lo, ln2/64 hi/lo
+  const float *powf;  // double-float power tables (df64.cuh, kPowFLen floats)
   int S;
 };
 constexpr int kPowTabLen = 452;
@@ -234,6 +239,7 @@ int ctx_sync_main(ns_ctx *c);                       // bounded wait for the cont
 int host_spring_directions(int S, double *q, double *w);
 int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, int32_t *nc);
 void host_material_constants(const ns_material &m, double f1, double f2, MatConst *out);
-void host_pow_tables(double *out);  // kPowTabLen entries
+void host_pow_tables(double *out);   // kPowTabLen entries
+void host_powf_tables(float *out);   // kPowFLen entries (df64.cuh)
 
 }  // namespace ns

@@ -139,14 +139,18 @@ def test_thirty_steps_surface_parity(scatter, precision):
 
 
 def test_colour_scatter_is_deterministic_and_streaming_is_invisible():
+    """Deterministic scatter: repeated runs, state streamed through device chunk buffers
+    (part or all of it, two ring depths) and state updated in place in pinned host memory
+    (zero-copy) all give bit-identical fields, tangents and spring states."""
     wl = small(dims=(4, 3, 3), nt=60)
     n = 12
     S = wl.n_springs
     per_elem = B.ns_state_bytes(1, S)
     res = []
-    for budget, chunk, ring in ((-1, 100000, 3), (-1, 100000, 3), (per_elem * 37, 13, 3), (0, 29, 2)):
+    for budget, chunk, ring, mode in ((-1, 100000, 3, 0), (-1, 100000, 3, 0), (per_elem * 37, 13, 3, 0), (0, 29, 2, 0),
+                                      (per_elem * 37, 13, 3, B.NS_STREAM_ZERO_COPY)):
         with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR, surface_ring_steps=n, device_state_budget=budget,
-                          chunk_elems=chunk, ring_depth=ring) as sim:
+                          chunk_elems=chunk, ring_depth=ring, stream_mode=mode) as sim:
             sim.advance(n)
             st = sim.stats()
             res.append((sim.nodal("u"), sim.nodal("v"), sim.state(), st))
@@ -158,6 +162,9 @@ def test_colour_scatter_is_deterministic_and_streaming_is_invisible():
     assert res[2][3]["streamed_elems"] == wl.mesh.n_elems - 37
     assert res[3][3]["streamed_elems"] == wl.mesh.n_elems
     assert res[3][3]["h2d_bytes"] == n * wl.mesh.n_elems * per_elem
+    # zero-copy: the kernel updated the host-resident springs in place
+    assert res[4][3]["streamed_elems"] == wl.mesh.n_elems - 37
+    assert res[4][3]["h2d_bytes"] == n * (wl.mesh.n_elems - 37) * per_elem
 
 
 def test_checkpoint_restore_bit_identical():

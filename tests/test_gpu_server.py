@@ -66,12 +66,12 @@ def test_admission_waits_for_memory_and_streams_when_it_must():
     for k in range(1, 3):
         assert st[k]["t_admit"] >= st[k - 1]["t_done"]
     # too little device memory for a resident state, enough pinned host memory: streamed
-    # (through a ring of three 100-element chunks)
-    dev, state, dstr = B.ns_case_bytes(wls[0], NSTEPS, scatter=B.NS_SCATTER_COLOUR, chunk_elems=100, ring_depth=3)
+    # (through a ring of three 32-element chunks)
+    dev, state, dstr = B.ns_case_bytes(wls[0], NSTEPS, scatter=B.NS_SCATTER_COLOUR, chunk_elems=32, ring_depth=3)
     budget = (dstr + dev) // 2
     assert dstr < budget < dev
     with B.Server(device_budget=budget, pinned_budget=4 * state, max_active=2, quantum_steps=5) as srv:
-        i = srv.submit(wls[0], NSTEPS, scatter=B.NS_SCATTER_COLOUR, chunk_elems=100, ring_depth=3)
+        i = srv.submit(wls[0], NSTEPS, scatter=B.NS_SCATTER_COLOUR, chunk_elems=32, ring_depth=3)
         s = srv.wait(i, 600)
         v = srv.result(i)["v"]
         assert s["streamed"] == 1 and s["state"] == B.NS_CASE_DONE
