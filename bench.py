@@ -251,6 +251,8 @@ def main():
     ap.add_argument("--stage", type=int, default=0, choices=[0, 1],
                     help="FP32 inner operator: stage element tiles in shared memory with bulk copies (1) or "
                          "per-thread loads (0)")
+    ap.add_argument("--x0", default="prev", choices=["prev", "zero"],
+                    help="CG start: the previous step's increment (default) or zero")
     ap.add_argument("--inner-iters", type=int, default=30,
                     help="FP32 inner CG iterations per outer iteration of the flexible solver")
     ap.add_argument("--requests", type=int, default=12, help="requests of the served trace")
@@ -317,7 +319,7 @@ def main():
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
-              stage_elements=args.stage, inner_max_iter=args.inner_iters)
+              stage_elements=args.stage, inner_max_iter=args.inner_iters, x0_prev=int(args.x0 == "prev"))
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
     B.ns_reset_stats(sim.ctx)
@@ -393,7 +395,7 @@ def main():
         def streamed_run(mode):
             sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
                                ring_depth=ring, precision=prec, graphs=graphs, stage_elements=args.stage,
-                               inner_max_iter=args.inner_iters, stream_mode=mode)
+                               inner_max_iter=args.inner_iters, stream_mode=mode, x0_prev=int(args.x0 == "prev"))
             sim.advance(1)
             B.ns_reset_stats(sim.ctx)
             h0 = sim.stats()

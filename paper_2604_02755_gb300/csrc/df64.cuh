@@ -170,4 +170,97 @@ NS_HD bool df64_pow(float xh, float xl, const PowBeta &B, const float *__restric
   return true;
 }
 
+// ---------------------------------------------------------------------------------------
+// Pair arithmetic used by the root step below (results renormalised: |lo| <= ulp(hi)/2).
+NS_HD void fast_two_sum(float a, float b, float &s, float &e) {  // |a| >= |b|
+  s = df_add(a, b);
+  e = df_sub(b, df_sub(s, a));
+}
+NS_HD void pair_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+  float p, e;
+  two_prod(ah, bh, p, e);
+  e = df_add(e, df_fma(ah, bl, df_mul(al, bh)));
+  fast_two_sum(p, e, ph, pl);
+}
+NS_HD void pair_add(float ah, float al, float bh, float bl, float &sh, float &sl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = df_add(e, df_add(al, bl));
+  fast_two_sum(s, e, sh, sl);
+}
+NS_HD void pair_rcp(float bh, float bl, float &rh, float &rl) {  // 1 / (bh + bl), one Newton step
+  const float r0 = df_rcp(bh);
+  const float e = df_sub(df_fma(-bh, r0, 1.0f), df_mul(bl, r0));
+  fast_two_sum(r0, df_mul(r0, e), rh, rl);
+}
+
+// Material constants of the spring law as float pairs (built on the host).
+struct RoPairs {
+  float iG0h, iG0l;    // 1 / G0
+  float alh, all;      // alpha = 2^beta
+  float ab1h, ab1l;    // alpha (1 + beta)
+  float G0h, G0l;      // G0
+  float itrh, itrl;    // 1 / (G0 gamma_ref)
+  float hab1b, c2;     // alpha (1 + beta) beta / 2 and beta (beta - 1) / 2 (small corrections)
+  PowBeta pb;          // beta
+};
+
+// One Halley step of the skeleton equation g(tau) = tau/G0 (1 + alpha (tau itref)^beta)
+// = ga > 0 from the FP32 seed t, in pair arithmetic, with the tangent at the new root:
+//   w0 = (t itref)^beta,  r = g(t) - ga,  h = r / g'(t) = r G0 / (1 + alpha (1 + beta) w0),
+//   step = h (1 + h g''/(2 g')),  tau1 = t - step,  d = -step / t,
+//   w1 = w0 (1 + d)^beta ~ w0 (1 + beta d + beta (beta - 1)/2 d^2),
+//   G = G0 / (1 + alpha (1 + beta) w1)  (= 1 / g'(tau1), the spring's tangent).
+// ga = gah + gal.  Returns false when the power declines its input (the caller falls back
+// to FP64).  The residual r is a small difference of two pairs, so tau1 is accurate to
+// about 2^-47 tau, and G to about 2^-45.
+NS_HD bool df64_ro_halley(float t, float gah, float gal, const RoPairs &P, const float *__restrict__ tab,
+                          float &tauh, float &taul, float &d, float &Gh, float &Gl) {
+  float xh, xl, wh, wl;
+  two_prod(t, P.itrh, xh, xl);
+  xl = df_fma(t, P.itrl, xl);
+  if (!df64_pow(xh, xl, P.pb, tab, wh, wl)) return false;
+  // r = t iG0 (1 + alpha w0) - ga
+  float ah, al, th, tl, gh, gl, rh, rl;
+  pair_mul(P.alh, P.all, wh, wl, ah, al);
+  pair_add(1.0f, 0.0f, ah, al, ah, al);
+  two_prod(t, P.iG0h, th, tl);
+  tl = df_fma(t, P.iG0l, tl);
+  pair_mul(th, tl, ah, al, gh, gl);
+  pair_add(gh, gl, -gah, -gal, rh, rl);
+  // h = r G0 / (1 + ab1 w0)
+  float bh, bl, qh, ql, hh, hl;
+  pair_mul(P.ab1h, P.ab1l, wh, wl, bh, bl);
+  pair_add(1.0f, 0.0f, bh, bl, bh, bl);
+  pair_rcp(bh, bl, qh, ql);
+  pair_mul(rh, rl, P.G0h, P.G0l, hh, hl);
+  pair_mul(hh, hl, qh, ql, hh, hl);
+  // Halley: the correction factor h g''/(2 g') ~ the seed's relative error, needed to ~1e-7
+  const float rt = df_rcp(t);
+  const float hc = df_mul(df_mul(df_mul(hh, P.hab1b), df_mul(wh, rt)), qh);
+  float sh, sl;
+  two_sum(hh, df_mul(hh, hc), sh, sl);
+  sl = df_add(sl, hl);
+  two_sum(t, -sh, tauh, taul);
+  taul = df_sub(taul, sl);
+  // d = -step / t as a pair (1/t refined once)
+  const float et = df_fma(-t, rt, 1.0f);
+  float dh, dl;
+  two_prod(sh, rt, dh, dl);
+  dl = df_add(dl, df_fma(df_mul(sh, rt), et, df_mul(sl, rt)));
+  d = -dh;
+  // w1 = w0 (1 + beta d + c2 d^2), c3 d^3 < 1e-16 dropped
+  float zh, zl, vh, vl;
+  pair_mul(P.pb.bh, P.pb.bl, -dh, -dl, zh, zl);
+  zl = df_fma(df_mul(P.c2, dh), dh, zl);
+  pair_mul(wh, wl, zh, zl, vh, vl);
+  pair_add(wh, wl, vh, vl, wh, wl);
+  // G = G0 / (1 + ab1 w1)
+  pair_mul(P.ab1h, P.ab1l, wh, wl, bh, bl);
+  pair_add(1.0f, 0.0f, bh, bl, bh, bl);
+  pair_rcp(bh, bl, qh, ql);
+  pair_mul(P.G0h, P.G0l, qh, ql, Gh, Gl);
+  return true;
+}
+
 }  // namespace ns

@@ -107,25 +107,40 @@ __device__ double ro_F_safe(double ga, double tau, const MatConst &p, const PowT
   return tau;
 }
 
-// Root tau = F(ga) of the skeleton g(tau) = (tau/G0)(1 + alpha (tau/tref)^beta) = ga > 0
-// (g odd, increasing, convex for tau > 0, tau <= G0 ga), or -- when `solve` is false --
-// only the power at tau = ga.  Every lane evaluates exactly one FP64 power, so a warp
-// whose springs follow different Masing paths does not diverge around it:
-//  1. (solve) FP32 Newton from the guess if it lies in (0, G0 ga], else from G0 ga,
-//     until a step is below 4e-6 of the iterate;
-//  2. w = (tau/tref)^beta in FP64 (table-driven power);
-//  3. (solve) one FP64 Halley step (cubic: a seed error e leaves ~e^3), the power
-//     carried to the new iterate by the series (1 + d)^beta.  Unless the FP32 stage
-//     converged and the step is below 2e-5 of tau the safeguarded loop takes over.
-// *pw returns (F/tref)^beta at the returned root.
+// G0 / g'(tau) with g' = 1 + alpha (1 + beta) pw.
+__device__ __forceinline__ double ro_tangent_from_pw(double pw, const MatConst &p) {
+  return p.G0 * rcp1(fma(p.ab1, pw, 1.0));
+}
+
+// A positive FP64 modulus as an unevaluated sum of two floats: the high part is G with its
+// low 29 significand bits cleared, built as a float from the bit pattern on the integer
+// pipes (G in the normal float range), the low part the rounded rest.
+__device__ __forceinline__ float2 split_pair(double G) {
+  const long long gb = __double_as_longlong(G);
+  const double Ghi = __longlong_as_double(gb & ~0x1FFFFFFFLL);
+  const unsigned int fb = (unsigned int)((((gb >> 52) & 0x7FF) - 896) << 23) | (unsigned int)((gb >> 29) & 0x7FFFFF);
+  return make_float2(__uint_as_float(fb), (float)(G - Ghi));
+}
+
+// Root tau = F(ga) of the skeleton g(tau) = (tau/G0)(1 + alpha (tau/tref)^beta) = ga >= 0
+// (g odd, increasing, convex for tau > 0, tau <= G0 ga) and the tangent G = 1/g'(tau) as a
+// float pair; or -- when `solve` is false -- only the tangent at tau = ga (the current
+// stress).  The usual path:
+//  1. FP32 Newton from the guess if it lies in (0, G0 ga], else from G0 ga, until a step
+//     is below 4e-6 of the iterate;
+//  2. one Halley step from that FP32 seed in double-float arithmetic on the FP32 pipes
+//     (df64_ro_halley: the power, the residual against ga, the step and the tangent at
+//     the new root; root to ~2^-47, tangent to ~2^-45).
+// When the seed did not converge, the step exceeds 2e-5 of the root, or the power's
+// argument is out of its range, the FP64 path takes over: table-driven FP64 power, FP64
+// Halley step and, unless that certifies, the safeguarded Newton loop.
 __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, const MatConst &p, const PowTab &tb,
-                                           const float *__restrict__ tabf, double *pw) {
+                                           const float *__restrict__ tabf, float2 *Gp) {
   double tau = ga;
   bool seeded = true;
-  float t = 0.0f;  // the FP32 seed (tau == t exactly when t > 0)
   if (solve) {
     const float gaf = (float)ga, hif = p.G0_f * gaf, gs = (float)guess;
-    t = (gs > 0.0f && gs < hif) ? gs : hif;
+    float t = (gs > 0.0f && gs < hif) ? gs : hif;
     seeded = false;
     for (int it = 0; it < 40 && t > 0.0f; ++it) {
       const float pwf = __powf(t * p.itref_f, p.beta_f);
@@ -141,26 +156,21 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
         break;
       }
     }
+    if (seeded && t > 0.0f) {
+      const float gal = (float)(ga - (double)gaf);
+      float th, tl, d, Gh, Gl;
+      if (df64_ro_halley(t, gaf, gal, p.rp, tabf, th, tl, d, Gh, Gl) && fabsf(d) <= 2e-5f) {
+        *Gp = make_float2(Gh, Gl);
+        return (double)th + (double)tl;
+      }
+    }
     tau = (t > 0.0f) ? (double)t : p.G0 * ga;  // FP32 underflow: start from the linear bound
   }
-  if (d_is_zero(tau)) {  // zero strain (or zero stress): the power vanishes
-    *pw = 0.0;
+  if (d_is_zero(tau)) {  // zero strain (or zero stress): the power vanishes, G = G0
+    *Gp = split_pair(p.G0);
     return 0.0;
   }
-  // the power at the seed: on the FP32 pipes in double-float arithmetic when the seed is an
-  // FP32 number in range (x = t itref as a float pair), else the FP64 table-driven power
-  double w;
-  bool have = false;
-  if (solve && t > 0.0f) {
-    float xh, xl, wh, wl;
-    two_prod(t, p.itref_f, xh, xl);
-    xl = df_fma(t, p.itref_lo, xl);
-    if (df64_pow(xh, xl, p.pbeta, tabf, wh, wl)) {
-      w = (double)wh + (double)wl;
-      have = true;
-    }
-  }
-  if (!have) w = pow_pos(tau * p.itref, p.beta_ro, tb);
+  double w = pow_pos(tau * p.itref, p.beta_ro, tb);
   if (solve) {
     // Halley: step = h / (1 - h f''/(2 f')) with h = f/f' the Newton step; |h f''/(2 f')|
     // is ~ the seed error (<= 4e-6), so 1/(1 - c) = 1 + c to far below rounding
@@ -178,13 +188,8 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
       tau = ro_F_safe(ga, (tau > 0.0 && tau <= hi) ? tau : hi, p, tb, &w);
     }
   }
-  *pw = w;
+  *Gp = split_pair(ro_tangent_from_pw(w, p));
   return tau;
-}
-
-// G0 / g'(tau) with g' = 1 + alpha (1 + beta) pw.
-__device__ __forceinline__ double ro_tangent_from_pw(double pw, const MatConst &p) {
-  return p.G0 * rcp1(fma(p.ab1, pw, 1.0));
 }
 
 // One spring (Masing bookkeeping of the documented reading): virgin -> skeleton in the
@@ -192,8 +197,8 @@ __device__ __forceinline__ double ro_tangent_from_pw(double pw, const MatConst &
 // tau = tR + 2 F((gamma - gR)/2); moving outward with |gamma| >= gmax returns to the
 // skeleton tau = F(gamma) (decided before the root solve, so each spring solves once).
 // With no increment the state is kept and only the tangent is evaluated.
-// Returns the tangent dtau/dgamma at the end state.
-__device__ __forceinline__ double spring_update(double g, double dg, const MatConst &p, const PowTab &tb,
+// Returns the tangent dtau/dgamma at the end state as a float pair.
+__device__ __forceinline__ float2 spring_update(double g, double dg, const MatConst &p, const PowTab &tb,
                                                 const float *__restrict__ tabf, double &tau, double &gR, double &tR,
                                                 double &gmax, int &dir, int &mode) {
   const bool active = !d_is_zero(dg);
@@ -224,8 +229,8 @@ __device__ __forceinline__ double spring_update(double g, double dg, const MatCo
   } else {
     x = (mode == 0) ? tau : 0.5 * (tau - tR);  // the power at the current state only
   }
-  double pw;
-  const double f = ro_solve(active, d_abs(x), guess, p, tb, tabf, &pw);
+  float2 G;
+  const double f = ro_solve(active, d_abs(x), guess, p, tb, tabf, &G);
   if (active) {
     const double fs = d_copysign(f, x);
     if (mode == 0) {
@@ -236,7 +241,7 @@ __device__ __forceinline__ double spring_update(double g, double dg, const MatCo
       tau = fma(2.0, fs, tR);
     }
   }
-  return ro_tangent_from_pw(pw, p);
+  return G;
 }
 
 // Block = a tile of TP consecutive points (TP multiple of 4) with all their S springs.
@@ -273,8 +278,8 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
     const int64_t si = (p - base) * S + k;
     double tau = tau_a[si], gR = gR_a[si], tR = tR_a[si], gmax = gmax_a[si];
     int dir = dir_a[si], mode = mode_a[si];
-    const double G = spring_update(gam, dgam, rp, tb, ptabf, tau, gR, tR, gmax, dir, mode);
-    if (dgam != 0.0) {
+    const float2 G = spring_update(gam, dgam, rp, tb, ptabf, tau, gR, tR, gmax, dir, mode);
+    if (!d_is_zero(dgam)) {
       tau_a[si] = tau;
       gR_a[si] = gR;
       tR_a[si] = tR;
@@ -282,13 +287,7 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
       dir_a[si] = dir;
       mode_a[si] = mode;
     }
-    // G as an unevaluated sum of two floats for the double-float accumulation: the high
-    // part is G with its low 29 significand bits cleared, built as a float from the bit
-    // pattern on the integer pipes (G is a positive modulus in the normal float range)
-    const long long gb = __double_as_longlong(G);
-    const double Ghi = __longlong_as_double(gb & ~0x1FFFFFFFLL);
-    const unsigned int fb = (unsigned int)((((gb >> 52) & 0x7FF) - 896) << 23) | (unsigned int)((gb >> 29) & 0x7FFFFF);
-    Gs[g] = make_float2(__uint_as_float(fb), (float)(G - Ghi));
+    Gs[g] = G;  // the tangent as an unevaluated float pair for the double-float accumulation
   }
   __syncthreads();
   const int nout = np * 21;

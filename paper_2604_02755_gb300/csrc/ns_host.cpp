@@ -153,17 +153,29 @@ void host_material_constants(const ns_material &m, double f1, double f2, MatCons
   o->alpha_f = (float)o->alpha_ro;
   o->beta_f = (float)o->beta_ro;
   o->G0_f = (float)o->G0;
-  o->itref_lo = (float)(o->itref - (double)o->itref_f);
-  // beta as a float pair, and as b0 (multiple of 2^-15) + b1 (multiple of 2^-31) + b2
-  const long double b = (long double)o->beta_ro;
-  o->pbeta.bh = (float)b;
-  o->pbeta.bl = (float)(b - (long double)o->pbeta.bh);
+  o->pad_f = 0.0f;
+  // float pairs for the double-float root step, from extended-precision values
+  auto split = [](long double v, float &h, float &l) {
+    h = (float)v;
+    l = (float)(v - (long double)h);
+  };
+  const long double b = (long double)o->beta_ro, G0 = (long double)o->G0;
+  const long double al = exp2l(b), itr = 1.0L / (G0 * (long double)o->gref);
+  RoPairs &r = o->rp;
+  split(1.0L / G0, r.iG0h, r.iG0l);
+  split(al, r.alh, r.all);
+  split(al * (1.0L + b), r.ab1h, r.ab1l);
+  split(G0, r.G0h, r.G0l);
+  split(itr, r.itrh, r.itrl);
+  r.hab1b = (float)(al * (1.0L + b) * b * 0.5L);
+  r.c2 = (float)(b * (b - 1.0L) * 0.5L);
+  // beta as a pair, and as b0 (a multiple of 2^-15) + b1 (a multiple of 2^-31) + b2
+  split(b, r.pb.bh, r.pb.bl);
   const long double b0 = roundl(b * 32768.0L) / 32768.0L;
   const long double b1 = roundl((b - b0) * 2147483648.0L) / 2147483648.0L;
-  o->pbeta.b0 = (float)b0;
-  o->pbeta.b1 = (float)b1;
-  o->pbeta.b2 = (float)(b - b0 - b1);
-  o->pad_f = 0.0f;
+  r.pb.b0 = (float)b0;
+  r.pb.b1 = (float)b1;
+  r.pb.b2 = (float)(b - b0 - b1);
 }
 
 // Tables of the double-float power (df64.cuh), in extended precision: r_j = 1/(1 + (j +

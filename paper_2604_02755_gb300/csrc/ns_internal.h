@@ -23,9 +23,8 @@ struct MatConst {
   // series coefficients beta (beta - 1)/2 and beta (beta - 1)(beta - 2)/6, FP32 copies
   double iG0, itref, ab1, ab1b, c2, c3, hab1b;
   float itref_f, iG0_f, alpha_f, beta_f, G0_f;
-  float itref_lo;   // itref = itref_f + itref_lo (a float pair)
-  PowBeta pbeta;    // beta_ro for the double-float power
   float pad_f;
+  RoPairs rp;       // the same constants as float pairs for the double-float root step
 };
 
 // Coefficients of one element-by-element operator application, per material:

@@ -1,8 +1,10 @@
-"""The double-float power of the spring kernel (csrc/df64.cuh), compiled for the host
-with the library's tables and checked against long-double powl over the range the
-spring law meets: normalised stresses x = tau/(G0 gamma_ref) from 1e-8 to 200 and
-exponents beta from 0.5 to 1.8 (h_max up to 0.3).  The device runs the same IEEE
-single-precision operations (no contraction, explicit fma)."""
+"""The double-float arithmetic of the spring kernel (csrc/df64.cuh), compiled for the
+host with the library's tables: the power x^beta against long-double powl, and one
+Halley step of the skeleton root from an FP32 seed (with the tangent at the new root)
+against the root and tangent solved in long double -- over the range the spring law
+meets: normalised stresses tau/(G0 gamma_ref) from 1e-8 to 200, exponents beta from 0.5
+to 1.8 (h_max up to 0.3).  The device runs the same IEEE single-precision operations
+(no contraction, explicit fma)."""
 import os
 import shutil
 import subprocess
@@ -14,18 +16,22 @@ from paper_2604_02755_gb300 import build
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.fixture(scope="module")
-def checker(tmp_path_factory):
+def compile_check(tmp_path_factory, name):
     if not shutil.which("g++"):
         pytest.skip("g++ not available")
     lib = build.build()
-    exe = str(tmp_path_factory.mktemp("df64") / "df64_check")
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", os.path.join(ROOT, "tests", "native", "df64_check.cpp"),
+    exe = str(tmp_path_factory.mktemp("df64") / name)
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", os.path.join(ROOT, "tests", "native", name + ".cpp"),
            "-o", exe, lib, "-Wl,-rpath," + os.path.dirname(lib)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        pytest.fail("df64_check build failed:\n" + r.stderr)
+        pytest.fail(name + " build failed:\n" + r.stderr)
     return exe
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    return compile_check(tmp_path_factory, "df64_check")
 
 
 def run(exe, lx0, lx1, n):
@@ -45,3 +51,13 @@ def test_out_of_range_inputs_are_declined(checker):
     # x below 2^-100 is left to the FP64 path
     _, _, declined = run(checker, -75.0, -72.0, 1000)
     assert declined == 1000
+
+
+def test_halley_step_root_and_tangent(tmp_path_factory):
+    exe = compile_check(tmp_path_factory, "ro_check")
+    out = subprocess.run([exe, "100000"], capture_output=True, text=True, check=True).stdout
+    err_tau, err_G, max_step, declined = out.split()
+    assert int(declined) == 0
+    assert float(max_step) <= 2e-5        # within the step bound the kernel accepts
+    assert float(err_tau) < 1e-13         # root of the skeleton equation
+    assert float(err_G) < 1e-13           # tangent 1/g'(tau) at it
