@@ -251,6 +251,10 @@ def main():
     ap.add_argument("--stage", type=int, default=0, choices=[0, 1],
                     help="FP32 inner operator: stage element tiles in shared memory with bulk copies (1) or "
                          "per-thread loads (0)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the library's autotuner (spring-kernel block shape) after the warm-up steps")
+    ap.add_argument("--pair-op", type=int, default=0, choices=[0, 1],
+                    help="FP64-accuracy operator applications in double-float arithmetic on the FP32 pipes")
     ap.add_argument("--x0", default="prev", choices=["prev", "zero"],
                     help="CG start: the previous step's increment (default) or zero")
     ap.add_argument("--inner-iters", type=int, default=30,
@@ -319,9 +323,11 @@ def main():
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
-              stage_elements=args.stage, inner_max_iter=args.inner_iters, x0_prev=int(args.x0 == "prev"))
+              stage_elements=args.stage, inner_max_iter=args.inner_iters, x0_prev=int(args.x0 == "prev"),
+              pair_operator=args.pair_op)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
+    tuning = B.ns_autotune(sim.ctx) if args.autotune else None
     B.ns_reset_stats(sim.ctx)
     st0 = sim.stats()
 
@@ -395,7 +401,8 @@ def main():
         def streamed_run(mode):
             sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
                                ring_depth=ring, precision=prec, graphs=graphs, stage_elements=args.stage,
-                               inner_max_iter=args.inner_iters, stream_mode=mode, x0_prev=int(args.x0 == "prev"))
+                               inner_max_iter=args.inner_iters, stream_mode=mode, x0_prev=int(args.x0 == "prev"),
+                               pair_operator=args.pair_op)
             sim.advance(1)
             B.ns_reset_stats(sim.ctx)
             h0 = sim.stats()
@@ -440,7 +447,8 @@ def main():
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
                 "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
-                "staged_operator": args.stage, "inner_iters": args.inner_iters,
+                "staged_operator": args.stage, "inner_iters": args.inner_iters, "autotune": tuning,
+                "pair_operator": args.pair_op, "x0": args.x0,
                 "state_stream": stream}
         print(json.dumps(line), flush=True)
     dist.finalize(dd)

@@ -85,6 +85,9 @@ typedef struct {
   int32_t stage_elements;      /* 1: the FP32 inner operator stages each 256-element tile of element
                                   data in shared memory with bulk copies (atomic scatter, one member);
                                   0 (default): per-thread loads, which measured faster on GB300 */
+  int32_t pair_operator;       /* 1: the FP64-accuracy operator applications (right-hand side, outer
+                                  CG, q update) run in double-float arithmetic on the FP32 pipes
+                                  (relative accuracy ~1e-13, FP64 node vectors); 0: FP64 */
   int32_t stream_mode;         /* spring state beyond device_state_budget: NS_STREAM_RING (chunks
                                   copied through device buffers, Alg. 3) or NS_STREAM_ZERO_COPY
                                   (the spring kernel reads and writes the pinned host arrays in
@@ -240,6 +243,29 @@ int64_t ns_spring_points_noalloc_capacity(int32_t S);
 
 int ns_get_stats(ns_ctx *ctx, ns_stats *st);
 int ns_reset_stats(ns_ctx *ctx);
+
+/* Result of ns_autotune: the candidates it timed and what it chose. */
+typedef struct {
+  int32_t n_tile;                 /* spring-kernel block shapes tried */
+  int32_t tile_points[8];         /* integration points per block of each */
+  float tile_ms[8];               /* spring kernel time of each on the sample (ms) */
+  int32_t chosen_tile_points;
+  int32_t n_chunk;                /* streamed-state chunk sizes tried (0: no streamed state) */
+  int64_t chunk_elems[6];
+  float chunk_gbps[6];            /* H2D + D2H bytes per second of each over the ring */
+  int64_t chosen_chunk_elems;
+} ns_tuning;
+
+/* Autotuner (a tool of this library; the paper tunes nothing at run time): times the
+ * spring kernel's block shape (integration points per block) on a sample of up to 32,768
+ * resident elements -- a copy of their spring state, the last step's strains -- and the
+ * streamed state's chunk size (a copy round trip through the ring buffers, which leaves
+ * the host state as it was), and keeps the fastest of each for the following steps.
+ * The simulation's state and results are unchanged (the block shape does not change the
+ * order of any sum).  Call between ns_advance calls, after at least one step (the strains
+ * of a step make the spring timings representative).  Allocates a temporary copy of the
+ * sampled state. */
+int ns_autotune(ns_ctx *ctx, ns_tuning *out);
 
 /* Checkpoint of the whole time-stepping state (step counter, u, v, a, q, du,
  * D, spring state).  ns_checkpoint_size gives the byte count; the buffers are

@@ -40,7 +40,7 @@ class ns_config(C.Structure):
                 ("rayleigh_f2", C.c_double), ("surface_ring_steps", C.c_int64), ("device", C.c_int32),
                 ("timing", C.c_int32), ("inner_max_iter", C.c_int32), ("inner_tol", C.c_double),
                 ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32),
-                ("stream_mode", C.c_int32)]
+                ("pair_operator", C.c_int32), ("stream_mode", C.c_int32)]
 
 
 class ns_material(C.Structure):
@@ -61,6 +61,18 @@ class ns_stats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ns_tuning(C.Structure):
+    _fields_ = [("n_tile", C.c_int32), ("tile_points", C.c_int32 * 8), ("tile_ms", C.c_float * 8),
+                ("chosen_tile_points", C.c_int32), ("n_chunk", C.c_int32), ("chunk_elems", C.c_int64 * 6),
+                ("chunk_gbps", C.c_float * 6), ("chosen_chunk_elems", C.c_int64)]
+
+    def as_dict(self):
+        return {"tile_points": list(self.tile_points[:self.n_tile]), "tile_ms": list(self.tile_ms[:self.n_tile]),
+                "chosen_tile_points": self.chosen_tile_points,
+                "chunk_elems": list(self.chunk_elems[:self.n_chunk]), "chunk_gbps": list(self.chunk_gbps[:self.n_chunk]),
+                "chosen_chunk_elems": self.chosen_chunk_elems}
 
 
 class ns_server_config(C.Structure):
@@ -94,7 +106,7 @@ EXPORTED = ["ns_config_default", "ns_create", "ns_upload_mesh", "ns_set_material
             "ns_reset_stats", "ns_checkpoint_size", "ns_checkpoint", "ns_restore", "ns_destroy", "ns_last_error",
             "ns_spring_directions", "ns_colour_elements", "ns_state_bytes", "ns_spring_points_noalloc",
             "ns_spring_points_noalloc_capacity", "ns_set_members", "ns_set_member_ground_motion",
-            "ns_get_member_iters", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
+            "ns_get_member_iters", "ns_autotune", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
             "ns_server_wait", "ns_server_result", "ns_server_release", "ns_server_destroy"]
 
 _lib = None
@@ -139,6 +151,7 @@ def lib():
             "ns_set_members": ([vp, i32, vp, vp], C.c_int),
             "ns_set_member_ground_motion": ([vp, i32, i64, d, vp], C.c_int),
             "ns_get_member_iters": ([vp, i32, vp], C.c_int),
+            "ns_autotune": ([vp, C.POINTER(ns_tuning)], C.c_int),
             "ns_case_bytes": ([C.POINTER(ns_case), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
             "ns_server_create": ([C.POINTER(vp), C.POINTER(ns_server_config)], C.c_int),
             "ns_server_submit": ([vp, C.POINTER(ns_case), C.POINTER(i64)], C.c_int),
@@ -297,6 +310,12 @@ def ns_get_stats(ctx) -> dict:
     st = ns_stats()
     _check(ctx, lib().ns_get_stats(ctx, C.byref(st)))
     return st.as_dict()
+
+
+def ns_autotune(ctx) -> dict:
+    t = ns_tuning()
+    _check(ctx, lib().ns_autotune(ctx, C.byref(t)))
+    return t.as_dict()
 
 
 def ns_reset_stats(ctx):

@@ -263,4 +263,55 @@ NS_HD bool df64_ro_halley(float t, float gah, float gal, const RoPairs &P, const
   return true;
 }
 
+// ---------------------------------------------------------------------------------------
+// A double-float number as an arithmetic type (renormalised after every operation), so
+// that templated element kernels written for float and double also run in pair
+// arithmetic on the FP32 pipes.  Constants convert exactly enough from double.
+struct dd {
+  float h, l;
+  dd() = default;
+  NS_HD dd(float v) : h(v), l(0.0f) {}
+  NS_HD dd(int v) : h((float)v), l(0.0f) {}
+  NS_HD dd(double v) : h((float)v), l((float)(v - (double)(float)v)) {}
+  NS_HD dd(float hi, float lo) : h(hi), l(lo) {}
+  NS_HD explicit operator double() const { return (double)h + (double)l; }
+};
+NS_HD dd operator+(dd a, dd b) {
+  dd r;
+  pair_add(a.h, a.l, b.h, b.l, r.h, r.l);
+  return r;
+}
+NS_HD dd operator-(dd a) { return dd(-a.h, -a.l); }
+NS_HD dd operator-(dd a, dd b) { return a + (-b); }
+NS_HD dd operator*(dd a, dd b) {
+  dd r;
+  pair_mul(a.h, a.l, b.h, b.l, r.h, r.l);
+  return r;
+}
+NS_HD dd &operator+=(dd &a, dd b) { return a = a + b; }
+NS_HD dd &operator-=(dd &a, dd b) { return a = a - b; }
+NS_HD dd &operator*=(dd &a, dd b) { return a = a * b; }
+NS_HD bool operator==(dd a, dd b) { return a.h == b.h && a.l == b.l; }
+NS_HD bool operator!=(dd a, dd b) { return !(a == b); }
+
+// A double as a pair: on the device the high part is the double with its low 29
+// significand bits cleared, built on the integer pipes, and the low part the rounded rest
+// (two FP64-pipe operations instead of three conversions); zero and values outside the
+// normal float range are rounded to one float.
+NS_HD dd dd_from_double(double v) {
+#if defined(__CUDA_ARCH__)
+  const long long b = __double_as_longlong(v);
+  const int ed = (int)((b >> 52) & 0x7FF);
+  if (ed > 896 && ed < 1151) {
+    const double vh = __longlong_as_double(b & ~0x1FFFFFFFLL);
+    return dd(__uint_as_float((unsigned int)((b >> 32) & 0x80000000LL) | (unsigned int)((ed - 896) << 23) |
+                              (unsigned int)((b >> 29) & 0x7FFFFF)),
+              (float)(v - vh));
+  }
+  return dd((float)v, 0.0f);
+#else
+  return dd(v);
+#endif
+}
+
 }  // namespace ns

@@ -119,6 +119,9 @@ __device__ __forceinline__ float dload(const __half2 *__restrict__ D, int64_t ep
   const __half2 h = __ldg(D + (m >> 1) * epad + e);
   return (m & 1) ? __high2float(h) : __low2float(h);
 }
+__device__ __forceinline__ dd dload(const dd *__restrict__ D, int64_t epad, int64_t e, int m) {
+  return ldg(D + m * epad + e);
+}
 
 // Stress of integration point Q: sig = w D_Q eps_Q(x); dl(m) gives entry m of the
 // element's [84] point-major tangent.
@@ -146,8 +149,8 @@ __device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], 
 // returns x_e . y_e when DOT.
 template <typename T, int VS, bool HAS_XM, bool ATOMIC, bool DOT, typename DL>
 __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][3], T vol, const DL &dl,
-                                         const OpCoef *__restrict__ op, const T *__restrict__ xm,
-                                         const T *__restrict__ xk, T *y) {
+                                         const OpCoef *__restrict__ op, const typename VecOf<T>::type *__restrict__ xm,
+                                         const typename VecOf<T>::type *__restrict__ xk, typename VecOf<T>::type *y) {
   const T cK = (T)op->kK[mt], cMk = (T)op->mK[mt];
   const T cMm = HAS_XM ? (T)op->mM[mt] : (T)0;
   T ye[10][3];
@@ -180,8 +183,8 @@ __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][
       T w[10];
 #pragma unroll
       for (int a = 0; a < 10; ++a) {
-        w[a] = cMk * ldg(xk + VS * (int64_t)nd[a] + r);
-        if (HAS_XM) w[a] += cMm * ldg(xm + VS * (int64_t)nd[a] + r);
+        w[a] = cMk * vload<T>(xk + VS * (int64_t)nd[a] + r);
+        if (HAS_XM) w[a] += cMm * vload<T>(xm + VS * (int64_t)nd[a] + r);
       }
       mass_apply_1(w, c, ye, r);
     }
@@ -211,7 +214,8 @@ template <typename T, typename TD, int VS, bool HAS_XM, bool ATOMIC, bool DOT>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
     k_ebe(int64_t e0, int64_t e1, const int32_t *__restrict__ ids, const int32_t *__restrict__ conn,
           const T *__restrict__ geom, const int32_t *__restrict__ mat, const TD *__restrict__ D, int64_t epad,
-          const OpCoef *__restrict__ op, const T *__restrict__ xm, const T *__restrict__ xk, T *y, double *dot,
+          const OpCoef *__restrict__ op, const typename VecOf<T>::type *__restrict__ xm,
+          const typename VecOf<T>::type *__restrict__ xk, typename VecOf<T>::type *y, double *dot,
           const int32_t *skip, const Seg *seg) {
   int64_t i, end;
   if (seg) {  // members: this block's slice of one member's elements, that member's skip flag
@@ -359,8 +363,9 @@ __global__ void __launch_bounds__(kTile, 2)
 }
 
 template <typename T, typename TD, int VS, bool HAS_XM>
-static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, const OpCoef *op, const T *xm,
-                                const T *xk, T *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic,
+static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, const OpCoef *op,
+                                const typename VecOf<T>::type *xm, const typename VecOf<T>::type *xk,
+                                typename VecOf<T>::type *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic,
                                 double *dot, const int32_t *skip, cudaStream_t s, const SegList &sg) {
   if (!sg.seg && e1 <= e0) return cudaSuccess;
   const unsigned nb = sg.seg ? (unsigned)sg.n : (unsigned)((e1 - e0 + kBlock - 1) / kBlock);
@@ -384,7 +389,12 @@ static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, co
 
 cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
-                         const int32_t *skip, cudaStream_t s, SegList sg) {
+                         const int32_t *skip, cudaStream_t s, SegList sg, const void *D2) {
+  if (D2 && m.geom2) {  // FP64-accurate operator in double-float arithmetic
+    const dd *Dp = static_cast<const dd *>(D2);
+    if (xm) return ebe_dispatch<dd, dd, 3, true>(m, Dp, m.geom2, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s, sg);
+    return ebe_dispatch<dd, dd, 3, false>(m, Dp, m.geom2, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s, sg);
+  }
   if (xm)
     return ebe_dispatch<double, double, 3, true>(m, D, m.geom, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s, sg);
   return ebe_dispatch<double, double, 3, false>(m, D, m.geom, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s,
@@ -684,6 +694,19 @@ cudaError_t launch_jacobi_faces32(const DevMesh &m, const MatConst *mc, double c
   if (f1 <= f0) return cudaSuccess;
   k_jacobi_faces<float><<<(unsigned)((f1 - f0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
       f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, mc, cC, Jd, atomic);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pair copies for the double-float operator
+
+__global__ void k_to_pairs(const double *__restrict__ src, dd *dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = dd_from_double(src[i]);
+}
+
+cudaError_t launch_to_pairs(const double *src, void *dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_to_pairs<<<152 * 8, kBlock, 0, s>>>(src, static_cast<dd *>(dst), n);
   return cudaGetLastError();
 }
 

@@ -122,6 +122,23 @@ __device__ __forceinline__ float2 split_pair(double G) {
   return make_float2(__uint_as_float(fb), (float)(G - Ghi));
 }
 
+// Any double as an unevaluated float pair: the high part is v with its low 29 significand
+// bits cleared (built on the integer pipes), the low part the rounded rest; values outside
+// the normal float range (zero included) are rounded to one float.
+__device__ __forceinline__ void dsplit(double v, float &h, float &l) {
+  const long long b = __double_as_longlong(v);
+  const int ed = (int)((b >> 52) & 0x7FF);
+  if (ed > 896 && ed < 1151) {
+    const double vh = __longlong_as_double(b & ~0x1FFFFFFFLL);
+    h = __uint_as_float((unsigned int)((b >> 32) & 0x80000000LL) | (unsigned int)((ed - 896) << 23) |
+                        (unsigned int)((b >> 29) & 0x7FFFFF));
+    l = (float)(v - vh);
+  } else {
+    h = (float)v;
+    l = 0.0f;
+  }
+}
+
 // Root tau = F(ga) of the skeleton g(tau) = (tau/G0)(1 + alpha (tau/tref)^beta) = ga >= 0
 // (g odd, increasing, convex for tau > 0, tau <= G0 ga) and the tangent G = 1/g'(tau) as a
 // float pair; or -- when `solve` is false -- only the tangent at tau = ga (the current
@@ -192,62 +209,149 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
   return tau;
 }
 
+// As ro_solve (solving), for ga = gah + gal > 0 given as a float pair (the usual path
+// never forms ga in FP64).
+__device__ __forceinline__ double ro_solve_pair(float gah, float gal, float guess, const MatConst &p,
+                                                const PowTab &tb, const float *__restrict__ tabf, float2 *Gp) {
+  if (!(gah > 0.0f)) {  // zero strain: zero stress, G = G0
+    *Gp = split_pair(p.G0);
+    return 0.0;
+  }
+  const float hif = p.G0_f * gah;
+  float t = (guess > 0.0f && guess < hif) ? guess : hif;
+  bool seeded = false;
+  for (int it = 0; it < 40 && t > 0.0f; ++it) {
+    const float pwf = __powf(t * p.itref_f, p.beta_f);
+    const float gp = 1.0f + p.alpha_f * (1.0f + p.beta_f) * pwf;
+    const float step = (t * p.iG0_f * (1.0f + p.alpha_f * pwf) - gah) * __fdividef(p.G0_f, gp);
+    float tn = t - step;
+    if (!(tn > 0.0f)) tn = 0.5f * t;
+    if (tn > hif) tn = hif;
+    const bool conv = fabsf(step) <= 4e-6f * t;
+    t = tn;
+    if (conv) {
+      seeded = true;
+      break;
+    }
+  }
+  if (seeded && t > 0.0f) {
+    float th, tl, d, Gh, Gl;
+    if (df64_ro_halley(t, gah, gal, p.rp, tabf, th, tl, d, Gh, Gl) && fabsf(d) <= 2e-5f) {
+      *Gp = make_float2(Gh, Gl);
+      return (double)th + (double)tl;
+    }
+  }
+  // the FP64 path from the seed (or from the linear bound)
+  const double ga = (double)gah + (double)gal;
+  double tau = (t > 0.0f) ? (double)t : p.G0 * ga;
+  double w = pow_pos(tau * p.itref, p.beta_ro, tb);
+  const double it0 = rcp1(tau);
+  const double gval = tau * p.iG0 * fma(p.alpha_ro, w, 1.0);
+  const double rg = rcp1(fma(p.ab1, w, 1.0));
+  const double h = (gval - ga) * p.G0 * rg;
+  const double hc = h * p.hab1b * w * it0 * rg;
+  const double step = fma(h, hc, h);
+  const double d = -step * it0;
+  tau -= step;
+  w *= fma(d, fma(d, fma(d, p.c3, p.c2), p.beta_ro), 1.0);
+  if (!(seeded && fabs(d) <= 2e-5)) {
+    const double hi = p.G0 * ga;
+    tau = ro_F_safe(ga, (tau > 0.0 && tau <= hi) ? tau : hi, p, tb, &w);
+  }
+  *Gp = split_pair(ro_tangent_from_pw(w, p));
+  return tau;
+}
+
 // One spring (Masing bookkeeping of the documented reading): virgin -> skeleton in the
 // direction of motion; reversal stores (gamma_old, tau_old) and follows
 // tau = tR + 2 F((gamma - gR)/2); moving outward with |gamma| >= gmax returns to the
 // skeleton tau = F(gamma) (decided before the root solve, so each spring solves once).
 // With no increment the state is kept and only the tangent is evaluated.
 // Returns the tangent dtau/dgamma at the end state as a float pair.
-__device__ __forceinline__ float2 spring_update(double g, double dg, const MatConst &p, const PowTab &tb,
-                                                const float *__restrict__ tabf, double &tau, double &gR, double &tR,
-                                                double &gmax, int &dir, int &mode) {
-  const bool active = !d_is_zero(dg);
-  double x, guess = 0.0;
-  if (active) {
-    const int sgn = d_sign(dg) ? -1 : 1;
-    bool same = true;
-    if (dir == 0) {
-      dir = sgn;
-      mode = 0;
-      same = false;
-    } else if (sgn != dir) {
-      gR = g - dg;
-      tR = tau;
-      mode = 1;
-      dir = sgn;
-      same = false;
-    }
-    // outward (g on the side of dir, nonzero) with |g| >= gmax: back on the skeleton
-    const bool outward = !d_is_zero(g) && (d_sign(g) == (dir < 0));
-    if (mode == 1 && outward && dbits(d_abs(g)) >= dbits(gmax)) {
-      mode = 0;
-      guess = d_abs(tau);
-    } else if (same) {
-      guess = (mode == 0) ? d_abs(tau) : 0.5 * d_abs(tau - tR);
-    }
-    x = (mode == 0) ? g : 0.5 * (g - gR);
-  } else {
-    x = (mode == 0) ? tau : 0.5 * (tau - tR);  // the power at the current state only
-  }
+// The spring strain gamma = gh + gl and its increment dgamma = dh + dl come as normalised
+// float pairs (the dot products q_k . eps in double-float arithmetic); the stored state
+// stays FP64, and comparisons with it are made on pair differences.
+__device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float dh, float dl, const MatConst &p,
+                                                     const PowTab &tb, const float *__restrict__ tabf, double &tau,
+                                                     double &gR, double &tR, double &gmax, int &dir, int &mode) {
   float2 G;
-  const double f = ro_solve(active, d_abs(x), guess, p, tb, tabf, &G);
-  if (active) {
-    const double fs = d_copysign(f, x);
-    if (mode == 0) {
-      tau = fs;
-      const double ag = d_abs(g);
-      if (dbits(ag) > dbits(gmax)) gmax = ag;
-    } else {
-      tau = fma(2.0, fs, tR);
-    }
+  if (dh == 0.0f) {  // no increment: only the tangent at the current state
+    const double x = (mode == 0) ? tau : 0.5 * (tau - tR);
+    ro_solve(false, d_abs(x), 0.0, p, tb, tabf, &G);
+    return G;
+  }
+  const int sgn = dh < 0.0f ? -1 : 1;
+  bool same = true;
+  if (dir == 0) {
+    dir = sgn;
+    mode = 0;
+    same = false;
+  } else if (sgn != dir) {  // reversal: (gamma - dgamma, tau) becomes the branch origin
+    float rh, rl;
+    pair_add(gh, gl, -dh, -dl, rh, rl);
+    gR = (double)rh + (double)rl;
+    tR = tau;
+    mode = 1;
+    dir = sgn;
+    same = false;
+  }
+  // |gamma| - gmax as a pair
+  const bool gneg = gh < 0.0f;
+  const float agh = fabsf(gh), agl = gneg ? -gl : gl;
+  float mh, ml, ch, cl;
+  dsplit(gmax, mh, ml);
+  pair_add(agh, agl, -mh, -ml, ch, cl);
+  const bool beyond = ch > 0.0f || (ch == 0.0f && cl >= 0.0f);
+  // outward (gamma on the side of dir, nonzero) with |gamma| >= gmax: back on the skeleton
+  const bool outward = gh != 0.0f && (gneg == (dir < 0));
+  float guess = 0.0f;
+  if (mode == 1 && outward && beyond) {
+    mode = 0;
+    guess = fabsf((float)tau);
+  } else if (same) {
+    guess = (mode == 0) ? fabsf((float)tau) : 0.5f * fabsf((float)tau - (float)tR);
+  }
+  float xh = gh, xl = gl;
+  if (mode == 1) {  // (gamma - gR) / 2
+    float rh, rl;
+    dsplit(gR, rh, rl);
+    pair_add(gh, gl, -rh, -rl, xh, xl);
+    xh *= 0.5f;
+    xl *= 0.5f;
+  }
+  const bool xneg = xh < 0.0f;
+  const double f = ro_solve_pair(fabsf(xh), xneg ? -xl : xl, guess, p, tb, tabf, &G);
+  const double fs = xneg ? -f : f;
+  if (mode == 0) {
+    tau = fs;
+    if (ch > 0.0f || (ch == 0.0f && cl > 0.0f)) gmax = (double)agh + (double)agl;
+  } else {
+    tau = fma(2.0, fs, tR);
   }
   return G;
+}
+
+// gamma = q_k . e for a float-pair direction q (6) and a float-pair strain e (6), as a
+// normalised pair: exact products (FMA error terms) and compensated sums.
+__device__ __forceinline__ void pair_dot6(const float2 *__restrict__ q, const float2 *e, float &sh, float &sl) {
+  float s = 0.0f, c = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float2 qi = __ldg(q + i), ei = e[i];
+    float p, pe, t, te;
+    two_prod(qi.x, ei.x, p, pe);
+    pe = df_add(pe, df_fma(qi.x, ei.y, df_mul(qi.y, ei.x)));
+    two_sum(s, p, t, te);
+    s = t;
+    c = df_add(c, df_add(te, pe));
+  }
+  fast_two_sum(s, c, sh, sl);
 }
 
 // Block = a tile of TP consecutive points (TP multiple of 4) with all their S springs.
 // Phase 1: each thread updates springs of the tile (coalesced state access), stores
 // G_k in shared memory.  Phase 2: D_p[ij] = Kb [i,j < 3] + sum_k G_k T_k[ij].
-__global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q, const float2 *__restrict__ T2, int S,
+__global__ void __launch_bounds__(kBlock) k_springs(const float2 *__restrict__ q2, const float2 *__restrict__ T2, int S,
                                                     int TP, const MatConst *__restrict__ mc,
                                                     const int32_t *__restrict__ mat_e, const int32_t *__restrict__ mat_p,
                                                     const double *__restrict__ eps, double *tau_a, double *gR_a,
@@ -255,31 +359,33 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
                                                     int64_t base, int64_t p0, int64_t p1, double *D, int64_t epad,
                                                     double *dpts, const double *__restrict__ ptab,
                                                     const float *__restrict__ ptabf) {
-  extern __shared__ float2 Gs[];
+  extern __shared__ float2 Gs[];  // [TP][S] tangents, then [TP][12] strains as pairs
   const PowTab tb{ptab, ptab + 128, ptab + 256, ptab + 384, __ldg(ptab + 448), __ldg(ptab + 449), __ldg(ptab + 450),
                   __ldg(ptab + 451)};
   const int64_t pt = p0 + (int64_t)blockIdx.x * TP;
   const int np = (int)((p1 - pt) < TP ? (p1 - pt) : TP);
   const int nspr = np * S;
+  // phase 0: the tile's strains and increments as float pairs (once per point, not per spring)
+  float2 *Es = Gs + (size_t)TP * S;
+  for (int i = threadIdx.x; i < np * 12; i += blockDim.x) {
+    float h, l;
+    dsplit(eps[12 * pt + i], h, l);
+    Es[i] = make_float2(h, l);
+  }
+  __syncthreads();
   for (int g = threadIdx.x; g < nspr; g += blockDim.x) {
     const int lp = g / S, k = g - lp * S;
     const int64_t p = pt + lp;
     const int mt = mat_p ? mat_p[p] : mat_e[p >> 2];
     const MatConst &rp = mc[mt];
-    const double *ep = eps + 12 * p;
-    const double *qk = q + 6 * k;
-    double gam = 0.0, dgam = 0.0;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const double qc = __ldg(qk + c);
-      gam += qc * __ldg(ep + c);
-      dgam += qc * __ldg(ep + 6 + c);
-    }
+    float gh, gl, dh, dl;
+    pair_dot6(q2 + 6 * k, Es + 12 * lp, gh, gl);
+    pair_dot6(q2 + 6 * k, Es + 12 * lp + 6, dh, dl);
     const int64_t si = (p - base) * S + k;
     double tau = tau_a[si], gR = gR_a[si], tR = tR_a[si], gmax = gmax_a[si];
     int dir = dir_a[si], mode = mode_a[si];
-    const float2 G = spring_update(gam, dgam, rp, tb, ptabf, tau, gR, tR, gmax, dir, mode);
-    if (!d_is_zero(dgam)) {
+    const float2 G = spring_update_pair(gh, gl, dh, dl, rp, tb, ptabf, tau, gR, tR, gmax, dir, mode);
+    if (dh != 0.0f) {
       tau_a[si] = tau;
       gR_a[si] = gR;
       tR_a[si] = tR;
@@ -333,19 +439,23 @@ __global__ void __launch_bounds__(kBlock) k_springs(const double *__restrict__ q
   }
 }
 
-static int tile_points(int S) {
+// Points per block: whole elements (a multiple of 4), about 4096 springs per block by
+// default; the G_k of a block's springs and its points' strains sit in shared memory as
+// float pairs (8 bytes each, <= 200 KB).
+int spring_tile_default(int S) {
   int te = 4096 / (4 * S);
   int p2 = 1;
   while (p2 * 2 <= te && p2 < 64) p2 *= 2;
   return 4 * p2;
 }
+bool spring_tile_ok(int tp, int S) { return tp >= 4 && tp % 4 == 0 && (size_t)tp * (S + 12) * 8 <= 200 * 1024; }
 
 cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const int32_t *mat_of_elem,
                            const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
                            int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
-  const int TP = tile_points(tab.S);
-  const size_t smem = sizeof(float2) * TP * tab.S;
+  const int TP = spring_tile_ok(tab.tp, tab.S) ? tab.tp : spring_tile_default(tab.S);
+  const size_t smem = sizeof(float2) * ((size_t)TP * tab.S + (size_t)TP * 12);
   // the shared-memory opt-in is a per-device attribute, set once per device (any thread)
   static std::atomic<unsigned long long> attr_done{0};
   int dev = 0;
@@ -356,7 +466,7 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
     attr_done.fetch_or(bit);
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
-  k_springs<<<nb, kBlock, smem, s>>>(tab.q, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, st.gR,
+  k_springs<<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, st.gR,
                                      st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow, tab.powf);
   return cudaGetLastError();
 }

@@ -31,6 +31,34 @@ template <typename T>
 __device__ __forceinline__ T ldg(const T *p) {
   return __ldg(p);
 }
+// pairs are stored as float2
+__device__ __forceinline__ dd ldg(const dd *p) {
+  const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+  return dd(v.x, v.y);
+}
+
+// Node vectors of an operator in arithmetic type T: T itself, except that the pair type
+// works on FP64 vectors (split on load, summed back to FP64 on store).
+template <typename T>
+struct VecOf {
+  using type = T;
+};
+template <>
+struct VecOf<dd> {
+  using type = double;
+};
+template <typename T>
+__device__ __forceinline__ T vld(const T *p) {
+  return __ldg(p);
+}
+__device__ __forceinline__ dd vld_dd(const double *p) { return dd_from_double(__ldg(p)); }
+template <typename T, typename TV>
+__device__ __forceinline__ T vload(const TV *p) {
+  if constexpr (std::is_same<T, dd>::value)
+    return vld_dd(p);
+  else
+    return vld(p);
+}
 
 __device__ __forceinline__ void atomic_add(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add(float *p, float v) { atomicAdd(p, v); }
@@ -38,9 +66,12 @@ __device__ __forceinline__ void atomic_add(float *p, float v) { atomicAdd(p, v);
 // Node vectors are [N][VS]: VS = 3 (packed x y z) or, for the FP32 inner solve, VS = 4
 // (x y z and a zero pad, one 16-byte row per node: one vector load per node gather and
 // one vector atomic per node scatter).
-template <int VS, typename T>
-__device__ __forceinline__ void load_node(const T *__restrict__ x, int64_t n, T v[3]) {
-  if constexpr (VS == 4 && std::is_same<T, float>::value) {
+template <int VS, typename T, typename TV>
+__device__ __forceinline__ void load_node(const TV *__restrict__ x, int64_t n, T v[3]) {
+  if constexpr (std::is_same<T, dd>::value) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[r] = vld_dd(x + VS * n + r);
+  } else if constexpr (VS == 4 && std::is_same<T, float>::value) {
     const float4 q = __ldg(reinterpret_cast<const float4 *>(x) + n);
     v[0] = q.x;
     v[1] = q.y;
@@ -51,9 +82,18 @@ __device__ __forceinline__ void load_node(const T *__restrict__ x, int64_t n, T 
   }
 }
 
-template <int VS, bool ATOMIC, typename T>
-__device__ __forceinline__ void add_node(T *y, int64_t n, const T v[3]) {
-  if constexpr (VS == 4 && std::is_same<T, float>::value) {
+template <int VS, bool ATOMIC, typename T, typename TV>
+__device__ __forceinline__ void add_node(TV *y, int64_t n, const T v[3]) {
+  if constexpr (std::is_same<T, dd>::value) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double d = (double)v[r];
+      if (ATOMIC)
+        atomicAdd(y + VS * n + r, d);
+      else
+        y[VS * n + r] += d;
+    }
+  } else if constexpr (VS == 4 && std::is_same<T, float>::value) {
     float4 *d = reinterpret_cast<float4 *>(y) + n;
     if (ATOMIC) {
       atomicAdd(d, make_float4(v[0], v[1], v[2], 0.0f));

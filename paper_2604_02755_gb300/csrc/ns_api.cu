@@ -55,12 +55,14 @@ struct ns_ctx {
   MatConst *mats_d = nullptr;
   OpCoef *op_A = nullptr, *op_K = nullptr, *op_M = nullptr, *op_Cr = nullptr, *op_rhs = nullptr;
   double *q_d = nullptr, *T_d = nullptr, *pow_d = nullptr;
+  float2 *q2_d = nullptr;
   float *powf_d = nullptr;
   float2 *T2_d = nullptr;
   SpringTables tab{};
   double *D = nullptr;
   float *D32 = nullptr;   // NS_PREC_FP64_IR: FP32 copy of D for the inner operator
   __half *D16 = nullptr;  // NS_PREC_FP64_IR16: FP16 pairs of D / G0
+  dd *D2 = nullptr;       // pair_operator: D as float pairs, refreshed at the start of each step
   OpCoef *op_A16 = nullptr;  // op_A with kK scaled by G0 (reads D16)
   // spring state: resident elements [0, E_res) on the device, [E_res, E) in pinned host memory
   int64_t E_res = 0;
@@ -263,13 +265,13 @@ int apply_elems64(ns_ctx *c, const OpCoef *op, const double *xm, const double *x
   const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
   int off = 0;
   if (atomic) {
-    LAUNCH(c, launch_ebe64(c->m, c->D, op, xm, xk, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main, esegs(c)));
+    LAUNCH(c, launch_ebe64(c->m, c->D, op, xm, xk, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main, esegs(c), c->D2));
     off = c->M > 1 ? c->neseg : nblk(c->m.E);
   } else {
     for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k) {
       const int64_t e0 = c->m.ecol_off[k], e1 = c->m.ecol_off[k + 1];
       LAUNCH(c, launch_ebe64(c->m, c->D, op, xm, xk, y, c->m.ecol_ids, e0, e1, false, dot ? dot + off : nullptr, skip,
-                             c->s_main));
+                             c->s_main, SegList{}, c->D2));
       off += nblk(e1 - e0);
     }
   }
@@ -606,8 +608,12 @@ int solve_ir(ns_ctx *c) {
   const SegList vs = vsegs(c);
   const PartMap vm = vmap(c), om = opmap(c);
   double *pv = c->part + c->part_pap_cap;
-  if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
-  if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
+  if (c->cfg.x0_prev) {
+    if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
+  } else {  // from zero: A x0 = 0, no operator application
+    CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+    CKC(c, cudaMemsetAsync(c->Ap, 0, sizeof(double) * 3 * N, c->s_main));
+  }
   LAUNCH(c, launch_fcg_init(c->b, c->Ap, c->r, N, pv, c->s_main, vs));
   LAUNCH(c, launch_cg_final(pv, nbv, 2, c->sc, NS_FIN_FCG_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M, vm));
   if ((rc = read_scalars(c)) != NS_OK) return rc;
@@ -664,8 +670,12 @@ int solve_pcg(ns_ctx *c) {
   const SegList vs = vsegs(c);
   const PartMap vm = vmap(c), om = opmap(c);
   double *pv = c->part + c->part_pap_cap;
-  if (!c->cfg.x0_prev) CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
-  if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
+  if (c->cfg.x0_prev) {
+    if ((rc = apply_A(c, c->du, c->Ap, true, nullptr, nullptr, nullptr, false)) != NS_OK) return rc;
+  } else {  // from zero: A x0 = 0, no operator application
+    CKC(c, cudaMemsetAsync(c->du, 0, sizeof(double) * 3 * N, c->s_main));
+    CKC(c, cudaMemsetAsync(c->Ap, 0, sizeof(double) * 3 * N, c->s_main));
+  }
   LAUNCH(c, launch_cg_init(c->b, c->Ap, c->Jinv, c->r, c->z, c->p, N, pv, c->s_main, vs));
   LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc, NS_FIN_INIT, c->cfg.cg_tol, c->cfg.cg_max_iter, c->s_main, M, vm));
   if ((rc = read_scalars(c)) != NS_OK) return rc;
@@ -712,6 +722,7 @@ int one_step(ns_ctx *c) {
   // serves the inner single-precision solve)
   tbegin(c, TK_JAC, c->s_main, &t0);
   CKC(c, cudaMemsetAsync(c->flag_d, 0, sizeof(int32_t), c->s_main));
+  if (c->D2) LAUNCH(c, launch_to_pairs(c->D, c->D2, 84 * c->m.epad, c->s_main));
   if (c->cfg.precision != NS_PREC_FP64) {
     // FP32 blocks from the inner operator's own copy of the tangent (FP32, or FP16 / G0)
     const bool h16 = c->cfg.precision == NS_PREC_FP64_IR16;
@@ -852,6 +863,7 @@ void ns_config_default(ns_config *cfg) {
   cfg->graphs = 1;
   cfg->stage_elements = 0;
   cfg->stream_mode = NS_STREAM_RING;
+  cfg->pair_operator = 0;
 }
 
 static thread_local std::string g_create_err;
@@ -960,6 +972,10 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
   CKC(c, cudaMemsetAsync(m.kerr, 0, 4, c->s_main));
   CKC(c, cudaMemsetAsync(c->flag_d, 0, 4, c->s_main));
   LAUNCH(c, launch_geometry(m, c->xyz_d, c->flag_d, c->s_main));
+  if (c->cfg.pair_operator) {
+    if ((rc = dalloc(c, &m.geom2, 10 * (size_t)m.epad))) return rc;
+    LAUNCH(c, launch_to_pairs(m.geom, m.geom2, 10 * m.epad, c->s_main));
+  }
   CKC(c, cudaStreamSynchronize(c->s_main));
   int32_t bad = 0;
   CKC(c, cudaMemcpy(&bad, c->flag_d, 4, cudaMemcpyDeviceToHost));
@@ -1035,6 +1051,11 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   host_pow_tables(ph.data());
   std::vector<float> pfh(kPowFLen);
   host_powf_tables(pfh.data());
+  std::vector<float2> q2h(6 * (size_t)S);
+  for (size_t i = 0; i < q2h.size(); ++i) {
+    const float hi = (float)qh[i];
+    q2h[i] = make_float2(hi, (float)(qh[i] - (double)hi));
+  }
   std::vector<float2> T2h(21 * (size_t)S);
   for (size_t i = 0; i < T2h.size(); ++i) {
     const float hi = (float)Th[i];
@@ -1042,9 +1063,10 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   }
   if ((rc = dalloc(c, &c->q_d, qh.size())) || (rc = dalloc(c, &c->T_d, Th.size())) ||
       (rc = dalloc(c, &c->pow_d, ph.size())) || (rc = dalloc(c, &c->T2_d, T2h.size())) ||
-      (rc = dalloc(c, &c->powf_d, pfh.size())))
+      (rc = dalloc(c, &c->powf_d, pfh.size())) || (rc = dalloc(c, &c->q2_d, q2h.size())))
     return rc;
   CKC(c, cudaMemcpy(c->T2_d, T2h.data(), T2h.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->q2_d, q2h.data(), q2h.size() * sizeof(float2), cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->q_d, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->T_d, Th.data(), Th.size() * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->pow_d, ph.data(), ph.size() * 8, cudaMemcpyHostToDevice));
@@ -1054,10 +1076,12 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   c->tab.pow = c->pow_d;
   c->tab.powf = c->powf_d;
   c->tab.T2 = c->T2_d;
+  c->tab.q2 = c->q2_d;
   c->tab.S = S;
   // tangent D (element SoA [84][epad]) and spring state placement
   const int64_t E = c->m.E, epad = c->m.epad;
   if ((rc = dalloc(c, &c->D, 84 * (size_t)epad))) return rc;
+  if (c->cfg.pair_operator && (rc = dalloc(c, &c->D2, 84 * (size_t)epad))) return rc;
   if (c->cfg.precision == NS_PREC_FP64_IR && (rc = dalloc(c, &c->D32, 84 * (size_t)epad))) return rc;
   if (c->cfg.precision == NS_PREC_FP64_IR16) {
     if ((rc = dalloc(c, &c->D16, 84 * (size_t)epad))) return rc;
@@ -1537,6 +1561,7 @@ int ns_apply_operator(ns_ctx *c, int32_t op, const double *x, double *y) {
   const size_t n3 = 3 * (size_t)c->m.N;
   CKC(c, cudaMemcpy(c->p, x, n3 * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemsetAsync(c->Ap, 0, n3 * 8, c->s_main));
+  if (c->D2) LAUNCH(c, launch_to_pairs(c->D, c->D2, 84 * c->m.epad, c->s_main));  // D may have been written
   switch (op) {
     case NS_OP_K: rc = apply_elems64(c, c->op_K, nullptr, c->p, c->Ap, nullptr, nullptr, nullptr); break;
     case NS_OP_M: rc = apply_elems64(c, c->op_M, nullptr, c->p, c->Ap, nullptr, nullptr, nullptr); break;
@@ -1606,6 +1631,124 @@ int ns_spring_points(ns_ctx *c, int64_t npts, const int32_t *mat, const double *
     for (int i = 0; i < 6; ++i)
       for (int j = 0; j < 6; ++j) D[p * 36 + i * 6 + j] = dh[p * 21 + sym6(i, j)];
   return NS_OK;
+}
+
+int ns_autotune(ns_ctx *c, ns_tuning *out) {
+  if (!c || !out) return NS_ERR_INVALID_ARG;
+  if (!c->has_mat || !c->has_bnd || c->step < 1) NS_SET(c, NS_ERR_STATE, "autotune after at least one step");
+  memset(out, 0, sizeof(*out));
+  const int S = c->tab.S;
+  int rc = NS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CKC(c, cudaEventCreate(&e0));
+  CKC(c, cudaEventCreate(&e1));
+  auto timed = [&](cudaStream_t s, auto &&work, float *ms) -> int {
+    CKC(c, cudaEventRecord(e0, s));
+    int r = work();
+    if (r) return r;
+    CKC(c, cudaEventRecord(e1, s));
+    if ((r = sync_stream(c, s)) != NS_OK) return r;
+    CKC(c, cudaEventElapsedTime(ms, e0, e1));
+    return NS_OK;
+  };
+  // 1. spring kernel block shape on a copy of the first resident elements' state
+  const int64_t ne = std::min<int64_t>(c->E_res, 32768);
+  if (ne > 0) {
+    const int64_t np = 4 * ne, nspr = np * S;
+    SpringSoA scr;
+    double *dpts = nullptr;
+    if ((rc = alloc_soa(c, scr, nspr, false)) == NS_OK && (rc = dalloc(c, &dpts, 21 * (size_t)np)) == NS_OK) {
+      const int cands[8] = {4, 8, 16, 32, 64, 128, 256, 512};
+      float best = 1e30f;
+      int chosen = spring_tile_default(S);
+      for (int k = 0; k < 8 && rc == NS_OK; ++k) {
+        if (!spring_tile_ok(cands[k], S)) continue;
+        SpringTables tb = c->tab;
+        tb.tp = cands[k];
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3 && rc == NS_OK; ++rep) {
+          if ((rc = copy_soa(c, scr, 0, c->st, 0, nspr, cudaMemcpyDeviceToDevice, c->s_main)) != NS_OK) break;
+          float ms = 0.0f;
+          rc = timed(c->s_main, [&]() -> int {
+            LAUNCH(c, launch_springs(tb, c->mats_d, c->m.mat, nullptr, c->eps, scr, 0, 0, np, nullptr, c->m.epad,
+                                     dpts, c->s_main));
+            return NS_OK;
+          }, &ms);
+          ms_best = std::min(ms_best, ms);
+        }
+        if (rc != NS_OK) break;
+        out->tile_points[out->n_tile] = cands[k];
+        out->tile_ms[out->n_tile] = ms_best;
+        out->n_tile++;
+        if (ms_best < best) {
+          best = ms_best;
+          chosen = cands[k];
+        }
+      }
+      if (rc == NS_OK) {
+        c->tab.tp = chosen;
+        out->chosen_tile_points = chosen;
+      }
+    }
+    free_soa(scr, false);
+    dfree(dpts);
+  }
+  // 2. chunk size of the streamed state: H2D of a ring's worth of chunks and D2H of the same
+  //    bytes back to where they came from (the host state is left as it was)
+  const int64_t nstream = c->m.E - c->E_res;
+  if (rc == NS_OK && nstream > 0 && c->cfg.stream_mode == NS_STREAM_RING && !c->ring.empty()) {
+    const int64_t cap = std::min<int64_t>(c->cfg.chunk_elems, nstream);  // ring buffers hold this many
+    const int64_t S4 = 4 * (int64_t)S;
+    const int R = (int)c->ring.size();
+    int64_t cands[6] = {cap / 8, cap / 4, cap / 2, cap, 0, 0};
+    double best = 0.0;
+    int64_t chosen = c->cfg.chunk_elems;
+    for (int k = 0; k < 4 && rc == NS_OK; ++k) {
+      const int64_t ch = cands[k];
+      if (ch < 1) continue;
+      const int64_t nch = std::min<int64_t>((nstream + ch - 1) / ch, 2 * (int64_t)R);
+      float ms = 0.0f;
+      int64_t bytes = 0;
+      rc = timed(c->s_h2d, [&]() -> int {
+        for (int64_t j = 0; j < nch; ++j) {
+          const int slot = (int)(j % R);
+          const int64_t a = j * ch, n = std::min(ch, nstream - a);
+          if (n <= 0) break;
+          if (j >= R) CKC(c, cudaStreamWaitEvent(c->s_h2d, c->ev_d2h[slot], 0));
+          int r = copy_soa(c, c->ring[slot], 0, c->hst, a * S4, n * S4, cudaMemcpyHostToDevice, c->s_h2d);
+          if (r) return r;
+          CKC(c, cudaEventRecord(c->ev_h2d[slot], c->s_h2d));
+          CKC(c, cudaStreamWaitEvent(c->s_d2h, c->ev_h2d[slot], 0));
+          if ((r = copy_soa(c, c->hst, a * S4, c->ring[slot], 0, n * S4, cudaMemcpyDeviceToHost, c->s_d2h))) return r;
+          CKC(c, cudaEventRecord(c->ev_d2h[slot], c->s_d2h));
+          bytes += 2 * n * S4 * 40;
+        }
+        // the measured window ends when the last D2H has landed
+        CKC(c, cudaEventRecord(c->ev_join, c->s_d2h));
+        CKC(c, cudaStreamWaitEvent(c->s_h2d, c->ev_join, 0));
+        return NS_OK;
+      }, &ms);
+      if (rc != NS_OK) break;
+      const double gbps = bytes / (ms / 1e3) / 1e9;
+      out->chunk_elems[out->n_chunk] = ch;
+      out->chunk_gbps[out->n_chunk] = (float)gbps;
+      out->n_chunk++;
+      if (gbps > best) {
+        best = gbps;
+        chosen = ch;
+      }
+    }
+    if (rc == NS_OK) {
+      int r = sync_stream(c, c->s_d2h);
+      if (r) rc = r;
+      c->cfg.chunk_elems = chosen;
+      out->chosen_chunk_elems = chosen;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == NS_OK) CKC(c, cudaStreamSynchronize(c->s_main));
+  return rc;
 }
 
 int ns_get_stats(ns_ctx *c, ns_stats *st) {
@@ -1691,11 +1834,11 @@ void ns_destroy(ns_ctx *c) {
   if (c->s_h2d) cudaStreamSynchronize(c->s_h2d);
   if (c->s_d2h) cudaStreamSynchronize(c->s_d2h);
   DevMesh &m = c->m;
-  dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.kerr); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
+  dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.kerr); dfree(m.geom2); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
   dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
   dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
-  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->powf_d); dfree(c->T2_d); dfree(c->D); dfree(c->D32);
-  dfree(c->D16); dfree(c->op_A16);
+  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->powf_d); dfree(c->T2_d); dfree(c->q2_d); dfree(c->D); dfree(c->D32);
+  dfree(c->D16); dfree(c->op_A16); dfree(c->D2);
   destroy_graphs(c);
   dfree(c->vseg_d); dfree(c->eseg_d); dfree(c->fseg_d); dfree(c->voff_d); dfree(c->eoff_d); dfree(c->foff_d);
   dfree(c->fmem_d);

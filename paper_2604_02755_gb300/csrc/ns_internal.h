@@ -51,6 +51,7 @@ struct DevMesh {
   int32_t *ecol_ids = nullptr, *fcol_ids = nullptr;
   std::vector<int64_t> ecol_off, fcol_off;
   int32_t *kerr = nullptr;  // device flag: a bounded wait inside a kernel gave up
+  dd *geom2 = nullptr;      // [10][epad] geometry as float pairs (double-float operator)
 };
 
 // Spring state arrays (structure of arrays over springs ordered [elem][point][spring]).
@@ -101,9 +102,13 @@ cudaError_t launch_face_geometry(const DevMesh &m, const double *xyz, cudaStream
 // to dot[blockIdx.x] (the element-local energy of the application).
 // With sg.seg set (members, atomic scatter) the launch covers sg's blocks instead of
 // [e0, e1), and the skip flag of each block is that of its member (skip + m * kScStride).
+// D2 (optional): the tangent as float pairs [84][epad]; with it (and m.geom2) the operator
+// runs in double-float arithmetic on the FP32 pipes (relative accuracy ~1e-13).
 cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
-                         const int32_t *skip, cudaStream_t s, SegList sg = {});
+                         const int32_t *skip, cudaStream_t s, SegList sg = {}, const void *D2 = nullptr);
+// dst[i] = src[i] as a float pair (n values)
+cudaError_t launch_to_pairs(const double *src, void *dst, int64_t n, cudaStream_t s);
 // staged: whole-mesh atomic launches stage each tile of elements in shared memory with
 // bulk copies (cp.async.bulk) instead of per-thread loads.
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
@@ -199,12 +204,17 @@ cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, dou
 // ------------------------------------------------------------------ k_spring.cu
 struct SpringTables {
   const double *q;    // [S][6]
+  const float2 *q2;   // [S][6] the same as (hi, lo) float pairs
   const double *T;    // [S][21] w q q^T packed upper triangle (+ one row with their sum)
   const float2 *T2;   // [S][21] the same entries as (hi, lo) float pairs
   const double *pow;  // power tables: r[128], -ln r hi[128], lo[128], 2^(i/64)[64], ln2 hi/lo, ln2/64 hi/lo
   const float *powf;  // double-float power tables (df64.cuh, kPowFLen floats)
   int S;
+  int tp = 0;         // integration points per block of the spring kernel (0: size heuristic)
 };
+// the spring kernel's default points per block for S springs, and whether tp is usable
+int spring_tile_default(int S);
+bool spring_tile_ok(int tp, int S);
 constexpr int kPowTabLen = 452;
 // Spring update of points [p0, p1) (point p = elem*4 + qp), strains from eps [P][12];
 // state arrays indexed relative to `base` point; D written to D[(qp*21 + k) * epad + elem]

@@ -34,12 +34,15 @@ def rel(a, b):
     return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
 
 
-@pytest.mark.parametrize("scatter", [B.NS_SCATTER_ATOMIC, B.NS_SCATTER_COLOUR])
-def test_operators_match_oracle(scatter):
+@pytest.mark.parametrize("scatter,pair", [(B.NS_SCATTER_ATOMIC, 0), (B.NS_SCATTER_COLOUR, 0),
+                                          (B.NS_SCATTER_ATOMIC, 1), (B.NS_SCATTER_COLOUR, 1)])
+def test_operators_match_oracle(scatter, pair):
+    """Element operators against the oracle's; pair = 1 runs them in double-float
+    arithmetic on the FP32 pipes, which must still meet the FP64 bound."""
     wl = small(dims=(4, 3, 2))
     o = oracle.Oracle.from_workload(wl)
     rng = np.random.default_rng(0)
-    with B.Simulation(wl, scatter=scatter) as sim:
+    with B.Simulation(wl, scatter=scatter, pair_operator=pair) as sim:
         # random symmetric positive definite tangents at every point
         E = wl.mesh.n_elems
         A = rng.normal(size=(E, 4, 6, 6)) * 1e7
@@ -117,13 +120,19 @@ def test_one_step_matches_oracle():
                                                (B.NS_SCATTER_ATOMIC, B.NS_PREC_FP64_IR),
                                                (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64_IR),
                                                (B.NS_SCATTER_ATOMIC, B.NS_PREC_FP64_IR16),
-                                               (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64_IR16)])
+                                               (B.NS_SCATTER_COLOUR, B.NS_PREC_FP64_IR16),
+                                               (B.NS_SCATTER_ATOMIC, -1), (B.NS_SCATTER_COLOUR, -2)])
 def test_thirty_steps_surface_parity(scatter, precision):
+    """precision -1 / -2: the FP64 + FP32-inner / FP16-tangent forms with the FP64-accuracy
+    operator applications in double-float arithmetic."""
     wl = small(dims=(4, 3, 3), nt=60)
     nsteps = 30
     o = oracle.Oracle.from_workload(wl)
     us, vs = [], []
-    with B.Simulation(wl, surface_ring_steps=nsteps, scatter=scatter, precision=precision) as sim:
+    pair = int(precision < 0)
+    precision = {-1: B.NS_PREC_FP64_IR, -2: B.NS_PREC_FP64_IR16}.get(precision, precision)
+    with B.Simulation(wl, surface_ring_steps=nsteps, scatter=scatter, precision=precision,
+                      pair_operator=pair) as sim:
         for _ in range(nsteps):
             o.step()
             us.append(o.u[wl.mesh.surf].copy())
@@ -332,3 +341,26 @@ def test_staged_operator_equals_direct_loads():
                 out.append(sim.surface(1, 30)["v"])
     assert rel(out[2], out[0]) <= 1e-9 and rel(out[3], out[1]) <= 1e-9
     assert rel(out[1], out[0]) <= 1e-9  # FP16 storage only changes the preconditioner
+
+
+def test_autotune_keeps_results_and_state():
+    """The autotuner times block shapes on a copy of the state and chunk sizes by round
+    trips through the ring; the run it tunes is bit-identical to an untuned one."""
+    wl = small(dims=(4, 3, 3), nt=60)
+    per_elem = B.ns_state_bytes(1, wl.n_springs)
+    out = []
+    for tune in (False, True):
+        with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR, surface_ring_steps=12, device_state_budget=per_elem * 40,
+                          chunk_elems=16, ring_depth=3) as sim:
+            sim.advance(4)
+            before = sim.state()
+            if tune:
+                t = B.ns_autotune(sim.ctx)
+                after = sim.state()
+                assert after[0].tobytes() == before[0].tobytes() and np.array_equal(after[1], before[1])
+                assert t["chosen_tile_points"] in t["tile_points"] and min(t["tile_ms"]) > 0
+                assert t["chosen_chunk_elems"] in t["chunk_elems"] and min(t["chunk_gbps"]) > 0
+            sim.advance(8)
+            out.append((sim.nodal("u"), sim.state()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1][0].tobytes() == out[1][1][0].tobytes()

@@ -41,18 +41,20 @@ def reference():
     return wl, np.array(us), np.array(vs), o
 
 
-@pytest.mark.parametrize("precision,bound", [(B.NS_PREC_FP64, 1e-6), (B.NS_PREC_FP64_IR, 1e-4),
-                                             (B.NS_PREC_FP64_IR16, 1e-4)])
-def test_precision_form_against_oracle(reference, precision, bound):
+@pytest.mark.parametrize("precision,pair,bound", [(B.NS_PREC_FP64, 0, 1e-6), (B.NS_PREC_FP64_IR, 0, 1e-4),
+                                                  (B.NS_PREC_FP64_IR16, 0, 1e-4), (B.NS_PREC_FP64_IR16, 1, 1e-4)])
+def test_precision_form_against_oracle(reference, precision, pair, bound):
+    """pair = 1: the FP64-accuracy operator applications (right-hand side, outer CG, q
+    update) in double-float arithmetic as well."""
     wl, us, vs, o = reference
-    with B.Simulation(wl, surface_ring_steps=NSTEPS, precision=precision) as sim:
+    with B.Simulation(wl, surface_ring_steps=NSTEPS, precision=precision, pair_operator=pair) as sim:
         sim.advance(NSTEPS)
         s = sim.surface(1, NSTEPS)
         th, _ = sim.state()
         st = sim.stats()
     eu, ev = rel(s["u"], us), rel(s["v"], vs)
-    print("precision %d: rel L2 surface u %.3e v %.3e, outer CG iterations %d over %d steps"
-          % (precision, eu, ev, st["cg_iters_total"], NSTEPS))
+    print("precision %d pair %d: rel L2 surface u %.3e v %.3e, outer CG iterations %d over %d steps"
+          % (precision, pair, eu, ev, st["cg_iters_total"], NSTEPS))
     assert eu <= bound and ev <= bound
     assert (o.th["mode"] == 1).mean() > 0.01  # the record drives the springs into hysteresis
     assert np.mean(th["mode"] == o.th["mode"]) > 0.999
