@@ -364,3 +364,20 @@ def test_autotune_keeps_results_and_state():
             out.append((sim.nodal("u"), sim.state()))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1][0].tobytes() == out[1][1][0].tobytes()
+
+
+@pytest.mark.parametrize("precision", [B.NS_PREC_FP64, B.NS_PREC_FP64_IR])
+def test_zero_start_parity(precision):
+    """CG started from zero (no operator application for the initial residual) against
+    the oracle started from zero."""
+    wl = small(dims=(4, 3, 3), nt=60)
+    nsteps = 20
+    o = oracle.Oracle.from_workload(wl, x0_prev=False)
+    us = []
+    with B.Simulation(wl, surface_ring_steps=nsteps, precision=precision, x0_prev=0) as sim:
+        for _ in range(nsteps):
+            o.step()
+            us.append(o.u[wl.mesh.surf].copy())
+        sim.advance(nsteps)
+        s = sim.surface(1, nsteps)
+    assert rel(s["u"], np.array(us)) <= 1e-6
