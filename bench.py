@@ -261,6 +261,8 @@ def main():
                          "per-thread loads (0)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the library's autotuner (spring-kernel block shape) after the warm-up steps")
+    ap.add_argument("--prefetch", type=int, default=1, choices=[0, 1],
+                    help="element operators prefetch their element rows into L2 (bulk prefetch)")
     ap.add_argument("--pair-op", type=int, default=0, choices=[0, 1],
                     help="FP64-accuracy operator applications in double-float arithmetic on the FP32 pipes")
     ap.add_argument("--x0", default="zero", choices=["prev", "zero"],
@@ -333,7 +335,7 @@ def main():
     graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
               stage_elements=args.stage, inner_max_iter=args.inner_iters, x0_prev=int(args.x0 == "prev"),
-              pair_operator=args.pair_op)
+              pair_operator=args.pair_op, l2_prefetch=args.prefetch)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
     tuning = B.ns_autotune(sim.ctx) if args.autotune else None
@@ -422,7 +424,7 @@ def main():
             sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
                                ring_depth=ring, precision=prec, graphs=graphs, stage_elements=args.stage,
                                inner_max_iter=args.inner_iters, stream_mode=mode, x0_prev=int(args.x0 == "prev"),
-                               pair_operator=args.pair_op)
+                               pair_operator=args.pair_op, l2_prefetch=args.prefetch)
             sim.advance(1)
             B.ns_reset_stats(sim.ctx)
             h0 = sim.stats()
@@ -468,7 +470,7 @@ def main():
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
                 "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
                 "staged_operator": args.stage, "inner_iters": args.inner_iters, "autotune": tuning,
-                "pair_operator": args.pair_op, "x0": args.x0,
+                "pair_operator": args.pair_op, "x0": args.x0, "l2_prefetch": args.prefetch,
                 "state_stream": stream}
         print(json.dumps(line), flush=True)
     dist.finalize(dd)

@@ -85,6 +85,8 @@ typedef struct {
   int32_t stage_elements;      /* 1: the FP32 inner operator stages each 256-element tile of element
                                   data in shared memory with bulk copies (atomic scatter, one member);
                                   0 (default): per-thread loads, which measured faster on GB300 */
+  int32_t l2_prefetch;         /* 1: each block of the element operators first prefetches its slice
+                                  of the element rows into L2 with a bulk prefetch */
   int32_t pair_operator;       /* 1: the FP64-accuracy operator applications (right-hand side, outer
                                   CG, q update) run in double-float arithmetic on the FP32 pipes
                                   (relative accuracy ~1e-13, FP64 node vectors); 0: FP64 */

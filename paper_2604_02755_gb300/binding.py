@@ -40,7 +40,7 @@ class ns_config(C.Structure):
                 ("rayleigh_f2", C.c_double), ("surface_ring_steps", C.c_int64), ("device", C.c_int32),
                 ("timing", C.c_int32), ("inner_max_iter", C.c_int32), ("inner_tol", C.c_double),
                 ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32),
-                ("pair_operator", C.c_int32), ("stream_mode", C.c_int32)]
+                ("l2_prefetch", C.c_int32), ("pair_operator", C.c_int32), ("stream_mode", C.c_int32)]
 
 
 class ns_material(C.Structure):

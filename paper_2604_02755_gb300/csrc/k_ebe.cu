@@ -141,9 +141,6 @@ __device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], 
   sig[5] = w * (d[5] * eps[0] + d[10] * eps[1] + d[14] * eps[2] + d[17] * eps[3] + d[19] * eps[4] + d[20] * eps[5]);
 }
 
-// Operator kernel, one thread per element.  Phases keep the register footprint small:
-// (1) gather x, stresses at the four points; (2) nodal forces B^T sig; (3) consistent mass
-// one displacement component at a time (re-gathered from cache); (4) scatter.
 // One element of the operator: y_e = (kK K_e + mK M_e) x_e + mM M_e xm_e scattered into y
 // (nodes nd, material mt, barycentric gradients g, volume vol, tangent entries dl(m));
 // returns x_e . y_e when DOT.
@@ -205,6 +202,31 @@ __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][
   return ld;
 }
 
+// L2 prefetch of a block's slice of the element rows (cp.async.bulk.prefetch: the TMA
+// engine's linear prefetch, fire and forget): thread r < rows fetches one row's slice, so
+// the per-thread loads that follow find the tangent, geometry, connectivity and material
+// in L2 instead of waiting on DRAM one dependent load at a time.
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+template <typename T, typename TD>
+__device__ __forceinline__ void prefetch_tile(int64_t eb, int64_t epad, const int32_t *conn, const T *geom,
+                                              const int32_t *mat, const TD *D) {
+  // rows start at 256-byte boundaries (epad a multiple of 64, eb of kBlock) and the slice
+  // ends inside the row (epad - eb >= 64)
+  const int64_t n = (epad - eb) < kBlock ? (epad - eb) : kBlock;
+  constexpr int DR = std::is_same<TD, __half2>::value ? 42 : 84;
+  const int r = threadIdx.x;
+  if (r < DR)
+    l2_prefetch(D + r * epad + eb, (uint32_t)(n * sizeof(TD)));
+  else if (r < DR + 10)
+    l2_prefetch(geom + (r - DR) * epad + eb, (uint32_t)(n * sizeof(T)));
+  else if (r < DR + 20)
+    l2_prefetch(conn + (r - DR - 10) * epad + eb, (uint32_t)(n * 4));
+  else if (r == DR + 20)
+    l2_prefetch(mat + eb, (uint32_t)(n * 4));
+}
+
 // Operator kernel, one thread per element.  Phases keep the register footprint small:
 // (1) gather x, stresses at the four points; (2) nodal forces B^T sig; (3) consistent mass
 // one displacement component at a time (re-gathered from cache); (4) scatter.
@@ -216,7 +238,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
           const T *__restrict__ geom, const int32_t *__restrict__ mat, const TD *__restrict__ D, int64_t epad,
           const OpCoef *__restrict__ op, const typename VecOf<T>::type *__restrict__ xm,
           const typename VecOf<T>::type *__restrict__ xk, typename VecOf<T>::type *y, double *dot,
-          const int32_t *skip, const Seg *seg) {
+          const int32_t *skip, const Seg *seg, int prefetch) {
   int64_t i, end;
   if (seg) {  // members: this block's slice of one member's elements, that member's skip flag
     const Seg sg = seg[blockIdx.x];
@@ -228,6 +250,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
     end = e1;
   }
   if (skip && *skip) return;
+  if (prefetch && !seg && !ids && e0 == 0) prefetch_tile(blockIdx.x * (int64_t)kBlock, epad, conn, geom, mat, D);
   double mydot = 0.0;
   if (i < end) {
     const int64_t e = ids ? (int64_t)ids[i] : i;
@@ -371,7 +394,7 @@ static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, co
   const unsigned nb = sg.seg ? (unsigned)sg.n : (unsigned)((e1 - e0 + kBlock - 1) / kBlock);
 #define NS_EBE_LAUNCH(A, DT)                                                                                  \
   k_ebe<T, TD, VS, HAS_XM, A, DT><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, \
-                                                     dot, skip, sg.seg)
+                                                     dot, skip, sg.seg, m.prefetch)
   if (atomic) {
     if (dot)
       NS_EBE_LAUNCH(true, true);

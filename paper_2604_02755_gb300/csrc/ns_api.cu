@@ -864,6 +864,7 @@ void ns_config_default(ns_config *cfg) {
   cfg->stage_elements = 0;
   cfg->stream_mode = NS_STREAM_RING;
   cfg->pair_operator = 0;
+  cfg->l2_prefetch = 1;
 }
 
 static thread_local std::string g_create_err;
@@ -955,6 +956,7 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
   DevMesh &m = c->m;
   m.N = N;
   m.E = E;
+  m.prefetch = c->cfg.l2_prefetch ? 1 : 0;
   m.epad = pad64(E);
   std::vector<int32_t> soa((size_t)10 * m.epad, 0);
   for (int64_t e = 0; e < E; ++e)

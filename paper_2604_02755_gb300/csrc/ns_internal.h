@@ -52,6 +52,7 @@ struct DevMesh {
   std::vector<int64_t> ecol_off, fcol_off;
   int32_t *kerr = nullptr;  // device flag: a bounded wait inside a kernel gave up
   dd *geom2 = nullptr;      // [10][epad] geometry as float pairs (double-float operator)
+  int prefetch = 0;         // element kernels prefetch their blocks' element rows into L2
 };
 
 // Spring state arrays (structure of arrays over springs ordered [elem][point][spring]).
