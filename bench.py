@@ -268,6 +268,8 @@ def main():
     ap.add_argument("--x0", default="zero", choices=["prev", "zero"],
                     help="CG start: zero (default: no operator application for the initial residual) or the "
                          "previous step's increment")
+    ap.add_argument("--inner-tol", type=float, default=1e-3,
+                    help="relative residual at which the FP32 inner CG stops early")
     ap.add_argument("--inner-iters", type=int, default=30,
                     help="FP32 inner CG iterations per outer iteration of the flexible solver")
     ap.add_argument("--requests", type=int, default=12, help="requests of the served trace")
@@ -334,7 +336,7 @@ def main():
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
-              stage_elements=args.stage, inner_max_iter=args.inner_iters, x0_prev=int(args.x0 == "prev"),
+              stage_elements=args.stage, inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, x0_prev=int(args.x0 == "prev"),
               pair_operator=args.pair_op, l2_prefetch=args.prefetch)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
@@ -423,7 +425,7 @@ def main():
         def streamed_run(mode):
             sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
                                ring_depth=ring, precision=prec, graphs=graphs, stage_elements=args.stage,
-                               inner_max_iter=args.inner_iters, stream_mode=mode, x0_prev=int(args.x0 == "prev"),
+                               inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, stream_mode=mode, x0_prev=int(args.x0 == "prev"),
                                pair_operator=args.pair_op, l2_prefetch=args.prefetch)
             sim.advance(1)
             B.ns_reset_stats(sim.ctx)
@@ -469,7 +471,7 @@ def main():
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
                 "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
-                "staged_operator": args.stage, "inner_iters": args.inner_iters, "autotune": tuning,
+                "staged_operator": args.stage, "inner_iters": args.inner_iters, "inner_tol": args.inner_tol, "autotune": tuning,
                 "pair_operator": args.pair_op, "x0": args.x0, "l2_prefetch": args.prefetch,
                 "state_stream": stream}
         print(json.dumps(line), flush=True)

@@ -33,7 +33,9 @@ def test_zero_record_leaves_everything_at_rest(precision):
         th, D = sim.state()
         st = sim.stats()
     assert not np.any(s["u"]) and not np.any(s["v"]) and not np.any(s["a"])
-    assert th.tobytes() == th0.tobytes() and np.array_equal(D, D0)  # virgin springs, elastic tangent
+    assert th.tobytes() == th0.tobytes()  # virgin springs
+    # elastic tangent again, up to the rounding of its (double-float) accumulation over the springs
+    assert np.max(np.abs(D - D0)) <= 1e-13 * np.max(np.abs(D0))
     assert st["cg_iters_last"] == 0
 
 
