@@ -144,10 +144,12 @@ __device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], 
 // One element of the operator: y_e = (kK K_e + mK M_e) x_e + mM M_e xm_e scattered into y
 // (nodes nd, material mt, barycentric gradients g, volume vol, tangent entries dl(m));
 // returns x_e . y_e when DOT.
-template <typename T, int VS, bool HAS_XM, bool ATOMIC, bool DOT, typename DL>
+// OUTK: the stiffness part K_e xk (unscaled) is also scattered into yk.
+template <typename T, int VS, bool HAS_XM, bool ATOMIC, bool DOT, typename DL, bool OUTK = false>
 __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][3], T vol, const DL &dl,
                                          const OpCoef *__restrict__ op, const typename VecOf<T>::type *__restrict__ xm,
-                                         const typename VecOf<T>::type *__restrict__ xk, typename VecOf<T>::type *y) {
+                                         const typename VecOf<T>::type *__restrict__ xk, typename VecOf<T>::type *y,
+                                         typename VecOf<T>::type *yk = nullptr) {
   const T cK = (T)op->kK[mt], cMk = (T)op->mK[mt];
   const T cMm = HAS_XM ? (T)op->mM[mt] : (T)0;
   T ye[10][3];
@@ -162,7 +164,7 @@ __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][
 #pragma unroll
       for (int a = 0; a < 10; ++a) load_node<VS>(xk, nd[a], x[a]);
       compute_P(x, P);
-      const T w = cK * vol * (T)0.25;
+      const T w = OUTK ? vol * (T)0.25 : cK * vol * (T)0.25;
       point_stress<T, 0>(x, P, g, dl, w, sig[0]);
       point_stress<T, 1>(x, P, g, dl, w, sig[1]);
       point_stress<T, 2>(x, P, g, dl, w, sig[2]);
@@ -172,6 +174,14 @@ __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][
     point_force<T, 1>(sig[1], g, ye);
     point_force<T, 2>(sig[2], g, ye);
     point_force<T, 3>(sig[3], g, ye);
+    if (OUTK) {  // K_e x to yk, then the coefficient
+#pragma unroll
+      for (int a = 0; a < 10; ++a) add_node<VS, ATOMIC>(yk, nd[a], ye[a]);
+#pragma unroll
+      for (int a = 0; a < 10; ++a)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) ye[a][r] = cK * ye[a][r];
+    }
   }
   if (cMk != (T)0 || cMm != (T)0) {
     const T c = vol * (T)(1.0 / 420.0);
@@ -232,13 +242,13 @@ __device__ __forceinline__ void prefetch_tile(int64_t eb, int64_t epad, const in
 // one displacement component at a time (re-gathered from cache); (4) scatter.
 // FP32 variants are held to two resident blocks per SM (128 registers): the gathers and
 // the tangent loads of more warps in flight outweigh the few spilled registers.
-template <typename T, typename TD, int VS, bool HAS_XM, bool ATOMIC, bool DOT>
+template <typename T, typename TD, int VS, bool HAS_XM, bool ATOMIC, bool DOT, bool OUTK = false>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
     k_ebe(int64_t e0, int64_t e1, const int32_t *__restrict__ ids, const int32_t *__restrict__ conn,
           const T *__restrict__ geom, const int32_t *__restrict__ mat, const TD *__restrict__ D, int64_t epad,
           const OpCoef *__restrict__ op, const typename VecOf<T>::type *__restrict__ xm,
           const typename VecOf<T>::type *__restrict__ xk, typename VecOf<T>::type *y, double *dot,
-          const int32_t *skip, const Seg *seg, int prefetch) {
+          const int32_t *skip, const Seg *seg, int prefetch, typename VecOf<T>::type *yk) {
   int64_t i, end;
   if (seg) {  // members: this block's slice of one member's elements, that member's skip flag
     const Seg sg = seg[blockIdx.x];
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
     T g[4][3], vol;
     load_grads(geom, epad, e, g, vol);
     const auto dl = [&](int k) { return dload(D, epad, e, k); };
-    mydot = (double)ebe_element<T, VS, HAS_XM, ATOMIC, DOT>(nd, mt, g, vol, dl, op, xm, xk, y);
+    mydot = (double)ebe_element<T, VS, HAS_XM, ATOMIC, DOT, decltype(dl), OUTK>(nd, mt, g, vol, dl, op, xm, xk, y, yk);
   }
   if (DOT) {
     double s = block_sum(mydot);
@@ -389,12 +399,25 @@ template <typename T, typename TD, int VS, bool HAS_XM>
 static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, const OpCoef *op,
                                 const typename VecOf<T>::type *xm, const typename VecOf<T>::type *xk,
                                 typename VecOf<T>::type *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic,
-                                double *dot, const int32_t *skip, cudaStream_t s, const SegList &sg) {
+                                double *dot, const int32_t *skip, cudaStream_t s, const SegList &sg,
+                                typename VecOf<T>::type *yk = nullptr) {
   if (!sg.seg && e1 <= e0) return cudaSuccess;
   const unsigned nb = sg.seg ? (unsigned)sg.n : (unsigned)((e1 - e0 + kBlock - 1) / kBlock);
+  if constexpr (!HAS_XM && VS == 3) {  // the outer CG's applications that also return K x
+    if (yk && dot) {
+      if (atomic)
+        k_ebe<T, TD, VS, HAS_XM, true, true, true><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad,
+                                                                       op, xm, xk, y, dot, skip, sg.seg, m.prefetch, yk);
+      else
+        k_ebe<T, TD, VS, HAS_XM, false, true, true><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad,
+                                                                        op, xm, xk, y, dot, skip, sg.seg, m.prefetch,
+                                                                        yk);
+      return cudaGetLastError();
+    }
+  }
 #define NS_EBE_LAUNCH(A, DT)                                                                                  \
   k_ebe<T, TD, VS, HAS_XM, A, DT><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, \
-                                                     dot, skip, sg.seg, m.prefetch)
+                                                     dot, skip, sg.seg, m.prefetch, nullptr)
   if (atomic) {
     if (dot)
       NS_EBE_LAUNCH(true, true);
@@ -412,16 +435,17 @@ static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, co
 
 cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
-                         const int32_t *skip, cudaStream_t s, SegList sg, const void *D2) {
+                         const int32_t *skip, cudaStream_t s, SegList sg, const void *D2, double *yk) {
   if (D2 && m.geom2) {  // FP64-accurate operator in double-float arithmetic
     const dd *Dp = static_cast<const dd *>(D2);
     if (xm) return ebe_dispatch<dd, dd, 3, true>(m, Dp, m.geom2, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s, sg);
-    return ebe_dispatch<dd, dd, 3, false>(m, Dp, m.geom2, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s, sg);
+    return ebe_dispatch<dd, dd, 3, false>(m, Dp, m.geom2, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s, sg,
+                                          yk);
   }
   if (xm)
     return ebe_dispatch<double, double, 3, true>(m, D, m.geom, op, xm, xk, y, ids, e0, e1, atomic, dot, skip, s, sg);
   return ebe_dispatch<double, double, 3, false>(m, D, m.geom, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s,
-                                                sg);
+                                                sg, yk);
 }
 
 template <typename TD>

@@ -262,10 +262,10 @@ __global__ void __launch_bounds__(kBlock) k_fcg_gamma(const float4 *__restrict__
   if (threadIdx.x == 0) part[blockIdx.x] = g;
 }
 
-// p = z + beta p; partial p . r; Ap = 0
+// p = z + beta p; partial p . r; Ap = 0 (and Kp = 0 when the solve also accumulates K du)
 __global__ void __launch_bounds__(kBlock) k_fcg_p(double *p, const double *__restrict__ z,
-                                                  const double *__restrict__ r, double *Ap, int64_t n3, double *part,
-                                                  const CgScalars *so, const Seg *seg) {
+                                                  const double *__restrict__ r, double *Ap, double *Kp, int64_t n3,
+                                                  double *part, const CgScalars *so, const Seg *seg) {
   const VRange R = vrange(seg, n3, 3);
   if (so[R.m].done) return;
   const double beta = so[R.m].beta;
@@ -275,14 +275,17 @@ __global__ void __launch_bounds__(kBlock) k_fcg_p(double *p, const double *__res
     p[i] = pi;
     a += pi * r[i];
     Ap[i] = 0.0;
+    if (Kp) Kp[i] = 0.0;
   }
   a = block_sum(a);
   if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
-// x += alpha p; r -= alpha A p; partial r . r
+// x += alpha p; r -= alpha A p; partial r . r.  With q: q += alpha K p, so that q gains
+// K x over the solve when x starts from zero (x = sum alpha_k p_k).
 __global__ void __launch_bounds__(kBlock) k_fcg_update(double *x, double *r, const double *__restrict__ p,
-                                                       const double *__restrict__ Ap, int64_t n3, double *part,
+                                                       const double *__restrict__ Ap, double *q,
+                                                       const double *__restrict__ Kp, int64_t n3, double *part,
                                                        const CgScalars *so, const Seg *seg) {
   const VRange R = vrange(seg, n3, 3);
   if (so[R.m].done) return;
@@ -290,6 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(double *x, double *r, con
   double a = 0.0;
   for (int64_t i = R.i; i < R.end; i += R.step) {
     x[i] += alpha * p[i];
+    if (q) q[i] += alpha * Kp[i];
     const double ri = r[i] - alpha * Ap[i];
     r[i] = ri;
     a += ri * ri;
@@ -325,14 +329,14 @@ cudaError_t launch_fcg_gamma(const float *xin, double *z, const double *Ap, int6
   k_fcg_gamma<<<vgrid(N, sg), kBlock, 0, s>>>(reinterpret_cast<const float4 *>(xin), z, Ap, N, part, so, sg.seg);
   return cudaGetLastError();
 }
-cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, int64_t N, double *part,
-                         const CgScalars *so, cudaStream_t s, SegList sg) {
-  k_fcg_p<<<vgrid(N, sg), kBlock, 0, s>>>(p, z, r, Ap, 3 * N, part, so, sg.seg);
+cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, double *Kp, int64_t N,
+                         double *part, const CgScalars *so, cudaStream_t s, SegList sg) {
+  k_fcg_p<<<vgrid(N, sg), kBlock, 0, s>>>(p, z, r, Ap, Kp, 3 * N, part, so, sg.seg);
   return cudaGetLastError();
 }
-cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, int64_t N, double *part,
-                              const CgScalars *so, cudaStream_t s, SegList sg) {
-  k_fcg_update<<<vgrid(N, sg), kBlock, 0, s>>>(x, r, p, Ap, 3 * N, part, so, sg.seg);
+cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, double *q, const double *Kp,
+                              int64_t N, double *part, const CgScalars *so, cudaStream_t s, SegList sg) {
+  k_fcg_update<<<vgrid(N, sg), kBlock, 0, s>>>(x, r, p, Ap, q, Kp, 3 * N, part, so, sg.seg);
   return cudaGetLastError();
 }
 

@@ -107,7 +107,9 @@ cudaError_t launch_face_geometry(const DevMesh &m, const double *xyz, cudaStream
 // runs in double-float arithmetic on the FP32 pipes (relative accuracy ~1e-13).
 cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, const double *xm, const double *xk,
                          double *y, const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot,
-                         const int32_t *skip, cudaStream_t s, SegList sg = {}, const void *D2 = nullptr);
+                         const int32_t *skip, cudaStream_t s, SegList sg = {}, const void *D2 = nullptr,
+                         double *yk = nullptr);
+// (with dot and yk set: the stiffness part K x, without its coefficient, also goes to yk)
 // dst[i] = src[i] as a float pair (n values)
 cudaError_t launch_to_pairs(const double *src, void *dst, int64_t n, cudaStream_t s);
 // staged: whole-mesh atomic launches stage each tile of elements in shared memory with
@@ -181,13 +183,14 @@ cudaError_t launch_fcg_init(const double *b, const double *Ap, double *r, int64_
                             SegList sg = {});
 cudaError_t launch_fcg_gamma(const float *xin, double *z, const double *Ap, int64_t N, double *part,
                              const CgScalars *so, cudaStream_t s, SegList sg = {});
-cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, int64_t N, double *part,
-                         const CgScalars *so, cudaStream_t s, SegList sg = {});
+cudaError_t launch_fcg_p(double *p, const double *z, const double *r, double *Ap, double *Kp, int64_t N,
+                         double *part, const CgScalars *so, cudaStream_t s, SegList sg = {});
 // alpha = (p.r)/(p.Ap): pr holds vector partials (member m: pmr), pap operator partials (pma)
 cudaError_t launch_fcg_alpha(const double *pr, int npr, const double *pap, int npap, CgScalars *sc, cudaStream_t s,
                              int M = 1, PartMap pmr = {}, PartMap pma = {});
-cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, int64_t N, double *part,
-                              const CgScalars *so, cudaStream_t s, SegList sg = {});
+// (q, Kp non-null: q += alpha Kp as well -- K du accumulated during a solve from zero)
+cudaError_t launch_fcg_update(double *x, double *r, const double *p, const double *Ap, double *q, const double *Kp,
+                              int64_t N, double *part, const CgScalars *so, cudaStream_t s, SegList sg = {});
 cudaError_t launch_in_init(const double *r, const CgScalars *so, const float *J, float *rin, float *zin, float *pin,
                            float *xin, float *Apin, int64_t N, double *part, cudaStream_t s, SegList sg = {});
 cudaError_t launch_in_update(float *xin, float *rin, float *zin, const float *pin, const float *Apin, const float *J,

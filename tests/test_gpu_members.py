@@ -28,18 +28,21 @@ def ensemble(M=3, nt=200):
     return synth.ensemble_members(M=M, nt=nt, dims=(3, 2, 12), n_springs=10)
 
 
-@pytest.mark.parametrize("precision", [B.NS_PREC_FP64, B.NS_PREC_FP64_IR, B.NS_PREC_FP64_IR16])
-def test_members_match_their_runs_alone(precision):
+@pytest.mark.parametrize("precision,x0_prev", [(B.NS_PREC_FP64, 1), (B.NS_PREC_FP64_IR, 1), (B.NS_PREC_FP64_IR16, 1),
+                                              (B.NS_PREC_FP64, 0), (B.NS_PREC_FP64_IR, 0)])
+def test_members_match_their_runs_alone(precision, x0_prev):
     ens = ensemble()
     nsteps = 30
-    with B.BatchSimulation(ens, surface_ring_steps=nsteps, precision=precision, cg_tol=1e-12) as bs:
+    with B.BatchSimulation(ens, surface_ring_steps=nsteps, precision=precision, cg_tol=1e-12,
+                           x0_prev=x0_prev) as bs:
         bs.advance(nsteps)
         got = [bs.member_surface(m, 1, nsteps) for m in range(bs.M)]
         its = bs.member_iters()
         th_all, _ = bs.state()
     E = ens.mesh.n_elems
     for m in range(len(ens.members)):
-        with B.Simulation(ens.member(m), surface_ring_steps=nsteps, precision=precision, cg_tol=1e-12) as sim:
+        with B.Simulation(ens.member(m), surface_ring_steps=nsteps, precision=precision, cg_tol=1e-12,
+                          x0_prev=x0_prev) as sim:
             sim.advance(nsteps)
             alone = sim.surface(1, nsteps)
             th, _ = sim.state()
