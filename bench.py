@@ -259,6 +259,10 @@ def main():
     ap.add_argument("--stage", type=int, default=0, choices=[0, 1],
                     help="FP32 inner operator: stage element tiles in shared memory with bulk copies (1) or "
                          "per-thread loads (0)")
+    ap.add_argument("--spring-tile", type=int, default=0,
+                    help="spring kernel points per block before (or without) the autotuner; 0: heuristic")
+    ap.add_argument("--spring-blocks", type=int, default=1, choices=[1, 4],
+                    help="spring kernel register budget (resident blocks per SM) before (or without) the autotuner")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the library's autotuner (spring-kernel block shape) after the warm-up steps")
     ap.add_argument("--prefetch", type=int, default=1, choices=[0, 1],
@@ -268,9 +272,12 @@ def main():
     ap.add_argument("--x0", default="zero", choices=["prev", "zero"],
                     help="CG start: zero (default: no operator application for the initial residual) or the "
                          "previous step's increment")
-    ap.add_argument("--inner-tol", type=float, default=1e-3,
+    ap.add_argument("--numbering", default="grid", choices=["grid", "morton", "shuffled"],
+                    help="element and node numbering of the mesh: the generator's lexicographic grid order, "
+                         "Morton order of centroids, or a seeded shuffle (gather-locality worst case)")
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
                     help="relative residual at which the FP32 inner CG stops early")
-    ap.add_argument("--inner-iters", type=int, default=30,
+    ap.add_argument("--inner-iters", type=int, default=45,
                     help="FP32 inner CG iterations per outer iteration of the flexible solver")
     ap.add_argument("--requests", type=int, default=12, help="requests of the served trace")
     ap.add_argument("--step-scale", type=float, default=0.01,
@@ -328,6 +335,12 @@ def main():
         wl.name = "cut of the single large model: %dx%dx%d hexahedra at 5 m, 150 springs" % tuple(args.dims)
     else:
         wl = synth.large_single_model()
+    if args.numbering != "grid":
+        if ens is not None:
+            ens.mesh = synth.renumber(ens.mesh, args.numbering, seed=9)
+            wl.mesh = ens.mesh
+        else:
+            wl.mesh = synth.renumber(wl.mesh, args.numbering, seed=9)
     M = len(ens.members) if ens else 1
     E = wl.mesh.n_elems * M
     if ens is None:
@@ -337,10 +350,13 @@ def main():
     graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
               stage_elements=args.stage, inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, x0_prev=int(args.x0 == "prev"),
-              pair_operator=args.pair_op, l2_prefetch=args.prefetch)
+              pair_operator=args.pair_op, l2_prefetch=args.prefetch, spring_tile_points=args.spring_tile,
+              spring_tile_blocks=args.spring_blocks)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
     tuning = B.ns_autotune(sim.ctx) if args.autotune else None
+    if tuning:  # later contexts of this run (the streamed-state legs) start from the tuned shape
+        args.spring_tile, args.spring_blocks = tuning["chosen_tile_points"], tuning["chosen_tile_blocks"]
     B.ns_reset_stats(sim.ctx)
     st0 = sim.stats()
 
@@ -426,7 +442,8 @@ def main():
             sim = B.Simulation(wl, device=local, timing=1, device_state_budget=budget, chunk_elems=100000,
                                ring_depth=ring, precision=prec, graphs=graphs, stage_elements=args.stage,
                                inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, stream_mode=mode, x0_prev=int(args.x0 == "prev"),
-                               pair_operator=args.pair_op, l2_prefetch=args.prefetch)
+                               pair_operator=args.pair_op, l2_prefetch=args.prefetch,
+                               spring_tile_points=args.spring_tile, spring_tile_blocks=args.spring_blocks)
             sim.advance(1)
             B.ns_reset_stats(sim.ctx)
             h0 = sim.stats()
@@ -466,7 +483,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": wl.name, "elements": E, "nodes": wl.mesh.n_nodes * M, "members": M,
                            "springs_per_point": wl.n_springs, "dt": wl.dt, "cg_tol": 1e-8,
-                           "state": "resident in HBM", "l2": l2_note,
+                           "numbering": args.numbering, "state": "resident in HBM", "l2": l2_note,
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,

@@ -75,8 +75,9 @@ typedef struct {
   int64_t surface_ring_steps;  /* steps of surface response kept on the device */
   int32_t device;              /* CUDA device ordinal */
   int32_t timing;              /* 1: time kernels with CUDA events (ns_get_stats) */
-  int32_t inner_max_iter;      /* NS_PREC_FP64_IR: inner FP32 CG iterations per preconditioner call */
-  double inner_tol;            /* NS_PREC_FP64_IR: inner relative residual target */
+  int32_t inner_max_iter;      /* NS_PREC_FP64_IR*: at most this many inner FP32 CG iterations per
+                                  preconditioner call (default 45) */
+  double inner_tol;            /* NS_PREC_FP64_IR*: inner relative residual target (default 1e-4) */
   double wait_timeout_s;       /* bound on each host wait for the device */
   int32_t graphs;              /* 1: each outer iteration of the flexible solver (inner FP32 solve
                                   included) and each batch of plain CG iterations is captured once
@@ -94,6 +95,11 @@ typedef struct {
                                   copied through device buffers, Alg. 3) or NS_STREAM_ZERO_COPY
                                   (the spring kernel reads and writes the pinned host arrays in
                                   place over the host link) */
+  int32_t spring_tile_points;  /* spring kernel launch shape: integration points per block (a
+                                  multiple of 4 whose float pairs fit 200 KB of shared memory);
+                                  0 (default): a size heuristic until ns_autotune picks */
+  int32_t spring_tile_blocks;  /* its register budget: 1 (default; 0 reads as 1) or 4 resident
+                                  blocks per SM */
 } ns_config;
 
 #define NS_STREAM_RING 0
@@ -248,10 +254,13 @@ int ns_reset_stats(ns_ctx *ctx);
 
 /* Result of ns_autotune: the candidates it timed and what it chose. */
 typedef struct {
-  int32_t n_tile;                 /* spring-kernel block shapes tried */
-  int32_t tile_points[8];         /* integration points per block of each */
-  float tile_ms[8];               /* spring kernel time of each on the sample (ms) */
+  int32_t n_tile;                 /* spring-kernel launch shapes tried */
+  int32_t tile_points[16];        /* integration points per block of each */
+  int32_t tile_blocks[16];        /* its register budget: resident blocks per SM it was compiled
+                                     for (1: the compiler's choice, 4: 64 registers a thread) */
+  float tile_ms[16];              /* spring kernel time of each on the sample (ms) */
   int32_t chosen_tile_points;
+  int32_t chosen_tile_blocks;
   int32_t n_chunk;                /* streamed-state chunk sizes tried (0: no streamed state) */
   int64_t chunk_elems[6];
   float chunk_gbps[6];            /* H2D + D2H bytes per second of each over the ring */
@@ -259,7 +268,8 @@ typedef struct {
 } ns_tuning;
 
 /* Autotuner (a tool of this library; the paper tunes nothing at run time): times the
- * spring kernel's block shape (integration points per block) on a sample of up to 32,768
+ * spring kernel's launch shape (integration points per block, and one of two register
+ * budgets it is compiled with) on a sample of up to 32,768
  * resident elements -- a copy of their spring state, the last step's strains -- and the
  * streamed state's chunk size (a copy round trip through the ring buffers, which leaves
  * the host state as it was), and keeps the fastest of each for the following steps.

@@ -40,7 +40,8 @@ class ns_config(C.Structure):
                 ("rayleigh_f2", C.c_double), ("surface_ring_steps", C.c_int64), ("device", C.c_int32),
                 ("timing", C.c_int32), ("inner_max_iter", C.c_int32), ("inner_tol", C.c_double),
                 ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32),
-                ("l2_prefetch", C.c_int32), ("pair_operator", C.c_int32), ("stream_mode", C.c_int32)]
+                ("l2_prefetch", C.c_int32), ("pair_operator", C.c_int32), ("stream_mode", C.c_int32),
+                ("spring_tile_points", C.c_int32), ("spring_tile_blocks", C.c_int32)]
 
 
 class ns_material(C.Structure):
@@ -64,13 +65,15 @@ class ns_stats(C.Structure):
 
 
 class ns_tuning(C.Structure):
-    _fields_ = [("n_tile", C.c_int32), ("tile_points", C.c_int32 * 8), ("tile_ms", C.c_float * 8),
-                ("chosen_tile_points", C.c_int32), ("n_chunk", C.c_int32), ("chunk_elems", C.c_int64 * 6),
-                ("chunk_gbps", C.c_float * 6), ("chosen_chunk_elems", C.c_int64)]
+    _fields_ = [("n_tile", C.c_int32), ("tile_points", C.c_int32 * 16), ("tile_blocks", C.c_int32 * 16),
+                ("tile_ms", C.c_float * 16), ("chosen_tile_points", C.c_int32), ("chosen_tile_blocks", C.c_int32),
+                ("n_chunk", C.c_int32), ("chunk_elems", C.c_int64 * 6), ("chunk_gbps", C.c_float * 6),
+                ("chosen_chunk_elems", C.c_int64)]
 
     def as_dict(self):
-        return {"tile_points": list(self.tile_points[:self.n_tile]), "tile_ms": list(self.tile_ms[:self.n_tile]),
-                "chosen_tile_points": self.chosen_tile_points,
+        return {"tile_points": list(self.tile_points[:self.n_tile]), "tile_blocks": list(self.tile_blocks[:self.n_tile]),
+                "tile_ms": list(self.tile_ms[:self.n_tile]),
+                "chosen_tile_points": self.chosen_tile_points, "chosen_tile_blocks": self.chosen_tile_blocks,
                 "chunk_elems": list(self.chunk_elems[:self.n_chunk]), "chunk_gbps": list(self.chunk_gbps[:self.n_chunk]),
                 "chosen_chunk_elems": self.chosen_chunk_elems}
 

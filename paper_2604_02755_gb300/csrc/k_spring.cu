@@ -268,12 +268,17 @@ __device__ __forceinline__ double ro_solve_pair(float gah, float gal, float gues
 // skeleton tau = F(gamma) (decided before the root solve, so each spring solves once).
 // With no increment the state is kept and only the tangent is evaluated.
 // Returns the tangent dtau/dgamma at the end state as a float pair.
-// The spring strain gamma = gh + gl and its increment dgamma = dh + dl come as normalised
-// float pairs (the dot products q_k . eps in double-float arithmetic); the stored state
-// stays FP64, and comparisons with it are made on pair differences.
-__device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float dh, float dl, const MatConst &p,
-                                                     const PowTab &tb, const float *__restrict__ tabf, double &tau,
-                                                     double &gR, double &tR, double &gmax, int &dir, int &mode) {
+// The spring strain gamma = gh + gl comes as a normalised float pair (the dot product
+// q_k . eps in double-float arithmetic); the stored state stays FP64, and comparisons
+// with it are made on pair differences.  Of the increment dgamma only the sign is needed
+// unless the spring reverses: dh carries that sign (and is exactly zero for no
+// increment); when !dexact the pair dh + dl = q_k . deps is formed at a reversal.
+__device__ __forceinline__ void pair_dot6(const float2 *__restrict__ q, const float2 *e, float &sh, float &sl);
+__device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float dh, float dl, bool dexact,
+                                                     const float2 *__restrict__ qk, const float2 *de,
+                                                     const MatConst &p, const PowTab &tb,
+                                                     const float *__restrict__ tabf, double &tau, double &gR,
+                                                     double &tR, double &gmax, int &dir, int &mode) {
   float2 G;
   if (dh == 0.0f) {  // no increment: only the tangent at the current state
     const double x = (mode == 0) ? tau : 0.5 * (tau - tR);
@@ -287,6 +292,7 @@ __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float d
     mode = 0;
     same = false;
   } else if (sgn != dir) {  // reversal: (gamma - dgamma, tau) becomes the branch origin
+    if (!dexact) pair_dot6(qk, de, dh, dl);
     float rh, rl;
     pair_add(gh, gl, -dh, -dl, rh, rl);
     gR = (double)rh + (double)rl;
@@ -331,6 +337,23 @@ __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float d
   return G;
 }
 
+// Sign of q_k . e from an FP32 dot of the pairs' high parts.  Its error is below
+// 2^-20.9 sum |q_i e_i| (six fused steps, plus the dropped low parts, each under 2^-24 of
+// its high part), so beyond 2^-18 of that sum the sign is certain and equals that of the
+// pair dot product; a zero sum means every product, hence the dot, is exactly zero.
+// Returns false when the sign is not settled (the caller forms the pair dot).
+__device__ __forceinline__ bool dot6_sign(const float2 *__restrict__ q, const float2 *e, float &s) {
+  float a = 0.0f, b = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float qh = __ldg(&q[i].x), eh = e[i].x;
+    a = fmaf(qh, eh, a);
+    b = fmaf(fabsf(qh), fabsf(eh), b);
+  }
+  s = a;
+  return b == 0.0f || fabsf(a) > 0x1p-18f * b;
+}
+
 // gamma = q_k . e for a float-pair direction q (6) and a float-pair strain e (6), as a
 // normalised pair: exact products (FMA error terms) and compensated sums.
 __device__ __forceinline__ void pair_dot6(const float2 *__restrict__ q, const float2 *e, float &sh, float &sl) {
@@ -351,7 +374,11 @@ __device__ __forceinline__ void pair_dot6(const float2 *__restrict__ q, const fl
 // Block = a tile of TP consecutive points (TP multiple of 4) with all their S springs.
 // Phase 1: each thread updates springs of the tile (coalesced state access), stores
 // G_k in shared memory.  Phase 2: D_p[ij] = Kb [i,j < 3] + sum_k G_k T_k[ij].
-__global__ void __launch_bounds__(kBlock) k_springs(const float2 *__restrict__ q2, const float2 *__restrict__ T2, int S,
+// MINB: resident blocks per SM the registers are budgeted for (1: the compiler's choice,
+// 80 registers, three blocks; 4: 64 registers with a few bytes spilled, a third more
+// warps to hide the root solve's latencies) -- the autotuner picks.
+template <int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restrict__ q2, const float2 *__restrict__ T2, int S,
                                                     int TP, const MatConst *__restrict__ mc,
                                                     const int32_t *__restrict__ mat_e, const int32_t *__restrict__ mat_p,
                                                     const double *__restrict__ eps, double *tau_a, double *gR_a,
@@ -378,13 +405,15 @@ __global__ void __launch_bounds__(kBlock) k_springs(const float2 *__restrict__ q
     const int64_t p = pt + lp;
     const int mt = mat_p ? mat_p[p] : mat_e[p >> 2];
     const MatConst &rp = mc[mt];
-    float gh, gl, dh, dl;
+    float gh, gl, dh, dl = 0.0f;
     pair_dot6(q2 + 6 * k, Es + 12 * lp, gh, gl);
-    pair_dot6(q2 + 6 * k, Es + 12 * lp + 6, dh, dl);
+    const bool sure = dot6_sign(q2 + 6 * k, Es + 12 * lp + 6, dh);
+    if (!sure) pair_dot6(q2 + 6 * k, Es + 12 * lp + 6, dh, dl);
     const int64_t si = (p - base) * S + k;
     double tau = tau_a[si], gR = gR_a[si], tR = tR_a[si], gmax = gmax_a[si];
     int dir = dir_a[si], mode = mode_a[si];
-    const float2 G = spring_update_pair(gh, gl, dh, dl, rp, tb, ptabf, tau, gR, tR, gmax, dir, mode);
+    const float2 G = spring_update_pair(gh, gl, dh, dl, !sure, q2 + 6 * k, Es + 12 * lp + 6, rp, tb, ptabf, tau, gR,
+                                        tR, gmax, dir, mode);
     if (dh != 0.0f) {
       tau_a[si] = tau;
       gR_a[si] = gR;
@@ -433,7 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_springs(const float2 *__restrict__ q
     }
     const double acc = (nn ? mc[mt].Kb : 0.0) + (((double)sh0 + (double)sh1) + ((double)sl0 + (double)sl1));
     if (dpts)
-      dpts[21 * p + ij] = acc;
+      dpts[21 * (p - p0) + ij] = acc;
     else
       D[((p & 3) * 21 + ij) * epad + (p >> 2)] = acc;
   }
@@ -462,12 +491,19 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_done.load() & bit)) {
-    cudaFuncSetAttribute(k_springs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_springs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_springs<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_done.fetch_or(bit);
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
-  k_springs<<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, st.gR,
-                                     st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow, tab.powf);
+  if (tab.minb == 4)
+    k_springs<4><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau,
+                                          st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow,
+                                          tab.powf);
+  else
+    k_springs<1><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau,
+                                          st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow,
+                                          tab.powf);
   return cudaGetLastError();
 }
 

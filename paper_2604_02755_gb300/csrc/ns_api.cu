@@ -870,14 +870,16 @@ void ns_config_default(ns_config *cfg) {
   cfg->surface_ring_steps = 64;
   cfg->device = 0;
   cfg->timing = 0;
-  cfg->inner_max_iter = 30;
-  cfg->inner_tol = 1e-3;
+  cfg->inner_max_iter = 45;
+  cfg->inner_tol = 1e-4;
   cfg->wait_timeout_s = 120.0;
   cfg->graphs = 1;
   cfg->stage_elements = 0;
   cfg->stream_mode = NS_STREAM_RING;
   cfg->pair_operator = 0;
   cfg->l2_prefetch = 1;
+  cfg->spring_tile_points = 0;
+  cfg->spring_tile_blocks = 1;
 }
 
 static thread_local std::string g_create_err;
@@ -899,7 +901,9 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
        cfg->precision != NS_PREC_FP64_IR16) ||
       (cfg->scatter != NS_SCATTER_ATOMIC && cfg->scatter != NS_SCATTER_COLOUR) || !(cfg->wait_timeout_s > 0) ||
       cfg->inner_max_iter < 1 || !(cfg->inner_tol > 0) ||
-      (cfg->stream_mode != NS_STREAM_RING && cfg->stream_mode != NS_STREAM_ZERO_COPY)) {
+      (cfg->stream_mode != NS_STREAM_RING && cfg->stream_mode != NS_STREAM_ZERO_COPY) ||
+      (cfg->spring_tile_points != 0 && !spring_tile_ok(cfg->spring_tile_points, cfg->n_springs)) ||
+      (cfg->spring_tile_blocks != 0 && cfg->spring_tile_blocks != 1 && cfg->spring_tile_blocks != 4)) {
     g_create_err = "invalid configuration value";
     return NS_ERR_INVALID_ARG;
   }
@@ -1093,6 +1097,8 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   c->tab.T2 = c->T2_d;
   c->tab.q2 = c->q2_d;
   c->tab.S = S;
+  c->tab.tp = c->cfg.spring_tile_points;
+  c->tab.minb = c->cfg.spring_tile_blocks == 4 ? 4 : 1;
   // tangent D (element SoA [84][epad]) and spring state placement
   const int64_t E = c->m.E, epad = c->m.epad;
   if ((rc = dalloc(c, &c->D, 84 * (size_t)epad))) return rc;
@@ -1666,8 +1672,11 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
     CKC(c, cudaEventElapsedTime(ms, e0, e1));
     return NS_OK;
   };
-  // 1. spring kernel block shape on a copy of the first resident elements' state
+  // 1. spring kernel block shape on a copy of the state of 32,768 resident elements taken
+  //    as eight slices spread over the model (its layers load the springs differently)
   const int64_t ne = std::min<int64_t>(c->E_res, 32768);
+  const int nsl = ne == 32768 ? 8 : 1;
+  const int64_t nes = ne / nsl;
   if (ne > 0) {
     const int64_t np = 4 * ne, nspr = np * S;
     SpringSoA scr;
@@ -1675,34 +1684,47 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
     if ((rc = alloc_soa(c, scr, nspr, false)) == NS_OK && (rc = dalloc(c, &dpts, 21 * (size_t)np)) == NS_OK) {
       const int cands[8] = {4, 8, 16, 32, 64, 128, 256, 512};
       float best = 1e30f;
-      int chosen = spring_tile_default(S);
-      for (int k = 0; k < 8 && rc == NS_OK; ++k) {
+      int chosen = spring_tile_default(S), chosen_b = 1;
+      for (int kk = 0; kk < 16 && rc == NS_OK; ++kk) {
+        const int k = kk % 8, minb = kk < 8 ? 1 : 4;
         if (!spring_tile_ok(cands[k], S)) continue;
         SpringTables tb = c->tab;
         tb.tp = cands[k];
+        tb.minb = minb;
         float ms_best = 1e30f;
+        auto slice0 = [&](int j) { return nsl == 1 ? (int64_t)0 : j * ((c->E_res - nes) / (nsl - 1)); };
         for (int rep = 0; rep < 3 && rc == NS_OK; ++rep) {
-          if ((rc = copy_soa(c, scr, 0, c->st, 0, nspr, cudaMemcpyDeviceToDevice, c->s_main)) != NS_OK) break;
+          for (int j = 0; j < nsl && rc == NS_OK; ++j)
+            rc = copy_soa(c, scr, j * nes * 4 * S, c->st, slice0(j) * 4 * S, nes * 4 * S, cudaMemcpyDeviceToDevice,
+                          c->s_main);
+          if (rc != NS_OK) break;
           float ms = 0.0f;
           rc = timed(c->s_main, [&]() -> int {
-            LAUNCH(c, launch_springs(tb, c->mats_d, c->m.mat, nullptr, c->eps, scr, 0, 0, np, nullptr, c->m.epad,
-                                     dpts, c->s_main));
+            for (int j = 0; j < nsl; ++j) {  // scratch state of slice j at scr[j * nes * 4 * S]
+              const int64_t e0 = slice0(j);
+              LAUNCH(c, launch_springs(tb, c->mats_d, c->m.mat, nullptr, c->eps, scr, 4 * (e0 - j * nes), 4 * e0,
+                                       4 * (e0 + nes), nullptr, c->m.epad, dpts, c->s_main));
+            }
             return NS_OK;
           }, &ms);
           ms_best = std::min(ms_best, ms);
         }
         if (rc != NS_OK) break;
         out->tile_points[out->n_tile] = cands[k];
+        out->tile_blocks[out->n_tile] = minb;
         out->tile_ms[out->n_tile] = ms_best;
         out->n_tile++;
         if (ms_best < best) {
           best = ms_best;
           chosen = cands[k];
+          chosen_b = minb;
         }
       }
       if (rc == NS_OK) {
         c->tab.tp = chosen;
+        c->tab.minb = chosen_b;
         out->chosen_tile_points = chosen;
+        out->chosen_tile_blocks = chosen_b;
       }
     }
     free_soa(scr, false);

@@ -215,6 +215,7 @@ struct SpringTables {
   const float *powf;  // double-float power tables (df64.cuh, kPowFLen floats)
   int S;
   int tp = 0;         // integration points per block of the spring kernel (0: size heuristic)
+  int minb = 1;       // register budget of the spring kernel: 1 (compiler's choice) or 4 blocks per SM
 };
 // the spring kernel's default points per block for S springs, and whether tp is usable
 int spring_tile_default(int S);
@@ -222,7 +223,7 @@ bool spring_tile_ok(int tp, int S);
 constexpr int kPowTabLen = 452;
 // Spring update of points [p0, p1) (point p = elem*4 + qp), strains from eps [P][12];
 // state arrays indexed relative to `base` point; D written to D[(qp*21 + k) * epad + elem]
-// (element layout) or, if dpts != nullptr, to dpts[p][21] (free points).
+// (element layout) or, if dpts != nullptr, to dpts[p - p0][21] (free points).
 cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const int32_t *mat_of_elem,
                            const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
                            int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s);

@@ -250,6 +250,55 @@ def kuhn_box(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float, layer_d
     return m
 
 
+def _spread3(v: np.ndarray) -> np.ndarray:
+    """Spread the low 21 bits of v so that bit b lands on bit 3b (Morton interleave)."""
+    x = v.astype(np.uint64) & np.uint64(0x1FFFFF)
+    for shift, mask in ((32, 0x1F00000000FFFF), (16, 0x1F0000FF0000FF), (8, 0x100F00F00F00F00F),
+                        (4, 0x10C30C30C30C30C3), (2, 0x1249249249249249)):
+        x = (x | (x << np.uint64(shift))) & np.uint64(mask)
+    return x
+
+
+def morton_keys(p: np.ndarray) -> np.ndarray:
+    """Z-order keys of points p [n,3]: coordinates scaled to 21-bit integers over the
+    bounding box, bits interleaved x, y, z."""
+    lo, hi = p.min(axis=0), p.max(axis=0)
+    q = np.floor((p - lo) / np.maximum(hi - lo, 1e-300) * float((1 << 21) - 1)).astype(np.int64)
+    return _spread3(q[:, 0]) | (_spread3(q[:, 1]) << np.uint64(1)) | (_spread3(q[:, 2]) << np.uint64(2))
+
+
+def renumber(mesh: Mesh, how: str = "morton", seed: int = 0) -> Mesh:
+    """The same mesh with elements and nodes renumbered.
+
+    how: "grid" (unchanged: the generator's lexicographic order), "morton" (elements by
+    the Z-order key of their centroids, nodes by that of their positions) or "shuffled"
+    (seeded random permutations of both -- the worst case for the operator's gathers).
+    The surface node list keeps its order (so surface records line up), faces stay sorted
+    by their owning element."""
+    if how == "grid":
+        return mesh
+    E, N = mesh.n_elems, mesh.n_nodes
+    if how == "morton":
+        pe = np.argsort(morton_keys(mesh.xyz[mesh.conn[:, :4]].mean(axis=1)), kind="stable")
+        pn = np.argsort(morton_keys(mesh.xyz), kind="stable")
+    elif how == "shuffled":
+        pe = np.argsort(splitmix64(seed, E, stream=7), kind="stable")
+        pn = np.argsort(splitmix64(seed, N, stream=8), kind="stable")
+    else:
+        raise ValueError(f"unknown numbering {how!r}")
+    inv_e = np.empty(E, dtype=np.int64)
+    inv_e[pe] = np.arange(E)
+    inv_n = np.empty(N, dtype=np.int64)
+    inv_n[pn] = np.arange(N)
+    fe = inv_e[mesh.face_elem]
+    fo = np.argsort(fe, kind="stable")
+    return Mesh(xyz=np.ascontiguousarray(mesh.xyz[pn]), conn=np.ascontiguousarray(inv_n[mesh.conn[pe]].astype(np.int32)),
+                mat=np.ascontiguousarray(mesh.mat[pe]), faces=np.ascontiguousarray(inv_n[mesh.faces[fo]].astype(np.int32)),
+                face_elem=np.ascontiguousarray(fe[fo].astype(np.int32)), face_kind=np.ascontiguousarray(mesh.face_kind[fo]),
+                surf=inv_n[mesh.surf].astype(np.int32), dims=mesh.dims, size=mesh.size,
+                info=dict(mesh.info, numbering=how))
+
+
 # ----------------------------------------------------------------------------- input waves
 
 def band_limited_wave(seed: int, nt: int, dt: float, f_lo: float = 0.1, f_hi: float = 2.5,
