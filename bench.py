@@ -263,6 +263,8 @@ def main():
                     help="spring kernel points per block before (or without) the autotuner; 0: heuristic")
     ap.add_argument("--spring-blocks", type=int, default=1, choices=[1, 4],
                     help="spring kernel register budget (resident blocks per SM) before (or without) the autotuner")
+    ap.add_argument("--spring-tensor", type=int, default=0, choices=[0, 1],
+                    help="assemble the spring tangent on the tensor cores (1) or in double-float sums (0, default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the library's autotuner (spring-kernel block shape) after the warm-up steps")
     ap.add_argument("--prefetch", type=int, default=1, choices=[0, 1],
@@ -351,7 +353,7 @@ def main():
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
               stage_elements=args.stage, inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, x0_prev=int(args.x0 == "prev"),
               pair_operator=args.pair_op, l2_prefetch=args.prefetch, spring_tile_points=args.spring_tile,
-              spring_tile_blocks=args.spring_blocks)
+              spring_tile_blocks=args.spring_blocks, spring_tensor_cores=args.spring_tensor)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     sim.advance(args.warmup)
     tuning = B.ns_autotune(sim.ctx) if args.autotune else None
@@ -443,7 +445,8 @@ def main():
                                ring_depth=ring, precision=prec, graphs=graphs, stage_elements=args.stage,
                                inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, stream_mode=mode, x0_prev=int(args.x0 == "prev"),
                                pair_operator=args.pair_op, l2_prefetch=args.prefetch,
-                               spring_tile_points=args.spring_tile, spring_tile_blocks=args.spring_blocks)
+                               spring_tile_points=args.spring_tile, spring_tile_blocks=args.spring_blocks,
+                               spring_tensor_cores=args.spring_tensor)
             sim.advance(1)
             B.ns_reset_stats(sim.ctx)
             h0 = sim.stats()
@@ -488,7 +491,7 @@ def main():
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
                 "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
-                "staged_operator": args.stage, "inner_iters": args.inner_iters, "inner_tol": args.inner_tol, "autotune": tuning,
+                "staged_operator": args.stage, "inner_iters": args.inner_iters, "inner_tol": args.inner_tol, "spring_tensor_cores": args.spring_tensor, "autotune": tuning,
                 "pair_operator": args.pair_op, "x0": args.x0, "l2_prefetch": args.prefetch,
                 "state_stream": stream}
         print(json.dumps(line), flush=True)

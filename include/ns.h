@@ -100,6 +100,11 @@ typedef struct {
                                   0 (default): a size heuristic until ns_autotune picks */
   int32_t spring_tile_blocks;  /* its register budget: 1 (default; 0 reads as 1) or 4 resident
                                   blocks per SM */
+  int32_t spring_tensor_cores; /* 1: the tangent D = K_b m m^T + sum_k G_k T_k is assembled on
+                                  the tensor cores (bf16 digit products, exact FP32 sums,
+                                  FP64-level result) when the block holds a multiple of 16 points
+                                  and S <= 256; 0 (default, measured faster on GB300):
+                                  double-float sums on the FP32 pipes */
 } ns_config;
 
 #define NS_STREAM_RING 0

@@ -41,7 +41,8 @@ class ns_config(C.Structure):
                 ("timing", C.c_int32), ("inner_max_iter", C.c_int32), ("inner_tol", C.c_double),
                 ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32),
                 ("l2_prefetch", C.c_int32), ("pair_operator", C.c_int32), ("stream_mode", C.c_int32),
-                ("spring_tile_points", C.c_int32), ("spring_tile_blocks", C.c_int32)]
+                ("spring_tile_points", C.c_int32), ("spring_tile_blocks", C.c_int32),
+                ("spring_tensor_cores", C.c_int32)]
 
 
 class ns_material(C.Structure):

@@ -371,13 +371,56 @@ __device__ __forceinline__ void pair_dot6(const float2 *__restrict__ q, const fl
   fast_two_sum(s, c, sh, sl);
 }
 
+// ------------------------------------------------------------------ tangent assembly on tensor cores
+// D_p[ij] = Kb [i,j < 3] + sum_k G_pk T_k[ij] is a dense (points x S) . (S x 21) product.
+// It runs on the tensor cores (warp-level bf16 MMA, FP32 accumulation) with FP64-level
+// accuracy by splitting both operands into 6-bit integer digits: G_pk 2^-eG =
+// sum_i a_i 2^-6(i+1) (a_i in 0..63, eG per material with 2^eG > G0 >= G),
+// T_k[ij] 2^-eT[ij] = sum_j b_j 2^-6(j+1) (|b_j| <= 63, one exponent per column ij).
+// Every digit is exact in bf16, every digit product exact in FP32, and the sum over k of
+// the products of one level L = i + j (at most 8 pairs x S x 63^2 < 2^23 for S <= 256) is
+// an integer that FP32 holds exactly, so the MMA accumulators C_L are exact;
+// D = Kb + 2^(eG + eT[ij] - 12) sum_{L <= 8} 2^-6L C_L, the levels combined in
+// double-float arithmetic.  The digits beyond the eighth and the levels above 8 leave an
+// error below 2^-47 of G0 sum_k |T_k[ij]|.
+constexpr int kDigits = 8;
+constexpr int kLevels = 9;  // digit-pair levels L = i + j kept: 0 .. 8
+constexpr int kTcMaxS = 256;
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+// c += a . b for one 16 x 8 x 16 tile: a row-major bf16 (4 registers), b column-major bf16
+// (2 registers), c FP32 (rows lane/4 and lane/4 + 8, columns 2 (lane % 4) + {0, 1})
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// bf16 bits of a small non-negative integer d (< 2^8): 2^23 + d as a float, minus 2^23
+__device__ __forceinline__ unsigned short bf16_of_digit(uint32_t d) {
+  return (unsigned short)(__float_as_uint(__uint_as_float(0x4B000000u | d) - 8388608.0f) >> 16);
+}
+
+// row stride (bf16 elements) of a digit plane: 16 * ks + 8, so that the eight rows one
+// ldmatrix reads fall in distinct shared-memory banks
+__host__ __device__ inline int tc_stride(int ks) { return 16 * ks + 8; }
+
 // Block = a tile of TP consecutive points (TP multiple of 4) with all their S springs.
 // Phase 1: each thread updates springs of the tile (coalesced state access), stores
 // G_k in shared memory.  Phase 2: D_p[ij] = Kb [i,j < 3] + sum_k G_k T_k[ij].
 // MINB: resident blocks per SM the registers are budgeted for (1: the compiler's choice,
 // 80 registers, three blocks; 4: 64 registers with a few bytes spilled, a third more
 // warps to hide the root solve's latencies) -- the autotuner picks.
-template <int MINB>
+// TC: phase 1 stores the tangents as digit planes and phase 2 assembles D on the tensor
+// cores (TP a multiple of 16, S <= 256; tfrag holds the digits of T in MMA fragment order).
+template <int MINB, bool TC>
 __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restrict__ q2, const float2 *__restrict__ T2, int S,
                                                     int TP, const MatConst *__restrict__ mc,
                                                     const int32_t *__restrict__ mat_e, const int32_t *__restrict__ mat_p,
@@ -385,19 +428,31 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
                                                     double *tR_a, double *gmax_a, int32_t *dir_a, int32_t *mode_a,
                                                     int64_t base, int64_t p0, int64_t p1, double *D, int64_t epad,
                                                     double *dpts, const double *__restrict__ ptab,
-                                                    const float *__restrict__ ptabf) {
-  extern __shared__ float2 Gs[];  // [TP][S] tangents, then [TP][12] strains as pairs
+                                                    const float *__restrict__ ptabf, const uint2 *__restrict__ tfrag,
+                                                    const double *__restrict__ tsc) {
+  // shared: [TP][S] tangents as float pairs (or, TC, [8][TP][stride] bf16 digit planes),
+  // then [TP][12] strains as pairs
+  extern __shared__ float2 Gs[];
+  const int KS = (S + 15) >> 4, KST = tc_stride(KS);
+  unsigned short *planes = reinterpret_cast<unsigned short *>(Gs);
   const PowTab tb{ptab, ptab + 128, ptab + 256, ptab + 384, __ldg(ptab + 448), __ldg(ptab + 449), __ldg(ptab + 450),
                   __ldg(ptab + 451)};
   const int64_t pt = p0 + (int64_t)blockIdx.x * TP;
   const int np = (int)((p1 - pt) < TP ? (p1 - pt) : TP);
   const int nspr = np * S;
   // phase 0: the tile's strains and increments as float pairs (once per point, not per spring)
-  float2 *Es = Gs + (size_t)TP * S;
+  float2 *Es = TC ? reinterpret_cast<float2 *>(planes + (size_t)kDigits * TP * KST) : Gs + (size_t)TP * S;
   for (int i = threadIdx.x; i < np * 12; i += blockDim.x) {
     float h, l;
     dsplit(eps[12 * pt + i], h, l);
     Es[i] = make_float2(h, l);
+  }
+  if (TC) {  // zero digits in the padded springs S .. 16 KS - 1 (every plane, every row)
+    const int pad = 16 * KS - S, nz = kDigits * TP * pad;
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) {
+      const int row = i / pad;
+      planes[(size_t)row * KST + S + (i - row * pad)] = 0;
+    }
   }
   __syncthreads();
   for (int g = threadIdx.x; g < nspr; g += blockDim.x) {
@@ -422,9 +477,76 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
       dir_a[si] = dir;
       mode_a[si] = mode;
     }
-    Gs[g] = G;  // the tangent as an unevaluated float pair for the double-float accumulation
+    if (TC) {
+      // G 2^(48 - eG) as a 48-bit integer from the pair, then its eight 6-bit digits
+      const float sc = rp.gfix;
+      long long X = (long long)__float2ull_rz(G.x * sc) + __float2ll_rn(G.y * sc);
+      X = X < 0 ? 0 : (X > 0xFFFFFFFFFFFFll ? 0xFFFFFFFFFFFFll : X);
+      const unsigned long long U = (unsigned long long)X;
+      unsigned short *dst = planes + (size_t)lp * KST + k;
+#pragma unroll
+      for (int i = 0; i < kDigits; ++i)
+        dst[(size_t)i * TP * KST] = bf16_of_digit((uint32_t)(U >> (42 - 6 * i)) & 63u);
+    } else {
+      Gs[g] = G;  // the tangent as an unevaluated float pair for the double-float accumulation
+    }
   }
   __syncthreads();
+  if (TC) {
+    // one warp per (16-point tile, 8-column tile) of D; level by level, deepest first, each
+    // level's digit-pair MMAs accumulated in two alternating sets, then folded into
+    // v = sum_L 2^-6L C_L by Horner's rule in double-float arithmetic
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntask = (TP >> 4) * 3;
+    for (int task = warp; task < ntask; task += kBlock >> 5) {
+      const int mt = task / 3, nt = task - mt * 3;
+      const uint32_t arow = (uint32_t)__cvta_generic_to_shared(
+          planes + (size_t)(mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * KST + (lane >> 4) * 8);
+      const uint2 *bt = tfrag + (size_t)nt * 32 + lane;
+      float vh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, vl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int L = kLevels - 1; L >= 0; --L) {
+        float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int i = L < kDigits ? 0 : L - kDigits + 1; i <= L && i < kDigits; ++i) {
+          const uint32_t ai = arow + (uint32_t)((size_t)i * TP * KST * 2);
+          const uint2 *bj = bt + (size_t)(L - i) * KS * 3 * 32;
+          int ks = 0;
+          for (; ks + 1 < KS; ks += 2) {
+            uint32_t a0[4], a1[4];
+            ldsm_x4(a0, ai + (uint32_t)(ks * 32));
+            ldsm_x4(a1, ai + (uint32_t)(ks * 32 + 32));
+            mma_bf16(c0, a0, __ldg(bj + (size_t)ks * 96));
+            mma_bf16(c1, a1, __ldg(bj + (size_t)(ks + 1) * 96));
+          }
+          if (ks < KS) {
+            uint32_t a0[4];
+            ldsm_x4(a0, ai + (uint32_t)(ks * 32));
+            mma_bf16(c0, a0, __ldg(bj + (size_t)ks * 96));
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {  // c0 + c1 is exact (an integer below 2^23)
+          float s, e;
+          two_sum(c0[r] + c1[r], vh[r] * 0.015625f, s, e);
+          two_sum(s, e + vl[r] * 0.015625f, vh[r], vl[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int lp = mt * 16 + (lane >> 2) + (r >> 1) * 8, ij = nt * 8 + 2 * (lane & 3) + (r & 1);
+        if (lp < np && ij < 21) {
+          const int64_t p = pt + lp;
+          const MatConst &m = mc[mat_p ? mat_p[p] : mat_e[p >> 2]];
+          const bool nn = ij < 3 || ij == 6 || ij == 7 || ij == 11;  // (i,j) both < 3
+          const double val = (nn ? m.Kb : 0.0) + m.dsc * (__ldg(tsc + ij) * ((double)vh[r] + (double)vl[r]));
+          if (dpts)
+            dpts[21 * (p - p0) + ij] = val;
+          else
+            D[((p & 3) * 21 + ij) * epad + (p >> 2)] = val;
+        }
+      }
+    }
+    return;
+  }
   const int nout = np * 21;
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
     const int lp = o % np, ij = o / np;
@@ -478,32 +600,52 @@ int spring_tile_default(int S) {
   return 4 * p2;
 }
 bool spring_tile_ok(int tp, int S) { return tp >= 4 && tp % 4 == 0 && (size_t)tp * (S + 12) * 8 <= 200 * 1024; }
+// shared memory of a launch: float-pair tangents, or the tensor path's digit planes
+static size_t spring_smem(int tp, int S, bool tc) {
+  const size_t strains = sizeof(float2) * (size_t)tp * 12;
+  if (tc) return (size_t)kDigits * tp * tc_stride((S + 15) / 16) * 2 + strains;
+  return sizeof(float2) * (size_t)tp * S + strains;
+}
+static bool spring_tc_ok(const SpringTables &tab, int tp) {
+  return tab.tc && tab.tfrag && tab.tsc && tab.S <= kTcMaxS && tp % 16 == 0 && spring_smem(tp, tab.S, true) <= 200 * 1024;
+}
 
 cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const int32_t *mat_of_elem,
                            const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
                            int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
   const int TP = spring_tile_ok(tab.tp, tab.S) ? tab.tp : spring_tile_default(tab.S);
-  const size_t smem = sizeof(float2) * ((size_t)TP * tab.S + (size_t)TP * 12);
+  const bool tc = spring_tc_ok(tab, TP);
+  const size_t smem = spring_smem(TP, tab.S, tc);
   // the shared-memory opt-in is a per-device attribute, set once per device (any thread)
   static std::atomic<unsigned long long> attr_done{0};
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_done.load() & bit)) {
-    cudaFuncSetAttribute(k_springs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_springs<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_springs<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_springs<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_springs<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_springs<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_done.fetch_or(bit);
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
-  if (tab.minb == 4)
-    k_springs<4><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau,
-                                          st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow,
-                                          tab.powf);
-  else
-    k_springs<1><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau,
-                                          st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts, tab.pow,
-                                          tab.powf);
+#define NS_SPRINGS(MB, TC)                                                                                         \
+  k_springs<MB, TC><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, \
+                                             st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts,  \
+                                             tab.pow, tab.powf, tab.tfrag, tab.tsc)
+  if (tab.minb == 4) {
+    if (tc)
+      NS_SPRINGS(4, true);
+    else
+      NS_SPRINGS(4, false);
+  } else {
+    if (tc)
+      NS_SPRINGS(1, true);
+    else
+      NS_SPRINGS(1, false);
+  }
+#undef NS_SPRINGS
   return cudaGetLastError();
 }
 

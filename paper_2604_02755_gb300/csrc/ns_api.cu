@@ -58,6 +58,8 @@ struct ns_ctx {
   float2 *q2_d = nullptr;
   float *powf_d = nullptr;
   float2 *T2_d = nullptr;
+  uint2 *tfrag_d = nullptr;
+  double *tsc_d = nullptr;
   SpringTables tab{};
   double *D = nullptr;
   float *D32 = nullptr;   // NS_PREC_FP64_IR: FP32 copy of D for the inner operator
@@ -880,6 +882,7 @@ void ns_config_default(ns_config *cfg) {
   cfg->l2_prefetch = 1;
   cfg->spring_tile_points = 0;
   cfg->spring_tile_blocks = 1;
+  cfg->spring_tensor_cores = 0;
 }
 
 static thread_local std::string g_create_err;
@@ -1047,13 +1050,6 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   CKC(c, cudaMemcpy(mh.data(), c->m.mat, c->m.E * 4, cudaMemcpyDeviceToHost));
   for (int32_t x : mh)
     if (x >= n) NS_SET(c, NS_ERR_INVALID_ARG, "an element uses a material index beyond the table");
-  c->nmat = n;
-  c->mats_h.resize(n);
-  for (int i = 0; i < n; ++i) host_material_constants(mats[i], c->cfg.rayleigh_f1, c->cfg.rayleigh_f2, &c->mats_h[i]);
-  CKC(c, cudaMemcpy(c->mats_d, c->mats_h.data(), sizeof(MatConst) * n, cudaMemcpyHostToDevice));
-  int rc;
-  if ((rc = fill_opcoefs(c))) return rc;
-  if (c->has_mat) return NS_OK;  // state already allocated: only the constants change
   // spring tables: q [S][6], T [S+1][21] = w q q^T (last row: their sum)
   const int S = c->cfg.n_springs;
   std::vector<double> qh(6 * (size_t)S), Th(21 * (size_t)(S + 1), 0.0);
@@ -1066,6 +1062,13 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
         Th[21 * (size_t)k + sym6(i, j)] = t;
         Th[21 * (size_t)S + sym6(i, j)] += t;
       }
+  c->nmat = n;
+  c->mats_h.resize(n);
+  for (int i = 0; i < n; ++i) host_material_constants(mats[i], c->cfg.rayleigh_f1, c->cfg.rayleigh_f2, &c->mats_h[i]);
+  CKC(c, cudaMemcpy(c->mats_d, c->mats_h.data(), sizeof(MatConst) * n, cudaMemcpyHostToDevice));
+  int rc;
+  if ((rc = fill_opcoefs(c))) return rc;
+  if (c->has_mat) return NS_OK;  // state already allocated: only the constants change
   std::vector<double> ph(kPowTabLen);
   host_pow_tables(ph.data());
   std::vector<float> pfh(kPowFLen);
@@ -1085,6 +1088,19 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
       (rc = dalloc(c, &c->powf_d, pfh.size())) || (rc = dalloc(c, &c->q2_d, q2h.size())))
     return rc;
   CKC(c, cudaMemcpy(c->T2_d, T2h.data(), T2h.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  {  // digits of T for the tensor-core tangent assembly
+    std::vector<uint2> fr((size_t)8 * ((S + 15) / 16) * 3 * 32);
+    int et[21];
+    host_spring_digits(S, Th.data(), fr.data(), et);
+    double tsc[21];
+    for (int i = 0; i < 21; ++i) tsc[i] = ldexp(1.0, et[i] - 12);
+    if ((rc = dalloc(c, &c->tfrag_d, fr.size())) || (rc = dalloc(c, &c->tsc_d, 21))) return rc;
+    CKC(c, cudaMemcpy(c->tfrag_d, fr.data(), fr.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->tsc_d, tsc, sizeof(tsc), cudaMemcpyHostToDevice));
+    c->tab.tfrag = c->tfrag_d;
+    c->tab.tsc = c->tsc_d;
+    c->tab.tc = c->cfg.spring_tensor_cores ? 1 : 0;
+  }
   CKC(c, cudaMemcpy(c->q2_d, q2h.data(), q2h.size() * sizeof(float2), cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->q_d, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(c->T_d, Th.data(), Th.size() * 8, cudaMemcpyHostToDevice));
@@ -1874,7 +1890,7 @@ void ns_destroy(ns_ctx *c) {
   dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.kerr); dfree(m.geom2); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
   dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
   dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
-  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->powf_d); dfree(c->T2_d); dfree(c->q2_d); dfree(c->D); dfree(c->D32);
+  dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->powf_d); dfree(c->T2_d); dfree(c->tfrag_d); dfree(c->tsc_d); dfree(c->q2_d); dfree(c->D); dfree(c->D32);
   dfree(c->D16); dfree(c->op_A16); dfree(c->D2);
   destroy_graphs(c);
   dfree(c->vseg_d); dfree(c->eseg_d); dfree(c->fseg_d); dfree(c->voff_d); dfree(c->eoff_d); dfree(c->foff_d);

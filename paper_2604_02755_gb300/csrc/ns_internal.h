@@ -25,6 +25,12 @@ struct MatConst {
   float itref_f, iG0_f, alpha_f, beta_f, G0_f;
   float pad_f;
   RoPairs rp;       // the same constants as float pairs for the double-float root step
+  // tangent assembly on tensor cores: 2^eG > G0 (eG = floor(log2 G0) + 1), gfix = 2^(48 - eG)
+  // turns a tangent into a 48-bit integer, dsc = 2^eG scales the digit sums back (with the
+  // column scales of the spring tables)
+  float gfix;
+  int32_t eg;
+  double dsc;
 };
 
 // Coefficients of one element-by-element operator application, per material:
@@ -214,6 +220,9 @@ struct SpringTables {
   const double *pow;  // power tables: r[128], -ln r hi[128], lo[128], 2^(i/64)[64], ln2 hi/lo, ln2/64 hi/lo
   const float *powf;  // double-float power tables (df64.cuh, kPowFLen floats)
   int S;
+  const uint2 *tfrag = nullptr;  // digits of T in MMA fragment order (tensor-core assembly)
+  const double *tsc = nullptr;   // [21] 2^(et[ij] - 12): column scales of those digits
+  int tc = 1;         // 1: assemble D on the tensor cores where the launch shape allows
   int tp = 0;         // integration points per block of the spring kernel (0: size heuristic)
   int minb = 1;       // register budget of the spring kernel: 1 (compiler's choice) or 4 blocks per SM
 };
@@ -255,5 +264,9 @@ int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, i
 void host_material_constants(const ns_material &m, double f1, double f2, MatConst *out);
 void host_pow_tables(double *out);   // kPowTabLen entries
 void host_powf_tables(float *out);   // kPowFLen entries (df64.cuh)
+// per-column exponents et[21] of the spring tables T [S][21] (max_k |T_k[ij]| 2^-et[ij] in
+// [1/4, 1/2)) and their 6-bit digits in MMA fragment order, 8 x ceil(S/16) x 3 x 32 entries
+// (k_spring.cu)
+void host_spring_digits(int S, const double *T, uint2 *frag, int *et);
 
 }  // namespace ns

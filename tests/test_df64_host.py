@@ -61,3 +61,20 @@ def test_halley_step_root_and_tangent(tmp_path_factory):
     assert float(max_step) <= 2e-5        # within the step bound the kernel accepts
     assert float(err_tau) < 1e-13         # root of the skeleton equation
     assert float(err_G) < 1e-13           # tangent 1/g'(tau) at it
+
+
+@pytest.mark.parametrize("S", [10, 17, 50, 150, 256])
+def test_tensor_core_tangent_assembly_digits(tmp_path_factory, S):
+    """The tensor-core assembly of D = sum_k G_k T_k (csrc/k_spring.cu) emulated on the
+    host with the library's digit tables: the fragment table holds every (spring, column)
+    once and zeros in the padding, the digits of T reproduce T to 2^-48 of its column
+    scale, every level sum stays below 2^23 (so FP32 accumulates it exactly), and the
+    recombined D agrees with long double to 1e-12 of sum_k |G_k T_k| for tangents spread
+    over four decades below G0 (2e-13 from 50 springs up)."""
+    exe = compile_check(tmp_path_factory, "tc_check")
+    out = subprocess.run([exe, str(S), "200"], capture_output=True, text=True, check=True).stdout
+    worst, cmax, mism, worst_t = out.split()
+    assert int(mism) == 0
+    assert float(worst_t) <= 2.0 ** -48
+    assert float(cmax) < 1.0
+    assert float(worst) <= (2e-13 if S >= 50 else 1e-12)

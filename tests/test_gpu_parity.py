@@ -55,9 +55,11 @@ def test_operators_match_oracle(scatter, pair):
             assert np.abs(yg - yo).max() <= 1e-12 * np.abs(yo).max(), op
 
 
-def test_spring_points_match_oracle():
+@pytest.mark.parametrize("S,tensor", [(50, 1), (50, 0), (150, 1), (12, 1)])
+def test_spring_points_match_oracle(S, tensor):
+    """Multi-spring points against the oracle, the tangent assembled on the tensor cores
+    (digit products) or in double-float sums."""
     wl = small()
-    S = 50
     q, w = oracle.spring_dirs(S)
     mats = wl.materials
     rng = np.random.default_rng(3)
@@ -67,8 +69,8 @@ def test_spring_points_match_oracle():
     th_o = np.zeros((npts, S), oracle.SPRING_DTYPE)
     eps = np.zeros((npts, 6))
     wl2 = synth.Workload(wl.name, wl.mesh, mats, S, wl.dt, wl.n_steps, wl.wave)
-    with B.Simulation(wl2) as sim:
-        for it in range(40):
+    with B.Simulation(wl2, spring_tensor_cores=tensor) as sim:
+        for it in range(40 if S <= 50 else 12):
             scale = 10 ** rng.uniform(-6, -3, size=(npts, 1))
             deps = rng.normal(size=(npts, 6)) * scale
             if it == 5:
