@@ -405,6 +405,20 @@ def main():
         roof["hbm"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                        "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
+    # the HBM-bound matvec: the inner FP32 operator, per launch that did work (algorithmic
+    # bytes: connectivity 40, geometry 40, material 4, tangent 336 (FP32) or 168 (FP16),
+    # node gathers ~16 and scatters ~32 per element)
+    matvec = None
+    if st["inner_iters_total"] > 0 and st["ms_ebe32"] > 0:
+        bpe = 300.0 if prec == B.NS_PREC_FP64_IR16 else 468.0
+        per32 = st["ms_ebe32"] / st["inner_iters_total"] / 1e3
+        hbm_peak = measured_peaks().get("hbm_gbs")
+        gbs = bpe * E / per32 / 1e9
+        matvec = {"kernel": "k_ebe<float> (inner FP32 EBE operator)", "bound": "hbm", "achieved": gbs,
+                  "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if hbm_peak else None,
+                  "bytes_per_element": bpe, "avg_active_launch_ms": per32 * 1e3,
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
     # end to end through the public API: input record from host, advance, surface read-back to host
     t0 = time.perf_counter()
     if ens:
@@ -424,7 +438,9 @@ def main():
     kernels = {"ebe64": {"launches_per_step": st["n_ebe64"] / args.steps,
                          "avg_ms": st["ms_ebe64"] / max(st["n_ebe64"], 1)},
                "ebe32": {"launches_per_step": st["n_ebe32"] / args.steps,
-                         "avg_ms": st["ms_ebe32"] / max(st["n_ebe32"], 1)},
+                         "avg_ms": st["ms_ebe32"] / max(st["n_ebe32"], 1),
+                         "active_launches_per_step": st["inner_iters_total"] / args.steps,
+                         "avg_active_ms": st["ms_ebe32"] / max(st["inner_iters_total"], 1)},
                "springs": {"launches_per_step": st["n_spring"] / args.steps,
                            "avg_ms": st["ms_spring"] / max(st["n_spring"], 1)}}
     inner_iters = st["inner_iters_last"]
@@ -488,7 +504,8 @@ def main():
                            "springs_per_point": wl.n_springs, "dt": wl.dt, "cg_tol": 1e-8,
                            "numbering": args.numbering, "state": "resident in HBM", "l2": l2_note,
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
-                "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "matvec_roofline": matvec,
+                "cpu_baseline": cpu,
                 "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
                 "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
                 "staged_operator": args.stage, "inner_iters": args.inner_iters, "inner_tol": args.inner_tol, "spring_tensor_cores": args.spring_tensor, "autotune": tuning,

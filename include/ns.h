@@ -134,6 +134,8 @@ typedef struct {
   double ms_advance;          /* CUDA-event time of ns_advance calls, all streams joined (always valid) */
   int64_t h2d_bytes_early;    /* of h2d_bytes: chunks loaded at the start of a step, before its
                                  multi-spring phase (they overlap the solve) */
+  int64_t inner_iters_total;  /* inner FP32 iterations summed since the last ns_reset_stats: the
+                                 FP32 operator launches that did work (the others return at once) */
 } ns_stats;
 
 /* Fill cfg with defaults: 10 springs, dt 0.01, tol 1e-8, 10000 iterations,

@@ -59,7 +59,7 @@ class ns_stats(C.Structure):
                 ("ms_step", C.c_double), ("n_ebe64", C.c_int64), ("n_ebe32", C.c_int64), ("n_spring", C.c_int64),
                 ("ms_ebe64", C.c_double), ("ms_ebe32", C.c_double), ("ms_spring", C.c_double),
                 ("ms_stream_wall", C.c_double), ("ms_advance", C.c_double),
-                ("h2d_bytes_early", C.c_int64)]
+                ("h2d_bytes_early", C.c_int64), ("inner_iters_total", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

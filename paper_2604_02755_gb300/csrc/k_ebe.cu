@@ -170,10 +170,7 @@ __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][
       point_stress<T, 2>(x, P, g, dl, w, sig[2]);
       point_stress<T, 3>(x, P, g, dl, w, sig[3]);
     }
-    point_force<T, 0>(sig[0], g, ye);
-    point_force<T, 1>(sig[1], g, ye);
-    point_force<T, 2>(sig[2], g, ye);
-    point_force<T, 3>(sig[3], g, ye);
+    points_force<T>(sig, g, ye);
     if (OUTK) {  // K_e x to yk, then the coefficient
 #pragma unroll
       for (int a = 0; a < 10; ++a) add_node<VS, ATOMIC>(yk, nd[a], ye[a]);

@@ -175,31 +175,47 @@ __device__ __forceinline__ void voigt_strain(const T H[3][3], T eps[6]) {
   eps[5] = H[0][1] + H[1][0];
 }
 
-// Adds the nodal forces of stress sig (Voigt) at point q: y_i += grad N_i(q) . S.
-template <typename T, int q>
-__device__ __forceinline__ void point_force(const T sig[6], const T g[4][3], T y[10][3]) {
-  T R[4][3];
+// S g for a symmetric stress S in Voigt order (xx, yy, zz, yz, xz, xy)
+template <typename T>
+__device__ __forceinline__ void voigt_times(const T s[6], const T g[3], T out[3]) {
+  out[0] = s[0] * g[0] + s[5] * g[1] + s[4] * g[2];
+  out[1] = s[5] * g[0] + s[1] * g[1] + s[3] * g[2];
+  out[2] = s[4] * g[0] + s[3] * g[1] + s[2] * g[2];
+}
+
+// The nodal forces of the stresses at all four points at once: y_i += sum_q grad N_i(q) . S_q.
+// With L_k(q) = a (k = q) or b and U_j = 4 sum_q L_j(q) S_q = 4 b sum S + 4 (a - b) S_j, the
+// vertex k gets (U_k - sum S) g_k and the edge node (k, j) gets U_j g_k + U_k g_j -- the
+// same sums as point by point, in fewer operations.
+template <typename T>
+__device__ __forceinline__ void points_force(const T sig[4][6], const T g[4][3], T y[10][3]) {
+  const T b4 = (T)(4.0 * NS_QB), d4 = (T)(4.0 * (NS_QA - NS_QB));
+  T sum[6], U[4][6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sum[c] = (sig[0][c] + sig[1][c]) + (sig[2][c] + sig[3][c]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) U[j][c] = b4 * sum[c] + d4 * sig[j][c];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    R[k][0] = sig[0] * g[k][0] + sig[5] * g[k][1] + sig[4] * g[k][2];
-    R[k][1] = sig[5] * g[k][0] + sig[1] * g[k][1] + sig[3] * g[k][2];
-    R[k][2] = sig[4] * g[k][0] + sig[3] * g[k][1] + sig[2] * g[k][2];
-  }
-  const T la = (T)NS_QA, lb = (T)NS_QB;
+    T V[6], f[3];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const T ck = (k == q) ? (T)(4.0 * NS_QA - 1.0) : (T)(4.0 * NS_QB - 1.0);
+    for (int c = 0; c < 6; ++c) V[c] = U[k][c] - sum[c];
+    voigt_times(V, g[k], f);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) y[k][r] += ck * R[k][r];
+    for (int r = 0; r < 3; ++r) y[k][r] += f[r];
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
     for (int j = k + 1; j < 4; ++j) {
-      const T lk = (k == q) ? la : lb, lj = (j == q) ? la : lb;
+      T f1[3], f2[3];
+      voigt_times(U[j], g[k], f1);
+      voigt_times(U[k], g[j], f2);
       const int ne = edge_node(k, j);
 #pragma unroll
-      for (int r = 0; r < 3; ++r) y[ne][r] += (T)4 * (lj * R[k][r] + lk * R[j][r]);
+      for (int r = 0; r < 3; ++r) y[ne][r] += f1[r] + f2[r];
     }
 }
 

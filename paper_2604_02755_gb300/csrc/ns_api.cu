@@ -671,6 +671,7 @@ int solve_ir(ns_ctx *c) {
     inner_total += most;
   }
   c->stats.inner_iters_last = inner_total;
+  c->stats.inner_iters_total += inner_total;
   return NS_OK;
 }
 
