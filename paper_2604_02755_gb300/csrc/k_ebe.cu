@@ -158,19 +158,19 @@ __device__ __forceinline__ T ebe_element(const int nd[10], int mt, const T g[4][
 #pragma unroll
     for (int r = 0; r < 3; ++r) ye[a][r] = (T)0;
   if (cK != (T)0) {
-    T sig[4][6];
+    T sig[4][6];  // D eps at the four points, the quadrature weight applied in the force sums
     {
       T x[10][3], P[4][3];
 #pragma unroll
       for (int a = 0; a < 10; ++a) load_node<VS>(xk, nd[a], x[a]);
       compute_P(x, P);
-      const T w = OUTK ? vol * (T)0.25 : cK * vol * (T)0.25;
-      point_stress<T, 0>(x, P, g, dl, w, sig[0]);
-      point_stress<T, 1>(x, P, g, dl, w, sig[1]);
-      point_stress<T, 2>(x, P, g, dl, w, sig[2]);
-      point_stress<T, 3>(x, P, g, dl, w, sig[3]);
+      point_stress<T, 0>(x, P, g, dl, (T)1, sig[0]);
+      point_stress<T, 1>(x, P, g, dl, (T)1, sig[1]);
+      point_stress<T, 2>(x, P, g, dl, (T)1, sig[2]);
+      point_stress<T, 3>(x, P, g, dl, (T)1, sig[3]);
     }
-    points_force<T>(sig, g, ye);
+    const T w = OUTK ? vol * (T)0.25 : cK * vol * (T)0.25;
+    points_force<T>(sig, g, w, ye);
     if (OUTK) {  // K_e x to yk, then the coefficient
 #pragma unroll
       for (int a = 0; a < 10; ++a) add_node<VS, ATOMIC>(yk, nd[a], ye[a]);

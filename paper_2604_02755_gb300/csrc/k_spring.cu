@@ -455,8 +455,15 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
     }
   }
   __syncthreads();
-  for (int g = threadIdx.x; g < nspr; g += blockDim.x) {
-    const int lp = g / S, k = g - lp * S;
+  // spring g = lp * S + k of the tile; (lp, k) advanced by the block stride without a
+  // division per spring
+  const int dlp = (int)blockDim.x / S, dk = (int)blockDim.x - dlp * S;
+  int lp = (int)threadIdx.x / S, k = (int)threadIdx.x - lp * S;
+  for (int g = threadIdx.x; g < nspr; g += blockDim.x, lp += dlp, k += dk) {
+    if (k >= S) {
+      k -= S;
+      ++lp;
+    }
     const int64_t p = pt + lp;
     const int mt = mat_p ? mat_p[p] : mat_e[p >> 2];
     const MatConst &rp = mc[mt];

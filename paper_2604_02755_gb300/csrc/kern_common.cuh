@@ -183,13 +183,14 @@ __device__ __forceinline__ void voigt_times(const T s[6], const T g[3], T out[3]
   out[2] = s[4] * g[0] + s[3] * g[1] + s[2] * g[2];
 }
 
-// The nodal forces of the stresses at all four points at once: y_i += sum_q grad N_i(q) . S_q.
-// With L_k(q) = a (k = q) or b and U_j = 4 sum_q L_j(q) S_q = 4 b sum S + 4 (a - b) S_j, the
-// vertex k gets (U_k - sum S) g_k and the edge node (k, j) gets U_j g_k + U_k g_j -- the
-// same sums as point by point, in fewer operations.
+// The nodal forces of the stresses at all four points at once, each with quadrature weight
+// w: y_i += w sum_q grad N_i(q) . S_q.  With L_k(q) = a (k = q) or b and
+// U_j = 4 w sum_q L_j(q) S_q = 4 w b sum S + 4 w (a - b) S_j, the vertex k gets
+// (U_k - w sum S) g_k and the edge node (k, j) gets U_j g_k + U_k g_j -- the same sums as
+// point by point, in fewer operations.
 template <typename T>
-__device__ __forceinline__ void points_force(const T sig[4][6], const T g[4][3], T y[10][3]) {
-  const T b4 = (T)(4.0 * NS_QB), d4 = (T)(4.0 * (NS_QA - NS_QB));
+__device__ __forceinline__ void points_force(const T sig[4][6], const T g[4][3], T w, T y[10][3]) {
+  const T b4 = (T)(4.0 * NS_QB) * w, d4 = (T)(4.0 * (NS_QA - NS_QB)) * w;
   T sum[6], U[4][6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) sum[c] = (sig[0][c] + sig[1][c]) + (sig[2][c] + sig[3][c]);
@@ -201,7 +202,7 @@ __device__ __forceinline__ void points_force(const T sig[4][6], const T g[4][3],
   for (int k = 0; k < 4; ++k) {
     T V[6], f[3];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) V[c] = U[k][c] - sum[c];
+    for (int c = 0; c < 6; ++c) V[c] = U[k][c] - w * sum[c];
     voigt_times(V, g[k], f);
 #pragma unroll
     for (int r = 0; r < 3; ++r) y[k][r] += f[r];
