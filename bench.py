@@ -180,8 +180,10 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "single large model (bounded CPU sample)", "elements": wl.mesh.n_elems,
-                       "springs_per_point": 150, "dt": 0.005},
+            "config": {"workload": wl.name, "elements": 160 * 160 * 52 * 6, "springs_per_point": wl.n_springs,
+                       "dt": wl.dt, "cg_tol": 1e-8, "numbering": "grid",
+                       "sample": "a %dx%dx52-hexahedron column of it (%d elements) on the host cores"
+                                 % (col[2], col[3], wl.mesh.n_elems)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
