@@ -144,7 +144,8 @@ __device__ __forceinline__ void dsplit(double v, float &h, float &l) {
 // float pair; or -- when `solve` is false -- only the tangent at tau = ga (the current
 // stress).  The usual path:
 //  1. FP32 Newton from the guess if it lies in (0, G0 ga], else from G0 ga, until a step
-//     is below 4e-6 of the iterate;
+//     is below 1e-3 of the iterate (Newton's quadratic convergence leaves the new iterate
+//     within ~1e-6 of the root, which the cubic step below turns into rounding);
 //  2. one Halley step from that FP32 seed in double-float arithmetic on the FP32 pipes
 //     (df64_ro_halley: the power, the residual against ga, the step and the tangent at
 //     the new root; root to ~2^-47, tangent to ~2^-45).
@@ -166,7 +167,7 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
       float tn = t - step;
       if (!(tn > 0.0f)) tn = 0.5f * t;
       if (tn > hif) tn = hif;
-      const bool conv = fabsf(step) <= 4e-6f * t;
+      const bool conv = fabsf(step) <= 1e-3f * t;
       t = tn;
       if (conv) {
         seeded = true;
@@ -190,7 +191,7 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
   double w = pow_pos(tau * p.itref, p.beta_ro, tb);
   if (solve) {
     // Halley: step = h / (1 - h f''/(2 f')) with h = f/f' the Newton step; |h f''/(2 f')|
-    // is ~ the seed error (<= 4e-6), so 1/(1 - c) = 1 + c to far below rounding
+    // is ~ the seed error (~1e-6), so 1/(1 - c) = 1 + c to far below rounding
     const double it0 = rcp1(tau);
     const double gval = tau * p.iG0 * fma(p.alpha_ro, w, 1.0);
     const double rg = rcp1(fma(p.ab1, w, 1.0));
@@ -227,7 +228,7 @@ __device__ __forceinline__ double ro_solve_pair(float gah, float gal, float gues
     float tn = t - step;
     if (!(tn > 0.0f)) tn = 0.5f * t;
     if (tn > hif) tn = hif;
-    const bool conv = fabsf(step) <= 4e-6f * t;
+    const bool conv = fabsf(step) <= 1e-3f * t;
     t = tn;
     if (conv) {
       seeded = true;

@@ -20,6 +20,7 @@ static void split(long double v, float &h, float &l) {
 
 int main(int argc, char **argv) {
   const int n = argc > 1 ? atoi(argv[1]) : 200000;
+  const float stop = argc > 2 ? (float)atof(argv[2]) : 1e-3f;  // the seed's stopping step
   static float tab[kPowFLen];
   host_powf_tables(tab);
   std::mt19937_64 rng(5);
@@ -60,7 +61,7 @@ int main(int argc, char **argv) {
       tau = nt > 0 ? nt : tau / 2;
     }
     const long double Gref = G0 / (1 + alpha * (1 + beta) * powl(tau * itref, beta));
-    // FP32 Newton seed, stopped at a relative step of 4e-6 like the device's
+    // FP32 Newton seed, stopped at a relative step like the device's
     const float gaf = (float)ga, G0f = (float)G0, iG0f = (float)(1 / G0), itf = (float)itref, bf = (float)beta,
                 af = (float)alpha;
     float t = G0f * gaf;
@@ -69,7 +70,7 @@ int main(int argc, char **argv) {
       const float step = (t * iG0f * (1 + af * pw) - gaf) * (G0f / (1 + af * (1 + bf) * pw));
       float tn = t - step;
       if (!(tn > 0)) tn = 0.5f * t;
-      const bool conv = fabsf(step) <= 4e-6f * t;
+      const bool conv = fabsf(step) <= stop * t;
       t = tn;
       if (conv) break;
     }
