@@ -113,10 +113,13 @@ __device__ __forceinline__ double dload(const double *__restrict__ D, int64_t ep
   return __ldg(D + m * epad + e);
 }
 __device__ __forceinline__ float dload(const float *__restrict__ D, int64_t epad, int64_t e, int m) {
-  return __ldg(D + m * epad + e);
+  return ldg(D + m * epad + e);  // no L1 allocation (kern_common.cuh)
 }
 __device__ __forceinline__ float dload(const __half2 *__restrict__ D, int64_t epad, int64_t e, int m) {
-  const __half2 h = __ldg(D + (m >> 1) * epad + e);
+  unsigned u;
+  asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(u) : "l"(D + (m >> 1) * epad + e));
+  __half2 h;
+  memcpy(&h, &u, 4);
   return (m & 1) ? __high2float(h) : __low2float(h);
 }
 __device__ __forceinline__ dd dload(const dd *__restrict__ D, int64_t epad, int64_t e, int m) {

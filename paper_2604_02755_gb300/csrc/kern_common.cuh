@@ -27,9 +27,24 @@ __host__ __device__ __forceinline__ constexpr int sym6(int i, int j) {
   return (i < j ? i : j) * 6 - ((i < j ? i : j) * ((i < j ? i : j) - 1)) / 2 + ((i > j ? i : j) - (i < j ? i : j));
 }
 
+// Element rows (connectivity, material, geometry, tangent) are read once per launch: the
+// FP32 and integer ones bypass L1 allocation (ld.global.nc.L1::no_allocate) so that L1
+// keeps the node gathers, which elements share.
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) {
   return __ldg(p);
+}
+template <>
+__device__ __forceinline__ float ldg(const float *p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+template <>
+__device__ __forceinline__ int ldg(const int *p) {
+  int v;
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
 }
 // pairs are stored as float2
 __device__ __forceinline__ dd ldg(const dd *p) {
