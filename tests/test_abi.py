@@ -71,7 +71,14 @@ def test_create_without_device_reports_an_error_code():
     assert ei.value.code == -4
 
 
-def test_invalid_config_rejected_before_device_use():
+@pytest.mark.parametrize("bad", [dict(n_springs=3), dict(spring_tile_points=6), dict(spring_tile_points=2),
+                                 dict(n_springs=150, spring_tile_points=256), dict(spring_tile_blocks=3),
+                                 dict(precision=7), dict(stream_mode=2), dict(inner_max_iter=0),
+                                 dict(inner_tol=0.0), dict(ring_depth=1)])
+def test_invalid_config_rejected_before_device_use(bad):
+    """Out-of-range settings are refused by ns_create before any device call: a spring
+    tile that is not a multiple of 4 points or whose float pairs exceed 200 KB of shared
+    memory, a register budget other than 1 or 4 blocks per SM, unknown enums, and so on."""
     with pytest.raises(binding.NsError) as ei:
-        binding.ns_create(binding.ns_config_default(n_springs=3))
+        binding.ns_create(binding.ns_config_default(**bad))
     assert ei.value.code == -1
