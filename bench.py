@@ -50,8 +50,9 @@ SPRING_FLOP_PER_SPRING = 66.0   # gamma and dgamma (12 FMA) + D accumulation (21
 
 
 def profiled_bytes(name, key):
-    """DRAM bytes per unit that an ncu capture recorded for a kernel (a `key = value` line
-    of its summary under profiles/), or None when there is no such summary."""
+    """A per-unit figure (DRAM bytes, warp instructions) that an ncu capture recorded for a
+    kernel (a `key = value` line of its summary under profiles/), or None when there is no
+    such summary."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         for line in open(path):
@@ -406,6 +407,16 @@ def main():
                         "(see the spring profile: issue slots, FP64 and FMA pipes)")
         roof["hbm"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                        "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+        # the resource that binds it: instruction issue (one warp instruction per clock on
+        # each of the 4 schedulers of the 152 SMs), from the profiled instructions per spring
+        ips = profiled_bytes(SPRING_PROFILE, "warp_instructions_per_spring")
+        if ips:
+            issue_peak = 152 * 4 * 2.07
+            gips = ips * n_spr / per / 1e9
+            roof["issue"] = {"achieved": gips, "peak": issue_peak, "unit": "G warp-instructions/s",
+                             "frac": gips / issue_peak,
+                             "peak_source": "152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz (derived)",
+                             "per_unit": "%g warp-instructions/spring (ncu smsp__inst_executed, spring profile)" % ips}
 
     # the HBM-bound matvec: the inner FP32 operator, per launch that did work (algorithmic
     # bytes: connectivity 40, geometry 40, material 4, tangent 336 (FP32) or 168 (FP16),
