@@ -759,50 +759,55 @@ cudaError_t launch_to_pairs(const double *src, void *dst, int64_t n, cudaStream_
 
 // ------------------------------------------------------------------ strains for the spring update
 
-__global__ void __launch_bounds__(kBlock) k_strain(int64_t e0, int64_t e1, const int32_t *__restrict__ conn,
-                                                   const double *__restrict__ geom, int64_t epad,
-                                                   const double *__restrict__ u, const double *__restrict__ du,
-                                                   double *out) {
+// Strains for the spring update: eps = B u and deps = B du at the four integration points
+// of every element, in double-float arithmetic on the FP32 pipes, stored as the float pairs
+// the spring kernel works on (out as float2 [4E][12]: eps then deps per point); one
+// thread per element and vector (blockIdx.y: 0 for u, 1 for du).  The nodal values and gradients enter as pairs
+// (dd_from_double: two FP64-pipe operations each instead of the FP64 arithmetic).
+__global__ void __launch_bounds__(kBlock) k_strain_pairs(int64_t e0, int64_t e1, const int32_t *__restrict__ conn,
+                                                         const double *__restrict__ geom, int64_t epad,
+                                                         const double *__restrict__ u, const double *__restrict__ du,
+                                                         float2 *out) {
   const int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= e1) return;
-  int nd[10];
+  const int which = blockIdx.y;
+  const double *src = which ? du : u;
+  dd g[4][3];
 #pragma unroll
-  for (int a = 0; a < 10; ++a) nd[a] = conn[a * epad + e];
-  double g[4][3], vol;
-  load_grads(geom, epad, e, g, vol);
+  for (int k = 0; k < 3; ++k)
 #pragma unroll
-  for (int which = 0; which < 2; ++which) {
-    const double *src = which ? du : u;
-    double x[10][3], P[4][3];
+    for (int c = 0; c < 3; ++c) g[k + 1][c] = dd_from_double(__ldg(geom + (3 * k + c) * epad + e));
 #pragma unroll
-    for (int a = 0; a < 10; ++a)
+  for (int c = 0; c < 3; ++c) g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+  dd x[10][3], P[4][3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) x[a][r] = src[3 * (int64_t)nd[a] + r];
-    compute_P(x, P);
-    double H[3][3], eps[6];
-    point_grad<double, 0>(x, P, g, H);
-    voigt_strain(H, eps);
+  for (int a = 0; a < 10; ++a) {
+    const int64_t n = ldg(conn + a * epad + e);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) out[(e * 4 + 0) * 12 + 6 * which + k] = eps[k];
-    point_grad<double, 1>(x, P, g, H);
-    voigt_strain(H, eps);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) out[(e * 4 + 1) * 12 + 6 * which + k] = eps[k];
-    point_grad<double, 2>(x, P, g, H);
-    voigt_strain(H, eps);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) out[(e * 4 + 2) * 12 + 6 * which + k] = eps[k];
-    point_grad<double, 3>(x, P, g, H);
-    voigt_strain(H, eps);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) out[(e * 4 + 3) * 12 + 6 * which + k] = eps[k];
+    for (int r = 0; r < 3; ++r) x[a][r] = dd_from_double(__ldg(src + 3 * n + r));
   }
+  compute_P(x, P);
+  dd H[3][3], eps[6];
+  auto put = [&](int q) {
+    voigt_strain(H, eps);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[(e * 4 + q) * 12 + 6 * which + k] = make_float2(eps[k].h, eps[k].l);
+  };
+  point_grad<dd, 0>(x, P, g, H);
+  put(0);
+  point_grad<dd, 1>(x, P, g, H);
+  put(1);
+  point_grad<dd, 2>(x, P, g, H);
+  put(2);
+  point_grad<dd, 3>(x, P, g, H);
+  put(3);
 }
 
-cudaError_t launch_strain(const DevMesh &m, const double *u, const double *du, double *out, int64_t e0, int64_t e1,
-                          cudaStream_t s) {
+cudaError_t launch_strain_pairs(const DevMesh &m, const double *u, const double *du, void *out, int64_t e0, int64_t e1,
+                                cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
-  k_strain<<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(e0, e1, m.conn, m.geom, m.epad, u, du, out);
+  const dim3 grid((unsigned)((e1 - e0 + kBlock - 1) / kBlock), 2);
+  k_strain_pairs<<<grid, kBlock, 0, s>>>(e0, e1, m.conn, m.geom, m.epad, u, du, static_cast<float2 *>(out));
   return cudaGetLastError();
 }
 

@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
                                                     int64_t base, int64_t p0, int64_t p1, double *D, int64_t epad,
                                                     double *dpts, const double *__restrict__ ptab,
                                                     const float *__restrict__ ptabf, const uint2 *__restrict__ tfrag,
-                                                    const double *__restrict__ tsc) {
+                                                    const double *__restrict__ tsc, int eps_pairs) {
   // shared: [TP][S] tangents as float pairs (or, TC, [8][TP][stride] bf16 digit planes),
   // then [TP][12] strains as pairs
   extern __shared__ float2 Gs[];
@@ -444,9 +444,13 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
   // phase 0: the tile's strains and increments as float pairs (once per point, not per spring)
   float2 *Es = TC ? reinterpret_cast<float2 *>(planes + (size_t)kDigits * TP * KST) : Gs + (size_t)TP * S;
   for (int i = threadIdx.x; i < np * 12; i += blockDim.x) {
-    float h, l;
-    dsplit(eps[12 * pt + i], h, l);
-    Es[i] = make_float2(h, l);
+    if (eps_pairs) {  // already pairs (the strain kernel's double-float output)
+      Es[i] = reinterpret_cast<const float2 *>(eps)[12 * pt + i];
+    } else {
+      float h, l;
+      dsplit(eps[12 * pt + i], h, l);
+      Es[i] = make_float2(h, l);
+    }
   }
   if (TC) {  // zero digits in the padded springs S .. 16 KS - 1 (every plane, every row)
     const int pad = 16 * KS - S, nz = kDigits * TP * pad;
@@ -620,7 +624,7 @@ static bool spring_tc_ok(const SpringTables &tab, int tp) {
 
 cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const int32_t *mat_of_elem,
                            const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
-                           int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s) {
+                           int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s, bool eps_pairs) {
   if (p1 <= p0) return cudaSuccess;
   const int TP = spring_tile_ok(tab.tp, tab.S) ? tab.tp : spring_tile_default(tab.S);
   const bool tc = spring_tc_ok(tab, TP);
@@ -641,7 +645,7 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
 #define NS_SPRINGS(MB, TC)                                                                                         \
   k_springs<MB, TC><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, \
                                              st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts,  \
-                                             tab.pow, tab.powf, tab.tfrag, tab.tsc)
+                                             tab.pow, tab.powf, tab.tfrag, tab.tsc, eps_pairs ? 1 : 0)
   if (tab.minb == 4) {
     if (tc)
       NS_SPRINGS(4, true);

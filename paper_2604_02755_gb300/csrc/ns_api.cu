@@ -483,14 +483,14 @@ int spring_launch(ns_ctx *c, const SpringSoA &st, int64_t base_elem, int64_t e0,
   cudaEvent_t t0 = nullptr;
   tbegin(c, TK_SPRING, c->s_main, &t0);
   LAUNCH(c, launch_springs(c->tab, c->mats_d, c->m.mat, nullptr, c->eps, st, 4 * base_elem, 4 * e0, 4 * e1, c->D,
-                           c->m.epad, nullptr, c->s_main));
+                           c->m.epad, nullptr, c->s_main, true));
   tend(c, TK_SPRING, c->s_main, t0);
   return NS_OK;
 }
 
 int spring_phase(ns_ctx *c) {
   int rc;
-  LAUNCH(c, launch_strain(c->m, c->u, c->du, c->eps, 0, c->m.E, c->s_main));
+  LAUNCH(c, launch_strain_pairs(c->m, c->u, c->du, c->eps, 0, c->m.E, c->s_main));
   const int64_t nc = n_chunks(c);
   if (nc == 0) return spring_launch(c, c->st, 0, 0, c->E_res);
   if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t0, c->s_main));
@@ -1720,7 +1720,7 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
             for (int j = 0; j < nsl; ++j) {  // scratch state of slice j at scr[j * nes * 4 * S]
               const int64_t e0 = slice0(j);
               LAUNCH(c, launch_springs(tb, c->mats_d, c->m.mat, nullptr, c->eps, scr, 4 * (e0 - j * nes), 4 * e0,
-                                       4 * (e0 + nes), nullptr, c->m.epad, dpts, c->s_main));
+                                       4 * (e0 + nes), nullptr, c->m.epad, dpts, c->s_main, true));
             }
             return NS_OK;
           }, &ms);

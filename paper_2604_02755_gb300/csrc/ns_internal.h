@@ -151,9 +151,10 @@ cudaError_t launch_jacobi_elems16(const DevMesh &m, const void *D16, const OpCoe
 cudaError_t launch_jacobi_faces32(const DevMesh &m, const MatConst *mc, double cC, float *Jd, const int32_t *ids,
                                   int64_t f0, int64_t f1, bool atomic, cudaStream_t s);
 cudaError_t launch_invert_blocks32(const float *Jd, float *Jinv32, int64_t N, int32_t *bad, cudaStream_t s);
-// strains eps, deps at the 4 points of elements [e0, e1): out [E][4][12] (eps 6, deps 6)
-cudaError_t launch_strain(const DevMesh &m, const double *u, const double *du, double *out, int64_t e0, int64_t e1,
-                          cudaStream_t s);
+// strains eps, deps at the 4 points of elements [e0, e1), computed in double-float
+// arithmetic: out float2 [E][4][12] (eps 6, deps 6 per point)
+cudaError_t launch_strain_pairs(const DevMesh &m, const double *u, const double *du, void *out, int64_t e0, int64_t e1,
+                                cudaStream_t s);
 
 // ------------------------------------------------------------------ k_vec.cu
 cudaError_t launch_fill(double *x, double v, int64_t n, cudaStream_t s);
@@ -230,12 +231,14 @@ struct SpringTables {
 int spring_tile_default(int S);
 bool spring_tile_ok(int tp, int S);
 constexpr int kPowTabLen = 452;
-// Spring update of points [p0, p1) (point p = elem*4 + qp), strains from eps [P][12];
+// Spring update of points [p0, p1) (point p = elem*4 + qp), strains from eps [P][12]
+// (FP64, or float pairs when eps_pairs: the layout launch_strain_pairs writes);
 // state arrays indexed relative to `base` point; D written to D[(qp*21 + k) * epad + elem]
 // (element layout) or, if dpts != nullptr, to dpts[p - p0][21] (free points).
 cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const int32_t *mat_of_elem,
                            const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
-                           int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s);
+                           int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s,
+                           bool eps_pairs = false);
 // elastic tangent for elements [e0, e1)
 cudaError_t launch_elastic_D(const SpringTables &tab, const MatConst *mc, const int32_t *mat, double *D, int64_t epad,
                              int64_t e0, int64_t e1, cudaStream_t s);
