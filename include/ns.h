@@ -141,7 +141,10 @@ typedef struct {
 /* Fill cfg with defaults: 10 springs, dt 0.01, tol 1e-8, 10000 iterations,
  * x0_prev 1, NS_PREC_FP64, NS_SCATTER_ATOMIC, chunk 100000 elements (Sec. 2.3),
  * ring 3, all state resident, Rayleigh 0.1/2.5 Hz, 64 surface steps,
- * device 0, timing 0, inner 30 iterations / 1e-3, waits 120 s. */
+ * device 0, timing 0, inner 45 iterations / 1e-4, waits 120 s, graphs on,
+ * no staged operator, L2 prefetch on, FP64 operator (no pair arithmetic),
+ * NS_STREAM_RING, spring launch shape from the size heuristic (tile 0) with the
+ * compiler's register budget (1 block), tangent assembly off the tensor cores. */
 void ns_config_default(ns_config *cfg);
 
 /* Create a context on cfg->device.  *ctx is set on success. */
@@ -249,7 +252,9 @@ int ns_spring_points(ns_ctx *ctx, int64_t npts, const int32_t *mat, const double
  *    with that device current); make that first call before any stream capture.
  *  - All calls share the array; each call writes every byte it reads, so nothing of a
  *    previous call is reused, but calls that overlap on the GPU (several host threads or
- *    contexts on one device) race on it and must be serialised by the caller. */
+ *    contexts on one device) race on it and must be serialised by the caller.
+ *  - The call works on the context's device and makes the caller's current device
+ *    current again before it returns. */
 int ns_spring_points_noalloc(ns_ctx *ctx, int64_t npts, const int32_t *mat, const double *eps, const double *deps,
                              void *theta, double *D);
 

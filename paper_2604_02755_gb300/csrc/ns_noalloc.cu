@@ -61,6 +61,21 @@ __global__ void k_expand_D(const double *__restrict__ d21, double *__restrict__ 
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Puts the caller's current device back when the call returns (the call makes the
+// context's device current for its own work).
+struct DeviceRestore {
+  int prev = -1;
+  DeviceRestore() {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+  }
+  ~DeviceRestore() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 // Device address of the staging array for the current device, resolved once per device.
 int scratch_for_device(int dev, unsigned char **out) {
   if (dev < 0 || dev >= kMaxDevices) return -1;
@@ -113,6 +128,7 @@ extern "C" int ns_spring_points_noalloc(ns_ctx *c, int64_t npts, const int32_t *
       ctx_set_error(c, "material index out of range");
       return NS_ERR_INVALID_ARG;
     }
+  DeviceRestore restore;  // every return below leaves the caller's device current again
   unsigned char *base = nullptr;
   if (cudaSetDevice(v.device) != cudaSuccess || scratch_for_device(v.device, &base) != 0) {
     cudaGetLastError();
