@@ -5,8 +5,11 @@ benchmark's CPU-baseline / reference legs use it.  The CUDA library never
 imports, links or calls anything here, and this package shares no code with it:
 the two meet only in the seeded inputs of ``paper_2604_02755_gb300.synth``.
 
-The arithmetic lives in ``oracle.c`` (plain single-threaded C, FP64); this
-module compiles it with gcc and marshals arguments through ctypes.
+The arithmetic lives in ``oracle.c`` (plain C, FP64); this module compiles it
+with gcc and marshals arguments through ctypes.  It is built twice from that one
+source: ``liboracle.so`` (single thread) and ``liboracle_omp.so`` (the same code
+with -fopenmp, its independent element, node and spring loops split over the host
+cores; every sum keeps the single-thread order, so the two agree bit for bit).
 
 Parity: every function is pinned by tests under ``tests/test_oracle_*.py``
 against closed forms, invariants, brute force and exact symbolic integrals
@@ -22,7 +25,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-_lib = None
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
+_libs = {}
 
 SPRING_DTYPE = np.dtype([("tau", "<f8"), ("gR", "<f8"), ("tR", "<f8"), ("gmax", "<f8"), ("dir", "<i4"),
                          ("mode", "<i4")])
@@ -30,13 +34,16 @@ assert SPRING_DTYPE.itemsize == 40
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc -O2, no fast-math)."""
+    """Compile oracle.c into liboracle.so and liboracle_omp.so (gcc -O2, ISO C11 so that
+    no multiply-add contraction happens, no fast-math)."""
     src = os.path.join(_HERE, "oracle.c")
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+    newest = max(os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
+    for path, extra in ((_LIB_PATH, []), (_OMP_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+            tmp = path + ".tmp%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared"] + extra +
+                                  ["-o", tmp, src, "-lm"])
+            os.replace(tmp, path)
     return _LIB_PATH
 
 
@@ -59,11 +66,11 @@ class RO(C.Structure):
     _fields_ = [("G0", C.c_double), ("gref", C.c_double), ("alpha", C.c_double), ("beta", C.c_double)]
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(omp: bool = False):
+    """The single-thread oracle, or (omp=True) the OpenMP build of the same source."""
+    if omp not in _libs:
         build()
-        L = C.CDLL(_LIB_PATH)
+        L = C.CDLL(_OMP_PATH if omp else _LIB_PATH)
         dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_void_p
         L.or_shape.argtypes = [vp, vp]
         L.or_shape_dref.argtypes = [vp, vp]
@@ -97,8 +104,15 @@ def lib():
         L.or_input_velocity.argtypes = [C.POINTER(Model), C.c_int64, C.c_int]
         L.or_input_velocity.restype = C.c_double
         L.or_strain.argtypes = [C.POINTER(Model), C.c_int64, C.c_int, vp, vp]
-        _lib = L
-    return _lib
+        L.or_threads.argtypes = [C.c_int]
+        L.or_threads.restype = C.c_int
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(n: int = 0, omp: bool = True) -> int:
+    """Set (n > 0) and return the thread count of the OpenMP build (1 for the plain one)."""
+    return int(lib(omp).or_threads(int(n)))
 
 
 def _p(a: np.ndarray):
@@ -207,7 +221,8 @@ class Oracle:
 
     def __init__(self, xyz, conn, mat, materials, faces=None, face_elem=None, face_kind=None, n_springs=10,
                  dt=0.01, acc=None, tol=1e-8, max_iter=10000, f1=0.1, f2=2.5, x0_prev=True, elem_xyz=None,
-                 face_xyz=None):
+                 face_xyz=None, omp=False):
+        self.L = lib(omp)
         self.conn = np.ascontiguousarray(conn, np.int32)
         E = self.conn.shape[0]
         self.n_nodes = int(np.max(self.conn)) + 1 if xyz is None else int(np.asarray(xyz).shape[0])
@@ -239,7 +254,7 @@ class Oracle:
         self.th = np.zeros((E, 4, self.S), SPRING_DTYPE)
         self.s = State(u=_p(self.u), v=_p(self.v), a=_p(self.a), q=_p(self.q), du=_p(self.du), D=_p(self.D),
                        th=_p(self.th), step=0, iters=0, relres=0.0)
-        if lib().or_state_init(C.byref(self.m), C.byref(self.s)) != 0:
+        if self.L.or_state_init(C.byref(self.m), C.byref(self.s)) != 0:
             raise ValueError("oracle state init failed (n_springs >= 5 required)")
 
     @classmethod
@@ -257,7 +272,7 @@ class Oracle:
         return int(self.s.iters)
 
     def step(self) -> int:
-        rc = lib().or_step(C.byref(self.m), C.byref(self.s))
+        rc = self.L.or_step(C.byref(self.m), C.byref(self.s))
         if rc != 0:
             raise RuntimeError("oracle step failed: %d" % rc)
         return self.iters
@@ -267,12 +282,12 @@ class Oracle:
         x = np.ascontiguousarray(x, np.float64).reshape(self.n_nodes, 3)
         y = np.zeros_like(x)
         D = self.D if D is None else np.ascontiguousarray(D, np.float64)
-        lib().or_operator(C.byref(self.m), _p(D), code, _p(x), _p(y))
+        self.L.or_operator(C.byref(self.m), _p(D), code, _p(x), _p(y))
         return y
 
     def input_velocity(self, n: int) -> np.ndarray:
-        return np.array([lib().or_input_velocity(C.byref(self.m), int(n), c) for c in range(3)])
+        return np.array([self.L.or_input_velocity(C.byref(self.m), int(n), c) for c in range(3)])
 
     def strain(self, e: int, qp: int, u: np.ndarray) -> np.ndarray:
         u = np.ascontiguousarray(u, np.float64); eps = np.zeros(6)
-        lib().or_strain(C.byref(self.m), int(e), int(qp), _p(u), _p(eps)); return eps
+        self.L.or_strain(C.byref(self.m), int(e), int(qp), _p(u), _p(eps)); return eps

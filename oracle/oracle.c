@@ -20,6 +20,24 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Built twice from this one source: plain (single thread) and with -fopenmp.  The
+ * OpenMP pragmas only split loops whose iterations are independent (element matrices,
+ * element contributions, per-node gathers in a fixed order, per-point spring updates,
+ * elementwise vector updates); every sum keeps the order of the single-thread build,
+ * so both builds give bit-identical results. */
+int or_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 static const int EDGE[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
 static const double DLDXI[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
@@ -503,6 +521,9 @@ typedef struct {
   double *M;  /* [E][10][10] scalar mass */
   double *Cf; /* [F][18][18] dashpots */
   matc *mc;
+  /* node -> (element, local node) incidence, elements ascending: entries
+   * inc[inc_off[n] .. inc_off[n+1]) hold 10 e + a for conn[e][a] == n */
+  int64_t *inc_off, *inc;
 } opset;
 
 static void ops_build(const or_model *m, const double *D, opset *o) {
@@ -511,6 +532,17 @@ static void ops_build(const or_model *m, const double *D, opset *o) {
   o->K = (double *)malloc(sizeof(double) * 900 * (size_t)m->n_elems);
   o->M = (double *)malloc(sizeof(double) * 100 * (size_t)m->n_elems);
   o->Cf = (double *)malloc(sizeof(double) * 324 * (size_t)(m->n_faces > 0 ? m->n_faces : 1));
+  o->inc_off = (int64_t *)calloc((size_t)m->n_nodes + 1, sizeof(int64_t));
+  o->inc = (int64_t *)malloc(sizeof(int64_t) * 10 * (size_t)(m->n_elems > 0 ? m->n_elems : 1));
+  for (int64_t i = 0; i < 10 * m->n_elems; ++i) o->inc_off[m->conn[i] + 1]++;
+  for (int64_t n = 0; n < m->n_nodes; ++n) o->inc_off[n + 1] += o->inc_off[n];
+  {
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m->n_nodes > 0 ? m->n_nodes : 1));
+    memcpy(fill, o->inc_off, sizeof(int64_t) * (size_t)m->n_nodes);
+    for (int64_t i = 0; i < 10 * m->n_elems; ++i) o->inc[fill[m->conn[i]]++] = i; /* ascending e */
+    free(fill);
+  }
+#pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < m->n_elems; ++e) {
     const double(*X)[3] = (const double(*)[3])(m->X + e * 30);
     or_element_stiffness(X, (const double(*)[6][6])(D + e * 144), (double(*)[30])(o->K + e * 900));
@@ -527,29 +559,8 @@ static void ops_free(opset *o) {
   free(o->M);
   free(o->Cf);
   free(o->mc);
-}
-
-/* y += cM * (M_e x) + cK * (K_e x) for one element */
-static void elem_apply(const or_model *m, const opset *o, int64_t e, double cM, double cK, const double *x,
-                       double *y) {
-  const int32_t *cn = m->conn + e * 10;
-  double xe[30], ye[30];
-  for (int a = 0; a < 10; ++a)
-    for (int c = 0; c < 3; ++c) xe[3 * a + c] = x[(size_t)cn[a] * 3 + c];
-  const double *K = o->K + e * 900, *M = o->M + e * 100;
-  for (int i = 0; i < 30; ++i) {
-    double s = 0.0;
-    for (int j = 0; j < 30; ++j) s += K[i * 30 + j] * xe[j];
-    ye[i] = cK * s;
-  }
-  for (int a = 0; a < 10; ++a)
-    for (int c = 0; c < 3; ++c) {
-      double s = 0.0;
-      for (int b = 0; b < 10; ++b) s += M[a * 10 + b] * xe[3 * b + c];
-      ye[3 * a + c] += cM * s;
-    }
-  for (int a = 0; a < 10; ++a)
-    for (int c = 0; c < 3; ++c) y[(size_t)cn[a] * 3 + c] += ye[3 * a + c];
+  free(o->inc_off);
+  free(o->inc);
 }
 
 static void face_apply(const or_model *m, const opset *o, int64_t f, double cC, const double *x, const double *xconst,
@@ -566,16 +577,67 @@ static void face_apply(const or_model *m, const opset *o, int64_t f, double cC, 
   }
 }
 
+/* One element-level term y += cM M_e x + cK K_e x; with `rayleigh` set the coefficients
+ * are scale * (a, b) of the element's material instead (the Rayleigh part of C^n). */
+typedef struct {
+  const double *x;
+  double cM, cK, scale;
+  int rayleigh;
+} eterm;
+
+/* y += the terms, element by element in ascending order and term by term within an
+ * element -- the additions of a loop over elements applying each term in turn.  The
+ * element contributions are formed first (independently per element), then every node
+ * adds those of its elements in ascending element order, term by term, so each entry of
+ * y receives the same additions in the same order as in that loop. */
+static void elems_apply(const or_model *m, const opset *o, int nt, const eterm *t, double *y) {
+  const int64_t E = m->n_elems;
+  double *Y = (double *)malloc(sizeof(double) * 30 * (size_t)nt * (size_t)(E > 0 ? E : 1));
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < E; ++e) {
+    const matc *c = &o->mc[m->mat[e]];
+    for (int k = 0; k < nt; ++k) {
+      double *ye = Y + ((size_t)e * nt + k) * 30;
+      const double cM = t[k].rayleigh ? t[k].scale * c->ray_a : t[k].cM;
+      const double cK = t[k].rayleigh ? t[k].scale * c->ray_b : t[k].cK;
+      memset(ye, 0, sizeof(double) * 30);
+      /* y_e = cK K_e x_e + cM M_e x_e (scalar mass per displacement component) */
+      const int32_t *cn = m->conn + e * 10;
+      double xe[30];
+      for (int a = 0; a < 10; ++a)
+        for (int cc = 0; cc < 3; ++cc) xe[3 * a + cc] = t[k].x[(size_t)cn[a] * 3 + cc];
+      const double *K = o->K + e * 900, *M = o->M + e * 100;
+      for (int i = 0; i < 30; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < 30; ++j) s += K[i * 30 + j] * xe[j];
+        ye[i] = cK * s;
+      }
+      for (int a = 0; a < 10; ++a)
+        for (int cc = 0; cc < 3; ++cc) {
+          double s = 0.0;
+          for (int b = 0; b < 10; ++b) s += M[a * 10 + b] * xe[3 * b + cc];
+          ye[3 * a + cc] += cM * s;
+        }
+    }
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < m->n_nodes; ++n)
+    for (int64_t j = o->inc_off[n]; j < o->inc_off[n + 1]; ++j) {
+      const int64_t e = o->inc[j] / 10, a = o->inc[j] % 10;
+      for (int k = 0; k < nt; ++k)
+        for (int cc = 0; cc < 3; ++cc) y[(size_t)n * 3 + cc] += Y[((size_t)e * nt + k) * 30 + 3 * a + cc];
+    }
+  free(Y);
+}
+
 /* y = A x with A = 4/dt^2 M + 2/dt C^n + K^n (Eq. 1), C^n = a M + b K^n + C_b. */
 static void apply_A(const or_model *m, const opset *o, const double *x, double *y) {
   double dt = m->dt;
   memset(y, 0, sizeof(double) * 3 * (size_t)m->n_nodes);
-  for (int64_t e = 0; e < m->n_elems; ++e) {
-    const matc *c = &o->mc[m->mat[e]];
-    elem_apply(m, o, e, 4.0 / (dt * dt), 0.0, x, y);             /* 4/dt^2 M */
-    elem_apply(m, o, e, 2.0 / dt * c->ray_a, 2.0 / dt * c->ray_b, x, y); /* 2/dt (a M + b K) */
-    elem_apply(m, o, e, 0.0, 1.0, x, y);                          /* K */
-  }
+  const eterm t[3] = {{x, 4.0 / (dt * dt), 0.0, 0.0, 0}, /* 4/dt^2 M */
+                      {x, 0.0, 0.0, 2.0 / dt, 1},         /* 2/dt (a M + b K) */
+                      {x, 0.0, 1.0, 0.0, 0}};             /* K */
+  elems_apply(m, o, 3, t, y);
   for (int64_t f = 0; f < m->n_faces; ++f) face_apply(m, o, f, 2.0 / dt, x, NULL, y); /* 2/dt C_b */
 }
 
@@ -587,12 +649,14 @@ int or_operator(const or_model *m, const double *D, int which, const double *x, 
   if (which == 3) {
     apply_A(m, &o, x, y);
   } else {
-    for (int64_t e = 0; e < m->n_elems; ++e) {
-      const matc *c = &o.mc[m->mat[e]];
-      if (which == 0) elem_apply(m, &o, e, 0.0, 1.0, x, y);
-      if (which == 1) elem_apply(m, &o, e, 1.0, 0.0, x, y);
-      if (which == 4) elem_apply(m, &o, e, c->ray_a, c->ray_b, x, y);
+    eterm t = {x, 0.0, 0.0, 0.0, 0};
+    if (which == 0) t.cK = 1.0;
+    if (which == 1) t.cM = 1.0;
+    if (which == 4) {
+      t.rayleigh = 1;
+      t.scale = 1.0;
     }
+    if (which != 2) elems_apply(m, &o, 1, &t, y);
     if (which == 2)
       for (int64_t f = 0; f < m->n_faces; ++f) face_apply(m, &o, f, 1.0, x, NULL, y);
   }
@@ -645,10 +709,10 @@ int or_step(const or_model *m, or_state *s) {
 
   /* right-hand side of Eq. 1: f^n - q^{n-1} + C^n v^{n-1} + M (a^{n-1} + 4/dt v^{n-1}) */
   for (size_t i = 0; i < N3; ++i) t1[i] = s->a[i] + 4.0 / dt * s->v[i];
-  for (int64_t e = 0; e < m->n_elems; ++e) {
-    const matc *c = &o.mc[m->mat[e]];
-    elem_apply(m, &o, e, c->ray_a, c->ray_b, s->v, b); /* Rayleigh part of C^n v */
-    elem_apply(m, &o, e, 1.0, 0.0, t1, b);             /* M (a + 4/dt v) */
+  {
+    const eterm t[2] = {{s->v, 0.0, 0.0, 1.0, 1}, /* Rayleigh part of C^n v */
+                        {t1, 1.0, 0.0, 0.0, 0}};  /* M (a + 4/dt v) */
+    elems_apply(m, &o, 2, t, b);
   }
   double vin[3];
   for (int c = 0; c < 3; ++c) vin[c] = or_input_velocity(m, n, c);
@@ -661,17 +725,19 @@ int or_step(const or_model *m, or_state *s) {
   /* 3x3 block-Jacobi preconditioner: diagonal node blocks of A */
   {
     double *Jd = (double *)calloc((size_t)m->n_nodes * 9, sizeof(double));
-    for (int64_t e = 0; e < m->n_elems; ++e) {
-      const matc *c = &o.mc[m->mat[e]];
-      double cM = 4.0 / (dt * dt) + 2.0 / dt * c->ray_a, cK = 1.0 + 2.0 / dt * c->ray_b;
-      const double *K = o.K + e * 900, *M = o.M + e * 100;
-      for (int a = 0; a < 10; ++a) {
-        double *J = Jd + (size_t)m->conn[e * 10 + a] * 9;
+    /* each node adds its elements' diagonal blocks in ascending element order */
+#pragma omp parallel for schedule(static)
+    for (int64_t nd = 0; nd < m->n_nodes; ++nd)
+      for (int64_t jj = o.inc_off[nd]; jj < o.inc_off[nd + 1]; ++jj) {
+        const int64_t e = o.inc[jj] / 10, a = o.inc[jj] % 10;
+        const matc *c = &o.mc[m->mat[e]];
+        double cM = 4.0 / (dt * dt) + 2.0 / dt * c->ray_a, cK = 1.0 + 2.0 / dt * c->ray_b;
+        const double *K = o.K + e * 900, *M = o.M + e * 100;
+        double *J = Jd + (size_t)nd * 9;
         for (int i = 0; i < 3; ++i)
           for (int j = 0; j < 3; ++j)
             J[i * 3 + j] += cK * K[(3 * a + i) * 30 + 3 * a + j] + (i == j ? cM * M[a * 10 + a] : 0.0);
       }
-    }
     for (int64_t f = 0; f < m->n_faces; ++f) {
       const double *C = o.Cf + f * 324;
       for (int a = 0; a < 6; ++a) {
@@ -701,6 +767,7 @@ int or_step(const or_model *m, or_state *s) {
       rn = sqrt(dotv(N3, r, r));
       if (rn > m->tol * bn) {
         double rz = 0.0;
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < m->n_nodes; ++i)
           for (int k = 0; k < 3; ++k) {
             double sum = 0.0;
@@ -713,6 +780,7 @@ int or_step(const or_model *m, or_state *s) {
         for (int it = 1; it <= m->max_iter; ++it) {
           apply_A(m, &o, p, Ap);
           double alpha = rz / dotv(N3, p, Ap);
+#pragma omp parallel for schedule(static)
           for (size_t i = 0; i < N3; ++i) {
             x[i] += alpha * p[i];
             r[i] -= alpha * Ap[i];
@@ -723,6 +791,7 @@ int or_step(const or_model *m, or_state *s) {
             conv = 1;
             break;
           }
+#pragma omp parallel for schedule(static)
           for (int64_t i = 0; i < m->n_nodes; ++i)
             for (int k = 0; k < 3; ++k) {
               double sum = 0.0;
@@ -732,6 +801,7 @@ int or_step(const or_model *m, or_state *s) {
           double rz_new = dotv(N3, r, z);
           double beta = rz_new / rz;
           rz = rz_new;
+#pragma omp parallel for schedule(static)
           for (size_t i = 0; i < N3; ++i) p[i] = z[i] + beta * p[i];
         }
         if (!conv) status = -2;
@@ -743,7 +813,10 @@ int or_step(const or_model *m, or_state *s) {
 
   if (status == 0) {
     /* q^n = q^{n-1} + K^n du; u, v, a updates below Eq. 1 */
-    for (int64_t e = 0; e < m->n_elems; ++e) elem_apply(m, &o, e, 0.0, 1.0, x, s->q);
+    {
+      const eterm t = {x, 0.0, 1.0, 0.0, 0};
+      elems_apply(m, &o, 1, &t, s->q);
+    }
     for (size_t i = 0; i < N3; ++i) {
       double v_old = s->v[i];
       s->u[i] += x[i];
@@ -754,6 +827,7 @@ int or_step(const or_model *m, or_state *s) {
     /* multi-spring update at every integration point: D^n and theta^n (Eq. 2) */
     double *qd = (double *)malloc(sizeof(double) * 6 * S), w;
     or_spring_dirs(S, qd, &w);
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t e = 0; e < m->n_elems; ++e) {
       const matc *c = &o.mc[m->mat[e]];
       for (int qp = 0; qp < 4; ++qp) {

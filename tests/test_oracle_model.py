@@ -126,3 +126,22 @@ def test_greedy_colouring_valid_and_first_fit():
         assert all(col[f] != col[e] for f in neigh)
         earlier = {col[f] for f in neigh if f < e}
         assert all(c in earlier for c in range(col[e]))
+
+
+def test_openmp_build_is_bit_identical():
+    """The OpenMP build of the oracle (its independent element, node and spring loops split
+    over threads, every sum in the single-thread order) reproduces the single-thread build
+    bit for bit, so timing it on all host cores times the same computation."""
+    wl = small_workload(dims=(4, 3, 3), nt=40)
+    out = []
+    for omp in (False, True):
+        if omp:
+            assert oracle.threads(4) == 4
+        o = oracle.Oracle.from_workload(wl, omp=omp)
+        for _ in range(12):
+            o.step()
+        x = np.random.default_rng(1).normal(size=(o.n_nodes, 3))
+        out.append((o.u.copy(), o.q.copy(), o.D.copy(), o.th.tobytes(), o.operator("A", x), o.operator("K", x)))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b) if not isinstance(a, bytes) else a == b
+    assert (o.th["mode"] == 1).any()
