@@ -8,6 +8,11 @@ resident in HBM), dt = 0.005 s, CG tolerance 1e-8, FP64.  One benchmark step =
 one time step of the whole hot path (right-hand side, block-Jacobi set-up, PCG,
 Newmark update, multi-spring update at every integration point).
 
+Timed window: the input is a full-length record (2000 steps) tapered over 0.2 s;
+before the warm-up the model is advanced through a lead-in until the S waves have
+crossed the bedrock and the deepest soft layer (synth.lead_in_steps: 187 steps),
+so the warm-up and timed steps fall in the strong motion of the soft soil.
+
 Printed JSON line (rank 0): value = element-steps/s over all ranks (device time
 with CUDA events inside the library, all streams joined), e2e = the same metric
 through the public API with the input record copied from host and the surface
@@ -39,14 +44,19 @@ from paper_2604_02755_gb300 import dist, synth  # noqa: E402
 
 METRIC = "elem-steps/s at oracle tol"
 UNIT = "elem-steps/s"
-# FP64 ALU peak of a GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop x 2.07 GHz
-# (the 1.25 TFLOP/s nominal FP64 rate at the maximum SM clock).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# algorithmic work per unit of the two candidate dominant kernels
-EBE_FLOP_PER_ELEM = 1800.0      # y_e = A_e x_e with a dense 30 x 30 element matrix
-# ncu summary holding the spring kernel's DRAM bytes per spring (traffic scales with springs)
+# algorithmic bytes of the multi-spring update: the 40-byte state of each spring read and
+# written, 2 x 4 points x S springs x 40 B = 320 S bytes per element-step
+SPRING_STATE_BYTES_PER_SPRING = 80.0
+# the FP64-accuracy operator: 1,800 flop per element (dense 30 x 30 element matvec)
+EBE_FLOP_PER_ELEM = 1800.0
+# ncu summary holding the spring kernel's DRAM bytes and warp instructions per spring
+# (both scale with springs)
 SPRING_PROFILE = "k_springs_large_model_cut_16x16x52.md"
-SPRING_FLOP_PER_SPRING = 66.0   # gamma and dgamma (12 FMA) + D accumulation (21 FMA), transcendental work excluded
+# rated bandwidth of GB300's host link (NVLink-C2C, both directions together)
+C2C_RATED_GBPS = 900.0
+ARITHMETIC = ("FP64 state, Newmark update, outer CG and residuals; spring law (strains, power, Halley "
+              "step, tangent) in double-float (~48-bit) arithmetic on the FP32 pipes with an FP64 fallback; "
+              "inner preconditioner CG and its operator in FP32 (FP16 tangent storage with --solver fp64-ir16)")
 
 
 def profiled_bytes(name, key):
@@ -111,53 +121,78 @@ def sample_clocks_stop(proc, f, path, gpu_index=0):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def link_bandwidth(gb=2):
-    """Concurrent pinned H2D + D2H copy rate (GB/s, both directions summed), CUDA events."""
+def link_probe(sizes_mb=(256, 1024, 4096), streams=(1, 2)):
+    """Pinned host <-> HBM copy rates (GB/s, CUDA events, best of three): H2D alone, D2H
+    alone and both directions at once (bytes of both summed), for each copy size and for
+    one or two streams per direction (each stream copying its share).  Pinned buffers come
+    from cudaHostAlloc (torch pin_memory), the device buffers from the caching allocator."""
     import torch
-    n = gb << 30
-    h1 = torch.empty(n, dtype=torch.uint8, pin_memory=True)
-    h2 = torch.empty(n, dtype=torch.uint8, pin_memory=True)
-    d1 = torch.empty(n, dtype=torch.uint8, device="cuda")
-    d2 = torch.empty(n, dtype=torch.uint8, device="cuda")
-    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-    best = 0.0
-    for _ in range(3):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        s1.wait_event(e0)
-        s2.wait_event(e0)
-        with torch.cuda.stream(s1):
-            d1.copy_(h1, non_blocking=True)
-        with torch.cuda.stream(s2):
-            h2.copy_(d2, non_blocking=True)
-        j1, j2 = torch.cuda.Event(), torch.cuda.Event()
-        j1.record(s1)
-        j2.record(s2)
-        torch.cuda.current_stream().wait_event(j1)
-        torch.cuda.current_stream().wait_event(j2)
-        e1.record()
-        torch.cuda.synchronize()
-        best = max(best, 2 * n / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    nmax = max(sizes_mb) << 20
+    h1 = torch.empty(nmax, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nmax, dtype=torch.uint8, pin_memory=True)
+    d1 = torch.empty(nmax, dtype=torch.uint8, device="cuda")
+    d2 = torch.empty(nmax, dtype=torch.uint8, device="cuda")
+    ss = [torch.cuda.Stream() for _ in range(4)]
+
+    def timed(n, k, what):
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            used, moved = [], 0
+            for dirn in (("h2d", "d2h") if what == "bidir" else (what,)):
+                for j in range(k):
+                    s_ = ss[len(used)]
+                    s_.wait_event(e0)
+                    a, b = j * n // k, (j + 1) * n // k
+                    with torch.cuda.stream(s_):
+                        if dirn == "h2d":
+                            d1[a:b].copy_(h1[a:b], non_blocking=True)
+                        else:
+                            h2[a:b].copy_(d2[a:b], non_blocking=True)
+                    used.append(s_)
+                moved += n
+            for s_ in used:
+                ev = torch.cuda.Event()
+                ev.record(s_)
+                torch.cuda.current_stream().wait_event(ev)
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, moved / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        return best
+
+    out = {}
+    for mb in sizes_mb:
+        for k in streams:
+            for what in ("h2d", "d2h", "bidir"):
+                out["%s_%dMB_%ds" % (what, mb, k)] = timed(mb << 20, k, what)
     del h1, h2, d1, d2
     torch.cuda.empty_cache()
-    return best
+    best = {w: max(v for key, v in out.items() if key.startswith(w + "_")) for w in ("h2d", "d2h", "bidir")}
+    return {"best_GBps": best, "runs_GBps": out, "rated_bidir_GBps": C2C_RATED_GBPS,
+            "buffers": "cudaHostAlloc pinned (torch pin_memory) <-> device, sizes %s MB, %s stream(s) per direction"
+                       % (list(sizes_mb), list(streams))}
 
 
-def oracle_sample(steps=1, column=(0, 0, 8, 8)):
+def oracle_sample(steps=1, column=(0, 0, 8, 8), omp=False):
     """The CPU oracle on a bounded column of the large model (same spacing,
-    interface field, springs, dt and input); returns elem-steps/s and a description."""
+    interface field, springs, dt and input); returns elem-steps/s, the threads it used
+    and a description.  omp: the OpenMP build of the same oracle on all host cores."""
     import oracle
     wl = synth.large_single_model(column=column)
-    o = oracle.Oracle.from_workload(wl)
+    wl.wave = synth.main_motion_record()
+    cores = oracle.threads(os.cpu_count() or 1) if omp else 1
+    o = oracle.Oracle.from_workload(wl, omp=omp)
     t0 = time.perf_counter()
     for _ in range(steps):
         o.step()
     dt = time.perf_counter() - t0
-    desc = ("oracle (plain C, FP64, 1 thread) on a %dx%dx%d-hexahedron column of the large model "
+    desc = ("oracle (plain C, FP64, %s) on a %dx%dx%d-hexahedron column of the large model "
             "(%d elements, %d springs/point), %d step(s) from rest, %.1f s" %
-            (column[2], column[3], wl.mesh.dims[2], wl.mesh.n_elems, wl.n_springs, steps, dt))
-    return wl.mesh.n_elems * steps / dt, desc
+            ("OpenMP build, %d threads" % cores if omp else "1 thread", column[2], column[3], wl.mesh.dims[2],
+             wl.mesh.n_elems, wl.n_springs, steps, dt))
+    return wl.mesh.n_elems * steps / dt, cores, desc
 
 
 def reference_arm(args):
@@ -168,7 +203,9 @@ def reference_arm(args):
     oracle.build()
     col = (0, 0, 6, 6)
     wl = synth.large_single_model(column=col)
-    o = oracle.Oracle.from_workload(wl)
+    wl.wave = synth.main_motion_record()
+    cores = oracle.threads(os.cpu_count() or 1)
+    o = oracle.Oracle.from_workload(wl, omp=True)
     for _ in range(args.warmup):
         o.step()
     t0 = time.perf_counter()
@@ -177,7 +214,8 @@ def reference_arm(args):
     el = time.perf_counter() - t0
     v = wl.mesh.n_elems * args.steps / el
     sample = ("%d time steps of a 6x6x52-hexahedron column (%d elements, 150 springs/point) of the large model "
-              "after %d warm-up steps" % (args.steps, wl.mesh.n_elems, args.warmup))
+              "after %d warm-up steps, OpenMP build of the oracle on %d threads" % (args.steps, wl.mesh.n_elems,
+                                                                                 args.warmup, cores))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -185,7 +223,7 @@ def reference_arm(args):
                        "dt": wl.dt, "cg_tol": 1e-8, "numbering": "grid",
                        "sample": "a %dx%dx52-hexahedron column of it (%d elements) on the host cores"
                                  % (col[2], col[3], wl.mesh.n_elems)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -297,6 +335,11 @@ def main():
                          "used for profiling captures that must stay small")
     ap.add_argument("--no-stream", action="store_true", help="skip the streamed-state measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the short runs of the tiny and precision-form configurations")
+    ap.add_argument("--lead-in", type=int, default=-1,
+                    help="steps taken before the warm-up (default: the large model's lead-in into the strong "
+                         "motion, 0 for cuts and other workloads)")
     ap.add_argument("--stream-gb", type=float, default=128.0, help="spring state kept in pinned host memory (GB)")
     ap.add_argument("--ring-depth", type=int, default=12, help="device chunk buffers of the streamed state")
     ap.add_argument("--zero-copy", action="store_true",
@@ -324,9 +367,10 @@ def main():
     if args.workload == "served":
         return served(args, dd, rank, ws, local)
 
-    n_total = args.warmup + 2 * args.steps + 2
     ens = None
+    lead = 0
     if args.workload == "ensemble":
+        n_total = args.warmup + 2 * args.steps + 2
         ens = synth.ensemble_members(M=args.members, nt=max(n_total, 400),
                                      dims=tuple(args.dims) if args.dims else (40, 40, 21))
         wl = ens.member(0)
@@ -340,6 +384,13 @@ def main():
         wl.name = "cut of the single large model: %dx%dx%d hexahedra at 5 m, 150 springs" % tuple(args.dims)
     else:
         wl = synth.large_single_model()
+    if args.workload == "large":
+        # full-length record whose strong part starts after a short taper; the lead-in carries
+        # the model into the strong motion of the soft layer before warm-up and timing
+        wl.wave = synth.main_motion_record()
+        lead = args.lead_in if args.lead_in >= 0 else (0 if args.dims else synth.lead_in_steps(wl.dt))
+    elif ens is None:
+        wl.wave = synth.band_limited_wave(2, max(args.warmup + 2 * args.steps + 3, 400), wl.dt)
     if args.numbering != "grid":
         if ens is not None:
             ens.mesh = synth.renumber(ens.mesh, args.numbering, seed=9)
@@ -348,9 +399,7 @@ def main():
             wl.mesh = synth.renumber(wl.mesh, args.numbering, seed=9)
     M = len(ens.members) if ens else 1
     E = wl.mesh.n_elems * M
-    if ens is None:
-        wave = synth.band_limited_wave(2, max(n_total + 1, 400), wl.dt)
-        wl.wave = wave
+    wave = wl.wave
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     graphs = args.graphs if args.graphs >= 0 else (1 if args.workload == "tiny" else 0)
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
@@ -358,6 +407,10 @@ def main():
               pair_operator=args.pair_op, l2_prefetch=args.prefetch, spring_tile_points=args.spring_tile,
               spring_tile_blocks=args.spring_blocks, spring_tensor_cores=args.spring_tensor)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
+    t_lead = time.perf_counter()
+    if lead:
+        sim.advance(lead)
+    t_lead = time.perf_counter() - t_lead
     sim.advance(args.warmup)
     tuning = B.ns_autotune(sim.ctx) if args.autotune else None
     if tuning:  # later contexts of this run (the streamed-state legs) start from the tuned shape
@@ -368,7 +421,9 @@ def main():
     clk_path = os.path.join(tempfile.gettempdir(), "ns_clocks_%d.csv" % rank)
     proc, fh = sample_clocks_start(clk_path)
     dist.barrier(dd)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps' launches
     sim.advance(args.steps)
+    torch.cuda.nvtx.range_pop()
     dist.barrier(dd)
     clocks = sample_clocks_stop(proc, fh, clk_path, local)
     st = sim.stats()
@@ -376,46 +431,44 @@ def main():
     job_s, work = dist.reduce_time_and_work(dd, dev_s, float(E * args.steps), device="cuda")
     value = work / job_s
     launches = st["kernel_launches"] - st0["kernel_launches"]
+    first_timed = st0["steps"] + 1
+    window = {"lead_in_steps": lead, "warmup_steps": args.warmup, "timed_steps": [first_timed, st["steps"]],
+              "timed_t_s": [first_timed * wl.dt, st["steps"] * wl.dt], "lead_in_wall_s": t_lead,
+              "cg_outer_iters_per_step": st["cg_iters_total"] / args.steps,
+              "inner_iters_per_step": st["inner_iters_total"] / args.steps,
+              "springs_moved_per_step": st["spring_moved"] / args.steps,
+              "spring_reversal_rate": st["spring_reversals"] / max(st["spring_moved"], 1),
+              "spring_fp64_root_rate": st["spring_fp64_roots"] / max(st["spring_moved"], 1)}
 
-    # roofline of the dominant kernel (FP64 ALU bound)
-    traffic = None
-    if st["ms_ebe64"] >= st["ms_spring"]:
-        per = st["ms_ebe64"] / max(st["n_ebe64"], 1) / 1e3
-        flops = EBE_FLOP_PER_ELEM * E
-        kern = "k_ebe<double> (FP64 EBE operator of Eq. 1, one CG iteration)"
-        unit_desc = "%g flop/element (dense 30x30 element matvec) x %d elements" % (EBE_FLOP_PER_ELEM, E)
-    else:
-        per = st["ms_spring"] / max(st["n_spring"], 1) / 1e3
-        n_spr = 4 * E * wl.n_springs * max(st["resident_elems"], 1) / max(E, 1)
-        flops = SPRING_FLOP_PER_SPRING * n_spr
-        kern = "k_springs (multi-spring update, FP64)"
-        unit_desc = "%g flop/spring x %d springs" % (SPRING_FLOP_PER_SPRING, n_spr)
+    # roofline of the dominant kernel.  The multi-spring update (the largest share of the
+    # step) is HBM-bound by its algorithmic bytes: the 40-byte state of every spring read and
+    # written, 320 S bytes per element-step, against the measured copy bandwidth.  Its DRAM
+    # traffic and warp instructions per spring come from the ncu summary of the kernel.
+    hbm_peak = measured_peaks().get("hbm_gbs")
+    roof = None
+    if st["n_spring"] > 0:
+        per = st["ms_spring"] / st["n_spring"] / 1e3
+        n_spr = 4 * st["resident_elems"] * wl.n_springs / max(st["n_spring"] / args.steps, 1)
+        gbs = SPRING_STATE_BYTES_PER_SPRING * n_spr / per / 1e9
         bps = profiled_bytes(SPRING_PROFILE, "dram_bytes_per_spring")
-        traffic = bps * n_spr if bps else None
-    achieved = flops / per / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kern, "work_per_launch": unit_desc,
-            "avg_launch_ms": per * 1e3, "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)"}
-    if "springs" in kern:
-        # the FP64-accuracy arithmetic of the spring update runs partly in double-float
-        # arithmetic on the FP32 pipes, so its rate can pass the FP64 pipe's peak; its DRAM
-        # rate against the measured copy rate is given beside it
-        hbm_peak = measured_peaks().get("hbm_gbs")
-        bps = profiled_bytes(SPRING_PROFILE, "dram_bytes_per_spring") or 81.8
-        gbs = bps * n_spr / per / 1e9
-        roof["note"] = ("FP64-accuracy work of the spring law partly in double-float arithmetic on the FP32 pipes "
-                        "(see the spring profile: issue slots, FP64 and FMA pipes)")
-        roof["hbm"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                       "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-        # the resource that binds it: instruction issue (one warp instruction per clock on
-        # each of the 4 schedulers of the 152 SMs), from the profiled instructions per spring
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak if hbm_peak else None,
+                "traffic": bps * n_spr if bps else None,
+                "kernel": "k_springs (multi-spring update at every integration point)",
+                "work_per_launch": "320 S B per element-step: 2 x %d springs x 40 B (state read and written)" % n_spr,
+                "avg_launch_ms": per * 1e3, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per spring (%s) x springs"
+                                  % SPRING_PROFILE}
+        # what binds it: instruction issue (one warp instruction per clock on each of the 4
+        # schedulers of the 152 SMs), from the profiled warp instructions per spring
         ips = profiled_bytes(SPRING_PROFILE, "warp_instructions_per_spring")
         if ips:
-            issue_peak = 152 * 4 * 2.07
+            mhz = (clocks or {}).get("sm_mhz") or 2070.0
+            issue_peak = 152 * 4 * mhz / 1e3
             gips = ips * n_spr / per / 1e9
             roof["issue"] = {"achieved": gips, "peak": issue_peak, "unit": "G warp-instructions/s",
                              "frac": gips / issue_peak,
-                             "peak_source": "152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz (derived)",
+                             "peak_source": "152 SMs x 4 schedulers x 1 warp-instruction/clk x median SM clock (derived)",
                              "per_unit": "%g warp-instructions/spring (ncu smsp__inst_executed, spring profile)" % ips}
 
     # the HBM-bound matvec: the inner FP32 operator, per launch that did work (algorithmic
@@ -425,12 +478,17 @@ def main():
     if st["inner_iters_total"] > 0 and st["ms_ebe32"] > 0:
         bpe = 300.0 if prec == B.NS_PREC_FP64_IR16 else 468.0
         per32 = st["ms_ebe32"] / st["inner_iters_total"] / 1e3
-        hbm_peak = measured_peaks().get("hbm_gbs")
         gbs = bpe * E / per32 / 1e9
         matvec = {"kernel": "k_ebe<float> (inner FP32 EBE operator)", "bound": "hbm", "achieved": gbs,
                   "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if hbm_peak else None,
                   "bytes_per_element": bpe, "avg_active_launch_ms": per32 * 1e3,
-                  "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    ebe64 = None
+    if st["n_ebe64"] > 0:
+        per64 = st["ms_ebe64"] / st["n_ebe64"] / 1e3
+        ebe64 = {"kernel": "k_ebe<double> (FP64-accuracy operator)", "avg_launch_ms": per64 * 1e3,
+                 "achieved_TFLOPs": EBE_FLOP_PER_ELEM * E / per64 / 1e12,
+                 "flop_per_element": EBE_FLOP_PER_ELEM}
 
     # end to end through the public API: input record from host, advance, surface read-back to host
     t0 = time.perf_counter()
@@ -456,14 +514,13 @@ def main():
                          "avg_active_ms": st["ms_ebe32"] / max(st["inner_iters_total"], 1)},
                "springs": {"launches_per_step": st["n_spring"] / args.steps,
                            "avg_ms": st["ms_spring"] / max(st["n_spring"], 1)}}
-    inner_iters = st["inner_iters_last"]
-    cg_iters = st["cg_iters_total"] / args.steps
+    sim_steps = sim.stats()["steps"]
     sim.close()
     del sim
 
     stream = None
     if ws == 1 and not args.no_stream and args.workload == "large" and not args.dims:
-        link = link_bandwidth()
+        link = link_probe()
         per_elem = B.ns_state_bytes(1, wl.n_springs)
         stream_elems = int(args.stream_gb * 1e9 / per_elem)
         budget = (E - stream_elems) * per_elem
@@ -485,26 +542,53 @@ def main():
             moved = (st2["h2d_bytes"] - h0["h2d_bytes"]) + (st2["d2h_bytes"] - h0["d2h_bytes"])
             early = st2["h2d_bytes_early"] - h0["h2d_bytes_early"]
             gbs = (moved - early) / (st2["ms_stream_wall"] / 1e3) / 1e9
+            best = link["best_GBps"]["bidir"]
             return {"streamed_elems": st2["streamed_elems"], "bytes_per_step": moved / 2,
                     "early_h2d_bytes_per_step": early / 2,
-                    "stream_GBps": gbs, "link_GBps_measured": link, "frac_of_link": gbs / link,
-                    "step_ms": st2["ms_advance"] / 2, "resident_step_ms": job_s / args.steps * 1e3}
+                    "stream_GBps": gbs, "link_GBps_measured": best, "frac_of_link": gbs / best,
+                    "frac_of_rated_link": gbs / C2C_RATED_GBPS,
+                    "step_ms": st2["ms_advance"] / 2, "resident_step_ms": job_s / args.steps * 1e3,
+                    "steps": "steps 2-3 from rest (the link rate does not depend on the strain level)"}
 
         stream = streamed_run(B.NS_STREAM_RING)
         stream.update({"window": "multi-spring phase start to last D2H; H2D issued at step start (overlapping the "
-                                 "solve) excluded from the bytes", "chunk_elems": 100000, "ring_depth": ring})
+                                 "solve) excluded from the bytes", "chunk_elems": 100000, "ring_depth": ring,
+                       "link_probe": link})
         if args.zero_copy:
             zc = streamed_run(B.NS_STREAM_ZERO_COPY)
             zc["window"] = ("multi-spring phase (the kernel reads and writes the pinned host state in place); "
                             "bytes = 40 B read + 40 B written per streamed spring")
             stream["zero_copy"] = zc
 
+    # small summaries of the other single-GPU configurations (tiny plain-FP64 case, precision form)
+    others = None
+    if ws == 1 and args.workload == "large" and not args.dims and not args.no_others:
+        others = {}
+        for name, mk, solver, n_w, n_t in (("tiny_plain_fp64", synth.tiny_two_layer, B.NS_PREC_FP64, 10, 50),
+                                           ("precision_form_fp16_tangent", synth.precision_form_model,
+                                            B.NS_PREC_FP64_IR16, 3, 5)):
+            w2 = mk()
+            with B.Simulation(w2, device=local, timing=1, surface_ring_steps=n_t, precision=solver,
+                              graphs=1, x0_prev=0) as s2:
+                s2.advance(n_w)
+                B.ns_reset_stats(s2.ctx)
+                s2.advance(n_t)
+                st3 = s2.stats()
+            others[name] = {"workload": w2.name, "elements": w2.mesh.n_elems, "springs_per_point": w2.n_springs,
+                            "solver": {B.NS_PREC_FP64: "fp64-pcg", B.NS_PREC_FP64_IR16: "fp64-ir16"}[solver],
+                            "graphs": 1, "steps": [n_w + 1, n_w + n_t],
+                            "value": w2.mesh.n_elems * n_t / (st3["ms_advance"] / 1e3), "unit": UNIT,
+                            "ms_per_step": st3["ms_advance"] / n_t,
+                            "cg_iters_per_step": st3["cg_iters_total"] / n_t}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        v_cpu, desc = oracle_sample()
-        cpu = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        v_omp, cores, desc_omp = oracle_sample(steps=2, column=(0, 0, 16, 16), omp=True)
+        v_one, _, desc_one = oracle_sample(steps=1, column=(0, 0, 8, 8), omp=False)
+        cpu = {"value": v_omp, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc_omp,
+               "single_thread": {"value": v_one, "unit": UNIT, "cores": 1, "sample": desc_one}}
 
     state_gb = B.ns_state_bytes(E, wl.n_springs) / 1e9
     l2_note = ("inputs larger than L2: %.1f GB of spring state read and written per step, no flush needed" % state_gb
@@ -512,18 +596,22 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": job_s / args.steps * 1e3, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "arithmetic": ARITHMETIC,
+                "data": "synthetic",
                 "config": {"workload": wl.name, "elements": E, "nodes": wl.mesh.n_nodes * M, "members": M,
                            "springs_per_point": wl.n_springs, "dt": wl.dt, "cg_tol": 1e-8,
-                           "numbering": args.numbering, "state": "resident in HBM", "l2": l2_note,
-                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                           "numbering": args.numbering, "state": "resident in HBM (streamed form in state_stream)",
+                           "l2": l2_note, "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "input": "full-length record, 0.2 s taper" if lead else "record with 10% taper"},
+                "timed_window": window,
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "matvec_roofline": matvec,
-                "cpu_baseline": cpu,
-                "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": cg_iters,
-                "inner_iters_last_step": inner_iters, "kernels": kernels, "solver": args.solver, "graphs": graphs,
-                "staged_operator": args.stage, "inner_iters": args.inner_iters, "inner_tol": args.inner_tol, "spring_tensor_cores": args.spring_tensor, "autotune": tuning,
+                "ebe64": ebe64, "cpu_baseline": cpu,
+                "clocks": clocks, "phases_ms_per_step": phases, "cg_iters_per_step": st["cg_iters_total"] / args.steps,
+                "inner_iters_last_step": st["inner_iters_last"], "kernels": kernels, "solver": args.solver,
+                "graphs": graphs, "staged_operator": args.stage, "inner_iters": args.inner_iters,
+                "inner_tol": args.inner_tol, "spring_tensor_cores": args.spring_tensor, "autotune": tuning,
                 "pair_operator": args.pair_op, "x0": args.x0, "l2_prefetch": args.prefetch,
-                "state_stream": stream}
+                "steps_taken": sim_steps, "state_stream": stream, "other_configs": others}
         print(json.dumps(line), flush=True)
     dist.finalize(dd)
     return 0

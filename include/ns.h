@@ -105,6 +105,12 @@ typedef struct {
                                   FP64-level result) when the block holds a multiple of 16 points
                                   and S <= 256; 0 (default, measured faster on GB300):
                                   double-float sums on the FP32 pipes */
+  int32_t fault_pinned_alloc;  /* fault injection for tests (0 = off): the k-th pinned host
+                                  allocation of this context (counted from ns_create, k >= 1)
+                                  fails as if the host were out of pinned memory */
+  int32_t fault_state_copy;    /* fault injection for tests (0 = off): the k-th state-stream copy
+                                  of this context (a chunk's H2D or D2H, Alg. 3; k >= 1) fails
+                                  before it is issued, as a failed cudaMemcpyAsync would */
 } ns_config;
 
 #define NS_STREAM_RING 0
@@ -136,6 +142,11 @@ typedef struct {
                                  multi-spring phase (they overlap the solve) */
   int64_t inner_iters_total;  /* inner FP32 iterations summed since the last ns_reset_stats: the
                                  FP32 operator launches that did work (the others return at once) */
+  /* spring-update counts since the last ns_reset_stats (read when ns_advance returns) */
+  int64_t spring_moved;       /* springs whose strain changed (the others keep their state) */
+  int64_t spring_reversals;   /* of those, springs that reversed direction (Masing branch start) */
+  int64_t spring_fp64_roots;  /* springs whose skeleton root left the double-float fast path for the
+                                 FP64 one (seed not converged, step too large, argument out of range) */
 } ns_stats;
 
 /* Fill cfg with defaults: 10 springs, dt 0.01, tol 1e-8, 10000 iterations,

@@ -42,7 +42,8 @@ class ns_config(C.Structure):
                 ("wait_timeout_s", C.c_double), ("graphs", C.c_int32), ("stage_elements", C.c_int32),
                 ("l2_prefetch", C.c_int32), ("pair_operator", C.c_int32), ("stream_mode", C.c_int32),
                 ("spring_tile_points", C.c_int32), ("spring_tile_blocks", C.c_int32),
-                ("spring_tensor_cores", C.c_int32)]
+                ("spring_tensor_cores", C.c_int32), ("fault_pinned_alloc", C.c_int32),
+                ("fault_state_copy", C.c_int32)]
 
 
 class ns_material(C.Structure):
@@ -59,7 +60,8 @@ class ns_stats(C.Structure):
                 ("ms_step", C.c_double), ("n_ebe64", C.c_int64), ("n_ebe32", C.c_int64), ("n_spring", C.c_int64),
                 ("ms_ebe64", C.c_double), ("ms_ebe32", C.c_double), ("ms_spring", C.c_double),
                 ("ms_stream_wall", C.c_double), ("ms_advance", C.c_double),
-                ("h2d_bytes_early", C.c_int64), ("inner_iters_total", C.c_int64)]
+                ("h2d_bytes_early", C.c_int64), ("inner_iters_total", C.c_int64),
+                ("spring_moved", C.c_int64), ("spring_reversals", C.c_int64), ("spring_fp64_roots", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

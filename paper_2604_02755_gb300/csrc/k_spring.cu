@@ -213,7 +213,8 @@ __device__ __forceinline__ double ro_solve(bool solve, double ga, double guess, 
 // As ro_solve (solving), for ga = gah + gal > 0 given as a float pair (the usual path
 // never forms ga in FP64).
 __device__ __forceinline__ double ro_solve_pair(float gah, float gal, float guess, const MatConst &p,
-                                                const PowTab &tb, const float *__restrict__ tabf, float2 *Gp) {
+                                                const PowTab &tb, const float *__restrict__ tabf, float2 *Gp,
+                                                unsigned &ev) {
   if (!(gah > 0.0f)) {  // zero strain: zero stress, G = G0
     *Gp = split_pair(p.G0);
     return 0.0;
@@ -243,6 +244,7 @@ __device__ __forceinline__ double ro_solve_pair(float gah, float gal, float gues
     }
   }
   // the FP64 path from the seed (or from the linear bound)
+  ev |= 4u;
   const double ga = (double)gah + (double)gal;
   double tau = (t > 0.0f) ? (double)t : p.G0 * ga;
   double w = pow_pos(tau * p.itref, p.beta_ro, tb);
@@ -274,18 +276,21 @@ __device__ __forceinline__ double ro_solve_pair(float gah, float gal, float gues
 // with it are made on pair differences.  Of the increment dgamma only the sign is needed
 // unless the spring reverses: dh carries that sign (and is exactly zero for no
 // increment); when !dexact the pair dh + dl = q_k . deps is formed at a reversal.
+// ev collects what happened: 1 the spring moved, 2 it reversed, 4 its root took the FP64 path.
 __device__ __forceinline__ void pair_dot6(const float2 *__restrict__ q, const float2 *e, float &sh, float &sl);
 __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float dh, float dl, bool dexact,
                                                      const float2 *__restrict__ qk, const float2 *de,
                                                      const MatConst &p, const PowTab &tb,
                                                      const float *__restrict__ tabf, double &tau, double &gR,
-                                                     double &tR, double &gmax, int &dir, int &mode) {
+                                                     double &tR, double &gmax, int &dir, int &mode,
+                                                     unsigned &ev) {
   float2 G;
   if (dh == 0.0f) {  // no increment: only the tangent at the current state
     const double x = (mode == 0) ? tau : 0.5 * (tau - tR);
     ro_solve(false, d_abs(x), 0.0, p, tb, tabf, &G);
     return G;
   }
+  ev |= 1u;
   const int sgn = dh < 0.0f ? -1 : 1;
   bool same = true;
   if (dir == 0) {
@@ -301,6 +306,7 @@ __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float d
     mode = 1;
     dir = sgn;
     same = false;
+    ev |= 2u;
   }
   // |gamma| - gmax as a pair
   const bool gneg = gh < 0.0f;
@@ -327,7 +333,7 @@ __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float d
     xl *= 0.5f;
   }
   const bool xneg = xh < 0.0f;
-  const double f = ro_solve_pair(fabsf(xh), xneg ? -xl : xl, guess, p, tb, tabf, &G);
+  const double f = ro_solve_pair(fabsf(xh), xneg ? -xl : xl, guess, p, tb, tabf, &G, ev);
   const double fs = xneg ? -f : f;
   if (mode == 0) {
     tau = fs;
@@ -430,10 +436,12 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
                                                     int64_t base, int64_t p0, int64_t p1, double *D, int64_t epad,
                                                     double *dpts, const double *__restrict__ ptab,
                                                     const float *__restrict__ ptabf, const uint2 *__restrict__ tfrag,
-                                                    const double *__restrict__ tsc, int eps_pairs) {
+                                                    const double *__restrict__ tsc, int eps_pairs,
+                                                    unsigned long long *cnt) {
   // shared: [TP][S] tangents as float pairs (or, TC, [8][TP][stride] bf16 digit planes),
   // then [TP][12] strains as pairs
   extern __shared__ float2 Gs[];
+  __shared__ unsigned evc[3];  // the block's springs moved, reversed, with an FP64 root
   const int KS = (S + 15) >> 4, KST = tc_stride(KS);
   unsigned short *planes = reinterpret_cast<unsigned short *>(Gs);
   const PowTab tb{ptab, ptab + 128, ptab + 256, ptab + 384, __ldg(ptab + 448), __ldg(ptab + 449), __ldg(ptab + 450),
@@ -441,6 +449,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
   const int64_t pt = p0 + (int64_t)blockIdx.x * TP;
   const int np = (int)((p1 - pt) < TP ? (p1 - pt) : TP);
   const int nspr = np * S;
+  if (threadIdx.x < 3) evc[threadIdx.x] = 0u;
   // phase 0: the tile's strains and increments as float pairs (once per point, not per spring)
   float2 *Es = TC ? reinterpret_cast<float2 *>(planes + (size_t)kDigits * TP * KST) : Gs + (size_t)TP * S;
   for (int i = threadIdx.x; i < np * 12; i += blockDim.x) {
@@ -464,6 +473,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
   // division per spring
   const int dlp = (int)blockDim.x / S, dk = (int)blockDim.x - dlp * S;
   int lp = (int)threadIdx.x / S, k = (int)threadIdx.x - lp * S;
+  unsigned n_moved = 0, n_rev = 0, n_fp64 = 0;
   for (int g = threadIdx.x; g < nspr; g += blockDim.x, lp += dlp, k += dk) {
     if (k >= S) {
       k -= S;
@@ -479,8 +489,12 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
     const int64_t si = (p - base) * S + k;
     double tau = tau_a[si], gR = gR_a[si], tR = tR_a[si], gmax = gmax_a[si];
     int dir = dir_a[si], mode = mode_a[si];
+    unsigned ev = 0;
     const float2 G = spring_update_pair(gh, gl, dh, dl, !sure, q2 + 6 * k, Es + 12 * lp + 6, rp, tb, ptabf, tau, gR,
-                                        tR, gmax, dir, mode);
+                                        tR, gmax, dir, mode, ev);
+    n_moved += ev & 1u;
+    n_rev += (ev >> 1) & 1u;
+    n_fp64 += (ev >> 2) & 1u;
     if (dh != 0.0f) {
       tau_a[si] = tau;
       gR_a[si] = gR;
@@ -503,7 +517,19 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
       Gs[g] = G;  // the tangent as an unevaluated float pair for the double-float accumulation
     }
   }
+  if (cnt) {
+    n_moved = __reduce_add_sync(0xffffffffu, n_moved);
+    n_rev = __reduce_add_sync(0xffffffffu, n_rev);
+    n_fp64 = __reduce_add_sync(0xffffffffu, n_fp64);
+    if ((threadIdx.x & 31) == 0 && (n_moved | n_rev | n_fp64)) {
+      atomicAdd_block(&evc[0], n_moved);
+      atomicAdd_block(&evc[1], n_rev);
+      atomicAdd_block(&evc[2], n_fp64);
+    }
+  }
   __syncthreads();
+  if (cnt && threadIdx.x < 3 && evc[threadIdx.x])
+    atomicAdd(cnt + 3 * (blockIdx.x % kSpringCountSlots) + threadIdx.x, (unsigned long long)evc[threadIdx.x]);
   if (TC) {
     // one warp per (16-point tile, 8-column tile) of D; level by level, deepest first, each
     // level's digit-pair MMAs accumulated in two alternating sets, then folded into
@@ -645,7 +671,7 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
 #define NS_SPRINGS(MB, TC)                                                                                         \
   k_springs<MB, TC><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, \
                                              st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts,  \
-                                             tab.pow, tab.powf, tab.tfrag, tab.tsc, eps_pairs ? 1 : 0)
+                                             tab.pow, tab.powf, tab.tfrag, tab.tsc, eps_pairs ? 1 : 0, tab.cnt)
   if (tab.minb == 4) {
     if (tc)
       NS_SPRINGS(4, true);

@@ -107,6 +107,11 @@ struct ns_ctx {
   int64_t g_outer_cnt[3] = {0, 0, 0}, g_batch_cnt[3] = {0, 0, 0};
   int64_t cap_ebe32 = 0, cap_ebe64 = 0;
   ns_stats stats{};
+  // fault injection (cfg.fault_*): pinned allocations and state-stream copies made so far
+  int64_t n_pinned_allocs = 0, n_state_copies = 0;
+  // spring-update counters [kSpringCountSlots][3] (moved, reversals, FP64 roots), summed by
+  // the spring kernel since the last ns_reset_stats
+  unsigned long long *spr_cnt = nullptr;
   EventTimer timer;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
 };
@@ -161,6 +166,11 @@ template <typename T>
 int halloc(ns_ctx *c, T **p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
+  if (++c->n_pinned_allocs == c->cfg.fault_pinned_alloc) {
+    c->err = "cudaHostAlloc of " + std::to_string(n * sizeof(T)) + " bytes failed (injected fault: pinned allocation " +
+             std::to_string(c->n_pinned_allocs) + ")";
+    return NS_ERR_OOM_PINNED;
+  }
   cudaError_t e = cudaHostAlloc((void **)p, n * sizeof(T), cudaHostAllocDefault);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -434,6 +444,16 @@ int copy_soa(ns_ctx *c, const SpringSoA &dst, int64_t doff, const SpringSoA &src
   return NS_OK;
 }
 
+// A state-stream copy is about to be issued: the injected fault of cfg.fault_state_copy.
+int state_copy_fault(ns_ctx *c) {
+  if (++c->n_state_copies == c->cfg.fault_state_copy) {
+    c->err = "cudaMemcpyAsync of a state chunk failed (injected fault: state copy " + std::to_string(c->n_state_copies) +
+             ")";
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
 int64_t n_chunks(const ns_ctx *c) {
   const int64_t ns_el = c->m.E - c->E_res;
   return ns_el <= 0 ? 0 : (ns_el + c->cfg.chunk_elems - 1) / c->cfg.chunk_elems;
@@ -447,6 +467,7 @@ int issue_h2d(ns_ctx *c, int64_t k) {
   const int64_t e0 = c->E_res + k * c->cfg.chunk_elems;
   const int64_t e1 = std::min(c->m.E, e0 + c->cfg.chunk_elems);
   if (k >= R) CKC(c, cudaStreamWaitEvent(c->s_h2d, c->ev_d2h[slot], 0));
+  if (int f = state_copy_fault(c)) return f;
   int rc = copy_soa(c, c->ring[slot], 0, c->hst, (e0 - c->E_res) * S4, (e1 - e0) * S4, cudaMemcpyHostToDevice,
                     c->s_h2d);
   if (rc) return rc;
@@ -517,6 +538,7 @@ int spring_phase(ns_ctx *c) {
     if ((rc = spring_launch(c, c->ring[slot], e0, e0, e1)) != NS_OK) return rc;
     CKC(c, cudaEventRecord(c->ev_comp[slot], c->s_main));
     CKC(c, cudaStreamWaitEvent(c->s_d2h, c->ev_comp[slot], 0));
+    if ((rc = state_copy_fault(c)) != NS_OK) return rc;
     if ((rc = copy_soa(c, c->hst, (e0 - c->E_res) * S4, c->ring[slot], 0, (e1 - e0) * S4, cudaMemcpyDeviceToHost,
                        c->s_d2h)))
       return rc;
@@ -950,12 +972,13 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
   if (halloc(c, &c->sc_h, 2) || halloc(c, &c->flag_h, 1) || dalloc(c, &c->sc, 2) || dalloc(c, &c->flag_d, 1) ||
       dalloc(c, &c->op_A, 1) || dalloc(c, &c->op_A16, 1) ||
       dalloc(c, &c->op_K, 1) || dalloc(c, &c->op_M, 1) || dalloc(c, &c->op_Cr, 1) || dalloc(c, &c->op_rhs, 1) ||
-      dalloc(c, &c->mats_d, kMaxMat)) {
+      dalloc(c, &c->mats_d, kMaxMat) || dalloc(c, &c->spr_cnt, 3 * (size_t)kSpringCountSlots)) {
     g_create_err = c->err;
     ns_destroy(c);
     return NS_ERR_OOM_DEVICE;
   }
   cudaMemsetAsync(c->sc, 0, 2 * sizeof(CgScalars), c->s_main);
+  cudaMemsetAsync(c->spr_cnt, 0, 3 * kSpringCountSlots * sizeof(unsigned long long), c->s_main);
   cudaStreamSynchronize(c->s_main);
   c->sc_in = c->sc + 1;
   *c->flag_h = 0;
@@ -1115,6 +1138,7 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
   c->tab.q2 = c->q2_d;
   c->tab.S = S;
   c->tab.tp = c->cfg.spring_tile_points;
+  c->tab.cnt = c->spr_cnt;
   c->tab.minb = c->cfg.spring_tile_blocks == 4 ? 4 : 1;
   // tangent D (element SoA [84][epad]) and spring state placement
   const int64_t E = c->m.E, epad = c->m.epad;
@@ -1412,6 +1436,16 @@ int ns_advance(ns_ctx *c, int64_t nsteps) {
   if (cudaEventElapsedTime(&ms, c->ev_adv0, c->ev_adv1) == cudaSuccess) c->stats.ms_advance += ms;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) NS_SET(c, NS_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+  {
+    unsigned long long cnt[3 * kSpringCountSlots];
+    CKC(c, cudaMemcpy(cnt, c->spr_cnt, sizeof(cnt), cudaMemcpyDeviceToHost));
+    int64_t tot[3] = {0, 0, 0};
+    for (int i = 0; i < kSpringCountSlots; ++i)
+      for (int k = 0; k < 3; ++k) tot[k] += (int64_t)cnt[3 * i + k];
+    c->stats.spring_moved = tot[0];
+    c->stats.spring_reversals = tot[1];
+    c->stats.spring_fp64_roots = tot[2];
+  }
   int32_t kerr = 0;
   CKC(c, cudaMemcpy(&kerr, c->m.kerr, 4, cudaMemcpyDeviceToHost));
   if (kerr) NS_SET(c, NS_ERR_TIMEOUT, "a kernel's bounded wait for its shared-memory copies gave up");
@@ -1820,6 +1854,9 @@ int ns_reset_stats(ns_ctx *c) {
   c->stats.kernel_launches = launches;
   c->stats.resident_elems = re;
   c->stats.streamed_elems = se;
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  CKC(c, cudaMemset(c->spr_cnt, 0, 3 * kSpringCountSlots * sizeof(unsigned long long)));
   return NS_OK;
 }
 
@@ -1905,6 +1942,7 @@ void ns_destroy(ns_ctx *c) {
   dfree(c->Jinv32);
   dfree(c->rin); dfree(c->zin); dfree(c->pin); dfree(c->xin); dfree(c->Apin);
   dfree(c->sc);
+  dfree(c->spr_cnt);
   dfree(c->flag_d);
   hfree(c->sc_h);
   hfree(c->flag_h);

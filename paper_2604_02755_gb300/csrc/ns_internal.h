@@ -15,6 +15,7 @@ constexpr int kQ = 4;          // integration points per element
 constexpr int kDPack = 21;     // unique entries of a symmetric 6x6
 constexpr int kMaxMat = 1024;  // material table entries (members of a batch each bring their own)
 constexpr int kBlock = 256;
+constexpr int kSpringCountSlots = 64;  // spread of the spring kernel's counter atomics
 
 // Per-material constants derived on the host from ns_material and the config.
 struct MatConst {
@@ -226,6 +227,8 @@ struct SpringTables {
   int tc = 1;         // 1: assemble D on the tensor cores where the launch shape allows
   int tp = 0;         // integration points per block of the spring kernel (0: size heuristic)
   int minb = 1;       // register budget of the spring kernel: 1 (compiler's choice) or 4 blocks per SM
+  // counters [kSpringCountSlots][3]: springs moved, reversals, roots on the FP64 path (nullptr: none)
+  unsigned long long *cnt = nullptr;
 };
 // the spring kernel's default points per block for S springs, and whether tp is usable
 int spring_tile_default(int S);

@@ -302,14 +302,15 @@ def renumber(mesh: Mesh, how: str = "morton", seed: int = 0) -> Mesh:
 # ----------------------------------------------------------------------------- input waves
 
 def band_limited_wave(seed: int, nt: int, dt: float, f_lo: float = 0.1, f_hi: float = 2.5,
-                      peak: float = 3.0, taper: float = 0.1, components: int = 3) -> np.ndarray:
+                      peak: float = 3.0, taper: float = 0.1, components: int = 3, taper_s: float = None) -> np.ndarray:
     """Seeded Gaussian acceleration [nt, components]: N(0,1) samples, band-passed
     by zeroing DFT bins outside [f_lo, f_hi], cosine-tapered over the first and
-    last `taper` fraction, then scaled so each component's peak |a| = `peak`."""
+    last `taper` fraction (or, with taper_s, the first and last taper_s seconds),
+    then scaled so each component's peak |a| = `peak`."""
     out = np.zeros((nt, components))
     f = np.fft.rfftfreq(nt, dt)
     keep = (f >= f_lo) & (f <= f_hi)
-    nta = max(1, int(round(taper * nt)))
+    nta = max(1, int(round(taper_s / dt if taper_s is not None else taper * nt)))
     w = np.ones(nt)
     ramp = 0.5 - 0.5 * np.cos(np.pi * np.arange(nta) / nta)
     w[:nta] = ramp
@@ -375,6 +376,22 @@ def large_single_model(nt: int = 2000, seed: int = 2, n_springs: int = 150, dims
     w = band_limited_wave(seed, nt + 1, 0.005)
     return Workload("single large model 800x800x260 m, 5 m hex, 150 springs", m, two_layer_materials(0.02),
                     n_springs, 0.005, nt, w)
+
+
+def main_motion_record(seed: int = 2, nt: int = 2000, dt: float = 0.005, taper_s: float = 0.2) -> np.ndarray:
+    """Full-length input record of the large model (2000 steps of 0.005 s) whose strong
+    part starts early: the same seeded band-limited Gaussian, tapered over 0.2 s at each
+    end instead of a tenth of the record."""
+    return band_limited_wave(seed, nt + 1, dt, taper_s=taper_s)
+
+
+def lead_in_steps(dt: float, lz: float = 260.0, depth_max: float = 60.0, vs_soft: float = 150.0,
+                  vs_rock: float = 600.0, taper_s: float = 0.2) -> int:
+    """Steps until the input's S waves, past the taper, have crossed the bedrock and the
+    deepest soft layer and reached the surface: (taper + (lz - d)/Vs_rock + d/Vs_soft) / dt
+    with d the largest interface depth.  A timed window after this many steps sits in the
+    strong motion of the soft layer, not in the quiet lead-in."""
+    return int(math.ceil((taper_s + (lz - depth_max) / vs_rock + depth_max / vs_soft) / dt))
 
 
 def precision_form_model(nt: int = 3000, seed: int = 4, n_springs: int = 50, dims=(64, 64, 41),

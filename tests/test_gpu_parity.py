@@ -255,6 +255,21 @@ def test_tiny_two_layer_full_record():
     assert rel(s["u"], np.array(us)) <= 1e-6
     assert rel(s["v"], np.array(vs)) <= 1e-6
     assert np.mean(th["mode"] == o.th["mode"]) > 0.999
+    # the plain FP64 method with both sides at the paper's 1e-8, over the whole record:
+    # reported beside the 1e-12 figure (the difference is the stopping tolerance's effect)
+    o8 = oracle.Oracle.from_workload(wl, tol=1e-8)
+    us8, vs8 = [], []
+    for _ in range(nsteps):
+        o8.step()
+        us8.append(o8.u[wl.mesh.surf].copy())
+        vs8.append(o8.v[wl.mesh.surf].copy())
+    with B.Simulation(wl, surface_ring_steps=nsteps, precision=B.NS_PREC_FP64, cg_tol=1e-8) as sim:
+        sim.advance(nsteps)
+        s8 = sim.surface(1, nsteps)
+    print("tiny full record: both at 1e-12 u %.2e v %.2e; plain FP64 both at 1e-8 u %.2e v %.2e" % (
+        rel(s["u"], np.array(us)), rel(s["v"], np.array(vs)), rel(s8["u"], np.array(us8)),
+        rel(s8["v"], np.array(vs8))))
+    assert rel(s8["u"], np.array(us8)) <= 1e-3 and rel(s8["v"], np.array(vs8)) <= 1e-3
 
 
 def incident(conn, node):
@@ -410,3 +425,89 @@ def test_renumbered_mesh_parity(how):
         sim.advance(nsteps)
         s = sim.surface(1, nsteps)
     assert rel(s["u"], np.array(us)) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", ["ring-part", "ring-all", "zero-copy"])
+def test_streamed_state_matches_oracle(mode):
+    """Spring state streamed from pinned host memory (Alg. 3) against the oracle, which
+    keeps all of it in one array: part of the state through a ring of three device
+    buffers, all of it through a ring of two, and part of it updated in place in pinned
+    host memory (zero-copy)."""
+    wl = small(dims=(4, 3, 3), nt=60)
+    nsteps = 30
+    per_elem = B.ns_state_bytes(1, wl.n_springs)
+    cfg = {"ring-part": dict(device_state_budget=per_elem * 37, chunk_elems=13, ring_depth=3),
+           "ring-all": dict(device_state_budget=0, chunk_elems=29, ring_depth=2),
+           "zero-copy": dict(device_state_budget=per_elem * 37, stream_mode=B.NS_STREAM_ZERO_COPY)}[mode]
+    o = oracle.Oracle.from_workload(wl)
+    us, vs = [], []
+    with B.Simulation(wl, surface_ring_steps=nsteps, **cfg) as sim:
+        for _ in range(nsteps):
+            o.step()
+            us.append(o.u[wl.mesh.surf].copy())
+            vs.append(o.v[wl.mesh.surf].copy())
+        sim.advance(nsteps)
+        s = sim.surface(1, nsteps)
+        th, _ = sim.state()
+        st = sim.stats()
+    assert st["streamed_elems"] == wl.mesh.n_elems - (0 if mode == "ring-all" else 37)
+    assert st["h2d_bytes"] >= nsteps * st["streamed_elems"] * per_elem
+    assert rel(s["u"], np.array(us)) <= 1e-6
+    assert rel(s["v"], np.array(vs)) <= 1e-6
+    assert np.mean(th["mode"] == o.th["mode"]) > 0.999 and np.mean(th["dir"] == o.th["dir"]) > 0.999
+    assert (o.th["mode"] == 1).mean() > 0.01
+
+
+def test_main_motion_column_matches_oracle():
+    """A 3 x 3 x 52 hexahedron column of the single large model (2,808 elements, 150
+    springs per point, dt 0.005 s) driven by a full-length record through its strong
+    motion: the timed window of the benchmark starts after the S waves have crossed the
+    bedrock and the deepest soft layer (synth.lead_in_steps), and this run goes 40 steps
+    past that.  The oracle (OpenMP build, all host cores) and the benchmark's solver form
+    (flexible FP64 CG with the FP32 inner solve, started from zero) both solve to 1e-12,
+    where the answer no longer depends on the stopping tolerance; springs must have
+    reversed both on the skeleton and on Masing branches.  With both sides at the
+    paper's 1e-8 the records differ by the tolerance's own effect, reported here."""
+    wl = synth.large_single_model(column=(40, 40, 3, 3))
+    wl.wave = synth.main_motion_record()
+    nsteps = synth.lead_in_steps(wl.dt) + 40
+    surf = wl.mesh.surf
+    oracle.threads(0)
+
+    def run_oracle(tol, track):
+        o = oracle.Oracle.from_workload(wl, tol=tol, x0_prev=False, omp=True)
+        us, vs = [], []
+        skel = branch = 0
+        prev_mode, prev_gR = o.th["mode"].copy(), o.th["gR"].copy()
+        for _ in range(nsteps):
+            o.step()
+            us.append(o.u[surf].copy())
+            vs.append(o.v[surf].copy())
+            if track:
+                mode, gR = o.th["mode"], o.th["gR"]
+                skel += int(((prev_mode == 0) & (mode == 1)).sum())
+                branch += int(((prev_mode == 1) & (mode == 1) & (gR != prev_gR)).sum())
+                prev_mode, prev_gR = mode.copy(), gR.copy()
+        return o, np.array(us), np.array(vs), skel, branch
+
+    o, us, vs, skel, branch = run_oracle(1e-12, True)
+    assert skel > 0 and branch > 0, (skel, branch)
+    with B.Simulation(wl, surface_ring_steps=nsteps, precision=B.NS_PREC_FP64_IR, x0_prev=0, cg_tol=1e-12) as sim:
+        sim.advance(nsteps)
+        s = sim.surface(1, nsteps)
+        th, _ = sim.state()
+        st = sim.stats()
+    eu, ev = rel(s["u"], us), rel(s["v"], vs)
+    print("main-motion column, both at 1e-12: u %.2e v %.2e; reversals skeleton %d branch %d" % (eu, ev, skel, branch))
+    assert eu <= 1e-6 and ev <= 1e-6
+    assert np.mean(th["mode"] == o.th["mode"]) > 0.999 and np.mean(th["dir"] == o.th["dir"]) > 0.999
+    assert st["spring_reversals"] > 0
+    # both at the paper's tolerance 1e-8 (plain FP64 PCG on the GPU): the difference is the
+    # stopping tolerance's own effect on a path-dependent history, reported
+    _, us8, vs8, _, _ = run_oracle(1e-8, False)
+    with B.Simulation(wl, surface_ring_steps=nsteps, precision=B.NS_PREC_FP64, x0_prev=0, cg_tol=1e-8) as sim:
+        sim.advance(nsteps)
+        s8 = sim.surface(1, nsteps)
+    print("main-motion column, both at 1e-8: u %.2e v %.2e; oracle 1e-8 vs 1e-12: u %.2e v %.2e" % (
+        rel(s8["u"], us8), rel(s8["v"], vs8), rel(us8, us), rel(vs8, vs)))
+    assert rel(s8["u"], us8) <= 1e-3 and rel(s8["v"], vs8) <= 1e-3

@@ -81,3 +81,27 @@ def test_admission_waits_for_memory_and_streams_when_it_must():
         with pytest.raises(B.NsError) as ei:
             srv.submit(wls[0], NSTEPS)
         assert ei.value.code == -2
+
+
+def test_served_case_matches_oracle():
+    """Cases run through the server in a mix of four (atomic scatter, their kernels
+    overlapping on the device) against the FP64 oracle run on each case alone."""
+    import oracle
+    n = 60
+    wls = [(case(d, S, seed), prec) for d, S, seed, prec in CASES]
+    with B.Server(max_active=4, quantum_steps=7) as srv:
+        ids = [srv.submit(wl, n, precision=prec) for wl, prec in wls]
+        st = [srv.wait(i, 600) for i in ids]
+        got = [srv.result(i) for i in ids]
+    assert max(s["t_admit"] for s in st) < min(s["t_done"] for s in st)
+    for k in (0, 1, 2):
+        wl = wls[k][0]
+        o = oracle.Oracle.from_workload(wl)
+        us, vs = [], []
+        for _ in range(n):
+            o.step()
+            us.append(o.u[wl.mesh.surf].copy())
+            vs.append(o.v[wl.mesh.surf].copy())
+        for f, ref in (("u", np.array(us)), ("v", np.array(vs))):
+            err = np.linalg.norm(got[k][f] - ref) / np.linalg.norm(ref)
+            assert err <= 1e-6, (k, f, err)
