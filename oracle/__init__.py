@@ -104,6 +104,11 @@ def lib(omp: bool = False):
         L.or_input_velocity.argtypes = [C.POINTER(Model), C.c_int64, C.c_int]
         L.or_input_velocity.restype = C.c_double
         L.or_strain.argtypes = [C.POINTER(Model), C.c_int64, C.c_int, vp, vp]
+        L.or_coarse_map.argtypes = [C.c_int64, C.c_int64, vp, vp, vp]
+        L.or_coarse_map.restype = C.c_int64
+        L.or_p1_grads.argtypes = [vp, vp, dp]
+        L.or_coarse_operator.argtypes = [C.POINTER(Model), vp, C.c_int, C.c_int64, vp, vp, vp]
+        L.or_coarse_operator.restype = C.c_int
         L.or_threads.argtypes = [C.c_int]
         L.or_threads.restype = C.c_int
         _libs[omp] = L
@@ -208,6 +213,21 @@ def colouring(conn: np.ndarray, n_nodes: int):
     return col, nc
 
 
+def coarse_map(conn: np.ndarray, n_nodes: int):
+    """(cid [N], par [N][2], n_coarse) of the two-level preconditioner's P2 -> P1 map."""
+    conn = np.ascontiguousarray(conn, np.int32)
+    cid = np.zeros(n_nodes, np.int32); par = np.zeros((n_nodes, 2), np.int32)
+    nc = lib().or_coarse_map(conn.shape[0], int(n_nodes), _p(conn), _p(cid), _p(par))
+    if nc < 0:
+        raise ValueError("inconsistent quadratic mesh for the coarse map")
+    return cid, par, int(nc)
+
+
+def p1_grads(X):
+    X = np.ascontiguousarray(X, np.float64); g = np.zeros((4, 3)); v = C.c_double()
+    lib().or_p1_grads(_p(X), _p(g), C.byref(v)); return g, v.value
+
+
 # ------------------------------------------------------------------ model level
 
 MAT_KEYS = ("rho", "vs", "vp", "gamma_ref", "h_max", "rayleigh_h")
@@ -284,6 +304,17 @@ class Oracle:
         D = self.D if D is None else np.ascontiguousarray(D, np.float64)
         self.L.or_operator(C.byref(self.m), _p(D), code, _p(x), _p(y))
         return y
+
+    def coarse_operator(self, which: str, xc: np.ndarray, cid: np.ndarray, n_coarse: int, D=None) -> np.ndarray:
+        """y_c = Op_c x_c of the linear-element coarse model (K1, M1, Cb1 or A1)."""
+        code = {"K": 0, "M": 1, "Cb": 2, "A": 3}[which]
+        xc = np.ascontiguousarray(xc, np.float64).reshape(n_coarse, 3)
+        yc = np.zeros_like(xc)
+        D = self.D if D is None else np.ascontiguousarray(D, np.float64)
+        cid = np.ascontiguousarray(cid, np.int32)
+        if self.L.or_coarse_operator(C.byref(self.m), _p(D), code, int(n_coarse), _p(cid), _p(xc), _p(yc)) != 0:
+            raise ValueError("bad coarse operator")
+        return yc
 
     def input_velocity(self, n: int) -> np.ndarray:
         return np.array([self.L.or_input_velocity(C.byref(self.m), int(n), c) for c in range(3)])

@@ -875,3 +875,183 @@ int or_colouring(int64_t n_elems, int64_t n_nodes, const int32_t *conn, int32_t 
   free(used);
   return nc;
 }
+
+/* ------------------------------------------------------------------ two-level preconditioner pieces
+ * Sec. 2.2 names EBE-IPCG with a multigrid preconditioner after [SC14], whose details
+ * are not in the paper.  Reading: the coarse level is the linear (4-node) tetrahedral
+ * model on the same elements, reached from the quadratic model by linear interpolation
+ * P (a vertex keeps its value, an edge node takes the mean of its edge's end vertices)
+ * and its transpose; the coarse operator is the linear-element discretisation of the
+ * same equation, which for straight elements equals P^T A P. */
+
+int64_t or_coarse_map(int64_t n_elems, int64_t n_nodes, const int32_t *conn, int32_t *cid, int32_t *par) {
+  /* role of each node: 0 unseen, 1 vertex, 2 edge node */
+  int8_t *role = (int8_t *)calloc((size_t)(n_nodes > 0 ? n_nodes : 1), 1);
+  int64_t status = 0;
+  for (int64_t e = 0; e < n_elems && status == 0; ++e)
+    for (int a = 0; a < 10; ++a) {
+      const int32_t n = conn[e * 10 + a];
+      const int8_t r = a < 4 ? 1 : 2;
+      if (role[n] != 0 && role[n] != r) status = -1;
+      role[n] = r;
+    }
+  int64_t nc = 0;
+  for (int64_t n = 0; n < n_nodes; ++n) {
+    cid[n] = role[n] == 1 ? (int32_t)nc++ : -1;
+    par[2 * n] = par[2 * n + 1] = cid[n];
+  }
+  for (int64_t e = 0; e < n_elems && status == 0; ++e)
+    for (int k = 0; k < 6; ++k) {
+      const int32_t n = conn[e * 10 + 4 + k];
+      int32_t c0 = cid[conn[e * 10 + EDGE[k][0]]], c1 = cid[conn[e * 10 + EDGE[k][1]]];
+      if (c0 > c1) {
+        const int32_t t = c0;
+        c0 = c1;
+        c1 = t;
+      }
+      if (par[2 * n] == -1) {
+        par[2 * n] = c0;
+        par[2 * n + 1] = c1;
+      } else if (par[2 * n] != c0 || par[2 * n + 1] != c1) {
+        status = -1;
+      }
+    }
+  free(role);
+  return status == 0 ? nc : -1;
+}
+
+/* grad L1..L3 are the rows of J^{-1}, J = [x1 - x0, x2 - x0, x3 - x0] (columns);
+ * grad L0 = -(grad L1 + grad L2 + grad L3); V = det J / 6. */
+void or_p1_grads(const double X[4][3], double g[4][3], double *vol) {
+  double J[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) J[r][c] = X[c + 1][r] - X[0][r];
+  double Ji[3][3];
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) g[k + 1][c] = Ji[k][c];
+  for (int c = 0; c < 3; ++c) g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+  *vol = det / 6.0;
+}
+
+/* Coarse element: K1 = V B^T Dbar B (B the 6 x 12 strain matrix of the linear element,
+ * Voigt xx yy zz yz xz xy with engineering shear) and M1 = rho V (1 + delta_ab) / 20. */
+static void coarse_element(const double X[4][3], const double Dbar[6][6], double rho, double K[12][12],
+                           double M[4][4]) {
+  double g[4][3], V;
+  or_p1_grads(X, g, &V);
+  double B[6][12];
+  memset(B, 0, sizeof(B));
+  for (int a = 0; a < 4; ++a) {
+    const double gx = g[a][0], gy = g[a][1], gz = g[a][2];
+    B[0][3 * a] = gx;
+    B[1][3 * a + 1] = gy;
+    B[2][3 * a + 2] = gz;
+    B[3][3 * a + 1] = gz;
+    B[3][3 * a + 2] = gy;
+    B[4][3 * a] = gz;
+    B[4][3 * a + 2] = gx;
+    B[5][3 * a] = gy;
+    B[5][3 * a + 1] = gx;
+  }
+  for (int i = 0; i < 12; ++i)
+    for (int j = 0; j < 12; ++j) {
+      double s = 0.0;
+      for (int p = 0; p < 6; ++p)
+        for (int q = 0; q < 6; ++q) s += B[p][i] * Dbar[p][q] * B[q][j];
+      K[i][j] = V * s;
+    }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) M[a][b] = rho * V * (a == b ? 2.0 : 1.0) / 20.0;
+}
+
+/* Coarse dashpot face: (A (1 + delta_ab) / 12) rho [Vs I + (Vp - Vs) n n^T]. */
+static void coarse_face(const double FX[3][3], double rho, double vs, double vp, double C[9][9]) {
+  double a[3], b[3], n[3];
+  for (int c = 0; c < 3; ++c) {
+    a[c] = FX[1][c] - FX[0][c];
+    b[c] = FX[2][c] - FX[0][c];
+  }
+  n[0] = a[1] * b[2] - a[2] * b[1];
+  n[1] = a[2] * b[0] - a[0] * b[2];
+  n[2] = a[0] * b[1] - a[1] * b[0];
+  const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  const double area = 0.5 * len;
+  for (int c = 0; c < 3; ++c) n[c] /= len;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) {
+      const double w = area * (p == q ? 2.0 : 1.0) / 12.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          C[3 * p + i][3 * q + j] = w * rho * ((i == j ? vs : 0.0) + (vp - vs) * n[i] * n[j]);
+    }
+}
+
+int or_coarse_operator(const or_model *m, const double *D, int which, int64_t n_coarse, const int32_t *cid,
+                       const double *xc, double *yc) {
+  if (which < 0 || which > 3) return -1;
+  matc *mc = (matc *)malloc(sizeof(matc) * m->n_mat);
+  material_constants(m, mc);
+  const double dt = m->dt;
+  memset(yc, 0, sizeof(double) * 3 * (size_t)n_coarse);
+  for (int64_t e = 0; e < m->n_elems; ++e) {
+    const matc *c = &mc[m->mat[e]];
+    double X[4][3], Dbar[6][6], K[12][12], M[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) X[a][k] = m->X[e * 30 + 3 * a + k];
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < 4; ++q) s += D[((size_t)e * 4 + q) * 36 + 6 * i + j];
+        Dbar[i][j] = 0.25 * s;
+      }
+    coarse_element(X, Dbar, c->rho, K, M);
+    double cM = 0.0, cK = 0.0;
+    if (which == 0) cK = 1.0;
+    if (which == 1) cM = 1.0;
+    if (which == 3) {
+      cM = 4.0 / (dt * dt) + 2.0 / dt * c->ray_a;
+      cK = 1.0 + 2.0 / dt * c->ray_b;
+    }
+    if (which == 2) continue;
+    int32_t cn[4];
+    for (int a = 0; a < 4; ++a) cn[a] = cid[m->conn[e * 10 + a]];
+    for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int b = 0; b < 4; ++b)
+          for (int j = 0; j < 3; ++j)
+            s += (cK * K[3 * a + i][3 * b + j] + (i == j ? cM * M[a][b] : 0.0)) * xc[(size_t)cn[b] * 3 + j];
+        yc[(size_t)cn[a] * 3 + i] += s;
+      }
+  }
+  if (which == 2 || which == 3) {
+    const double cC = which == 2 ? 1.0 : 2.0 / dt;
+    for (int64_t f = 0; f < m->n_faces; ++f) {
+      const matc *c = &mc[m->fmat[f]];
+      double C[9][9];
+      coarse_face((const double(*)[3])(m->FX + f * 9), c->rho, c->vs, c->vp, C);
+      int32_t cn[3];
+      for (int p = 0; p < 3; ++p) cn[p] = cid[m->faces[f * 6 + p]];
+      for (int p = 0; p < 3; ++p)
+        for (int i = 0; i < 3; ++i) {
+          double s = 0.0;
+          for (int q = 0; q < 3; ++q)
+            for (int j = 0; j < 3; ++j) s += C[3 * p + i][3 * q + j] * xc[(size_t)cn[q] * 3 + j];
+          yc[(size_t)cn[p] * 3 + i] += cC * s;
+        }
+    }
+  }
+  free(mc);
+  return 0;
+}

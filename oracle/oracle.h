@@ -84,6 +84,25 @@ int or_state_init(const or_model *m, or_state *s);
 int or_step(const or_model *m, or_state *s);
 int or_operator(const or_model *m, const double *D, int which, const double *x, double *y);
 int or_colouring(int64_t n_elems, int64_t n_nodes, const int32_t *conn, int32_t *colour);
+
+/* --- two-level (P2 -> P1) preconditioner pieces (Sec. 2.2, after [SC14]) --------
+ * The coarse model is the linear 4-node tetrahedral model on the same elements: its
+ * nodes are the vertices of the quadratic mesh.  cid [n_nodes]: coarse index of each
+ * vertex node (vertices numbered in ascending fine-node order) or -1 for an edge node;
+ * par [n_nodes][2]: the coarse indices that interpolate the node -- (c, c) for a vertex,
+ * the two end vertices of its edge (ascending) for an edge node.  Returns the coarse node
+ * count, or -1 if a node is both a vertex and an edge node or its edge is inconsistent. */
+int64_t or_coarse_map(int64_t n_elems, int64_t n_nodes, const int32_t *conn, int32_t *cid, int32_t *par);
+/* Linear-tetrahedron gradients of the barycentric coordinates and volume. */
+void or_p1_grads(const double X[4][3], double g[4][3], double *vol);
+/* Coarse operator y_c = Op_c x_c on [n_coarse][3] vectors, element by element from the
+ * vertex coordinates: which 0 K1 (V B^T Dbar B, Dbar the mean of the element's four
+ * point tangents), 1 M1 (rho V (1 + delta_ab) / 20), 2 Cb1 (dashpots, A (1 + delta_ab)/12
+ * times rho [Vs I + (Vp - Vs) n n^T]), 3 A1 = (4/dt^2 + 2a/dt) M1 + (1 + 2b/dt) K1 +
+ * 2/dt Cb1.  For straight elements this is P^T Op P with P the linear interpolation of
+ * the vertices onto the quadratic nodes. */
+int or_coarse_operator(const or_model *m, const double *D, int which, int64_t n_coarse, const int32_t *cid,
+                       const double *xc, double *yc);
 double or_input_velocity(const or_model *m, int64_t n, int comp);
 void or_strain(const or_model *m, int64_t e, int qp, const double *u, double eps[6]);
 
