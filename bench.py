@@ -344,6 +344,11 @@ def main():
     ap.add_argument("--ring-depth", type=int, default=12, help="device chunk buffers of the streamed state")
     ap.add_argument("--zero-copy", action="store_true",
                     help="also measure the streamed state updated in place in pinned host memory (no ring)")
+    ap.add_argument("--multigrid", type=int, default=0, choices=[0, 1],
+                    help="two-level preconditioner: the inner FP32 solve starts from the interpolated solution of "
+                         "the linear-element coarse model (Sec. 2.2, after [SC14])")
+    ap.add_argument("--coarse-iters", type=int, default=20, help="multigrid: coarse PCG iterations at most")
+    ap.add_argument("--coarse-tol", type=float, default=1e-2, help="multigrid: coarse relative residual target")
     ap.add_argument("--solver", default="fp64-ir", choices=["fp64-ir", "fp64-ir16", "fp64-pcg"],
                     help="fp64-ir: FP64 flexible CG with an FP32 PCG preconditioner (the paper's precision policy); "
                          "fp64-ir16: the same with the inner operator reading D in FP16; "
@@ -406,6 +411,8 @@ def main():
               stage_elements=args.stage, inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, x0_prev=int(args.x0 == "prev"),
               pair_operator=args.pair_op, l2_prefetch=args.prefetch, spring_tile_points=args.spring_tile,
               spring_tile_blocks=args.spring_blocks, spring_tensor_cores=args.spring_tensor)
+    if args.multigrid:
+        kw.update(multigrid=1, coarse_max_iter=args.coarse_iters, coarse_tol=args.coarse_tol)
     sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
     t_lead = time.perf_counter()
     if lead:
@@ -436,6 +443,7 @@ def main():
               "timed_t_s": [first_timed * wl.dt, st["steps"] * wl.dt], "lead_in_wall_s": t_lead,
               "cg_outer_iters_per_step": st["cg_iters_total"] / args.steps,
               "inner_iters_per_step": st["inner_iters_total"] / args.steps,
+              "coarse_iters_per_step": st["coarse_iters_total"] / args.steps,
               "springs_moved_per_step": st["spring_moved"] / args.steps,
               "spring_reversal_rate": st["spring_reversals"] / max(st["spring_moved"], 1),
               "spring_fp64_root_rate": st["spring_fp64_roots"] / max(st["spring_moved"], 1)}
@@ -477,7 +485,10 @@ def main():
     matvec = None
     if st["inner_iters_total"] > 0 and st["ms_ebe32"] > 0:
         bpe = 300.0 if prec == B.NS_PREC_FP64_IR16 else 468.0
-        per32 = st["ms_ebe32"] / st["inner_iters_total"] / 1e3
+        # active launches: one per inner iteration, plus (multigrid) the residual of the
+        # interpolated start once per outer iteration
+        active = st["inner_iters_total"] + (st["cg_iters_total"] if args.multigrid else 0)
+        per32 = st["ms_ebe32"] / active / 1e3
         gbs = bpe * E / per32 / 1e9
         matvec = {"kernel": "k_ebe<float> (inner FP32 EBE operator)", "bound": "hbm", "achieved": gbs,
                   "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if hbm_peak else None,
@@ -610,6 +621,8 @@ def main():
                 "inner_iters_last_step": st["inner_iters_last"], "kernels": kernels, "solver": args.solver,
                 "graphs": graphs, "staged_operator": args.stage, "inner_iters": args.inner_iters,
                 "inner_tol": args.inner_tol, "spring_tensor_cores": args.spring_tensor, "autotune": tuning,
+                "multigrid": ({"coarse_max_iter": args.coarse_iters, "coarse_tol": args.coarse_tol}
+                              if args.multigrid else None),
                 "pair_operator": args.pair_op, "x0": args.x0, "l2_prefetch": args.prefetch,
                 "steps_taken": sim_steps, "state_stream": stream, "other_configs": others}
         print(json.dumps(line), flush=True)

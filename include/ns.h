@@ -111,6 +111,13 @@ typedef struct {
   int32_t fault_state_copy;    /* fault injection for tests (0 = off): the k-th state-stream copy
                                   of this context (a chunk's H2D or D2H, Alg. 3; k >= 1) fails
                                   before it is issued, as a failed cudaMemcpyAsync would */
+  int32_t multigrid;           /* NS_PREC_FP64_IR*: 1 = two-level preconditioner (Sec. 2.2, after
+                                  [SC14]): each outer iteration first solves the linear-element
+                                  coarse model (the vertices, P^T A P) roughly in FP32, interpolates
+                                  that solution onto the quadratic nodes and starts the inner FP32
+                                  PCG from it; one member only; 0 (default): inner PCG from zero */
+  int32_t coarse_max_iter;     /* multigrid: coarse PCG iterations per outer iteration (at most) */
+  double coarse_tol;           /* multigrid: coarse relative residual target */
 } ns_config;
 
 #define NS_STREAM_RING 0
@@ -147,6 +154,7 @@ typedef struct {
   int64_t spring_reversals;   /* of those, springs that reversed direction (Masing branch start) */
   int64_t spring_fp64_roots;  /* springs whose skeleton root left the double-float fast path for the
                                  FP64 one (seed not converged, step too large, argument out of range) */
+  int64_t coarse_iters_total; /* multigrid: coarse PCG iterations since the last ns_reset_stats */
 } ns_stats;
 
 /* Fill cfg with defaults: 10 springs, dt 0.01, tol 1e-8, 10000 iterations,
@@ -250,6 +258,13 @@ int ns_apply_operator(ns_ctx *ctx, int32_t op, const double *x, double *y);
 int ns_spring_points(ns_ctx *ctx, int64_t npts, const int32_t *mat, const double *eps, const double *deps,
                      void *theta, double *D);
 
+/* Coarse operator of the two-level preconditioner (cfg.multigrid): y_c = Op_c x_c with the
+ * linear-element model on the mesh vertices (Sec. 2.2; the coarse level of [SC14]), op one of
+ * NS_OP_K, NS_OP_M, NS_OP_CB, NS_OP_A, with the current tangent (its four-point mean per
+ * element); x_c and y_c [n_coarse][3] host buffers (FP32 arithmetic on the device, the
+ * inner solve's precision).  n_coarse must be the context's coarse node count. */
+int ns_apply_coarse_operator(ns_ctx *ctx, int32_t op, int64_t n_coarse, const double *xc, double *yc);
+
 /* Allocation-free ns_spring_points (no counterpart in the paper).  For callers that
  * must not allocate device memory at the point of the call -- e.g. a host application
  * that commits a fixed device-memory budget at start-up and forbids later allocation, or
@@ -324,6 +339,15 @@ int ns_spring_directions(int32_t S, double *q, double *w);
  * node get different colours).  colour [n_elems]; *n_colours out. */
 int ns_colour_elements(int64_t n_elems, int64_t n_nodes, const int32_t *conn, int32_t *colour,
                        int32_t *n_colours);
+
+/* Coarse level of the two-level preconditioner (Sec. 2.2): cid [n_nodes] receives the coarse
+ * index of each vertex node (vertices numbered in ascending node order) or -1 for an edge
+ * node; par [n_nodes][2] the two coarse nodes that interpolate each node (a vertex twice, an
+ * edge node its edge's end vertices, smaller first); *n_coarse the coarse node count.
+ * NS_ERR_BAD_MESH if a node is a vertex in one element and an edge node in another, or an
+ * edge node sits on two different edges. */
+int ns_coarse_map(int64_t n_elems, int64_t n_nodes, const int32_t *conn, int32_t *cid, int32_t *par,
+                  int64_t *n_coarse);
 
 /* Bytes of spring state for n_elems elements with S springs per point
  * (4 points per element, 40 bytes per spring). */

@@ -43,7 +43,8 @@ class ns_config(C.Structure):
                 ("l2_prefetch", C.c_int32), ("pair_operator", C.c_int32), ("stream_mode", C.c_int32),
                 ("spring_tile_points", C.c_int32), ("spring_tile_blocks", C.c_int32),
                 ("spring_tensor_cores", C.c_int32), ("fault_pinned_alloc", C.c_int32),
-                ("fault_state_copy", C.c_int32)]
+                ("fault_state_copy", C.c_int32), ("multigrid", C.c_int32), ("coarse_max_iter", C.c_int32),
+                ("coarse_tol", C.c_double)]
 
 
 class ns_material(C.Structure):
@@ -61,7 +62,8 @@ class ns_stats(C.Structure):
                 ("ms_ebe64", C.c_double), ("ms_ebe32", C.c_double), ("ms_spring", C.c_double),
                 ("ms_stream_wall", C.c_double), ("ms_advance", C.c_double),
                 ("h2d_bytes_early", C.c_int64), ("inner_iters_total", C.c_int64),
-                ("spring_moved", C.c_int64), ("spring_reversals", C.c_int64), ("spring_fp64_roots", C.c_int64)]
+                ("spring_moved", C.c_int64), ("spring_reversals", C.c_int64), ("spring_fp64_roots", C.c_int64),
+                ("coarse_iters_total", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,7 +114,7 @@ EXPORTED = ["ns_config_default", "ns_create", "ns_upload_mesh", "ns_set_material
             "ns_reset_stats", "ns_checkpoint_size", "ns_checkpoint", "ns_restore", "ns_destroy", "ns_last_error",
             "ns_spring_directions", "ns_colour_elements", "ns_state_bytes", "ns_spring_points_noalloc",
             "ns_spring_points_noalloc_capacity", "ns_set_members", "ns_set_member_ground_motion",
-            "ns_get_member_iters", "ns_autotune", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
+            "ns_get_member_iters", "ns_autotune", "ns_apply_coarse_operator", "ns_coarse_map", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
             "ns_server_wait", "ns_server_result", "ns_server_release", "ns_server_destroy"]
 
 _lib = None
@@ -158,6 +160,8 @@ def lib():
             "ns_set_member_ground_motion": ([vp, i32, i64, d, vp], C.c_int),
             "ns_get_member_iters": ([vp, i32, vp], C.c_int),
             "ns_autotune": ([vp, C.POINTER(ns_tuning)], C.c_int),
+            "ns_apply_coarse_operator": ([vp, i32, i64, vp, vp], C.c_int),
+            "ns_coarse_map": ([i64, i64, vp, vp, vp, C.POINTER(i64)], C.c_int),
             "ns_case_bytes": ([C.POINTER(ns_case), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
             "ns_server_create": ([C.POINTER(vp), C.POINTER(ns_server_config)], C.c_int),
             "ns_server_submit": ([vp, C.POINTER(ns_case), C.POINTER(i64)], C.c_int),
@@ -289,6 +293,24 @@ def ns_apply_operator(ctx, op, x):
     y = np.zeros_like(x)
     _check(ctx, lib().ns_apply_operator(ctx, NS_OP[op], _p(x), _p(y)))
     return y
+
+
+def ns_apply_coarse_operator(ctx, op, xc):
+    """y_c = Op_c x_c of the two-level preconditioner's coarse (linear-element) model."""
+    xc = _f64(xc).reshape(-1, 3)
+    yc = np.zeros_like(xc)
+    _check(ctx, lib().ns_apply_coarse_operator(ctx, NS_OP[op], xc.shape[0], _p(xc), _p(yc)))
+    return yc
+
+
+def ns_coarse_map(conn, n_nodes):
+    """(cid [N], par [N][2], n_coarse) of the coarse level (host-only helper)."""
+    conn = _i32(conn)
+    cid = np.zeros(int(n_nodes), np.int32); par = np.zeros((int(n_nodes), 2), np.int32); nc = C.c_int64()
+    rc = lib().ns_coarse_map(conn.shape[0], int(n_nodes), _p(conn), _p(cid), _p(par), C.byref(nc))
+    if rc != NS_OK:
+        raise NsError(rc, "coarse map failed")
+    return cid, par, nc.value
 
 
 def ns_spring_points(ctx, mat, eps, deps, theta):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libns.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CU_SOURCES = ["k_ebe.cu", "k_vec.cu", "k_spring.cu", "ns_api.cu", "ns_noalloc.cu"]
+CU_SOURCES = ["k_ebe.cu", "k_vec.cu", "k_spring.cu", "k_mg.cu", "ns_api.cu", "ns_noalloc.cu"]
 CPP_SOURCES = ["ns_host.cpp", "ns_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -81,6 +81,11 @@ struct ns_ctx {
   float *Jinv32 = nullptr;
   float *rin = nullptr, *zin = nullptr, *pin = nullptr, *xin = nullptr, *Apin = nullptr;  // inner FP32 PCG
   CgScalars *sc_in = nullptr;
+  // two-level preconditioner (cfg.multigrid): coarse level, its PCG scalars, coarse index of
+  // every node (host, for the boundary faces)
+  MgLevel mg;
+  CgScalars *sc_c = nullptr;
+  std::vector<int32_t> cid_h;
   double *eps = nullptr;
   double *part = nullptr;
   int64_t part_pap_cap = 0;
@@ -554,8 +559,77 @@ int spring_phase(ns_ctx *c) {
 }
 
 int read_scalars(ns_ctx *c) {
-  CKC(c, cudaMemcpyAsync(c->sc_h, c->sc, 2 * (size_t)c->M * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->s_main));
+  const size_t n = 2 * (size_t)c->M + (c->cfg.multigrid ? 1 : 0);
+  CKC(c, cudaMemcpyAsync(c->sc_h, c->sc, n * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->s_main));
   return sync_stream(c, c->s_main);
+}
+
+// y_c (+)= Op_c x_c over the coarse elements and (cC != 0) faces, atomic or colour by colour;
+// with dot the energy partials of the application (elements, then faces).
+int apply_mg(ns_ctx *c, const OpCoef *op, float cC, const float *x, float *y, double *dot, const int32_t *skip,
+             int *npart) {
+  const bool atomic = c->cfg.scatter == NS_SCATTER_ATOMIC;
+  int off = 0;
+  if (op) {
+    if (atomic) {
+      LAUNCH(c, launch_mg_ebe(c->m, c->mg, op, x, y, nullptr, 0, c->m.E, true, dot, skip, c->s_main));
+      off = nblk(c->m.E);
+    } else {
+      for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k) {
+        const int64_t e0 = c->m.ecol_off[k], e1 = c->m.ecol_off[k + 1];
+        LAUNCH(c, launch_mg_ebe(c->m, c->mg, op, x, y, c->m.ecol_ids, e0, e1, false, dot ? dot + off : nullptr, skip,
+                                c->s_main));
+        off += nblk(e1 - e0);
+      }
+    }
+  }
+  if (cC != 0.0f && c->m.F > 0) {
+    if (atomic) {
+      LAUNCH(c, launch_mg_faces(c->m, c->mg, c->mats_d, cC, x, y, nullptr, 0, c->m.F, true, dot ? dot + off : nullptr,
+                                skip, c->s_main));
+      off += nblk(c->m.F);
+    } else {
+      for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k) {
+        const int64_t f0 = c->m.fcol_off[k], f1 = c->m.fcol_off[k + 1];
+        LAUNCH(c, launch_mg_faces(c->m, c->mg, c->mats_d, cC, x, y, c->m.fcol_ids, f0, f1, false,
+                                  dot ? dot + off : nullptr, skip, c->s_main));
+        off += nblk(f1 - f0);
+      }
+    }
+  }
+  if (npart) *npart = off;
+  return NS_OK;
+}
+
+// Two-level start of the inner solve of one outer iteration: the coarse PCG on
+// P^T (r / ||r||) (at most coarse_max_iter iterations or to coarse_tol), its solution
+// interpolated onto the quadratic nodes as the inner solve's first iterate, the residual
+// of that iterate, and the inner scalars' initial reduction.
+int mg_start_inner(ns_ctx *c, double *pv) {
+  const int64_t N = c->m.N, Nc = c->mg.Nc;
+  const int nbc = vec_blocks(Nc), nbv = vec_blocks(N);
+  MgLevel &g = c->mg;
+  LAUNCH(c, launch_mg_restrict_init(c->r, c->sc, g, g.r, g.z, g.p, g.x, g.Ap, pv, c->s_main));
+  LAUNCH(c, launch_cg_final(pv, nbc, 3, c->sc_c, NS_FIN_INIT, c->cfg.coarse_tol, c->cfg.coarse_max_iter, c->s_main, 1,
+                            {}, c->sc));
+  const float cC = (float)(2.0 / c->cfg.dt);
+  for (int it = 0; it < c->cfg.coarse_max_iter; ++it) {
+    int np = 0, rc;
+    if ((rc = apply_mg(c, c->op_A, cC, g.p, g.Ap, c->part, &c->sc_c->done, &np)) != NS_OK) return rc;
+    LAUNCH(c, launch_cg_final(c->part, np, 1, c->sc_c, NS_FIN_PAP, c->cfg.coarse_tol, c->cfg.coarse_max_iter,
+                              c->s_main));
+    LAUNCH(c, launch_in_update(g.x, g.r, g.z, g.p, g.Ap, g.Jinv32, Nc, pv, c->sc_c, c->sc, c->s_main));
+    LAUNCH(c, launch_cg_final(pv, nbc, 2, c->sc_c, NS_FIN_UPDATE, c->cfg.coarse_tol, c->cfg.coarse_max_iter,
+                              c->s_main));
+    LAUNCH(c, launch_in_pupdate(g.p, g.z, g.Ap, Nc, c->sc_c, c->sc, c->s_main));
+  }
+  LAUNCH(c, launch_mg_prolong(g, g.x, c->xin, c->Apin, N, c->sc, c->s_main));
+  int np = 0, rc;
+  if ((rc = apply_A32(c, c->xin, c->Apin, c->part, &c->sc->done, &np)) != NS_OK) return rc;
+  LAUNCH(c, launch_mg_fine_init(c->r, c->sc, c->Jinv32, c->rin, c->zin, c->pin, c->Apin, N, pv, c->s_main));
+  LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc_in, NS_FIN_INIT, c->cfg.inner_tol, c->cfg.inner_max_iter, c->s_main, 1,
+                            {}, c->sc));
+  return NS_OK;
 }
 
 // outer solve finished for every member (scalars read back)
@@ -658,9 +732,14 @@ int solve_ir(ns_ctx *c) {
   // one outer iteration: inner FP32 solve A z ~= r from zero, then the flexible CG update
   auto outer_iteration = [&]() -> int {
     int rc;
-    LAUNCH(c, launch_in_init(c->r, c->sc, c->Jinv32, c->rin, c->zin, c->pin, c->xin, c->Apin, N, pv, c->s_main, vs));
-    LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc_in, NS_FIN_INIT, c->cfg.inner_tol, c->cfg.inner_max_iter, c->s_main,
-                              M, vm, c->sc));
+    if (c->cfg.multigrid) {
+      if ((rc = mg_start_inner(c, pv)) != NS_OK) return rc;
+    } else {
+      LAUNCH(c, launch_in_init(c->r, c->sc, c->Jinv32, c->rin, c->zin, c->pin, c->xin, c->Apin, N, pv, c->s_main,
+                               vs));
+      LAUNCH(c, launch_cg_final(pv, nbv, 3, c->sc_in, NS_FIN_INIT, c->cfg.inner_tol, c->cfg.inner_max_iter,
+                                c->s_main, M, vm, c->sc));
+    }
     for (int it = 0; it < c->cfg.inner_max_iter; ++it) {
       int np = 0;
       if ((rc = apply_A32(c, c->pin, c->Apin, c->part, skip_in, &np)) != NS_OK) return rc;
@@ -691,6 +770,7 @@ int solve_ir(ns_ctx *c) {
     int most = 0;
     for (int m = 0; m < M; ++m) most = std::max(most, c->sc_h[M + m].iters);
     inner_total += most;
+    if (c->cfg.multigrid) c->stats.coarse_iters_total += c->sc_h[2].iters;
   }
   c->stats.inner_iters_last = inner_total;
   c->stats.inner_iters_total += inner_total;
@@ -783,6 +863,24 @@ int one_step(ns_ctx *c) {
                                         c->m.fcol_off[k + 1], false, c->s_main));
     }
     LAUNCH(c, launch_invert_blocks32(Jd32, c->Jinv32, N, c->flag_d, c->s_main));
+    if (c->cfg.multigrid) {  // coarse tangent (four-point mean) and coarse block-Jacobi blocks
+      MgLevel &g = c->mg;
+      LAUNCH(c, launch_mg_dbar(c->D, g.Dbar, c->m.epad, c->m.E, c->s_main));
+      CKC(c, cudaMemsetAsync(g.Jd32, 0, sizeof(float) * 6 * g.Nc, c->s_main));
+      if (atomic) {
+        LAUNCH(c, launch_mg_jacobi(c->m, g, c->op_A, g.Jd32, nullptr, 0, c->m.E, true, c->s_main));
+        LAUNCH(c, launch_mg_jacobi_faces(c->m, g, c->mats_d, (float)(2.0 / dt), g.Jd32, nullptr, 0, c->m.F, true,
+                                         c->s_main));
+      } else {
+        for (size_t k = 0; k + 1 < c->m.ecol_off.size(); ++k)
+          LAUNCH(c, launch_mg_jacobi(c->m, g, c->op_A, g.Jd32, c->m.ecol_ids, c->m.ecol_off[k], c->m.ecol_off[k + 1],
+                                     false, c->s_main));
+        for (size_t k = 0; k + 1 < c->m.fcol_off.size(); ++k)
+          LAUNCH(c, launch_mg_jacobi_faces(c->m, g, c->mats_d, (float)(2.0 / dt), g.Jd32, c->m.fcol_ids,
+                                           c->m.fcol_off[k], c->m.fcol_off[k + 1], false, c->s_main));
+      }
+      LAUNCH(c, launch_invert_blocks32(g.Jd32, g.Jinv32, g.Nc, c->flag_d, c->s_main));
+    }
   } else {
     CKC(c, cudaMemsetAsync(c->Jd, 0, sizeof(double) * 6 * N, c->s_main));
     if (atomic) {
@@ -906,6 +1004,11 @@ void ns_config_default(ns_config *cfg) {
   cfg->spring_tile_points = 0;
   cfg->spring_tile_blocks = 1;
   cfg->spring_tensor_cores = 0;
+  cfg->fault_pinned_alloc = 0;
+  cfg->fault_state_copy = 0;
+  cfg->multigrid = 0;
+  cfg->coarse_max_iter = 20;
+  cfg->coarse_tol = 1e-2;
 }
 
 static thread_local std::string g_create_err;
@@ -929,7 +1032,9 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
       cfg->inner_max_iter < 1 || !(cfg->inner_tol > 0) ||
       (cfg->stream_mode != NS_STREAM_RING && cfg->stream_mode != NS_STREAM_ZERO_COPY) ||
       (cfg->spring_tile_points != 0 && !spring_tile_ok(cfg->spring_tile_points, cfg->n_springs)) ||
-      (cfg->spring_tile_blocks != 0 && cfg->spring_tile_blocks != 1 && cfg->spring_tile_blocks != 4)) {
+      (cfg->spring_tile_blocks != 0 && cfg->spring_tile_blocks != 1 && cfg->spring_tile_blocks != 4) ||
+      (cfg->multigrid != 0 && cfg->multigrid != 1) ||
+      (cfg->multigrid && (cfg->precision == NS_PREC_FP64 || cfg->coarse_max_iter < 1 || !(cfg->coarse_tol > 0)))) {
     g_create_err = "invalid configuration value";
     return NS_ERR_INVALID_ARG;
   }
@@ -969,7 +1074,7 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
     cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&c->ev_d2h[i], cudaEventDisableTiming);
   }
-  if (halloc(c, &c->sc_h, 2) || halloc(c, &c->flag_h, 1) || dalloc(c, &c->sc, 2) || dalloc(c, &c->flag_d, 1) ||
+  if (halloc(c, &c->sc_h, 3) || halloc(c, &c->flag_h, 1) || dalloc(c, &c->sc, 3) || dalloc(c, &c->flag_d, 1) ||
       dalloc(c, &c->op_A, 1) || dalloc(c, &c->op_A16, 1) ||
       dalloc(c, &c->op_K, 1) || dalloc(c, &c->op_M, 1) || dalloc(c, &c->op_Cr, 1) || dalloc(c, &c->op_rhs, 1) ||
       dalloc(c, &c->mats_d, kMaxMat) || dalloc(c, &c->spr_cnt, 3 * (size_t)kSpringCountSlots)) {
@@ -977,10 +1082,11 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
     ns_destroy(c);
     return NS_ERR_OOM_DEVICE;
   }
-  cudaMemsetAsync(c->sc, 0, 2 * sizeof(CgScalars), c->s_main);
+  cudaMemsetAsync(c->sc, 0, 3 * sizeof(CgScalars), c->s_main);
   cudaMemsetAsync(c->spr_cnt, 0, 3 * kSpringCountSlots * sizeof(unsigned long long), c->s_main);
   cudaStreamSynchronize(c->s_main);
   c->sc_in = c->sc + 1;
+  c->sc_c = c->sc + 2;
   *c->flag_h = 0;
   *out = c;
   return NS_OK;
@@ -1056,6 +1162,49 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
     CKC(c, cudaMemcpy(m.ecol_ids, ids.data(), E * 4, cudaMemcpyHostToDevice));
   }
   c->part_pap_cap = nblk(E) + (int64_t)nc + 64 + nblk(1) * 2;
+  if (c->cfg.multigrid) {  // coarse level of the two-level preconditioner
+    MgLevel &g = c->mg;
+    c->cid_h.assign((size_t)N, -1);
+    std::vector<int32_t> par((size_t)2 * N);
+    const int64_t Nc = host_coarse_map(E, N, conn, c->cid_h.data(), par.data());
+    if (Nc <= 0) NS_SET(c, NS_ERR_BAD_MESH, "a node is a vertex of one element and an edge node of another");
+    g.Nc = Nc;
+    std::vector<int32_t> c1((size_t)4 * m.epad, 0);
+    for (int64_t e = 0; e < E; ++e)
+      for (int a = 0; a < 4; ++a) c1[(size_t)a * m.epad + e] = c->cid_h[conn[e * 10 + a]];
+    // restriction lists: per coarse node the vertex itself, then its edge nodes in node order
+    std::vector<int64_t> rptr((size_t)Nc + 1, 0);
+    for (int64_t n = 0; n < N; ++n) {
+      if (par[2 * n] < 0) NS_SET(c, NS_ERR_BAD_MESH, "node " + std::to_string(n) + " belongs to no element");
+      rptr[par[2 * n] + 1]++;
+      if (par[2 * n + 1] != par[2 * n]) rptr[par[2 * n + 1] + 1]++;
+    }
+    for (int64_t v = 0; v < Nc; ++v) rptr[v + 1] += rptr[v];
+    std::vector<int32_t> rlist((size_t)rptr[Nc]);
+    std::vector<int64_t> fill(rptr.begin(), rptr.end() - 1);
+    for (int64_t n = 0; n < N; ++n) {
+      if (par[2 * n] == par[2 * n + 1]) {
+        rlist[fill[par[2 * n]]++] = (int32_t)n;
+      } else {
+        rlist[fill[par[2 * n]]++] = ~(int32_t)n;
+        rlist[fill[par[2 * n + 1]]++] = ~(int32_t)n;
+      }
+    }
+    if ((rc = dalloc(c, &g.conn1, c1.size())) || (rc = dalloc(c, &g.rptr, rptr.size())) ||
+        (rc = dalloc(c, &g.rlist, std::max<size_t>(rlist.size(), 1))) || (rc = dalloc(c, &g.par, (size_t)N)) ||
+        (rc = dalloc(c, &g.Dbar, 21 * (size_t)m.epad)) || (rc = dalloc(c, &g.Jd32, 6 * (size_t)Nc)) ||
+        (rc = dalloc(c, &g.Jinv32, 6 * (size_t)Nc)) || (rc = dalloc(c, &g.x, 4 * (size_t)Nc)) ||
+        (rc = dalloc(c, &g.r, 4 * (size_t)Nc)) || (rc = dalloc(c, &g.z, 4 * (size_t)Nc)) ||
+        (rc = dalloc(c, &g.p, 4 * (size_t)Nc)) || (rc = dalloc(c, &g.Ap, 4 * (size_t)Nc)))
+      return rc;
+    CKC(c, cudaMemcpy(g.conn1, c1.data(), c1.size() * 4, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(g.rptr, rptr.data(), rptr.size() * 8, cudaMemcpyHostToDevice));
+    if (!rlist.empty()) CKC(c, cudaMemcpy(g.rlist, rlist.data(), rlist.size() * 4, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(g.par, par.data(), par.size() * 4, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemsetAsync(g.Dbar, 0, 21 * m.epad * 4, c->s_main));
+    for (float *x : {g.x, g.r, g.z, g.p, g.Ap}) CKC(c, cudaMemsetAsync(x, 0, 16 * Nc, c->s_main));
+    CKC(c, cudaStreamSynchronize(c->s_main));
+  }
   c->has_mesh = true;
   return NS_OK;
 }
@@ -1226,6 +1375,17 @@ int ns_set_boundary(ns_ctx *c, int64_t F, const int32_t *faces, const int32_t *f
   if (F > 0) CKC(c, cudaMemcpy(m.fkind, face_kind, F * 4, cudaMemcpyHostToDevice));
   if (Ns > 0) CKC(c, cudaMemcpy(m.surf, surf, Ns * 4, cudaMemcpyHostToDevice));
   LAUNCH(c, launch_face_geometry(m, c->xyz_d, c->s_main));
+  if (c->cfg.multigrid) {
+    std::vector<int32_t> cf((size_t)3 * m.fpad, 0);
+    for (int64_t f = 0; f < F; ++f)
+      for (int a = 0; a < 3; ++a) {
+        const int32_t v = c->cid_h[faces[f * 6 + a]];
+        if (v < 0) NS_SET(c, NS_ERR_BAD_MESH, "a boundary face vertex is an edge node of the mesh");
+        cf[(size_t)a * m.fpad + f] = v;
+      }
+    if ((rc = dalloc(c, &c->mg.cfnode, cf.size()))) return rc;
+    CKC(c, cudaMemcpy(c->mg.cfnode, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice));
+  }
   CKC(c, cudaStreamSynchronize(c->s_main));
   if (c->cfg.scatter == NS_SCATTER_COLOUR && F > 0) {
     // greedy colouring of the faces (6 nodes each) in face order
@@ -1305,6 +1465,7 @@ int ns_set_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t 
   if (!c->has_mesh || !c->has_bnd) NS_SET(c, NS_ERR_STATE, "upload the mesh and the boundary before the members");
   if (c->has_motion || c->step > 0 || c->M > 1) NS_SET(c, NS_ERR_STATE, "members must be set before the ground motion");
   if (c->cfg.scatter != NS_SCATTER_ATOMIC) NS_SET(c, NS_ERR_INVALID_ARG, "members need the atomic scatter");
+  if (c->cfg.multigrid) NS_SET(c, NS_ERR_INVALID_ARG, "the two-level preconditioner serves one member only");
   if (M < 1 || M > 65536 || !elem_off || !node_off) NS_SET(c, NS_ERR_INVALID_ARG, "bad member count");
   const DevMesh &m = c->m;
   if (elem_off[0] != 0 || elem_off[M] != m.E || node_off[0] != 0 || node_off[M] != m.N)
@@ -1647,6 +1808,31 @@ int ns_apply_operator(ns_ctx *c, int32_t op, const double *x, double *y) {
   return NS_OK;
 }
 
+int ns_apply_coarse_operator(ns_ctx *c, int32_t op, int64_t nc, const double *xc, double *yc) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mesh || !c->has_mat || !c->has_bnd) NS_SET(c, NS_ERR_STATE, "mesh, materials and boundary required");
+  if (!c->cfg.multigrid) NS_SET(c, NS_ERR_STATE, "the context has no coarse level (cfg.multigrid = 0)");
+  if (!xc || !yc || nc != c->mg.Nc || (op != NS_OP_K && op != NS_OP_M && op != NS_OP_CB && op != NS_OP_A))
+    NS_SET(c, NS_ERR_INVALID_ARG, "bad operator, coarse size or null buffer");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  std::vector<float> x4((size_t)4 * nc, 0.0f), y4((size_t)4 * nc);
+  for (int64_t i = 0; i < nc; ++i)
+    for (int k = 0; k < 3; ++k) x4[4 * i + k] = (float)xc[3 * i + k];
+  MgLevel &g = c->mg;
+  CKC(c, cudaMemcpy(g.p, x4.data(), x4.size() * 4, cudaMemcpyHostToDevice));
+  CKC(c, cudaMemsetAsync(g.Ap, 0, x4.size() * 4, c->s_main));
+  LAUNCH(c, launch_mg_dbar(c->D, g.Dbar, c->m.epad, c->m.E, c->s_main));  // D may have been written
+  const OpCoef *oc = op == NS_OP_K ? c->op_K : op == NS_OP_M ? c->op_M : op == NS_OP_A ? c->op_A : nullptr;
+  const float cC = op == NS_OP_CB ? 1.0f : op == NS_OP_A ? (float)(2.0 / c->cfg.dt) : 0.0f;
+  if ((rc = apply_mg(c, oc, cC, g.p, g.Ap, nullptr, nullptr, nullptr)) != NS_OK) return rc;
+  if ((rc = sync_stream(c, c->s_main)) != NS_OK) return rc;
+  CKC(c, cudaMemcpy(y4.data(), g.Ap, y4.size() * 4, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < nc; ++i)
+    for (int k = 0; k < 3; ++k) yc[3 * i + k] = y4[4 * i + k];
+  return NS_OK;
+}
+
 int ns_spring_points(ns_ctx *c, int64_t npts, const int32_t *mat, const double *eps, const double *deps, void *theta,
                      double *D) {
   if (!c) return NS_ERR_INVALID_ARG;
@@ -1943,6 +2129,9 @@ void ns_destroy(ns_ctx *c) {
   dfree(c->rin); dfree(c->zin); dfree(c->pin); dfree(c->xin); dfree(c->Apin);
   dfree(c->sc);
   dfree(c->spr_cnt);
+  dfree(c->mg.conn1); dfree(c->mg.cfnode); dfree(c->mg.rptr); dfree(c->mg.rlist); dfree(c->mg.par);
+  dfree(c->mg.Dbar); dfree(c->mg.Jd32); dfree(c->mg.Jinv32);
+  dfree(c->mg.x); dfree(c->mg.r); dfree(c->mg.z); dfree(c->mg.p); dfree(c->mg.Ap);
   dfree(c->flag_d);
   hfree(c->sc_h);
   hfree(c->flag_h);
@@ -1985,5 +2174,15 @@ int ns_colour_elements(int64_t E, int64_t N, const int32_t *conn, int32_t *colou
 }
 
 int64_t ns_state_bytes(int64_t E, int32_t S) { return E * 4 * (int64_t)S * 40; }
+
+int ns_coarse_map(int64_t E, int64_t N, const int32_t *conn, int32_t *cid, int32_t *par, int64_t *nc) {
+  if (E < 0 || N <= 0 || !conn || !cid || !par || !nc) return NS_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < 10 * E; ++i)
+    if (conn[i] < 0 || conn[i] >= N) return NS_ERR_BAD_MESH;
+  const int64_t r = host_coarse_map(E, N, conn, cid, par);
+  if (r < 0) return NS_ERR_BAD_MESH;
+  *nc = r;
+  return NS_OK;
+}
 
 }  // extern "C"

@@ -126,6 +126,41 @@ int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, i
   return 0;
 }
 
+// Coarse level of the two-level preconditioner: the vertices of the quadratic mesh, numbered
+// in ascending node order; every node is interpolated from two coarse nodes (a vertex twice,
+// an edge node from its edge's end vertices, smaller index first).  Fails (-1) when a node
+// is a vertex of one element and an edge node of another, or an edge node is listed under
+// two different edges.
+int64_t host_coarse_map(int64_t E, int64_t N, const int32_t *conn, int32_t *cid, int32_t *par) {
+  static const int kEdge[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
+  std::vector<uint8_t> kind((size_t)N, 0);  // 1 vertex, 2 edge node
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 10; ++a) {
+      uint8_t &k = kind[(size_t)conn[e * 10 + a]];
+      const uint8_t want = a < 4 ? 1 : 2;
+      if (k && k != want) return -1;
+      k = want;
+    }
+  int64_t nc = 0;
+  for (int64_t n = 0; n < N; ++n) {
+    cid[n] = kind[(size_t)n] == 1 ? (int32_t)(nc++) : -1;
+    par[2 * n] = par[2 * n + 1] = cid[n];
+  }
+  for (int64_t e = 0; e < E; ++e)
+    for (int k = 0; k < 6; ++k) {
+      const int64_t n = conn[e * 10 + 4 + k];
+      const int32_t a = cid[conn[e * 10 + kEdge[k][0]]], b = cid[conn[e * 10 + kEdge[k][1]]];
+      const int32_t lo = a < b ? a : b, hi = a < b ? b : a;
+      if (par[2 * n] < 0) {
+        par[2 * n] = lo;
+        par[2 * n + 1] = hi;
+      } else if (par[2 * n] != lo || par[2 * n + 1] != hi) {
+        return -1;
+      }
+    }
+  return nc;
+}
+
 // Derived constants: G0 = rho Vs^2, bulk Kb = rho (Vp^2 - 4/3 Vs^2); RO exponent
 // beta = 2 pi h_max / (2 - pi h_max) (loop damping tends to h_max), alpha = 2^beta
 // (secant G0/2 at gamma_ref); Rayleigh a = 2 h w1 w2/(w1 + w2), b = 2 h/(w1 + w2).

@@ -100,6 +100,19 @@ struct PartMap {
   int32_t base2 = 0;
 };
 
+// Coarse level of the two-level preconditioner (linear tetrahedra on the vertices).
+struct MgLevel {
+  int64_t Nc = 0;
+  int32_t *conn1 = nullptr;   // [4][epad] coarse index of each element vertex
+  int32_t *cfnode = nullptr;  // [3][fpad] coarse index of each boundary-face vertex
+  int64_t *rptr = nullptr;    // [Nc + 1] restriction lists
+  int32_t *rlist = nullptr;   // fine nodes gathered into each coarse node: n (weight 1) or ~n (edge, 1/2)
+  int2 *par = nullptr;        // [N] the two coarse nodes that interpolate each fine node
+  float *Dbar = nullptr;      // [21][epad] mean of the element's four point tangents
+  float *Jd32 = nullptr, *Jinv32 = nullptr;  // [Nc][6] coarse diagonal blocks and their inverses
+  float *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;  // coarse PCG [Nc][4]
+};
+
 // ------------------------------------------------------------------ launchers (k_*.cu)
 // All return cudaGetLastError() of their launch.
 cudaError_t launch_geometry(const DevMesh &m, const double *xyz, int32_t *bad, cudaStream_t s);
@@ -156,6 +169,29 @@ cudaError_t launch_invert_blocks32(const float *Jd, float *Jinv32, int64_t N, in
 // arithmetic: out float2 [E][4][12] (eps 6, deps 6 per point)
 cudaError_t launch_strain_pairs(const DevMesh &m, const double *u, const double *du, void *out, int64_t e0, int64_t e1,
                                 cudaStream_t s);
+
+// ------------------------------------------------------------------ k_mg.cu (two-level preconditioner)
+cudaError_t launch_mg_dbar(const double *D, float *Dbar, int64_t epad, int64_t E, cudaStream_t s);
+cudaError_t launch_mg_jacobi(const DevMesh &m, const MgLevel &c, const OpCoef *op, float *Jd, const int32_t *ids,
+                             int64_t e0, int64_t e1, bool atomic, cudaStream_t s);
+cudaError_t launch_mg_jacobi_faces(const DevMesh &m, const MgLevel &c, const MatConst *mc, float cC, float *Jd,
+                                   const int32_t *ids, int64_t f0, int64_t f1, bool atomic, cudaStream_t s);
+// y_c += (kK K1 + mK M1) x_c (coefficients per material from op); dot: block partials of x_e . y_e
+cudaError_t launch_mg_ebe(const DevMesh &m, const MgLevel &c, const OpCoef *op, const float *x, float *y,
+                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
+                          cudaStream_t s);
+cudaError_t launch_mg_faces(const DevMesh &m, const MgLevel &c, const MatConst *mc, float cC, const float *x, float *y,
+                            const int32_t *ids, int64_t f0, int64_t f1, bool atomic, double *dot, const int32_t *skip,
+                            cudaStream_t s);
+// r_c = P^T (r / ||r||) and the start of the coarse PCG (3 partial sets into part)
+cudaError_t launch_mg_restrict_init(const double *r, const CgScalars *so, const MgLevel &c, float *rc, float *zc,
+                                    float *pc, float *xc, float *Apc, double *part, cudaStream_t s);
+// x_in = P x_c, Ap_in = 0
+cudaError_t launch_mg_prolong(const MgLevel &c, const float *xc, float *xin, float *Apin, int64_t N,
+                              const CgScalars *so, cudaStream_t s);
+// start of the fine inner PCG from x_in (Ap_in holds A x_in): 3 partial sets into part
+cudaError_t launch_mg_fine_init(const double *r, const CgScalars *so, const float *J, float *rin, float *zin,
+                                float *pin, float *Apin, int64_t N, double *part, cudaStream_t s);
 
 // ------------------------------------------------------------------ k_vec.cu
 cudaError_t launch_fill(double *x, double v, int64_t n, cudaStream_t s);
@@ -267,6 +303,8 @@ int ctx_sync_main(ns_ctx *c);                       // bounded wait for the cont
 // ------------------------------------------------------------------ ns_host.cpp
 int host_spring_directions(int S, double *q, double *w);
 int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, int32_t *nc);
+// coarse (vertex) numbering and interpolation parents of every node; returns the coarse count or -1
+int64_t host_coarse_map(int64_t E, int64_t N, const int32_t *conn, int32_t *cid, int32_t *par);
 void host_material_constants(const ns_material &m, double f1, double f2, MatConst *out);
 void host_pow_tables(double *out);   // kPowTabLen entries
 void host_powf_tables(float *out);   // kPowFLen entries (df64.cuh)

@@ -82,3 +82,28 @@ def test_invalid_config_rejected_before_device_use(bad):
     with pytest.raises(binding.NsError) as ei:
         binding.ns_create(binding.ns_config_default(**bad))
     assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("dims", [(3, 2, 2), (6, 5, 4)])
+def test_coarse_map_bit_exact_with_oracle(dims):
+    """The two-level preconditioner's P2 -> P1 map (host code of the library) equals the
+    oracle's independent derivation index for index."""
+    m = synth.kuhn_box(*dims, 10.0 * dims[0], 10.0 * dims[1], 10.0 * dims[2], jitter=0.1, seed=4)
+    cg, pg, ncg = binding.ns_coarse_map(m.conn, m.n_nodes)
+    co, po, nco = oracle.coarse_map(m.conn, m.n_nodes)
+    assert ncg == nco and np.array_equal(cg, co) and np.array_equal(pg, po)
+    bad = m.conn.copy()
+    bad[0, 4], bad[0, 5] = bad[0, 5], bad[0, 4]
+    with pytest.raises(binding.NsError) as ei:
+        binding.ns_coarse_map(bad, m.n_nodes)
+    assert ei.value.code == -5
+
+
+@pytest.mark.parametrize("bad", [dict(multigrid=1), dict(multigrid=2, precision=1),
+                                 dict(multigrid=1, precision=1, coarse_max_iter=0),
+                                 dict(multigrid=1, precision=1, coarse_tol=0.0)])
+def test_invalid_multigrid_config_rejected(bad):
+    """The two-level preconditioner needs a flexible solver form and sane coarse limits."""
+    with pytest.raises(binding.NsError) as ei:
+        binding.ns_create(binding.ns_config_default(**bad))
+    assert ei.value.code == -1
