@@ -297,6 +297,8 @@ def main():
                          "precision-form model; ensemble: --members cases on a shared 201,600-element mesh "
                          "advanced together; tiny: the 3,600-element two-layer case")
     ap.add_argument("--members", type=int, default=64, help="members of the ensemble workload")
+    ap.add_argument("--union", action="store_true",
+                    help="ensemble: store the disjoint union of the members' mesh copies instead of one shared mesh")
     ap.add_argument("--stage", type=int, default=0, choices=[0, 1],
                     help="FP32 inner operator: stage element tiles in shared memory with bulk copies (1) or "
                          "per-thread loads (0)")
@@ -413,7 +415,7 @@ def main():
               spring_tile_blocks=args.spring_blocks, spring_tensor_cores=args.spring_tensor)
     if args.multigrid:
         kw.update(multigrid=1, coarse_max_iter=args.coarse_iters, coarse_tol=args.coarse_tol)
-    sim = B.BatchSimulation(ens, **kw) if ens else B.Simulation(wl, **kw)
+    sim = B.BatchSimulation(ens, shared=not args.union, **kw) if ens else B.Simulation(wl, **kw)
     t_lead = time.perf_counter()
     if lead:
         sim.advance(lead)
@@ -612,6 +614,9 @@ def main():
                 "config": {"workload": wl.name, "elements": E, "nodes": wl.mesh.n_nodes * M, "members": M,
                            "springs_per_point": wl.n_springs, "dt": wl.dt, "cg_tol": 1e-8,
                            "numbering": args.numbering, "state": "resident in HBM (streamed form in state_stream)",
+                           "mesh_storage": (None if ens is None else
+                                            "disjoint union of member copies" if args.union else
+                                            "one shared mesh (connectivity and geometry stored once)"),
                            "l2": l2_note, "parallelism": "replicas" if ws > 1 else "single GPU",
                            "input": "full-length record, 0.2 s taper" if lead else "record with 10% taper"},
                 "timed_window": window,

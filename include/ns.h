@@ -118,6 +118,16 @@ typedef struct {
                                   PCG from it; one member only; 0 (default): inner PCG from zero */
   int32_t coarse_max_iter;     /* multigrid: coarse PCG iterations per outer iteration (at most) */
   double coarse_tol;           /* multigrid: coarse relative residual target */
+  int32_t shared_members;      /* M > 1: a batch of M members on ONE mesh (Sec. 2.2, Alg. 4: the
+                                  problem sets share the mesh).  ns_upload_mesh and ns_set_boundary
+                                  then take the shared mesh once; its connectivity and geometry are
+                                  stored once and read by every member, while tangent, spring state,
+                                  materials and node vectors are per member, member after member
+                                  (member k: elements [k E, (k+1) E), nodes [k N, (k+1) N), surface
+                                  rows [k Ns, (k+1) Ns), material table entry mat[e] + k (1 +
+                                  max mat)).  The members are set by ns_set_boundary (no
+                                  ns_set_members); each solves its own CG.  Atomic scatter, no
+                                  multigrid.  0 or 1: one model */
 } ns_config;
 
 #define NS_STREAM_RING 0

@@ -44,7 +44,7 @@ class ns_config(C.Structure):
                 ("spring_tile_points", C.c_int32), ("spring_tile_blocks", C.c_int32),
                 ("spring_tensor_cores", C.c_int32), ("fault_pinned_alloc", C.c_int32),
                 ("fault_state_copy", C.c_int32), ("multigrid", C.c_int32), ("coarse_max_iter", C.c_int32),
-                ("coarse_tol", C.c_double)]
+                ("coarse_tol", C.c_double), ("shared_members", C.c_int32)]
 
 
 class ns_material(C.Structure):
@@ -456,27 +456,41 @@ class Simulation:
 
 class BatchSimulation(Simulation):
     """Members advanced together in one context (synth.Ensemble-like: one mesh shared by
-    all members, per-member materials and waves).  The context holds the disjoint union
-    of M copies of the mesh (synth.union_of_copies); member m's surface response is
-    rows [m * n_surf, (m + 1) * n_surf) of the context's surface record."""
+    all members, per-member materials and waves).  shared=True (default): the context
+    stores the mesh once (ns_config.shared_members = M) and keeps per member only the
+    tangent, spring state, materials and node vectors; shared=False: it holds the disjoint
+    union of M copies of the mesh (synth.union_of_copies, ns_set_members).  Either way
+    member m's surface response is rows [m * n_surf, (m + 1) * n_surf) of the context's
+    surface record."""
 
-    def __init__(self, ens, **cfg_overrides):
+    def __init__(self, ens, shared=True, **cfg_overrides):
         from . import synth
         M = len(ens.members)
         cfg = dict(n_springs=ens.n_springs, dt=ens.dt)
+        if shared:
+            cfg["shared_members"] = M
         cfg.update(cfg_overrides)
         self.cfg = ns_config_default(**cfg)
         self.ctx = ns_create(self.cfg)
         self.M = M
-        U = synth.union_of_copies(ens.mesh, M, n_materials=len(ens.members[0]))
-        self.n_nodes, self.n_elems, self.n_surf = U.mesh.n_nodes, U.mesh.n_elems, int(U.mesh.surf.shape[0])
-        self.member_surf = int(ens.mesh.surf.shape[0])
+        nmb = int(ens.mesh.mat.max()) + 1
+        assert all(len(mats) == nmb for mats in ens.members), "one material row per layer and member"
+        m0 = ens.mesh
+        self.member_surf = int(m0.surf.shape[0])
+        self.n_nodes, self.n_elems, self.n_surf = M * m0.n_nodes, M * m0.n_elems, M * self.member_surf
         self.S = ens.n_springs
         try:
-            ns_upload_mesh(self.ctx, U.mesh.xyz, U.mesh.conn, U.mesh.mat)
-            ns_set_materials(self.ctx, [row for mats in ens.members for row in mats])
-            ns_set_boundary(self.ctx, U.mesh.faces, U.mesh.face_elem, U.mesh.face_kind, U.mesh.surf)
-            ns_set_members(self.ctx, U.elem_off, U.node_off)
+            table = [row for mats in ens.members for row in mats]
+            if shared:
+                ns_upload_mesh(self.ctx, m0.xyz, m0.conn, m0.mat)
+                ns_set_materials(self.ctx, table)
+                ns_set_boundary(self.ctx, m0.faces, m0.face_elem, m0.face_kind, m0.surf)
+            else:
+                U = synth.union_of_copies(m0, M, n_materials=nmb)
+                ns_upload_mesh(self.ctx, U.mesh.xyz, U.mesh.conn, U.mesh.mat)
+                ns_set_materials(self.ctx, table)
+                ns_set_boundary(self.ctx, U.mesh.faces, U.mesh.face_elem, U.mesh.face_kind, U.mesh.surf)
+                ns_set_members(self.ctx, U.elem_off, U.node_off)
             ns_set_ground_motion(self.ctx, ens.waves[0], ens.dt)
             for m in range(M):
                 ns_set_member_ground_motion(self.ctx, m, ens.waves[m], ens.dt)

@@ -93,15 +93,15 @@ __global__ void k_face_geometry(int64_t F, int64_t fpad, const int32_t *__restri
 }
 
 cudaError_t launch_geometry(const DevMesh &m, const double *xyz, int32_t *bad, cudaStream_t s) {
-  if (m.E == 0) return cudaSuccess;
-  k_geometry<<<(unsigned)((m.E + kBlock - 1) / kBlock), kBlock, 0, s>>>(m.E, m.epad, m.conn, xyz, m.geom, m.geom32,
-                                                                        bad);
+  if (m.Eb == 0) return cudaSuccess;
+  k_geometry<<<(unsigned)((m.Eb + kBlock - 1) / kBlock), kBlock, 0, s>>>(m.Eb, m.epg, m.conn, xyz, m.geom, m.geom32,
+                                                                         bad);
   return cudaGetLastError();
 }
 
 cudaError_t launch_face_geometry(const DevMesh &m, const double *xyz, cudaStream_t s) {
-  if (m.F == 0) return cudaSuccess;
-  k_face_geometry<<<(unsigned)((m.F + kBlock - 1) / kBlock), kBlock, 0, s>>>(m.F, m.fpad, m.fnode, xyz, m.fgeom);
+  if (m.Fb == 0) return cudaSuccess;
+  k_face_geometry<<<(unsigned)((m.Fb + kBlock - 1) / kBlock), kBlock, 0, s>>>(m.Fb, m.fpg, m.fnode, xyz, m.fgeom);
   return cudaGetLastError();
 }
 
@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
           const T *__restrict__ geom, const int32_t *__restrict__ mat, const TD *__restrict__ D, int64_t epad,
           const OpCoef *__restrict__ op, const typename VecOf<T>::type *__restrict__ xm,
           const typename VecOf<T>::type *__restrict__ xk, typename VecOf<T>::type *y, double *dot,
-          const int32_t *skip, const Seg *seg, int prefetch, typename VecOf<T>::type *yk) {
+          const int32_t *skip, const Seg *seg, int prefetch, typename VecOf<T>::type *yk, int64_t epg, int64_t Eb,
+          int64_t Nb) {
   int64_t i, end;
   if (seg) {  // members: this block's slice of one member's elements, that member's skip flag
     const Seg sg = seg[blockIdx.x];
@@ -264,12 +265,15 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
   double mydot = 0.0;
   if (i < end) {
     const int64_t e = ids ? (int64_t)ids[i] : i;
+    int64_t eg;
+    int32_t noff;
+    shared_elem(e, Eb, Nb, eg, noff);
     int nd[10];
 #pragma unroll
-    for (int a = 0; a < 10; ++a) nd[a] = ldg(conn + a * epad + e);
+    for (int a = 0; a < 10; ++a) nd[a] = ldg(conn + a * epg + eg) + noff;
     const int mt = ldg(mat + e);
     T g[4][3], vol;
-    load_grads(geom, epad, e, g, vol);
+    load_grads(geom, epg, eg, g, vol);
     const auto dl = [&](int k) { return dload(D, epad, e, k); };
     mydot = (double)ebe_element<T, VS, HAS_XM, ATOMIC, DOT, decltype(dl), OUTK>(nd, mt, g, vol, dl, op, xm, xk, y, yk);
   }
@@ -406,18 +410,19 @@ static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, co
   if constexpr (!HAS_XM && VS == 3) {  // the outer CG's applications that also return K x
     if (yk && dot) {
       if (atomic)
-        k_ebe<T, TD, VS, HAS_XM, true, true, true><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad,
-                                                                       op, xm, xk, y, dot, skip, sg.seg, m.prefetch, yk);
+        k_ebe<T, TD, VS, HAS_XM, true, true, true><<<nb, kBlock, 0, s>>>(
+            e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, dot, skip, sg.seg, m.prefetch, yk, m.epg,
+            m.eb_arg(), m.Nb);
       else
-        k_ebe<T, TD, VS, HAS_XM, false, true, true><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad,
-                                                                        op, xm, xk, y, dot, skip, sg.seg, m.prefetch,
-                                                                        yk);
+        k_ebe<T, TD, VS, HAS_XM, false, true, true><<<nb, kBlock, 0, s>>>(
+            e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, dot, skip, sg.seg, m.prefetch, yk, m.epg,
+            m.eb_arg(), m.Nb);
       return cudaGetLastError();
     }
   }
 #define NS_EBE_LAUNCH(A, DT)                                                                                  \
   k_ebe<T, TD, VS, HAS_XM, A, DT><<<nb, kBlock, 0, s>>>(e0, e1, ids, m.conn, geom, m.mat, D, m.epad, op, xm, xk, y, \
-                                                     dot, skip, sg.seg, m.prefetch, nullptr)
+                                                     dot, skip, sg.seg, m.prefetch, nullptr, m.epg, m.eb_arg(), m.Nb)
   if (atomic) {
     if (dot)
       NS_EBE_LAUNCH(true, true);
@@ -475,7 +480,7 @@ static cudaError_t staged_dispatch(const DevMesh &m, const TD *D, const OpCoef *
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
                          cudaStream_t s, SegList sg, bool staged) {
-  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr)
+  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr && m.Msh == 1)
     return staged_dispatch<float>(m, D, op, xk, y, dot, skip, s);
   // inner-solve vectors are [N][4]
   return ebe_dispatch<float, float, 4, false>(m, D, m.geom32, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s,
@@ -485,7 +490,7 @@ cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, con
 cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
                          cudaStream_t s, SegList sg, bool staged) {
-  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr)
+  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr && m.Msh == 1)
     return staged_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
   return ebe_dispatch<float, __half2, 4, false>(m, static_cast<const __half2 *>(D16), m.geom32, op, nullptr, xk, y,
                                                 ids, e0, e1, atomic, dot, skip, s, sg);
@@ -502,7 +507,8 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
                                                   const int32_t *__restrict__ fkind, const MatConst *__restrict__ mc,
                                                   T cC, const T *__restrict__ x, const double *__restrict__ vin,
                                                   T *y, double *dot, const int32_t *skip, const Seg *seg,
-                                                  const int32_t *__restrict__ fmem, int64_t vin_stride) {
+                                                  const int32_t *__restrict__ fmem, int64_t vin_stride, int64_t fpg,
+                                                  int64_t Fb, int64_t Nb) {
   int64_t i, end;
   if (seg) {
     const Seg sg = seg[blockIdx.x];
@@ -517,14 +523,17 @@ __global__ void __launch_bounds__(kBlock) k_faces(int64_t f0, int64_t f1, const 
   double mydot = 0.0;
   if (i < end) {
     const int64_t f = ids ? (int64_t)ids[i] : i;
+    int64_t fg;
+    int32_t noff;
+    shared_elem(f, Fb, Nb, fg, noff);
     int nd[6];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) nd[a] = fnode[a * fpad + f];
-    const T area = (T)fgeom[f];
-    const T n[3] = {(T)fgeom[fpad + f], (T)fgeom[2 * fpad + f], (T)fgeom[3 * fpad + f]};
+    for (int a = 0; a < 6; ++a) nd[a] = fnode[a * fpg + fg] + noff;
+    const T area = (T)fgeom[fg];
+    const T n[3] = {(T)fgeom[fpg + fg], (T)fgeom[2 * fpg + fg], (T)fgeom[3 * fpg + fg]};
     const MatConst &mm = mc[fmat[f]];
     const T rvs = (T)(mm.rho * mm.vs), rvd = (T)(mm.rho * (mm.vp - mm.vs));
-    const bool inp = vin && fkind[f] == 0;
+    const bool inp = vin && fkind[fg] == 0;
     const double *vf = (vin && fmem) ? vin + fmem[f] * vin_stride : vin;  // the face's member's input
     T w[6][3];
 #pragma unroll
@@ -574,7 +583,7 @@ static cudaError_t faces_dispatch(const DevMesh &m, const MatConst *mc, T cC, co
   const unsigned nb = sg.seg ? (unsigned)sg.n : (unsigned)((f1 - f0 + kBlock - 1) / kBlock);
 #define NS_F_LAUNCH(A, DT) \
   k_faces<T, VS, A, DT><<<nb, kBlock, 0, s>>>(f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, m.fkind, mc, cC, x, vin, y, \
-                                              dot, skip, sg.seg, fmem, vin_stride)
+                                              dot, skip, sg.seg, fmem, vin_stride, m.fpg, m.fb_arg(), m.Nb)
   if (atomic) {
     if (dot)
       NS_F_LAUNCH(true, true);
@@ -611,14 +620,18 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1,
                                                          const T *__restrict__ geom,
                                                          const int32_t *__restrict__ mat,
                                                          const TD *__restrict__ D, int64_t epad,
-                                                         const OpCoef *__restrict__ op, T *Jd, bool atomic) {
+                                                         const OpCoef *__restrict__ op, T *Jd, bool atomic,
+                                                         int64_t epg, int64_t Eb, int64_t Nb) {
   const int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= e1) return;
   const int64_t e = ids ? (int64_t)ids[i] : i;
+  int64_t eg;
+  int32_t noff;
+  shared_elem(e, Eb, Nb, eg, noff);
   const int mt = mat[e];
   const T cK = (T)op->kK[mt], cM = (T)op->mK[mt];
   T g[4][3], vol;
-  load_grads(geom, epad, e, g, vol);
+  load_grads(geom, epg, eg, g, vol);
   T acc[10][6];
 #pragma unroll
   for (int a = 0; a < 10; ++a)
@@ -667,7 +680,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_elems(int64_t e0, int64_t e1,
     acc[a][0] += md;
     acc[a][1] += md;
     acc[a][2] += md;
-    const int64_t n = conn[a * epad + e];
+    const int64_t n = conn[a * epg + eg] + noff;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       if (atomic)
@@ -682,17 +695,20 @@ template <typename T>
 __global__ void k_jacobi_faces(int64_t f0, int64_t f1, const int32_t *__restrict__ ids, int64_t fpad,
                                const int32_t *__restrict__ fnode, const double *__restrict__ fgeom,
                                const int32_t *__restrict__ fmat, const MatConst *__restrict__ mc, double cC,
-                               T *Jd, bool atomic) {
+                               T *Jd, bool atomic, int64_t Fb, int64_t Nb) {
   const int64_t i = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= f1) return;
   const int64_t f = ids ? (int64_t)ids[i] : i;
-  const double area = fgeom[f], n[3] = {fgeom[fpad + f], fgeom[2 * fpad + f], fgeom[3 * fpad + f]};
+  int64_t fg;
+  int32_t noff;
+  shared_elem(f, Fb, Nb, fg, noff);
+  const double area = fgeom[fg], n[3] = {fgeom[fpad + fg], fgeom[2 * fpad + fg], fgeom[3 * fpad + fg]};
   const MatConst &mm = mc[fmat[f]];
   const double rvs = mm.rho * mm.vs, rvd = mm.rho * (mm.vp - mm.vs);
   const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
   for (int a = 0; a < 6; ++a) {
     const double md = cC * area / 180.0 * (a < 3 ? 6.0 : 32.0);
-    const int64_t nd = fnode[a * fpad + f];
+    const int64_t nd = fnode[a * fpad + fg] + noff;
     for (int k = 0; k < 6; ++k) {
       const int r = pr[k][0], c = pr[k][1];
       const T v = (T)(md * ((r == c ? rvs : 0.0) + rvd * n[r] * n[c]));
@@ -708,7 +724,7 @@ cudaError_t launch_jacobi_elems(const DevMesh &m, const double *D, const OpCoef 
                                 int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
   k_jacobi_elems<double, double><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      e0, e1, ids, m.conn, m.geom, m.mat, D, m.epad, op, Jd, atomic);
+      e0, e1, ids, m.conn, m.geom, m.mat, D, m.epad, op, Jd, atomic, m.epg, m.eb_arg(), m.Nb);
   return cudaGetLastError();
 }
 
@@ -716,7 +732,7 @@ cudaError_t launch_jacobi_elems32(const DevMesh &m, const float *D, const OpCoef
                                   int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
   k_jacobi_elems<float, float><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      e0, e1, ids, m.conn, m.geom32, m.mat, D, m.epad, op, Jd, atomic);
+      e0, e1, ids, m.conn, m.geom32, m.mat, D, m.epad, op, Jd, atomic, m.epg, m.eb_arg(), m.Nb);
   return cudaGetLastError();
 }
 
@@ -724,7 +740,8 @@ cudaError_t launch_jacobi_elems16(const DevMesh &m, const void *D16, const OpCoe
                                   int64_t e0, int64_t e1, bool atomic, cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
   k_jacobi_elems<float, __half2><<<(unsigned)((e1 - e0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      e0, e1, ids, m.conn, m.geom32, m.mat, static_cast<const __half2 *>(D16), m.epad, op, Jd, atomic);
+      e0, e1, ids, m.conn, m.geom32, m.mat, static_cast<const __half2 *>(D16), m.epad, op, Jd, atomic, m.epg,
+      m.eb_arg(), m.Nb);
   return cudaGetLastError();
 }
 
@@ -732,7 +749,7 @@ cudaError_t launch_jacobi_faces(const DevMesh &m, const MatConst *mc, double cC,
                                 int64_t f0, int64_t f1, bool atomic, cudaStream_t s) {
   if (f1 <= f0) return cudaSuccess;
   k_jacobi_faces<double><<<(unsigned)((f1 - f0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, mc, cC, Jd, atomic);
+      f0, f1, ids, m.fpg, m.fnode, m.fgeom, m.fmat, mc, cC, Jd, atomic, m.fb_arg(), m.Nb);
   return cudaGetLastError();
 }
 
@@ -740,7 +757,7 @@ cudaError_t launch_jacobi_faces32(const DevMesh &m, const MatConst *mc, double c
                                   int64_t f0, int64_t f1, bool atomic, cudaStream_t s) {
   if (f1 <= f0) return cudaSuccess;
   k_jacobi_faces<float><<<(unsigned)((f1 - f0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      f0, f1, ids, m.fpad, m.fnode, m.fgeom, m.fmat, mc, cC, Jd, atomic);
+      f0, f1, ids, m.fpg, m.fnode, m.fgeom, m.fmat, mc, cC, Jd, atomic, m.fb_arg(), m.Nb);
   return cudaGetLastError();
 }
 
@@ -765,24 +782,27 @@ cudaError_t launch_to_pairs(const double *src, void *dst, int64_t n, cudaStream_
 // thread per element and vector (blockIdx.y: 0 for u, 1 for du).  The nodal values and gradients enter as pairs
 // (dd_from_double: two FP64-pipe operations each instead of the FP64 arithmetic).
 __global__ void __launch_bounds__(kBlock) k_strain_pairs(int64_t e0, int64_t e1, const int32_t *__restrict__ conn,
-                                                         const double *__restrict__ geom, int64_t epad,
+                                                         const double *__restrict__ geom, int64_t epg,
                                                          const double *__restrict__ u, const double *__restrict__ du,
-                                                         float2 *out) {
+                                                         float2 *out, int64_t Eb, int64_t Nb) {
   const int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= e1) return;
+  int64_t eg;
+  int32_t noff;
+  shared_elem(e, Eb, Nb, eg, noff);
   const int which = blockIdx.y;
   const double *src = which ? du : u;
   dd g[4][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) g[k + 1][c] = dd_from_double(__ldg(geom + (3 * k + c) * epad + e));
+    for (int c = 0; c < 3; ++c) g[k + 1][c] = dd_from_double(__ldg(geom + (3 * k + c) * epg + eg));
 #pragma unroll
   for (int c = 0; c < 3; ++c) g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
   dd x[10][3], P[4][3];
 #pragma unroll
   for (int a = 0; a < 10; ++a) {
-    const int64_t n = ldg(conn + a * epad + e);
+    const int64_t n = ldg(conn + a * epg + eg) + noff;
 #pragma unroll
     for (int r = 0; r < 3; ++r) x[a][r] = dd_from_double(__ldg(src + 3 * n + r));
   }
@@ -807,7 +827,8 @@ cudaError_t launch_strain_pairs(const DevMesh &m, const double *u, const double 
                                 cudaStream_t s) {
   if (e1 <= e0) return cudaSuccess;
   const dim3 grid((unsigned)((e1 - e0 + kBlock - 1) / kBlock), 2);
-  k_strain_pairs<<<grid, kBlock, 0, s>>>(e0, e1, m.conn, m.geom, m.epad, u, du, static_cast<float2 *>(out));
+  k_strain_pairs<<<grid, kBlock, 0, s>>>(e0, e1, m.conn, m.geom, m.epg, u, du, static_cast<float2 *>(out), m.eb_arg(),
+                                         m.Nb);
   return cudaGetLastError();
 }
 

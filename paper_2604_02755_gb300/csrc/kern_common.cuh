@@ -130,6 +130,20 @@ __device__ __forceinline__ void add_node(TV *y, int64_t n, const T v[3]) {
   }
 }
 
+// Members that share one mesh are stored member after member: element i of a launch reads
+// row i - m Eb of the shared connectivity and geometry, and its nodes are those of the shared
+// mesh shifted by m Nb (m = i / Eb, the member).  Eb = 0: no sharing (row i, no shift).
+__device__ __forceinline__ void shared_elem(int64_t i, int64_t Eb, int64_t Nb, int64_t &row, int32_t &noff) {
+  if (Eb) {
+    const int64_t m = i / Eb;
+    row = i - m * Eb;
+    noff = (int32_t)(m * Nb);
+  } else {
+    row = i;
+    noff = 0;
+  }
+}
+
 // Barycentric gradients of one element: g[0..3][3], from the stored grad L1..L3.
 template <typename T>
 __device__ __forceinline__ void load_grads(const T *__restrict__ geom, int64_t epad, int64_t e, T g[4][3], T &vol) {

@@ -85,6 +85,7 @@ struct ns_ctx {
   // every node (host, for the boundary faces)
   MgLevel mg;
   CgScalars *sc_c = nullptr;
+  int32_t shared_nmat = 1;  // shared members: material-table entries per member
   std::vector<int32_t> cid_h;
   double *eps = nullptr;
   double *part = nullptr;
@@ -1009,9 +1010,11 @@ void ns_config_default(ns_config *cfg) {
   cfg->multigrid = 0;
   cfg->coarse_max_iter = 20;
   cfg->coarse_tol = 1e-2;
+  cfg->shared_members = 0;
 }
 
 static thread_local std::string g_create_err;
+static int setup_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t *node_off);
 
 const char *ns_last_error(ns_ctx *ctx) {
   if (!ctx) return g_create_err.c_str();
@@ -1033,7 +1036,8 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
       (cfg->stream_mode != NS_STREAM_RING && cfg->stream_mode != NS_STREAM_ZERO_COPY) ||
       (cfg->spring_tile_points != 0 && !spring_tile_ok(cfg->spring_tile_points, cfg->n_springs)) ||
       (cfg->spring_tile_blocks != 0 && cfg->spring_tile_blocks != 1 && cfg->spring_tile_blocks != 4) ||
-      (cfg->multigrid != 0 && cfg->multigrid != 1) ||
+      (cfg->multigrid != 0 && cfg->multigrid != 1) || cfg->shared_members < 0 || cfg->shared_members > 65536 ||
+      (cfg->shared_members > 1 && (cfg->scatter != NS_SCATTER_ATOMIC || cfg->multigrid)) ||
       (cfg->multigrid && (cfg->precision == NS_PREC_FP64 || cfg->coarse_max_iter < 1 || !(cfg->coarse_tol > 0)))) {
     g_create_err = "invalid configuration value";
     return NS_ERR_INVALID_ARG;
@@ -1104,44 +1108,65 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
   int rc;
   cudaSetDevice(c->cfg.device);
   DevMesh &m = c->m;
-  m.N = N;
-  m.E = E;
-  m.prefetch = c->cfg.l2_prefetch ? 1 : 0;
-  m.epad = pad64(E);
-  std::vector<int32_t> soa((size_t)10 * m.epad, 0);
+  // members sharing this mesh: one copy of connectivity and geometry, per-member element
+  // data and node vectors (member k's material of element e is table entry mat[e] + k nmb)
+  const int32_t Ms = c->cfg.shared_members > 1 ? c->cfg.shared_members : 1;
+  int32_t nmb = 1;
+  for (int64_t e = 0; e < E; ++e) nmb = std::max(nmb, mat[e] + 1);
+  if (Ms > 1 && (N * Ms > INT32_MAX || E * Ms > INT32_MAX))
+    NS_SET(c, NS_ERR_INVALID_ARG, "shared members: too many nodes or elements in all");
+  if (Ms > 1 && (int64_t)nmb * Ms > kMaxMat)
+    NS_SET(c, NS_ERR_INVALID_ARG, "shared members: the material table would exceed " + std::to_string(kMaxMat));
+  m.Msh = Ms;
+  m.Eb = E;
+  m.Nb = N;
+  m.N = N * Ms;
+  m.E = E * Ms;
+  m.prefetch = (c->cfg.l2_prefetch && Ms == 1) ? 1 : 0;
+  m.epg = pad64(E);
+  m.epad = pad64(m.E);
+  c->shared_nmat = nmb;
+  std::vector<int32_t> soa((size_t)10 * m.epg, 0);
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 10; ++a) soa[(size_t)a * m.epad + e] = conn[e * 10 + a];
-  if ((rc = dalloc(c, &m.conn, soa.size())) || (rc = dalloc(c, &m.geom, 10 * m.epad)) ||
-      (rc = dalloc(c, &m.geom32, 10 * m.epad)) || (rc = dalloc(c, &m.mat, m.epad)) || (rc = dalloc(c, &m.kerr, 1)) ||
+    for (int a = 0; a < 10; ++a) soa[(size_t)a * m.epg + e] = conn[e * 10 + a];
+  if ((rc = dalloc(c, &m.conn, soa.size())) || (rc = dalloc(c, &m.geom, 10 * m.epg)) ||
+      (rc = dalloc(c, &m.geom32, 10 * m.epg)) || (rc = dalloc(c, &m.mat, m.epad)) || (rc = dalloc(c, &m.kerr, 1)) ||
       (rc = dalloc(c, &c->xyz_d, 3 * N)))
     return rc;
   CKC(c, cudaMemcpy(m.conn, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice));
-  CKC(c, cudaMemcpy(m.mat, mat, E * 4, cudaMemcpyHostToDevice));
+  if (Ms == 1) {
+    CKC(c, cudaMemcpy(m.mat, mat, E * 4, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<int32_t> mv((size_t)m.E);
+    for (int32_t k = 0; k < Ms; ++k)
+      for (int64_t e = 0; e < E; ++e) mv[(size_t)k * E + e] = mat[e] + k * nmb;
+    CKC(c, cudaMemcpy(m.mat, mv.data(), mv.size() * 4, cudaMemcpyHostToDevice));
+  }
   CKC(c, cudaMemcpy(c->xyz_d, xyz, N * 24, cudaMemcpyHostToDevice));
-  CKC(c, cudaMemsetAsync(m.geom, 0, 10 * m.epad * 8, c->s_main));
-  CKC(c, cudaMemsetAsync(m.geom32, 0, 10 * m.epad * 4, c->s_main));
-  if (m.epad > E) CKC(c, cudaMemsetAsync(m.mat + E, 0, (m.epad - E) * 4, c->s_main));  // read by tile copies
+  CKC(c, cudaMemsetAsync(m.geom, 0, 10 * m.epg * 8, c->s_main));
+  CKC(c, cudaMemsetAsync(m.geom32, 0, 10 * m.epg * 4, c->s_main));
+  if (m.epad > m.E) CKC(c, cudaMemsetAsync(m.mat + m.E, 0, (m.epad - m.E) * 4, c->s_main));  // read by tile copies
   CKC(c, cudaMemsetAsync(m.kerr, 0, 4, c->s_main));
   CKC(c, cudaMemsetAsync(c->flag_d, 0, 4, c->s_main));
   LAUNCH(c, launch_geometry(m, c->xyz_d, c->flag_d, c->s_main));
   if (c->cfg.pair_operator) {
-    if ((rc = dalloc(c, &m.geom2, 10 * (size_t)m.epad))) return rc;
-    LAUNCH(c, launch_to_pairs(m.geom, m.geom2, 10 * m.epad, c->s_main));
+    if ((rc = dalloc(c, &m.geom2, 10 * (size_t)m.epg))) return rc;
+    LAUNCH(c, launch_to_pairs(m.geom, m.geom2, 10 * m.epg, c->s_main));
   }
   CKC(c, cudaStreamSynchronize(c->s_main));
   int32_t bad = 0;
   CKC(c, cudaMemcpy(&bad, c->flag_d, 4, cudaMemcpyDeviceToHost));
   if (bad) NS_SET(c, NS_ERR_BAD_MESH, "element " + std::to_string(bad - 1) + " has a non-positive volume or a curved edge");
-  // node vectors
-  const size_t n3 = 3 * (size_t)N;
+  // node vectors (every member's)
+  const size_t n3 = 3 * (size_t)m.N;
   if ((rc = dalloc(c, &c->u, n3)) || (rc = dalloc(c, &c->v, n3)) || (rc = dalloc(c, &c->a, n3)) ||
       (rc = dalloc(c, &c->q, n3)) || (rc = dalloc(c, &c->du, n3)) || (rc = dalloc(c, &c->b, n3)) ||
       (rc = dalloc(c, &c->r, n3)) || (rc = dalloc(c, &c->z, n3)) || (rc = dalloc(c, &c->p, n3)) ||
-      (rc = dalloc(c, &c->Ap, n3)) || (rc = dalloc(c, &c->Jd, 6 * (size_t)N)) ||
-      (rc = dalloc(c, &c->Jinv, 6 * (size_t)N)) || (rc = dalloc(c, &c->Jinv32, 6 * (size_t)N)) ||
-      (rc = dalloc(c, &c->eps, 48 * (size_t)E)))
+      (rc = dalloc(c, &c->Ap, n3)) || (rc = dalloc(c, &c->Jd, 6 * (size_t)m.N)) ||
+      (rc = dalloc(c, &c->Jinv, 6 * (size_t)m.N)) || (rc = dalloc(c, &c->Jinv32, 6 * (size_t)m.N)) ||
+      (rc = dalloc(c, &c->eps, 48 * (size_t)m.E)))
     return rc;
-  const size_t n4 = 4 * (size_t)N;  // inner FP32 vectors: [N][4] rows of 16 bytes
+  const size_t n4 = 4 * (size_t)m.N;  // inner FP32 vectors: [N][4] rows of 16 bytes
   if (c->cfg.precision != NS_PREC_FP64 &&
       ((rc = dalloc(c, &c->rin, n4)) || (rc = dalloc(c, &c->zin, n4)) || (rc = dalloc(c, &c->pin, n4)) ||
        (rc = dalloc(c, &c->xin, n4)) || (rc = dalloc(c, &c->Apin, n4))))
@@ -1161,7 +1186,7 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
     if ((rc = dalloc(c, &m.ecol_ids, (size_t)E))) return rc;
     CKC(c, cudaMemcpy(m.ecol_ids, ids.data(), E * 4, cudaMemcpyHostToDevice));
   }
-  c->part_pap_cap = nblk(E) + (int64_t)nc + 64 + nblk(1) * 2;
+  c->part_pap_cap = nblk(m.E) + (int64_t)nc + 64 + nblk(1) * 2;
   if (c->cfg.multigrid) {  // coarse level of the two-level preconditioner
     MgLevel &g = c->mg;
     c->cid_h.assign((size_t)N, -1);
@@ -1348,32 +1373,43 @@ int ns_set_boundary(ns_ctx *c, int64_t F, const int32_t *faces, const int32_t *f
     NS_SET(c, NS_ERR_INVALID_ARG, "bad boundary sizes or null pointers");
   DevMesh &m = c->m;
   for (int64_t i = 0; i < F * 6; ++i)
-    if (faces[i] < 0 || faces[i] >= m.N) NS_SET(c, NS_ERR_BAD_MESH, "face node index out of range");
+    if (faces[i] < 0 || faces[i] >= m.Nb) NS_SET(c, NS_ERR_BAD_MESH, "face node index out of range");
   for (int64_t f = 0; f < F; ++f)
-    if (face_elem[f] < 0 || face_elem[f] >= m.E || (face_kind[f] != 0 && face_kind[f] != 1))
+    if (face_elem[f] < 0 || face_elem[f] >= m.Eb || (face_kind[f] != 0 && face_kind[f] != 1))
       NS_SET(c, NS_ERR_BAD_MESH, "bad face element or kind");
   for (int64_t i = 0; i < Ns; ++i)
-    if (surf[i] < 0 || surf[i] >= m.N) NS_SET(c, NS_ERR_BAD_MESH, "surface node index out of range");
+    if (surf[i] < 0 || surf[i] >= m.Nb) NS_SET(c, NS_ERR_BAD_MESH, "surface node index out of range");
   int rc;
-  m.F = F;
-  m.fpad = pad64(std::max<int64_t>(F, 1));
-  m.Ns = Ns;
+  // with shared members: one copy of the faces' nodes, geometry and kinds; their materials
+  // and surface nodes per member, member after member
+  const int32_t Ms = m.Msh;
+  m.Fb = F;
+  m.F = F * Ms;
+  m.fpg = pad64(std::max<int64_t>(F, 1));
+  m.fpad = pad64(std::max<int64_t>(m.F, 1));
+  m.Ns = Ns * Ms;
   std::vector<int32_t> mh((size_t)m.E);
   CKC(c, cudaMemcpy(mh.data(), m.mat, m.E * 4, cudaMemcpyDeviceToHost));
-  std::vector<int32_t> soa((size_t)6 * m.fpad, 0), fm((size_t)std::max<int64_t>(F, 1), 0);
-  for (int64_t f = 0; f < F; ++f) {
-    for (int a = 0; a < 6; ++a) soa[(size_t)a * m.fpad + f] = faces[f * 6 + a];
-    fm[f] = mh[face_elem[f]];
-  }
-  c->face_elem_h.assign(face_elem, face_elem + F);
-  if ((rc = dalloc(c, &m.fnode, soa.size())) || (rc = dalloc(c, &m.fgeom, 4 * (size_t)m.fpad)) ||
-      (rc = dalloc(c, &m.fmat, fm.size())) || (rc = dalloc(c, &m.fkind, fm.size())) ||
-      (rc = dalloc(c, &m.surf, (size_t)std::max<int64_t>(Ns, 1))))
+  std::vector<int32_t> soa((size_t)6 * m.fpg, 0), fm((size_t)std::max<int64_t>(m.F, 1), 0);
+  c->face_elem_h.assign((size_t)m.F, 0);
+  for (int64_t f = 0; f < F; ++f)
+    for (int a = 0; a < 6; ++a) soa[(size_t)a * m.fpg + f] = faces[f * 6 + a];
+  for (int32_t k = 0; k < Ms; ++k)
+    for (int64_t f = 0; f < F; ++f) {
+      c->face_elem_h[(size_t)k * F + f] = (int32_t)(k * m.Eb + face_elem[f]);
+      fm[(size_t)k * F + f] = mh[(size_t)k * m.Eb + face_elem[f]];
+    }
+  std::vector<int32_t> sv((size_t)std::max<int64_t>(m.Ns, 1), 0);
+  for (int32_t k = 0; k < Ms; ++k)
+    for (int64_t i = 0; i < Ns; ++i) sv[(size_t)k * Ns + i] = (int32_t)(surf[i] + k * m.Nb);
+  if ((rc = dalloc(c, &m.fnode, soa.size())) || (rc = dalloc(c, &m.fgeom, 4 * (size_t)m.fpg)) ||
+      (rc = dalloc(c, &m.fmat, fm.size())) || (rc = dalloc(c, &m.fkind, (size_t)std::max<int64_t>(F, 1))) ||
+      (rc = dalloc(c, &m.surf, sv.size())))
     return rc;
   CKC(c, cudaMemcpy(m.fnode, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice));
   CKC(c, cudaMemcpy(m.fmat, fm.data(), fm.size() * 4, cudaMemcpyHostToDevice));
   if (F > 0) CKC(c, cudaMemcpy(m.fkind, face_kind, F * 4, cudaMemcpyHostToDevice));
-  if (Ns > 0) CKC(c, cudaMemcpy(m.surf, surf, Ns * 4, cudaMemcpyHostToDevice));
+  if (m.Ns > 0) CKC(c, cudaMemcpy(m.surf, sv.data(), m.Ns * 4, cudaMemcpyHostToDevice));
   LAUNCH(c, launch_face_geometry(m, c->xyz_d, c->s_main));
   if (c->cfg.multigrid) {
     std::vector<int32_t> cf((size_t)3 * m.fpad, 0);
@@ -1388,7 +1424,7 @@ int ns_set_boundary(ns_ctx *c, int64_t F, const int32_t *faces, const int32_t *f
   }
   CKC(c, cudaStreamSynchronize(c->s_main));
   if (c->cfg.scatter == NS_SCATTER_COLOUR && F > 0) {
-    // greedy colouring of the faces (6 nodes each) in face order
+    // greedy colouring of the faces (6 nodes each) in face order (no shared members here)
     std::vector<uint64_t> used((size_t)m.N, 0);
     std::vector<int32_t> col((size_t)F);
     int nc = 0;
@@ -1411,14 +1447,22 @@ int ns_set_boundary(ns_ctx *c, int64_t F, const int32_t *faces, const int32_t *f
     CKC(c, cudaMemcpy(m.fcol_ids, ids.data(), F * 4, cudaMemcpyHostToDevice));
     c->part_pap_cap += nblk(F) + nc;
   } else {
-    c->part_pap_cap += nblk(std::max<int64_t>(F, 1));
+    c->part_pap_cap += nblk(std::max<int64_t>(m.F, 1));
   }
   c->ring_steps = c->cfg.surface_ring_steps;
-  const size_t rs = (size_t)c->ring_steps * 3 * (size_t)std::max<int64_t>(Ns, 1);
+  const size_t rs = (size_t)c->ring_steps * 3 * (size_t)std::max<int64_t>(m.Ns, 1);
   if ((rc = dalloc(c, &c->surf_u, rs)) || (rc = dalloc(c, &c->surf_v, rs)) || (rc = dalloc(c, &c->surf_a, rs)))
     return rc;
   if ((rc = dalloc(c, &c->part, (size_t)(c->part_pap_cap + 3 * vec_blocks(m.N))))) return rc;
   c->has_bnd = true;
+  if (Ms > 1) {  // the members are implied: member k owns elements [k Eb, (k+1) Eb) and nodes [k Nb, (k+1) Nb)
+    std::vector<int64_t> eo(Ms + 1), no(Ms + 1);
+    for (int32_t k = 0; k <= Ms; ++k) {
+      eo[k] = k * m.Eb;
+      no[k] = k * m.Nb;
+    }
+    if ((rc = setup_members(c, Ms, eo.data(), no.data())) != NS_OK) return rc;
+  }
   return NS_OK;
 }
 
@@ -1466,6 +1510,7 @@ int ns_set_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t 
   if (c->has_motion || c->step > 0 || c->M > 1) NS_SET(c, NS_ERR_STATE, "members must be set before the ground motion");
   if (c->cfg.scatter != NS_SCATTER_ATOMIC) NS_SET(c, NS_ERR_INVALID_ARG, "members need the atomic scatter");
   if (c->cfg.multigrid) NS_SET(c, NS_ERR_INVALID_ARG, "the two-level preconditioner serves one member only");
+  if (c->m.Msh > 1) NS_SET(c, NS_ERR_STATE, "the members of a shared mesh are already set");
   if (M < 1 || M > 65536 || !elem_off || !node_off) NS_SET(c, NS_ERR_INVALID_ARG, "bad member count");
   const DevMesh &m = c->m;
   if (elem_off[0] != 0 || elem_off[M] != m.E || node_off[0] != 0 || node_off[M] != m.N)
@@ -1483,6 +1528,12 @@ int ns_set_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t 
         if (nd < node_off[k] || nd >= node_off[k + 1])
           NS_SET(c, NS_ERR_BAD_MESH, "element " + std::to_string(e) + " uses a node of another member");
       }
+  return setup_members(c, M, elem_off, node_off);
+}
+
+// Member ranges (already validated): launch cuts, per-member CG scalars and partial sums.
+static int setup_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t *node_off) {
+  const DevMesh &m = c->m;
   // faces ordered by member
   std::vector<int32_t> fmem((size_t)std::max<int64_t>(m.F, 1), 0);
   std::vector<int64_t> foff(M + 1, 0);

@@ -45,21 +45,32 @@ struct OpCoef {
 // Device mesh in structure-of-arrays form (element arrays have stride epad).
 struct DevMesh {
   int64_t N = 0, E = 0, epad = 0, F = 0, fpad = 0, Ns = 0;
-  int32_t *conn = nullptr;   // [10][epad]
-  double *geom = nullptr;    // [10][epad]: grad L1 (3), grad L2 (3), grad L3 (3), volume
-  float *geom32 = nullptr;   // [10][epad]
-  int32_t *mat = nullptr;    // [E]
-  int32_t *fnode = nullptr;  // [6][fpad]
-  double *fgeom = nullptr;   // [4][fpad]: area, unit normal
+  int32_t *conn = nullptr;   // [10][epg]
+  double *geom = nullptr;    // [10][epg]: grad L1 (3), grad L2 (3), grad L3 (3), volume
+  float *geom32 = nullptr;   // [10][epg]
+  int32_t *mat = nullptr;    // [epad]
+  int32_t *fnode = nullptr;  // [6][fpg]
+  double *fgeom = nullptr;   // [4][fpg]: area, unit normal
   int32_t *fmat = nullptr;   // [F]
-  int32_t *fkind = nullptr;  // [F]
+  int32_t *fkind = nullptr;  // [Fb]
   int32_t *surf = nullptr;   // [Ns]
   // colour mode: element and face ids sorted by colour
   int32_t *ecol_ids = nullptr, *fcol_ids = nullptr;
   std::vector<int64_t> ecol_off, fcol_off;
   int32_t *kerr = nullptr;  // device flag: a bounded wait inside a kernel gave up
-  dd *geom2 = nullptr;      // [10][epad] geometry as float pairs (double-float operator)
+  dd *geom2 = nullptr;      // [10][epg] geometry as float pairs (double-float operator)
   int prefetch = 0;         // element kernels prefetch their blocks' element rows into L2
+  // Members sharing one mesh (shared_members > 1): E, N, F and Ns count every member's
+  // elements, nodes, faces and surface nodes (member after member), while the connectivity,
+  // geometry, face nodes, face geometry and face kinds hold one copy of the shared mesh
+  // (Eb elements, Nb nodes, Fb faces; rows of stride epg and fpg).  Element data (material,
+  // tangent, state) and node vectors stay per member.  Without sharing Eb = E, Nb = N,
+  // Fb = F, epg = epad, fpg = fpad.
+  int32_t Msh = 1;
+  int64_t Eb = 0, Nb = 0, Fb = 0, epg = 0, fpg = 0;
+  // element offset argument of the kernels: 0 without sharing
+  int64_t eb_arg() const { return Msh > 1 ? Eb : 0; }
+  int64_t fb_arg() const { return Msh > 1 ? Fb : 0; }
 };
 
 // Spring state arrays (structure of arrays over springs ordered [elem][point][spring]).
