@@ -1078,13 +1078,15 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
     cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&c->ev_d2h[i], cudaEventDisableTiming);
   }
-  if (halloc(c, &c->sc_h, 3) || halloc(c, &c->flag_h, 1) || dalloc(c, &c->sc, 3) || dalloc(c, &c->flag_d, 1) ||
-      dalloc(c, &c->op_A, 1) || dalloc(c, &c->op_A16, 1) ||
-      dalloc(c, &c->op_K, 1) || dalloc(c, &c->op_M, 1) || dalloc(c, &c->op_Cr, 1) || dalloc(c, &c->op_rhs, 1) ||
-      dalloc(c, &c->mats_d, kMaxMat) || dalloc(c, &c->spr_cnt, 3 * (size_t)kSpringCountSlots)) {
-    g_create_err = c->err;
+  int arc = NS_OK;
+  if ((arc = halloc(c, &c->sc_h, 3)) || (arc = halloc(c, &c->flag_h, 1)) || (arc = dalloc(c, &c->sc, 3)) ||
+      (arc = dalloc(c, &c->flag_d, 1)) || (arc = dalloc(c, &c->op_A, 1)) || (arc = dalloc(c, &c->op_A16, 1)) ||
+      (arc = dalloc(c, &c->op_K, 1)) || (arc = dalloc(c, &c->op_M, 1)) || (arc = dalloc(c, &c->op_Cr, 1)) ||
+      (arc = dalloc(c, &c->op_rhs, 1)) || (arc = dalloc(c, &c->mats_d, kMaxMat)) ||
+      (arc = dalloc(c, &c->spr_cnt, 3 * (size_t)kSpringCountSlots))) {
+    g_create_err = c->err;  // the failing allocation's own code: pinned or device
     ns_destroy(c);
-    return NS_ERR_OOM_DEVICE;
+    return arc;
   }
   cudaMemsetAsync(c->sc, 0, 3 * sizeof(CgScalars), c->s_main);
   cudaMemsetAsync(c->spr_cnt, 0, 3 * kSpringCountSlots * sizeof(unsigned long long), c->s_main);
