@@ -123,20 +123,57 @@ __device__ __forceinline__ float2 split_pair(double G) {
 }
 
 // Any double as an unevaluated float pair: the high part is v with its low 29 significand
-// bits cleared (built on the integer pipes), the low part the rounded rest; values outside
-// the normal float range (zero included) are rounded to one float.
+// bits cleared, the low part the rest rounded to a float -- both built on the integer and
+// FP32 pipes (GB300 runs FP64 conversions at 1/64 of the FP32 rate): the rest is the low
+// 29 significand bits times 2^(e - 52), converted from the integer (round to nearest) and
+// scaled by an exact power of two.  Values outside the normal float range (zero included)
+// are rounded to one float; for |v| < 2^-74 the rest is formed in FP64.
 __device__ __forceinline__ void dsplit(double v, float &h, float &l) {
   const long long b = __double_as_longlong(v);
   const int ed = (int)((b >> 52) & 0x7FF);
   if (ed > 896 && ed < 1151) {
-    const double vh = __longlong_as_double(b & ~0x1FFFFFFFLL);
-    h = __uint_as_float((unsigned int)((b >> 32) & 0x80000000LL) | (unsigned int)((ed - 896) << 23) |
-                        (unsigned int)((b >> 29) & 0x7FFFFF));
-    l = (float)(v - vh);
+    const unsigned int sg = (unsigned int)((b >> 32) & 0x80000000LL);
+    h = __uint_as_float(sg | (unsigned int)((ed - 896) << 23) | (unsigned int)((b >> 29) & 0x7FFFFF));
+    if (ed >= 949) {
+      const unsigned int m29 = (unsigned int)(b & 0x1FFFFFFFLL);
+      const float lo = __uint2float_rn(m29);  // exact below 2^24, else rounded to nearest
+      l = m29 ? __uint_as_float(__float_as_uint(lo * __uint_as_float((unsigned int)(ed - 948) << 23)) | sg) : 0.0f;
+    } else {
+      l = (float)(v - __longlong_as_double(b & ~0x1FFFFFFFLL));
+    }
   } else {
     h = (float)v;
     l = 0.0f;
   }
+}
+
+// A float as a double, exactly, on the integer pipes (normal floats and zero; subnormal
+// floats -- below 1.2e-38, which the spring law's pairs do not hold -- become zero).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xFF;
+  const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned long long r =
+      e ? (sg | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)(b & 0x7FFFFF) << 29)) : sg;
+  return __longlong_as_double((long long)r);
+}
+
+// The value of a float pair as a double: the two parts converted exactly, one FP64 add.
+__device__ __forceinline__ double pair_to_double(float h, float l) { return f2d(h) + f2d(l); }
+
+// A double truncated to a float (a starting guess, not a result): the high part of dsplit.
+__device__ __forceinline__ float d2f_guess(double v) {
+  const long long b = __double_as_longlong(v);
+  const int ed = (int)((b >> 52) & 0x7FF);
+  if (ed > 896 && ed < 1151)
+    return __uint_as_float((unsigned int)((b >> 32) & 0x80000000LL) | (unsigned int)((ed - 896) << 23) |
+                           (unsigned int)((b >> 29) & 0x7FFFFF));
+  return (float)v;
+}
+
+// -v by its sign bit
+__device__ __forceinline__ double d_neg(double v) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
 }
 
 // Root tau = F(ga) of the skeleton g(tau) = (tau/G0)(1 + alpha (tau/tref)^beta) = ga >= 0
@@ -240,7 +277,7 @@ __device__ __forceinline__ double ro_solve_pair(float gah, float gal, float gues
     float th, tl, d, Gh, Gl;
     if (df64_ro_halley(t, gah, gal, p.rp, tabf, th, tl, d, Gh, Gl) && fabsf(d) <= 2e-5f) {
       *Gp = make_float2(Gh, Gl);
-      return (double)th + (double)tl;
+      return pair_to_double(th, tl);
     }
   }
   // the FP64 path from the seed (or from the linear bound)
@@ -301,7 +338,7 @@ __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float d
     if (!dexact) pair_dot6(qk, de, dh, dl);
     float rh, rl;
     pair_add(gh, gl, -dh, -dl, rh, rl);
-    gR = (double)rh + (double)rl;
+    gR = pair_to_double(rh, rl);
     tR = tau;
     mode = 1;
     dir = sgn;
@@ -320,9 +357,9 @@ __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float d
   float guess = 0.0f;
   if (mode == 1 && outward && beyond) {
     mode = 0;
-    guess = fabsf((float)tau);
+    guess = fabsf(d2f_guess(tau));
   } else if (same) {
-    guess = (mode == 0) ? fabsf((float)tau) : 0.5f * fabsf((float)tau - (float)tR);
+    guess = (mode == 0) ? fabsf(d2f_guess(tau)) : 0.5f * fabsf(d2f_guess(tau) - d2f_guess(tR));
   }
   float xh = gh, xl = gl;
   if (mode == 1) {  // (gamma - gR) / 2
@@ -334,10 +371,10 @@ __device__ __forceinline__ float2 spring_update_pair(float gh, float gl, float d
   }
   const bool xneg = xh < 0.0f;
   const double f = ro_solve_pair(fabsf(xh), xneg ? -xl : xl, guess, p, tb, tabf, &G, ev);
-  const double fs = xneg ? -f : f;
+  const double fs = xneg ? d_neg(f) : f;
   if (mode == 0) {
     tau = fs;
-    if (ch > 0.0f || (ch == 0.0f && cl > 0.0f)) gmax = (double)agh + (double)agl;
+    if (ch > 0.0f || (ch == 0.0f && cl > 0.0f)) gmax = pair_to_double(agh, agl);
   } else {
     tau = fma(2.0, fs, tR);
   }
@@ -473,7 +510,9 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
   // division per spring
   const int dlp = (int)blockDim.x / S, dk = (int)blockDim.x - dlp * S;
   int lp = (int)threadIdx.x / S, k = (int)threadIdx.x - lp * S;
-  unsigned n_moved = 0, n_rev = 0, n_fp64 = 0;
+  // springs moved (bits 0-9), reversed (10-19) and with an FP64 root (20-29) by this thread
+  // (a thread updates at most ceil(TP S / 256) <= 1,024 springs of its block)
+  unsigned evn = 0;
   for (int g = threadIdx.x; g < nspr; g += blockDim.x, lp += dlp, k += dk) {
     if (k >= S) {
       k -= S;
@@ -492,9 +531,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
     unsigned ev = 0;
     const float2 G = spring_update_pair(gh, gl, dh, dl, !sure, q2 + 6 * k, Es + 12 * lp + 6, rp, tb, ptabf, tau, gR,
                                         tR, gmax, dir, mode, ev);
-    n_moved += ev & 1u;
-    n_rev += (ev >> 1) & 1u;
-    n_fp64 += (ev >> 2) & 1u;
+    evn += (ev & 1u) | ((ev & 2u) << 9) | ((ev & 4u) << 18);
     if (dh != 0.0f) {
       tau_a[si] = tau;
       gR_a[si] = gR;
@@ -518,9 +555,9 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
     }
   }
   if (cnt) {
-    n_moved = __reduce_add_sync(0xffffffffu, n_moved);
-    n_rev = __reduce_add_sync(0xffffffffu, n_rev);
-    n_fp64 = __reduce_add_sync(0xffffffffu, n_fp64);
+    const unsigned n_moved = __reduce_add_sync(0xffffffffu, evn & 1023u);
+    const unsigned n_rev = __reduce_add_sync(0xffffffffu, (evn >> 10) & 1023u);
+    const unsigned n_fp64 = __reduce_add_sync(0xffffffffu, (evn >> 20) & 1023u);
     if ((threadIdx.x & 31) == 0 && (n_moved | n_rev | n_fp64)) {
       atomicAdd_block(&evc[0], n_moved);
       atomicAdd_block(&evc[1], n_rev);
@@ -620,7 +657,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
       sl0 += ((sh0 - (sn - bv)) + (pr - bv)) + (er + cr);
       sh0 = sn;
     }
-    const double acc = (nn ? mc[mt].Kb : 0.0) + (((double)sh0 + (double)sh1) + ((double)sl0 + (double)sl1));
+    const double acc = (nn ? mc[mt].Kb : 0.0) + ((f2d(sh0) + f2d(sh1)) + (f2d(sl0) + f2d(sl1)));
     if (dpts)
       dpts[21 * (p - p0) + ij] = acc;
     else

@@ -82,14 +82,16 @@ def test_multigrid_run_matches_oracle(precision, scatter):
 def test_coarse_start_cuts_inner_iterations():
     """A column of the large model (5 m hexahedra, dt 0.005 s, 150 springs): the inner FP32
     solve started from the interpolated coarse solution takes fewer iterations than from
-    zero, for the same outer convergence and the same answer (1e-6)."""
+    zero.  Both runs solve to 1e-12, where the record no longer depends on the path to the
+    solution, and agree to 1e-6 (at 1e-8 the two preconditioners' stopping points differ
+    by the tolerance's own effect, ~5e-5 on this record)."""
     wl = synth.large_single_model(column=(30, 30, 6, 6))
     wl.wave = synth.main_motion_record()
     n = 40
     out = {}
     for mg in (0, 1):
         with B.Simulation(wl, surface_ring_steps=n, precision=B.NS_PREC_FP64_IR, x0_prev=0, multigrid=mg,
-                          inner_max_iter=200) as sim:
+                          inner_max_iter=200, cg_tol=1e-12) as sim:
             sim.advance(n)
             st = sim.stats()
             out[mg] = (sim.surface(1, n)["v"], st["inner_iters_total"], st["coarse_iters_total"], st["cg_iters_total"])
