@@ -346,11 +346,11 @@ def main():
     ap.add_argument("--ring-depth", type=int, default=12, help="device chunk buffers of the streamed state")
     ap.add_argument("--zero-copy", action="store_true",
                     help="also measure the streamed state updated in place in pinned host memory (no ring)")
-    ap.add_argument("--multigrid", type=int, default=0, choices=[0, 1],
-                    help="two-level preconditioner: the inner FP32 solve starts from the interpolated solution of "
-                         "the linear-element coarse model (Sec. 2.2, after [SC14])")
+    ap.add_argument("--multigrid", type=int, default=1, choices=[0, 1],
+                    help="two-level preconditioner (default on): the inner FP32 solve starts from the interpolated "
+                         "solution of the linear-element coarse model (Sec. 2.2, after [SC14])")
     ap.add_argument("--coarse-iters", type=int, default=20, help="multigrid: coarse PCG iterations at most")
-    ap.add_argument("--coarse-tol", type=float, default=1e-2, help="multigrid: coarse relative residual target")
+    ap.add_argument("--coarse-tol", type=float, default=1e-3, help="multigrid: coarse relative residual target")
     ap.add_argument("--solver", default="fp64-ir", choices=["fp64-ir", "fp64-ir16", "fp64-pcg"],
                     help="fp64-ir: FP64 flexible CG with an FP32 PCG preconditioner (the paper's precision policy); "
                          "fp64-ir16: the same with the inner operator reading D in FP16; "
@@ -413,8 +413,10 @@ def main():
               stage_elements=args.stage, inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, x0_prev=int(args.x0 == "prev"),
               pair_operator=args.pair_op, l2_prefetch=args.prefetch, spring_tile_points=args.spring_tile,
               spring_tile_blocks=args.spring_blocks, spring_tensor_cores=args.spring_tensor)
-    if args.multigrid:
+    if args.multigrid and ens is None and prec != B.NS_PREC_FP64:
         kw.update(multigrid=1, coarse_max_iter=args.coarse_iters, coarse_tol=args.coarse_tol)
+    else:
+        args.multigrid = 0  # one member and a flexible solver form only
     sim = B.BatchSimulation(ens, shared=not args.union, **kw) if ens else B.Simulation(wl, **kw)
     t_lead = time.perf_counter()
     if lead:
@@ -545,7 +547,9 @@ def main():
                                inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, stream_mode=mode, x0_prev=int(args.x0 == "prev"),
                                pair_operator=args.pair_op, l2_prefetch=args.prefetch,
                                spring_tile_points=args.spring_tile, spring_tile_blocks=args.spring_blocks,
-                               spring_tensor_cores=args.spring_tensor)
+                               spring_tensor_cores=args.spring_tensor,
+                               **(dict(multigrid=1, coarse_max_iter=args.coarse_iters, coarse_tol=args.coarse_tol)
+                                  if args.multigrid else {}))
             sim.advance(1)
             B.ns_reset_stats(sim.ctx)
             h0 = sim.stats()
