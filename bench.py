@@ -238,7 +238,7 @@ def served(args, dd, rank, ws, local):
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     clk_path = os.path.join(tempfile.gettempdir(), "ns_clocks_%d.csv" % rank)
     srv = B.Server(device=local, pinned_budget=int(args.pinned_gb * 1e9), max_active=args.max_active,
-                   quantum_steps=16)
+                   quantum_steps=16, batch=args.batch)
     dist.barrier(dd)
     proc, fh = sample_clocks_start(clk_path)
     t0 = time.perf_counter()
@@ -270,11 +270,21 @@ def served(args, dd, rank, ws, local):
                                        "20-150 springs, steps U[1000,4000] x %g" %
                                        (len(trace), min(sizes), max(sizes), args.step_scale),
                            "max_active": args.max_active, "solver": args.solver, "graphs": 1,
+                           "batch": "continuous batching of each solver class" if args.batch else
+                                    "one context per request",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "time_to_solution_s": {"p50": float(np.percentile(tts, 50)), "p99": float(np.percentile(tts, 99)),
                                        "max": float(tts.max())},
                 "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "max": float(wait.max())},
                 "streamed_requests": int(sum(s_["streamed"] for s_ in st)), "failed": len(failed),
+                "batching": ({"batches_per_request": float(np.mean([s_["batches"] for s_ in st])),
+                              "requests_batched": int(sum(s_["batches"] > 0 for s_ in st))}
+                             if args.batch else None),
+                "offered_load": {"requests_per_s": 4.0,
+                                 "elem_steps_per_request_mean": float(np.mean([r.workload.mesh.n_elems * r.n_steps
+                                                                               for r in trace])),
+                                 "value": 4.0 * float(np.mean([r.workload.mesh.n_elems * r.n_steps for r in trace])),
+                                 "unit": "elem-steps/s"},
                 "e2e": {"value": work_all / job_s, "unit": "elem-steps/s",
                         "h2d_bytes_per_step": int(sum(r.workload.mesh.xyz.nbytes + r.workload.mesh.conn.nbytes +
                                                       r.workload.wave.nbytes for r in trace) / len(trace)),
@@ -328,6 +338,9 @@ def main():
     ap.add_argument("--step-scale", type=float, default=0.01,
                     help="served trace: fraction of the 1000-4000 steps each request runs")
     ap.add_argument("--max-active", type=int, default=4, help="served: requests in flight together")
+    ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
+                    help="served: continuous batching of compatible requests in one batched context (1) or one "
+                         "context per request (0)")
     ap.add_argument("--pinned-gb", type=float, default=32.0, help="served: pinned host budget for streamed state")
     ap.add_argument("--graphs", type=int, default=-1, choices=[-1, 0, 1],
                     help="replay solver iterations as captured CUDA graphs (1) or launch them one by one (0, "

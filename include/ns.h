@@ -222,6 +222,15 @@ int ns_set_members(ns_ctx *ctx, int32_t M, const int64_t *elem_off, const int64_
  * record given to ns_set_ground_motion, which every member starts with). */
 int ns_set_member_ground_motion(ns_ctx *ctx, int32_t member, int64_t n_samples, double dt, const double *acc);
 
+/* Springs per point of each member (S [M], each >= 5), for a batch whose members are
+ * different cases of the method (served requests differ in S).  Call after ns_set_members
+ * and before the first step, once; all spring state resident (device_state_budget < 0).
+ * Each member gets its own spring set (the multi-spring geometry of its S, Sec. 2.1) and
+ * its spring update is launched over its own points.  The spring state of such a context
+ * is not readable or writable through ns_read_state / ns_write_state, and it has no
+ * checkpoint or autotuner; tangents and node vectors are as usual. */
+int ns_set_member_springs(ns_ctx *ctx, int32_t M, const int32_t *S);
+
 /* Outer CG iterations of each member at the last step into iters[M] (M = the context's
  * member count, 1 without ns_set_members). */
 int ns_get_member_iters(ns_ctx *ctx, int32_t M, int32_t *iters);

@@ -6,10 +6,25 @@
  * a first-come-first-served queue of submitted cases and admits the head of the queue
  * as soon as a slot and memory are free: its spring state is kept in HBM when the
  * device budget allows, otherwise streamed from pinned host memory when the pinned
- * budget allows (Alg. 3), otherwise the case waits.  Every admitted case runs in its
- * own context (own streams and CUDA graphs) driven by its own host thread, so the
- * kernels of all admitted cases overlap on the device; a case's result does not depend
- * on what else runs (with NS_SCATTER_COLOUR it is bit-identical to running it alone).
+ * budget allows (Alg. 3), otherwise the case waits.
+ *
+ * Two ways to run the admitted cases:
+ *  - batch = 0: every case in its own context (own streams and CUDA graphs) driven by its
+ *    own host thread, so the kernels of all admitted cases overlap on the device; a
+ *    case's result does not depend on what else runs (with NS_SCATTER_COLOUR it is
+ *    bit-identical to running it alone);
+ *  - batch = 1 (continuous batching): admitted cases with resident state and the same
+ *    solver settings (precision form, dt, tolerances, inner solve, Rayleigh band, graphs)
+ *    advance together as the members of one batched context -- the disjoint union of
+ *    their meshes, each member with its own springs per point, materials, input and CG
+ *    (ns_set_members, ns_set_member_springs) -- so that one launch of every kernel
+ *    serves all of them.  When a case arrives or finishes, the batch is re-formed: a new
+ *    context for the new membership takes the continuing members' state from the old one
+ *    device to device and carries on from their own steps.  The atomic scatter is used
+ *    (a member's result agrees with the case run alone to rounding).  Cases that only fit
+ *    with streamed state run in their own context as with batch = 0.  Re-forming holds
+ *    the old and the new context at once, so with batch = 1 cases are admitted only while
+ *    the admitted cases' device bytes stay within half the device budget.
  *
  * Ownership: ns_server_submit copies every input array; results are copied into
  * caller-owned buffers by ns_server_result.  The server owns its threads, contexts and
@@ -34,7 +49,9 @@ typedef struct {
   int64_t device_budget;    /* bytes of device memory the admitted cases may hold together */
   int64_t pinned_budget;    /* bytes of pinned host memory for streamed spring state */
   int32_t max_active;       /* cases advanced concurrently (>= 1) */
-  int32_t quantum_steps;    /* steps a case advances between checks of the server's stop flag */
+  int32_t quantum_steps;    /* steps a case (or a batch) advances between checks of the stop flag,
+                               arrivals and departures */
+  int32_t batch;            /* 1: continuous batching of compatible cases (above); 0: a context per case */
 } ns_server_config;
 
 /* One case: the arrays of ns_upload_mesh, ns_set_materials, ns_set_boundary and
@@ -70,13 +87,14 @@ typedef struct {
   int32_t state;            /* NS_CASE_* */
   int32_t error;            /* NS_OK or the failing call's NS_ERR_* */
   int32_t streamed;         /* 1: admitted with its spring state in pinned host memory */
-  int32_t pad;
+  int32_t batches;          /* batched contexts the case ran in (0: its own context) */
   double t_submit, t_admit, t_done;  /* seconds since the server's creation */
   int64_t device_bytes;     /* device memory reserved for the case at admission */
   int64_t state_bytes;      /* its spring state */
   int64_t elem_steps;       /* n_elems * n_steps */
-  double ms_device;         /* CUDA-event time of its ns_advance calls */
-  int64_t kernel_launches;  /* the library's kernels its context launched */
+  double ms_device;         /* CUDA-event time of its ns_advance calls (batched: its share of the
+                               batches' time, in proportion to its elements) */
+  int64_t kernel_launches;  /* the library's kernels its context launched (batched: its share) */
 } ns_case_stats;
 
 /* Device bytes a case needs with all its state resident (*device_bytes), the part of it

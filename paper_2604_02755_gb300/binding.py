@@ -85,7 +85,7 @@ class ns_tuning(C.Structure):
 
 class ns_server_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("device_budget", C.c_int64), ("pinned_budget", C.c_int64),
-                ("max_active", C.c_int32), ("quantum_steps", C.c_int32)]
+                ("max_active", C.c_int32), ("quantum_steps", C.c_int32), ("batch", C.c_int32)]
 
 
 class ns_case(C.Structure):
@@ -97,13 +97,13 @@ class ns_case(C.Structure):
 
 
 class ns_case_stats(C.Structure):
-    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("streamed", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("streamed", C.c_int32), ("batches", C.c_int32),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
                 ("device_bytes", C.c_int64), ("state_bytes", C.c_int64), ("elem_steps", C.c_int64),
                 ("ms_device", C.c_double), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 NS_CASE_QUEUED, NS_CASE_RUNNING, NS_CASE_DONE, NS_CASE_FAILED = 0, 1, 2, 3
@@ -114,7 +114,7 @@ EXPORTED = ["ns_config_default", "ns_create", "ns_upload_mesh", "ns_set_material
             "ns_reset_stats", "ns_checkpoint_size", "ns_checkpoint", "ns_restore", "ns_destroy", "ns_last_error",
             "ns_spring_directions", "ns_colour_elements", "ns_state_bytes", "ns_spring_points_noalloc",
             "ns_spring_points_noalloc_capacity", "ns_set_members", "ns_set_member_ground_motion",
-            "ns_get_member_iters", "ns_autotune", "ns_apply_coarse_operator", "ns_coarse_map", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
+            "ns_get_member_iters", "ns_set_member_springs", "ns_autotune", "ns_apply_coarse_operator", "ns_coarse_map", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
             "ns_server_wait", "ns_server_result", "ns_server_release", "ns_server_destroy"]
 
 _lib = None
@@ -159,6 +159,7 @@ def lib():
             "ns_set_members": ([vp, i32, vp, vp], C.c_int),
             "ns_set_member_ground_motion": ([vp, i32, i64, d, vp], C.c_int),
             "ns_get_member_iters": ([vp, i32, vp], C.c_int),
+            "ns_set_member_springs": ([vp, i32, vp], C.c_int),
             "ns_autotune": ([vp, C.POINTER(ns_tuning)], C.c_int),
             "ns_apply_coarse_operator": ([vp, i32, i64, vp, vp], C.c_int),
             "ns_coarse_map": ([i64, i64, vp, vp, vp, C.POINTER(i64)], C.c_int),
@@ -244,6 +245,11 @@ def ns_set_members(ctx, elem_off, node_off):
 def ns_set_member_ground_motion(ctx, member, acc, dt):
     acc = _f64(acc).reshape(-1, 3)
     _check(ctx, lib().ns_set_member_ground_motion(ctx, int(member), acc.shape[0], float(dt), _p(acc)))
+
+
+def ns_set_member_springs(ctx, S):
+    S = np.ascontiguousarray(S, np.int32)
+    _check(ctx, lib().ns_set_member_springs(ctx, S.shape[0], _p(S)))
 
 
 def ns_get_member_iters(ctx, M):
@@ -543,13 +549,13 @@ class Server:
     """Served ensemble: cases queued first come first served and admitted into concurrent
     slots as device / pinned-host memory allows (include/ns_server.h)."""
 
-    def __init__(self, device=0, device_budget=None, pinned_budget=0, max_active=4, quantum_steps=16):
+    def __init__(self, device=0, device_budget=None, pinned_budget=0, max_active=4, quantum_steps=16, batch=0):
         if device_budget is None:
             import torch
             free, _ = torch.cuda.mem_get_info(device)
             device_budget = int(free * 0.85)
         cfg = ns_server_config(device=device, device_budget=int(device_budget), pinned_budget=int(pinned_budget),
-                               max_active=int(max_active), quantum_steps=int(quantum_steps))
+                               max_active=int(max_active), quantum_steps=int(quantum_steps), batch=int(batch))
         h = C.c_void_p()
         rc = lib().ns_server_create(C.byref(h), C.byref(cfg))
         if rc != NS_OK:

@@ -86,6 +86,12 @@ struct ns_ctx {
   MgLevel mg;
   CgScalars *sc_c = nullptr;
   int32_t shared_nmat = 1;  // shared members: material-table entries per member
+  // members with their own springs per point (ns_set_member_springs): per member the springs,
+  // the first spring of its state, its spring tables and the device arrays behind them
+  std::vector<int32_t> mS;
+  std::vector<int64_t> spr_off;
+  std::vector<SpringTables> mtab;
+  std::vector<void *> mtab_mem;
   std::vector<int32_t> cid_h;
   double *eps = nullptr;
   double *part = nullptr;
@@ -518,6 +524,18 @@ int spring_launch(ns_ctx *c, const SpringSoA &st, int64_t base_elem, int64_t e0,
 int spring_phase(ns_ctx *c) {
   int rc;
   LAUNCH(c, launch_strain_pairs(c->m, c->u, c->du, c->eps, 0, c->m.E, c->s_main));
+  if (!c->mS.empty()) {  // members with their own springs: one launch per member, all state resident
+    for (int m = 0; m < c->M; ++m) {
+      const int64_t e0 = c->moff_e[m], e1 = c->moff_e[m + 1], o = c->spr_off[m];
+      SpringSoA sm{c->st.tau + o, c->st.gR + o, c->st.tR + o, c->st.gmax + o, c->st.dir + o, c->st.mode + o};
+      cudaEvent_t t0 = nullptr;
+      tbegin(c, TK_SPRING, c->s_main, &t0);
+      LAUNCH(c, launch_springs(c->mtab[m], c->mats_d, c->m.mat, nullptr, c->eps, sm, 4 * e0, 4 * e0, 4 * e1, c->D,
+                               c->m.epad, nullptr, c->s_main, true));
+      tend(c, TK_SPRING, c->s_main, t0);
+    }
+    return NS_OK;
+  }
   const int64_t nc = n_chunks(c);
   if (nc == 0) return spring_launch(c, c->st, 0, 0, c->E_res);
   if (c->cfg.timing) CKC(c, cudaEventRecord(c->ev_stream_t0, c->s_main));
@@ -969,6 +987,56 @@ int ctx_spring_view(ns_ctx *c, SpringCtxView *v) {
   return NS_OK;
 }
 void ctx_set_error(ns_ctx *c, const char *msg) { c->err = msg; }
+
+int64_t ctx_steps(ns_ctx *c) { return c->step; }
+
+int ctx_copy_member(ns_ctx *dst, int md, ns_ctx *src, int ms) {
+  auto range = [](const ns_ctx *c, int m, const std::vector<int64_t> &off, int64_t all, int64_t &a0, int64_t &n) {
+    if (c->M > 1) {
+      a0 = off[m];
+      n = off[m + 1] - off[m];
+    } else {
+      a0 = 0;
+      n = all;
+    }
+  };
+  if (!dst || !src || !dst->has_mat || !src->has_mat) return NS_ERR_STATE;
+  if (dst->E_res < dst->m.E || src->E_res < src->m.E) NS_SET(dst, NS_ERR_STATE, "member copy needs resident state");
+  int64_t en0s, ens, en0d, end_, nn0s, nns, nn0d, nnd;
+  range(src, ms, src->moff_e, src->m.E, en0s, ens);
+  range(dst, md, dst->moff_e, dst->m.E, en0d, end_);
+  range(src, ms, src->moff_n, src->m.N, nn0s, nns);
+  range(dst, md, dst->moff_n, dst->m.N, nn0d, nnd);
+  const int Ss = src->mS.empty() ? src->tab.S : src->mS[ms], Sd = dst->mS.empty() ? dst->tab.S : dst->mS[md];
+  if (ens != end_ || nns != nnd || Ss != Sd) NS_SET(dst, NS_ERR_INVALID_ARG, "member copy between different cases");
+  const int64_t sps = src->mS.empty() ? en0s * 4 * Ss : src->spr_off[ms];
+  const int64_t spd = dst->mS.empty() ? en0d * 4 * Sd : dst->spr_off[md];
+  const int64_t nspr = ens * 4 * (int64_t)Ss;
+  int rc;
+  if ((rc = sync_all(src)) != NS_OK) return rc;
+  if ((rc = sync_all(dst)) != NS_OK) return rc;
+  cudaStream_t s = dst->s_main;
+  const double *vs[5] = {src->u, src->v, src->a, src->q, src->du};
+  double *vd[5] = {dst->u, dst->v, dst->a, dst->q, dst->du};
+  for (int f = 0; f < 5; ++f)
+    CKC(dst, cudaMemcpyAsync(vd[f] + 3 * nn0d, vs[f] + 3 * nn0s, 24 * nns, cudaMemcpyDeviceToDevice, s));
+  for (int k = 0; k < 84; ++k)
+    CKC(dst, cudaMemcpyAsync(dst->D + (size_t)k * dst->m.epad + en0d, src->D + (size_t)k * src->m.epad + en0s, 8 * ens,
+                             cudaMemcpyDeviceToDevice, s));
+  if ((rc = copy_soa(dst, dst->st, spd, src->st, sps, nspr, cudaMemcpyDeviceToDevice, s)) != NS_OK) return rc;
+  return sync_stream(dst, s);
+}
+
+int ctx_set_member_velocity(ns_ctx *c, int m, const double *vin, int64_t n) {
+  if (!c || !vin || n < 1) return NS_ERR_INVALID_ARG;
+  if (!c->has_motion) NS_SET(c, NS_ERR_STATE, "set the ground motion first");
+  if (m < 0 || m >= c->M) NS_SET(c, NS_ERR_INVALID_ARG, "member index out of range");
+  std::vector<double> row(3 * (size_t)c->n_vin);
+  for (int64_t k = 0; k < c->n_vin; ++k)
+    for (int cc = 0; cc < 3; ++cc) row[3 * k + cc] = vin[3 * std::min(k, n - 1) + cc];
+  CKC(c, cudaMemcpy(c->vin_d + (size_t)m * row.size(), row.data(), row.size() * 8, cudaMemcpyHostToDevice));
+  return NS_OK;
+}
 void ctx_count_launches(ns_ctx *c, int n) { c->stats.kernel_launches += n; }
 int ctx_sync_main(ns_ctx *c) { return sync_stream(c, c->s_main); }
 }  // namespace ns
@@ -1474,11 +1542,7 @@ int ns_set_ground_motion(ns_ctx *c, int64_t ns_, double dt, const double *acc) {
   if (!(fabs(dt - c->cfg.dt) <= 1e-12 * c->cfg.dt)) NS_SET(c, NS_ERR_INVALID_ARG, "record dt differs from the step dt");
   // trapezoidal input velocity, v(0) = 0; one extra entry for the first step past the record
   std::vector<double> vin(3 * (size_t)(ns_ + 1), 0.0);
-  for (int64_t k = 1; k <= ns_; ++k)
-    for (int cc = 0; cc < 3; ++cc) {
-      const double a0 = acc[3 * (k - 1) + cc], a1 = (k < ns_) ? acc[3 * k + cc] : 0.0;
-      vin[3 * k + cc] = vin[3 * (k - 1) + cc] + 0.5 * dt * (a0 + a1);
-    }
+  host_input_velocity(acc, ns_, dt, vin.data());
   int rc;
   dfree(c->vin_d);
   // [M][n_vin][3]: every member starts with this record
@@ -1497,11 +1561,7 @@ int ns_set_member_ground_motion(ns_ctx *c, int32_t member, int64_t ns_, double d
   if (ns_ + 1 != c->n_vin || !acc) NS_SET(c, NS_ERR_INVALID_ARG, "member records must have the common record's length");
   if (!(fabs(dt - c->cfg.dt) <= 1e-12 * c->cfg.dt)) NS_SET(c, NS_ERR_INVALID_ARG, "record dt differs from the step dt");
   std::vector<double> vin(3 * (size_t)(ns_ + 1), 0.0);
-  for (int64_t k = 1; k <= ns_; ++k)
-    for (int cc = 0; cc < 3; ++cc) {
-      const double a0 = acc[3 * (k - 1) + cc], a1 = (k < ns_) ? acc[3 * k + cc] : 0.0;
-      vin[3 * k + cc] = vin[3 * (k - 1) + cc] + 0.5 * dt * (a0 + a1);
-    }
+  host_input_velocity(acc, ns_, dt, vin.data());
   CKC(c, cudaMemcpy(c->vin_d + (size_t)member * vin.size(), vin.data(), vin.size() * 8, cudaMemcpyHostToDevice));
   return NS_OK;
 }
@@ -1603,6 +1663,82 @@ static int setup_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const in
   c->M = M;
   c->member_iters.assign(M, 0);
   return NS_OK;
+}
+
+int ns_set_member_springs(ns_ctx *c, int32_t M, const int32_t *S) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (!c->has_mat || !c->has_bnd || c->M < 2 || c->m.Msh > 1)
+    NS_SET(c, NS_ERR_STATE, "set the materials and the members (ns_set_members) first");
+  if (c->step > 0 || !c->mS.empty()) NS_SET(c, NS_ERR_STATE, "member springs are set once, before the first step");
+  if (c->E_res < c->m.E) NS_SET(c, NS_ERR_INVALID_ARG, "members with their own springs keep all state resident");
+  if (M != c->M || !S) NS_SET(c, NS_ERR_INVALID_ARG, "one spring count per member");
+  for (int m = 0; m < M; ++m)
+    if (S[m] < 5 || !spring_tile_ok(spring_tile_default(S[m]), S[m]))
+      NS_SET(c, NS_ERR_INVALID_ARG, "member " + std::to_string(m) + ": bad spring count");
+  int rc;
+  if ((rc = sync_all(c)) != NS_OK) return rc;
+  std::vector<int64_t> off(M + 1, 0);
+  for (int m = 0; m < M; ++m) off[m + 1] = off[m] + 4 * (c->moff_e[m + 1] - c->moff_e[m]) * (int64_t)S[m];
+  std::vector<SpringTables> tabs(M);
+  std::vector<void *> mem;
+  auto up = [&](const void *src, size_t bytes) -> void * {
+    void *d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    mem.push_back(d);
+    if (cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    return d;
+  };
+  for (int m = 0; m < M && rc == NS_OK; ++m) {
+    const int Sm = S[m];
+    std::vector<double> qh(6 * (size_t)Sm), Th(21 * (size_t)(Sm + 1), 0.0);
+    double w = 0;
+    host_spring_directions(Sm, qh.data(), &w);
+    for (int k = 0; k < Sm; ++k)
+      for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+          const double t = w * qh[6 * k + i] * qh[6 * k + j];
+          Th[21 * (size_t)k + sym6(i, j)] = t;
+          Th[21 * (size_t)Sm + sym6(i, j)] += t;
+        }
+    std::vector<float2> q2h(6 * (size_t)Sm), T2h(21 * (size_t)Sm);
+    for (size_t i = 0; i < q2h.size(); ++i) q2h[i] = make_float2((float)qh[i], (float)(qh[i] - (double)(float)qh[i]));
+    for (size_t i = 0; i < T2h.size(); ++i) T2h[i] = make_float2((float)Th[i], (float)(Th[i] - (double)(float)Th[i]));
+    SpringTables t = c->tab;  // power tables, launch shape and counters as the context's
+    t.S = Sm;
+    t.tc = 0;  // the tangent in double-float sums
+    t.tfrag = nullptr;
+    t.tsc = nullptr;
+    t.tp = 0;  // the size heuristic for this spring count
+    t.q = (const double *)up(qh.data(), qh.size() * 8);
+    t.T = (const double *)up(Th.data(), Th.size() * 8);
+    t.q2 = (const float2 *)up(q2h.data(), q2h.size() * sizeof(float2));
+    t.T2 = (const float2 *)up(T2h.data(), T2h.size() * sizeof(float2));
+    if (!t.q || !t.T || !t.q2 || !t.T2) {
+      c->err = "allocation of the member spring tables failed";
+      rc = NS_ERR_OOM_DEVICE;
+    }
+    tabs[m] = t;
+  }
+  SpringSoA st;
+  if (rc == NS_OK) rc = alloc_soa(c, st, std::max<int64_t>(1, off[M]), false);
+  if (rc != NS_OK) {
+    for (void *p : mem) cudaFree(p);
+    return rc;
+  }
+  free_soa(c->st, false);
+  c->st = st;
+  c->mS.assign(S, S + M);
+  c->spr_off = off;
+  c->mtab = tabs;
+  c->mtab_mem = mem;
+  for (int m = 0; m < M; ++m)  // elastic tangent of each member's spring set
+    LAUNCH(c, launch_elastic_D(c->mtab[m], c->mats_d, c->m.mat, c->D, c->m.epad, c->moff_e[m], c->moff_e[m + 1],
+                               c->s_main));
+  c->stats.resident_elems = c->m.E;
+  return sync_stream(c, c->s_main);
 }
 
 int ns_get_member_iters(ns_ctx *c, int32_t M, int32_t *iters) {
@@ -1758,6 +1894,7 @@ void unpack_D(const std::vector<double> &Dsoa, int64_t epad_src, int64_t e_local
 int ns_read_state(ns_ctx *c, int64_t e0, int64_t n, void *theta, double *D) {
   if (!c) return NS_ERR_INVALID_ARG;
   if (!c->has_mat) NS_SET(c, NS_ERR_STATE, "no state yet");
+  if (!c->mS.empty() && theta) NS_SET(c, NS_ERR_STATE, "members with their own springs: spring state not readable");
   if (e0 < 0 || n < 0 || e0 + n > c->m.E) NS_SET(c, NS_ERR_INVALID_ARG, "element range out of bounds");
   int rc;
   if ((rc = sync_all(c)) != NS_OK) return rc;
@@ -1780,6 +1917,7 @@ int ns_read_state(ns_ctx *c, int64_t e0, int64_t n, void *theta, double *D) {
 int ns_write_state(ns_ctx *c, int64_t e0, int64_t n, const void *theta, const double *D) {
   if (!c) return NS_ERR_INVALID_ARG;
   if (!c->has_mat) NS_SET(c, NS_ERR_STATE, "no state yet");
+  if (!c->mS.empty() && theta) NS_SET(c, NS_ERR_STATE, "members with their own springs: spring state not writable");
   if (e0 < 0 || n < 0 || e0 + n > c->m.E) NS_SET(c, NS_ERR_INVALID_ARG, "element range out of bounds");
   int rc;
   if ((rc = sync_all(c)) != NS_OK) return rc;
@@ -1947,6 +2085,7 @@ int ns_spring_points(ns_ctx *c, int64_t npts, const int32_t *mat, const double *
 int ns_autotune(ns_ctx *c, ns_tuning *out) {
   if (!c || !out) return NS_ERR_INVALID_ARG;
   if (!c->has_mat || !c->has_bnd || c->step < 1) NS_SET(c, NS_ERR_STATE, "autotune after at least one step");
+  if (!c->mS.empty()) NS_SET(c, NS_ERR_STATE, "members with their own springs keep the default launch shape");
   memset(out, 0, sizeof(*out));
   const int S = c->tab.S;
   int rc = NS_OK;
@@ -2109,6 +2248,7 @@ struct CkptHeader {
 int ns_checkpoint_size(ns_ctx *c, int64_t *bytes) {
   if (!c || !bytes) return NS_ERR_INVALID_ARG;
   if (!c->has_mat) NS_SET(c, NS_ERR_STATE, "no state yet");
+  if (!c->mS.empty()) NS_SET(c, NS_ERR_STATE, "members with their own springs: no checkpoint");
   *bytes = (int64_t)sizeof(CkptHeader) + 5 * 3 * c->m.N * 8 + c->m.E * 144 * 8 + ns_state_bytes(c->m.E, c->tab.S);
   return NS_OK;
 }
@@ -2185,6 +2325,7 @@ void ns_destroy(ns_ctx *c) {
   dfree(c->mg.conn1); dfree(c->mg.cfnode); dfree(c->mg.rptr); dfree(c->mg.rlist); dfree(c->mg.par);
   dfree(c->mg.Dbar); dfree(c->mg.Jd32); dfree(c->mg.Jinv32);
   dfree(c->mg.x); dfree(c->mg.r); dfree(c->mg.z); dfree(c->mg.p); dfree(c->mg.Ap);
+  for (void *p : c->mtab_mem) cudaFree(p);
   dfree(c->flag_d);
   hfree(c->sc_h);
   hfree(c->flag_h);

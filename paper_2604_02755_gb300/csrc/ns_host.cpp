@@ -161,6 +161,15 @@ int64_t host_coarse_map(int64_t E, int64_t N, const int32_t *conn, int32_t *cid,
   return nc;
 }
 
+void host_input_velocity(const double *acc, int64_t n, double dt, double *vin) {
+  for (int cc = 0; cc < 3; ++cc) vin[cc] = 0.0;
+  for (int64_t k = 1; k <= n; ++k)
+    for (int cc = 0; cc < 3; ++cc) {
+      const double a0 = acc[3 * (k - 1) + cc], a1 = (k < n) ? acc[3 * k + cc] : 0.0;
+      vin[3 * k + cc] = vin[3 * (k - 1) + cc] + 0.5 * dt * (a0 + a1);
+    }
+}
+
 // Derived constants: G0 = rho Vs^2, bulk Kb = rho (Vp^2 - 4/3 Vs^2); RO exponent
 // beta = 2 pi h_max / (2 - pi h_max) (loop damping tends to h_max), alpha = 2^beta
 // (secant G0/2 at gamma_ref); Rayleigh a = 2 h w1 w2/(w1 + w2), b = 2 h/(w1 + w2).

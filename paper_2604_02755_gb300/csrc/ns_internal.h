@@ -310,6 +310,15 @@ int ctx_spring_view(ns_ctx *c, SpringCtxView *v);  // NS_OK once materials are s
 void ctx_set_error(ns_ctx *c, const char *msg);
 void ctx_count_launches(ns_ctx *c, int n);
 int ctx_sync_main(ns_ctx *c);                       // bounded wait for the context's main stream
+// Served batches (ns_server.cpp).  Copy member ms of src into member md of dst, device to
+// device: node vectors u, v, a, q, du, tangent D and spring state (same element, node and
+// spring counts; a context without members counts as member 0).  All state resident.
+int ctx_copy_member(ns_ctx *dst, int md, ns_ctx *src, int ms);
+// Input velocity of member m at the context's steps k = 0 .. n-1 (vin [n][3]); later steps
+// take vin[n-1].  Call after ns_set_ground_motion (which fixes the record length).
+int ctx_set_member_velocity(ns_ctx *c, int m, const double *vin, int64_t n);
+// device bytes the context holds (its own allocations)
+int64_t ctx_steps(ns_ctx *c);
 
 // ------------------------------------------------------------------ ns_host.cpp
 int host_spring_directions(int S, double *q, double *w);
@@ -317,6 +326,9 @@ int host_colouring(int64_t E, int64_t N, const int32_t *conn, int32_t *colour, i
 // coarse (vertex) numbering and interpolation parents of every node; returns the coarse count or -1
 int64_t host_coarse_map(int64_t E, int64_t N, const int32_t *conn, int32_t *cid, int32_t *par);
 void host_material_constants(const ns_material &m, double f1, double f2, MatConst *out);
+// outcrop input velocity: the trapezoidal integral of acc [n][3] from v(0) = 0, with one
+// entry past the record (zero acceleration there): out [n + 1][3]
+void host_input_velocity(const double *acc, int64_t n, double dt, double *out);
 void host_pow_tables(double *out);   // kPowTabLen entries
 void host_powf_tables(float *out);   // kPowFLen entries (df64.cuh)
 // per-column exponents et[21] of the spring tables T [S][21] (max_k |T_k[ij]| 2^-et[ij] in

@@ -1,9 +1,12 @@
 // Served ensemble runtime (include/ns_server.h): a first-come-first-served queue of
-// independent cases, admitted into concurrent slots by device and pinned-host memory,
-// each slot one context of the time stepper driven by its own host thread.
+// independent cases, admitted into concurrent slots by device and pinned-host memory;
+// each admitted case runs in a context of its own driven by its own host thread, or --
+// continuous batching -- as a member of the batched context of its solver class, which a
+// worker thread per class re-forms whenever a member arrives or finishes.
 #include "../../include/ns_server.h"
 
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -15,6 +18,8 @@
 #include <string>
 #include <thread>
 #include <vector>
+
+#include "ns_internal.h"
 
 namespace {
 
@@ -34,6 +39,39 @@ struct CaseRec {
   std::string err;
   std::vector<double> ru, rv, ra;
   std::thread th;
+  // batched: input velocity of the whole record ([n_samples + 1][3]) and steps done
+  std::vector<double> vin;
+  int64_t done = 0;
+  double ms_share = 0.0, launch_share = 0.0;
+};
+
+// Solver class of a case: the settings that one batched context shares among its members.
+struct ClassKey {
+  int32_t precision, x0_prev, cg_max_iter, inner_max_iter, graphs, pair_operator;
+  double dt, cg_tol, inner_tol, f1, f2;
+  bool operator<(const ClassKey &o) const { return memcmp(this, &o, sizeof(ClassKey)) < 0; }
+};
+ClassKey class_of(const ns_config &c) {
+  ClassKey k;
+  memset(&k, 0, sizeof(k));
+  k.precision = c.precision;
+  k.x0_prev = c.x0_prev;
+  k.cg_max_iter = c.cg_max_iter;
+  k.inner_max_iter = c.inner_max_iter;
+  k.graphs = c.graphs;
+  k.pair_operator = c.pair_operator;
+  k.dt = c.dt;
+  k.cg_tol = c.cg_tol;
+  k.inner_tol = c.inner_tol;
+  k.f1 = c.rayleigh_f1;
+  k.f2 = c.rayleigh_f2;
+  return k;
+}
+
+struct ClassWorker {
+  std::vector<CaseRec *> pending;  // admitted, not yet in the batch
+  std::thread th;
+  bool running = false;
 };
 
 }  // namespace
@@ -49,6 +87,7 @@ struct ns_server {
   int64_t dev_used = 0, pin_used = 0;
   bool stop = false;
   std::thread sched;
+  std::map<ClassKey, ClassWorker> classes;  // continuous batching (cfg.batch)
   std::chrono::steady_clock::time_point t0;
 
   double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -59,7 +98,8 @@ namespace {
 // Head of the queue admissible now?  Decides resident or streamed placement.
 bool can_admit(ns_server *s, CaseRec &r) {
   if (s->active >= s->cfg.max_active) return false;
-  if (s->dev_used + r.dev_resident <= s->cfg.device_budget) {
+  const int64_t dev_cap = s->cfg.batch ? s->cfg.device_budget / 2 : s->cfg.device_budget;
+  if (s->dev_used + r.dev_resident <= dev_cap) {
     r.st.streamed = 0;
     r.reserved_dev = r.dev_resident;
     r.reserved_pin = 0;
@@ -130,6 +170,232 @@ void run_case(ns_server *s, CaseRec *r) {
   s->cv.notify_all();
 }
 
+// ------------------------------------------------------------------ continuous batching
+
+void finish_case(ns_server *s, CaseRec *r, int rc) {  // with s->mu held
+  r->st.error = rc;
+  r->st.state = rc == NS_OK ? NS_CASE_DONE : NS_CASE_FAILED;
+  r->st.t_done = s->now();
+  r->st.ms_device = r->ms_share;
+  r->st.kernel_launches = (int64_t)(r->launch_share + 0.5);
+  s->dev_used -= r->reserved_dev;
+  s->pin_used -= r->reserved_pin;
+  s->active--;
+  s->cv.notify_all();
+}
+
+// A batched context for the members, in order: the disjoint union of their meshes, their
+// material tables one after another, their springs per point, and each member's input
+// velocity from its own step on.  *surf_off receives the members' surface-row ranges.
+int form_batch(ns_server *s, const std::vector<CaseRec *> &mem, ns_ctx **out, std::vector<int64_t> &surf_off) {
+  *out = nullptr;
+  const int M = (int)mem.size();
+  std::vector<int64_t> eo(M + 1, 0), no(M + 1, 0), fo(M + 1, 0), so(M + 1, 0);
+  int32_t nmat = 0;
+  for (int m = 0; m < M; ++m) {
+    eo[m + 1] = eo[m] + mem[m]->n_elems;
+    no[m + 1] = no[m] + mem[m]->n_nodes;
+    fo[m + 1] = fo[m] + mem[m]->n_faces;
+    so[m + 1] = so[m] + mem[m]->n_surf;
+    nmat += mem[m]->n_mat;
+  }
+  if (nmat > 1024) return NS_ERR_INVALID_ARG;
+  std::vector<double> xyz(3 * (size_t)no[M]);
+  std::vector<int32_t> conn(10 * (size_t)eo[M]), mat((size_t)eo[M]), faces(6 * (size_t)fo[M]), fe((size_t)fo[M]),
+      fk((size_t)fo[M]), surf((size_t)so[M]);
+  std::vector<ns_material> mats;
+  std::vector<int32_t> S(M);
+  int64_t horizon = 0;
+  int32_t mo = 0;
+  for (int m = 0; m < M; ++m) {
+    const CaseRec &r = *mem[m];
+    std::copy(r.xyz.begin(), r.xyz.end(), xyz.begin() + 3 * no[m]);
+    for (int64_t i = 0; i < 10 * r.n_elems; ++i) conn[10 * eo[m] + i] = r.conn[i] + (int32_t)no[m];
+    for (int64_t e = 0; e < r.n_elems; ++e) mat[eo[m] + e] = r.mat[e] + mo;
+    for (int64_t i = 0; i < 6 * r.n_faces; ++i) faces[6 * fo[m] + i] = r.faces[i] + (int32_t)no[m];
+    for (int64_t f = 0; f < r.n_faces; ++f) {
+      fe[fo[m] + f] = r.face_elem[f] + (int32_t)eo[m];
+      fk[fo[m] + f] = r.face_kind[f];
+    }
+    for (int64_t i = 0; i < r.n_surf; ++i) surf[so[m] + i] = r.surf[i] + (int32_t)no[m];
+    mats.insert(mats.end(), r.mats.begin(), r.mats.end());
+    mo += r.n_mat;
+    S[m] = r.cfg.n_springs;
+    horizon = std::max(horizon, r.n_steps - r.done);
+  }
+  ns_config cfg = mem[0]->cfg;
+  cfg.device = s->cfg.device;
+  cfg.surface_ring_steps = std::max(1, s->cfg.quantum_steps);
+  cfg.device_state_budget = -1;
+  cfg.scatter = NS_SCATTER_ATOMIC;
+  cfg.shared_members = 0;
+  cfg.multigrid = 0;
+  cfg.spring_tile_points = 0;
+  cudaSetDevice(s->cfg.device);
+  ns_ctx *c = nullptr;
+  int rc = ns_create(&c, &cfg);
+  if (rc == NS_OK) rc = ns_upload_mesh(c, no[M], xyz.data(), eo[M], conn.data(), mat.data());
+  if (rc == NS_OK) rc = ns_set_materials(c, nmat, mats.data());
+  if (rc == NS_OK)
+    rc = ns_set_boundary(c, fo[M], faces.data(), fe.data(), fk.data(), so[M], surf.data());
+  if (rc == NS_OK && M > 1) rc = ns_set_members(c, M, eo.data(), no.data());
+  if (rc == NS_OK && M > 1) rc = ns_set_member_springs(c, M, S.data());
+  if (rc == NS_OK) {  // a zero record of the batch's length, then each member's own velocity
+    std::vector<double> zero(3 * (size_t)(horizon + 1), 0.0);
+    rc = ns_set_ground_motion(c, horizon + 1, cfg.dt, zero.data());
+  }
+  for (int m = 0; m < M && rc == NS_OK; ++m) {
+    const CaseRec &r = *mem[m];
+    const int64_t k0 = std::min<int64_t>(r.done, r.n_samples);
+    rc = ns::ctx_set_member_velocity(c, m, r.vin.data() + 3 * k0, r.n_samples + 1 - k0);
+  }
+  if (rc != NS_OK) {
+    if (c) ns_destroy(c);
+    return rc;
+  }
+  surf_off = so;
+  *out = c;
+  return NS_OK;
+}
+
+// Worker of one solver class: keeps its admitted cases in one batched context, re-formed
+// when a case arrives or finishes, and advances it a quantum at a time.
+void class_worker(ns_server *s, ClassKey key) {
+  std::vector<CaseRec *> mem;
+  ns_ctx *ctx = nullptr;
+  std::vector<int64_t> soff;
+  for (;;) {
+    std::vector<CaseRec *> arrived;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      ClassWorker &w = s->classes[key];
+      if (mem.empty())
+        s->cv.wait(lk, [&] { return s->stop || !w.pending.empty(); });
+      if (s->stop) {
+        for (CaseRec *r : mem) {
+          r->err = "server stopped";
+          finish_case(s, r, NS_ERR_STATE);
+        }
+        for (CaseRec *r : w.pending) {
+          r->err = "server stopped";
+          finish_case(s, r, NS_ERR_STATE);
+        }
+        w.pending.clear();
+        w.running = false;
+        break;
+      }
+      arrived.swap(w.pending);
+    }
+    int rc = NS_OK;
+    if (!arrived.empty() || !ctx) {  // re-form: continuing members first, then the arrivals
+      std::vector<CaseRec *> next = mem;
+      next.insert(next.end(), arrived.begin(), arrived.end());
+      ns_ctx *nc = nullptr;
+      std::vector<int64_t> so;
+      rc = form_batch(s, next, &nc, so);
+      for (size_t m = 0; m < mem.size() && rc == NS_OK; ++m) rc = ns::ctx_copy_member(nc, (int)m, ctx, (int)m);
+      if (rc != NS_OK) {
+        std::string e = nc ? ns_last_error(nc) : (ctx ? ns_last_error(ctx) : "batch formation failed");
+        if (nc) ns_destroy(nc);
+        if (ctx) ns_destroy(ctx);
+        ctx = nullptr;
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (CaseRec *r : next) {
+          r->err = e;
+          finish_case(s, r, rc);
+        }
+        mem.clear();
+        continue;
+      }
+      if (ctx) ns_destroy(ctx);
+      ctx = nc;
+      soff = so;
+      mem = next;
+      for (CaseRec *r : mem) r->st.batches++;
+    }
+    // one quantum, no further than the nearest finishing member
+    int64_t q = s->cfg.quantum_steps;
+    for (CaseRec *r : mem) q = std::min(q, r->n_steps - r->done);
+    ns_stats st0{}, st1{};
+    ns_get_stats(ctx, &st0);
+    rc = ns_advance(ctx, q);
+    ns_get_stats(ctx, &st1);
+    int64_t Etot = 0;
+    for (CaseRec *r : mem) Etot += r->n_elems;
+    if (rc == NS_OK) {
+      const int64_t ns_all = soff.back(), step1 = ns::ctx_steps(ctx) - q + 1;
+      std::vector<double> u(3 * (size_t)ns_all * q), v(u.size()), a(u.size());
+      if (ns_all > 0) rc = ns_read_surface(ctx, step1, q, u.data(), v.data(), a.data());
+      for (size_t m = 0; m < mem.size() && rc == NS_OK; ++m) {
+        CaseRec *r = mem[m];
+        const int64_t k = soff[m + 1] - soff[m];
+        for (int64_t t = 0; t < q; ++t) {
+          const size_t dst = ((size_t)(r->done + t) * r->n_surf) * 3, src = ((size_t)t * ns_all + soff[m]) * 3;
+          std::copy(u.begin() + src, u.begin() + src + 3 * k, r->ru.begin() + dst);
+          std::copy(v.begin() + src, v.begin() + src + 3 * k, r->rv.begin() + dst);
+          std::copy(a.begin() + src, a.begin() + src + 3 * k, r->ra.begin() + dst);
+        }
+        const double share = (double)r->n_elems / (double)std::max<int64_t>(Etot, 1);
+        r->ms_share += share * (st1.ms_advance - st0.ms_advance);
+        r->launch_share += share * (double)(st1.kernel_launches - st0.kernel_launches);
+        r->done += q;
+      }
+    }
+    std::vector<CaseRec *> keep;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (rc != NS_OK) {
+        const std::string e = ns_last_error(ctx);
+        for (CaseRec *r : mem) {
+          r->err = e;
+          finish_case(s, r, rc);
+        }
+      } else {
+        for (CaseRec *r : mem) {
+          if (r->done >= r->n_steps)
+            finish_case(s, r, NS_OK);
+          else
+            keep.push_back(r);
+        }
+      }
+    }
+    if (rc != NS_OK || keep.size() != mem.size()) {  // a member left: re-form (or close)
+      if (!keep.empty()) {
+        ns_ctx *nc = nullptr;
+        std::vector<int64_t> so;
+        int r2 = form_batch(s, keep, &nc, so);
+        for (size_t m = 0, j = 0; m < mem.size() && r2 == NS_OK; ++m) {
+          if (j < keep.size() && mem[m] == keep[j]) {
+            r2 = ns::ctx_copy_member(nc, (int)j, ctx, (int)m);
+            ++j;
+          }
+        }
+        ns_destroy(ctx);
+        ctx = nullptr;
+        if (r2 != NS_OK) {
+          std::string e = nc ? ns_last_error(nc) : "batch formation failed";
+          if (nc) ns_destroy(nc);
+          std::lock_guard<std::mutex> lk(s->mu);
+          for (CaseRec *r : keep) {
+            r->err = e;
+            finish_case(s, r, r2);
+          }
+          keep.clear();
+        } else {
+          ctx = nc;
+          soff = so;
+          for (CaseRec *r : keep) r->st.batches++;
+        }
+      } else {
+        ns_destroy(ctx);
+        ctx = nullptr;
+      }
+      mem = keep;
+    }
+  }
+  if (ctx) ns_destroy(ctx);
+}
+
 void scheduler(ns_server *s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
@@ -144,7 +410,25 @@ void scheduler(ns_server *s) {
     s->dev_used += r->reserved_dev;
     s->pin_used += r->reserved_pin;
     s->active++;
-    r->th = std::thread(run_case, s, r);
+    if (s->cfg.batch && !r->st.streamed) {  // a member of its class's batch
+      const size_t n = (size_t)r->n_steps * (size_t)r->n_surf * 3;
+      r->ru.assign(n, 0.0);
+      r->rv.assign(n, 0.0);
+      r->ra.assign(n, 0.0);
+      r->vin.assign(3 * (size_t)(r->n_samples + 1), 0.0);
+      ns::host_input_velocity(r->acc.data(), r->n_samples, r->cfg.dt, r->vin.data());
+      const ClassKey key = class_of(r->cfg);
+      ClassWorker &w = s->classes[key];
+      w.pending.push_back(r);
+      if (!w.running) {
+        if (w.th.joinable()) w.th.join();
+        w.running = true;
+        w.th = std::thread(class_worker, s, key);
+      }
+      s->cv.notify_all();
+    } else {
+      r->th = std::thread(run_case, s, r);
+    }
   }
 }
 
@@ -178,7 +462,8 @@ int ns_case_bytes(const ns_case *c, int64_t *device_bytes, int64_t *state_bytes,
 }
 
 int ns_server_create(ns_server **out, const ns_server_config *cfg) {
-  if (!out || !cfg || cfg->max_active < 1 || cfg->device_budget <= 0 || cfg->pinned_budget < 0 || cfg->device < 0)
+  if (!out || !cfg || cfg->max_active < 1 || cfg->device_budget <= 0 || cfg->pinned_budget < 0 || cfg->device < 0 ||
+      (cfg->batch != 0 && cfg->batch != 1))
     return NS_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device >= ndev) {
@@ -305,6 +590,8 @@ void ns_server_destroy(ns_server *s) {
   if (s->sched.joinable()) s->sched.join();
   for (auto &kv : s->cases)
     if (kv.second->th.joinable()) kv.second->th.join();
+  for (auto &kv : s->classes)
+    if (kv.second.th.joinable()) kv.second.th.join();
   delete s;
 }
 

@@ -105,3 +105,66 @@ def test_served_case_matches_oracle():
         for f, ref in (("u", np.array(us)), ("v", np.array(vs))):
             err = np.linalg.norm(got[k][f] - ref) / np.linalg.norm(ref)
             assert err <= 1e-6, (k, f, err)
+
+
+def test_batched_serving_matches_alone_and_oracle():
+    """Continuous batching (batch = 1): cases of one solver class with different meshes and
+    springs per point run as the members of one batched context, re-formed whenever a case
+    arrives or finishes; each record equals the case run alone (both solving to 1e-12, the
+    atomic sums leaving rounding only: 1e-9) and the FP64 oracle (1e-6)."""
+    import time
+
+    import oracle
+    spec = [((3, 2, 8), 10, 1, 110), ((4, 3, 8), 20, 2, 40), ((2, 2, 10), 15, 3, 55), ((5, 2, 8), 12, 4, 25)]
+    wls = [case(d, S, seed, nt=n) for d, S, seed, n in spec]
+    steps = [n for *_, n in spec]
+    kw = dict(precision=B.NS_PREC_FP64_IR, cg_tol=1e-12)
+    with B.Server(max_active=4, quantum_steps=5, batch=1) as srv:
+        ids = [srv.submit(wls[0], steps[0], **kw)]
+        time.sleep(0.2)  # the others arrive while the first one runs
+        ids += [srv.submit(w, n, **kw) for w, n in zip(wls[1:], steps[1:])]
+        st = [srv.wait(i, 600) for i in ids]
+        got = [srv.result(i) for i in ids]
+    assert all(s["state"] == B.NS_CASE_DONE and s["error"] == 0 for s in st)
+    # the longest case saw the batch re-formed as the others joined and left
+    assert st[0]["batches"] >= 3, st[0]
+    for k, (wl, n) in enumerate(zip(wls, steps)):
+        with B.Simulation(wl, surface_ring_steps=n, **kw) as sim:
+            sim.advance(n)
+            ref = sim.surface(1, n)
+        for f in ("u", "v"):
+            err = np.linalg.norm(got[k][f] - ref[f]) / np.linalg.norm(ref[f])
+            assert err <= 1e-9, (k, f, err)
+    wl, n = wls[1], steps[1]
+    o = oracle.Oracle.from_workload(wl, tol=1e-12)
+    vs = []
+    for _ in range(n):
+        o.step()
+        vs.append(o.v[wl.mesh.surf].copy())
+    err = np.linalg.norm(got[1]["v"] - np.array(vs)) / np.linalg.norm(np.array(vs))
+    assert err <= 1e-6, err
+
+
+def test_member_springs_validation():
+    """Per-member springs: after the members, before the first step, all state resident."""
+    wls = [case((3, 2, 8), 10, 1), case((3, 2, 8), 10, 2)]
+    U = synth.union_of_copies(wls[0].mesh, 2, n_materials=2)
+    ctx = B.ns_create(B.ns_config_default(n_springs=10, dt=0.005))
+    try:
+        B.ns_upload_mesh(ctx, U.mesh.xyz, U.mesh.conn, U.mesh.mat)
+        B.ns_set_materials(ctx, wls[0].materials + wls[1].materials)
+        B.ns_set_boundary(ctx, U.mesh.faces, U.mesh.face_elem, U.mesh.face_kind, U.mesh.surf)
+        with pytest.raises(B.NsError):  # no members yet
+            B.ns_set_member_springs(ctx, [10, 20])
+        B.ns_set_members(ctx, U.elem_off, U.node_off)
+        with pytest.raises(B.NsError):  # too few springs
+            B.ns_set_member_springs(ctx, [10, 4])
+        B.ns_set_member_springs(ctx, [10, 20])
+        B.ns_set_ground_motion(ctx, wls[0].wave, 0.005)
+        B.ns_advance(ctx, 3)
+        with pytest.raises(B.NsError):  # set once
+            B.ns_set_member_springs(ctx, [10, 20])
+        with pytest.raises(B.NsError):  # the spring state of mixed members is not readable
+            B.ns_read_state(ctx, 0, 1, 10)
+    finally:
+        B.ns_destroy(ctx)
