@@ -322,6 +322,9 @@ def main():
                     help="skip the library's autotuner (spring-kernel block shape) after the warm-up steps")
     ap.add_argument("--prefetch", type=int, default=1, choices=[0, 1],
                     help="element operators prefetch their element rows into L2 (bulk prefetch)")
+    ap.add_argument("--local-gather", type=int, default=0, choices=[0, 1],
+                    help="FP32 inner operator: gather each block's distinct nodes into shared memory once (1) or "
+                         "per element (0)")
     ap.add_argument("--pair-op", type=int, default=0, choices=[0, 1],
                     help="FP64-accuracy operator applications in double-float arithmetic on the FP32 pipes")
     ap.add_argument("--x0", default="zero", choices=["prev", "zero"],
@@ -425,7 +428,8 @@ def main():
     kw = dict(device=local, timing=1, surface_ring_steps=max(args.steps, 1), precision=prec, graphs=graphs,
               stage_elements=args.stage, inner_max_iter=args.inner_iters, inner_tol=args.inner_tol, x0_prev=int(args.x0 == "prev"),
               pair_operator=args.pair_op, l2_prefetch=args.prefetch, spring_tile_points=args.spring_tile,
-              spring_tile_blocks=args.spring_blocks, spring_tensor_cores=args.spring_tensor)
+              spring_tile_blocks=args.spring_blocks, spring_tensor_cores=args.spring_tensor,
+              local_gather=args.local_gather)
     if args.multigrid and ens is None and prec != B.NS_PREC_FP64:
         kw.update(multigrid=1, coarse_max_iter=args.coarse_iters, coarse_tol=args.coarse_tol)
     else:
@@ -646,6 +650,7 @@ def main():
                 "multigrid": ({"coarse_max_iter": args.coarse_iters, "coarse_tol": args.coarse_tol}
                               if args.multigrid else None),
                 "pair_operator": args.pair_op, "x0": args.x0, "l2_prefetch": args.prefetch,
+                "local_gather": args.local_gather,
                 "steps_taken": sim_steps, "state_stream": stream, "other_configs": others}
         print(json.dumps(line), flush=True)
     dist.finalize(dd)

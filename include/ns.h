@@ -128,6 +128,11 @@ typedef struct {
                                   max mat)).  The members are set by ns_set_boundary (no
                                   ns_set_members); each solves its own CG.  Atomic scatter, no
                                   multigrid.  0 or 1: one model */
+  int32_t local_gather;        /* 1: the FP32 inner operator (one model, atomic scatter) gathers each
+                                  block's distinct nodes into shared memory once and adds its forces
+                                  there before one global atomic per node (node lists built at
+                                  ns_upload_mesh; skipped when a block's list exceeds 1,536 nodes);
+                                  0: per-element gathers and atomics */
 } ns_config;
 
 #define NS_STREAM_RING 0

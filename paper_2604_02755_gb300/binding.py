@@ -44,7 +44,7 @@ class ns_config(C.Structure):
                 ("spring_tile_points", C.c_int32), ("spring_tile_blocks", C.c_int32),
                 ("spring_tensor_cores", C.c_int32), ("fault_pinned_alloc", C.c_int32),
                 ("fault_state_copy", C.c_int32), ("multigrid", C.c_int32), ("coarse_max_iter", C.c_int32),
-                ("coarse_tol", C.c_double), ("shared_members", C.c_int32)]
+                ("coarse_tol", C.c_double), ("shared_members", C.c_int32), ("local_gather", C.c_int32)]
 
 
 class ns_material(C.Structure):

@@ -399,6 +399,127 @@ __global__ void __launch_bounds__(kTile, 2)
   }
 }
 
+// ------------------------------------------------------------------ locally gathered FP32 operator
+// One block = kBlock consecutive elements.  Phase 1 gathers the block's distinct nodes (its
+// node list, usually ~0.3 of its 10 kBlock element-node slots in a structured numbering)
+// from x into shared memory with independent loads; phase 2 computes every element from
+// shared memory (local 16-bit connectivity) and adds its forces into a shared accumulator
+// with shared atomics; phase 3 adds the accumulator to y, one global vector atomic per
+// distinct node.  The element arithmetic is ebe_element's (same point stresses, nodal
+// forces and consistent mass), so only the order of the FP32 sums differs.
+template <bool DOT, typename DL>
+__device__ __forceinline__ float ebe_element_local(const int nd[10], int mt, const float g[4][3], float vol,
+                                                   const DL &dl, const OpCoef *__restrict__ op, const float4 *xs,
+                                                   float *ys) {
+  const float cK = (float)op->kK[mt], cMk = (float)op->mK[mt];
+  float ye[10][3];
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ye[a][r] = 0.0f;
+  if (cK != 0.0f) {
+    float sig[4][6];
+    {
+      float x[10][3], P[4][3];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) {
+        const float4 q = xs[nd[a]];
+        x[a][0] = q.x;
+        x[a][1] = q.y;
+        x[a][2] = q.z;
+      }
+      compute_P(x, P);
+      point_stress<float, 0>(x, P, g, dl, 1.0f, sig[0]);
+      point_stress<float, 1>(x, P, g, dl, 1.0f, sig[1]);
+      point_stress<float, 2>(x, P, g, dl, 1.0f, sig[2]);
+      point_stress<float, 3>(x, P, g, dl, 1.0f, sig[3]);
+    }
+    points_force<float>(sig, g, cK * vol * 0.25f, ye);
+  }
+  if (cMk != 0.0f) {
+    const float c = vol * (1.0f / 420.0f);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      float w[10];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) w[a] = cMk * reinterpret_cast<const float *>(xs + nd[a])[r];
+      mass_apply_1(w, c, ye, r);
+    }
+  }
+  float ld = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 10; ++a) {
+    const float4 q = xs[nd[a]];
+    if (DOT) ld += q.x * ye[a][0] + q.y * ye[a][1] + q.z * ye[a][2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) atomicAdd(ys + 4 * nd[a] + r, ye[a][r]);
+  }
+  return ld;
+}
+
+template <typename TD, bool DOT>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_ebe32_local(int64_t E, int64_t epad, int64_t epg, const uint16_t *__restrict__ lconn,
+                  const int32_t *__restrict__ lnode, const int64_t *__restrict__ loff, const float *__restrict__ geom,
+                  const int32_t *__restrict__ mat, const TD *__restrict__ D, const OpCoef *__restrict__ op,
+                  const float4 *__restrict__ x, float4 *y, double *dot, const int32_t *skip) {
+  extern __shared__ float4 lsm[];
+  if (skip && *skip) return;
+  const int64_t b = blockIdx.x, u0 = loff[b];
+  const int n = (int)(loff[b + 1] - u0);
+  float4 *xs = lsm;
+  float4 *ys = lsm + n;
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    xs[i] = __ldg(x + lnode[u0 + i]);
+    ys[i] = zero;
+  }
+  __syncthreads();
+  double mydot = 0.0;
+  const int64_t e = b * kBlock + threadIdx.x;
+  if (e < E) {
+    int nd[10];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) nd[a] = (int)__ldg(lconn + a * epg + e);
+    const int mt = ldg(mat + e);
+    float g[4][3], vol;
+    load_grads(geom, epg, e, g, vol);
+    const auto dl = [&](int k) { return dload(D, epad, e, k); };
+    mydot = (double)ebe_element_local<DOT>(nd, mt, g, vol, dl, op, xs, reinterpret_cast<float *>(ys));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(y + lnode[u0 + i], ys[i]);
+  if (DOT) {
+    const double s = block_sum(mydot);
+    if (threadIdx.x == 0) dot[blockIdx.x] = s;
+  }
+}
+
+template <typename TD>
+static cudaError_t local_dispatch(const DevMesh &m, const TD *D, const OpCoef *op, const float *xk, float *y,
+                                  double *dot, const int32_t *skip, cudaStream_t s) {
+  const size_t smem = (size_t)m.lmax * 2 * sizeof(float4);
+  static std::atomic<unsigned long long> done{0};  // per-device shared-memory opt-in
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load() & bit)) {
+    cudaFuncSetAttribute(k_ebe32_local<TD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLocalMaxNodes * 32);
+    cudaFuncSetAttribute(k_ebe32_local<TD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLocalMaxNodes * 32);
+    done.fetch_or(bit);
+  }
+  const unsigned nb = (unsigned)((m.E + kBlock - 1) / kBlock);
+  const float4 *x4 = reinterpret_cast<const float4 *>(xk);
+  float4 *y4 = reinterpret_cast<float4 *>(y);
+  if (dot)
+    k_ebe32_local<TD, true><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.epg, m.lconn, m.lnode, m.loff, m.geom32, m.mat, D,
+                                                    op, x4, y4, dot, skip);
+  else
+    k_ebe32_local<TD, false><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.epg, m.lconn, m.lnode, m.loff, m.geom32, m.mat,
+                                                     D, op, x4, y4, dot, skip);
+  return cudaGetLastError();
+}
+
 template <typename T, typename TD, int VS, bool HAS_XM>
 static cudaError_t ebe_dispatch(const DevMesh &m, const TD *D, const T *geom, const OpCoef *op,
                                 const typename VecOf<T>::type *xm, const typename VecOf<T>::type *xk,
@@ -482,6 +603,8 @@ cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, con
                          cudaStream_t s, SegList sg, bool staged) {
   if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr && m.Msh == 1)
     return staged_dispatch<float>(m, D, op, xk, y, dot, skip, s);
+  if (m.lmax > 0 && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1)
+    return local_dispatch<float>(m, D, op, xk, y, dot, skip, s);
   // inner-solve vectors are [N][4]
   return ebe_dispatch<float, float, 4, false>(m, D, m.geom32, op, nullptr, xk, y, ids, e0, e1, atomic, dot, skip, s,
                                               sg);
@@ -492,6 +615,8 @@ cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, co
                          cudaStream_t s, SegList sg, bool staged) {
   if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr && m.Msh == 1)
     return staged_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
+  if (m.lmax > 0 && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1)
+    return local_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
   return ebe_dispatch<float, __half2, 4, false>(m, static_cast<const __half2 *>(D16), m.geom32, op, nullptr, xk, y,
                                                 ids, e0, e1, atomic, dot, skip, s, sg);
 }

@@ -1079,6 +1079,7 @@ void ns_config_default(ns_config *cfg) {
   cfg->coarse_max_iter = 20;
   cfg->coarse_tol = 1e-2;
   cfg->shared_members = 0;
+  cfg->local_gather = 0;
 }
 
 static thread_local std::string g_create_err;
@@ -1104,7 +1105,7 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
       (cfg->stream_mode != NS_STREAM_RING && cfg->stream_mode != NS_STREAM_ZERO_COPY) ||
       (cfg->spring_tile_points != 0 && !spring_tile_ok(cfg->spring_tile_points, cfg->n_springs)) ||
       (cfg->spring_tile_blocks != 0 && cfg->spring_tile_blocks != 1 && cfg->spring_tile_blocks != 4) ||
-      (cfg->multigrid != 0 && cfg->multigrid != 1) || cfg->shared_members < 0 || cfg->shared_members > 65536 ||
+      (cfg->multigrid != 0 && cfg->multigrid != 1) || (cfg->local_gather != 0 && cfg->local_gather != 1) || cfg->shared_members < 0 || cfg->shared_members > 65536 ||
       (cfg->shared_members > 1 && (cfg->scatter != NS_SCATTER_ATOMIC || cfg->multigrid)) ||
       (cfg->multigrid && (cfg->precision == NS_PREC_FP64 || cfg->coarse_max_iter < 1 || !(cfg->coarse_tol > 0)))) {
     g_create_err = "invalid configuration value";
@@ -1257,6 +1258,44 @@ int ns_upload_mesh(ns_ctx *c, int64_t N, const double *xyz, int64_t E, const int
     CKC(c, cudaMemcpy(m.ecol_ids, ids.data(), E * 4, cudaMemcpyHostToDevice));
   }
   c->part_pap_cap = nblk(m.E) + (int64_t)nc + 64 + nblk(1) * 2;
+  if (c->cfg.local_gather && Ms == 1 && c->cfg.scatter == NS_SCATTER_ATOMIC) {
+    // node lists of the locally gathered FP32 operator: per block of kBlock elements its
+    // distinct nodes in first-use order, each element's nodes as indices into that list
+    const int64_t nb = nblk(E);
+    std::vector<int64_t> loff((size_t)nb + 1, 0);
+    std::vector<int32_t> lnode;
+    lnode.reserve((size_t)E * 4);
+    std::vector<uint16_t> lc((size_t)10 * m.epg, 0);
+    std::vector<int64_t> stamp((size_t)N, -1);
+    std::vector<int32_t> local((size_t)N, 0);
+    int32_t lmax = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+      const int64_t e0 = b * kBlock, e1 = std::min<int64_t>(E, e0 + kBlock);
+      int32_t k = 0;
+      for (int64_t e = e0; e < e1 && k <= kLocalMaxNodes; ++e)
+        for (int a = 0; a < 10; ++a) {
+          const int32_t nd = conn[e * 10 + a];
+          if (stamp[nd] != b) {
+            stamp[nd] = b;
+            local[nd] = k++;
+            lnode.push_back(nd);
+          }
+          lc[(size_t)a * m.epg + e] = (uint16_t)local[nd];
+        }
+      lmax = std::max(lmax, k);
+      loff[b + 1] = (int64_t)lnode.size();
+      if (lmax > kLocalMaxNodes) break;
+    }
+    if (lmax <= kLocalMaxNodes) {
+      if ((rc = dalloc(c, &m.lconn, lc.size())) || (rc = dalloc(c, &m.lnode, lnode.size())) ||
+          (rc = dalloc(c, &m.loff, loff.size())))
+        return rc;
+      CKC(c, cudaMemcpy(m.lconn, lc.data(), lc.size() * 2, cudaMemcpyHostToDevice));
+      CKC(c, cudaMemcpy(m.lnode, lnode.data(), lnode.size() * 4, cudaMemcpyHostToDevice));
+      CKC(c, cudaMemcpy(m.loff, loff.data(), loff.size() * 8, cudaMemcpyHostToDevice));
+      m.lmax = lmax;
+    }  // else: node lists too long for shared memory (e.g. a shuffled numbering): direct gathers
+  }
   if (c->cfg.multigrid) {  // coarse level of the two-level preconditioner
     MgLevel &g = c->mg;
     c->cid_h.assign((size_t)N, -1);
@@ -2306,6 +2345,7 @@ void ns_destroy(ns_ctx *c) {
   DevMesh &m = c->m;
   dfree(m.conn); dfree(m.geom); dfree(m.geom32); dfree(m.mat); dfree(m.kerr); dfree(m.geom2); dfree(m.fnode); dfree(m.fgeom); dfree(m.fmat);
   dfree(m.fkind); dfree(m.surf); dfree(m.ecol_ids); dfree(m.fcol_ids);
+  dfree(m.lconn); dfree(m.lnode); dfree(m.loff);
   dfree(c->xyz_d); dfree(c->mats_d); dfree(c->op_A); dfree(c->op_K); dfree(c->op_M); dfree(c->op_Cr);
   dfree(c->op_rhs); dfree(c->q_d); dfree(c->T_d); dfree(c->pow_d); dfree(c->powf_d); dfree(c->T2_d); dfree(c->tfrag_d); dfree(c->tsc_d); dfree(c->q2_d); dfree(c->D); dfree(c->D32);
   dfree(c->D16); dfree(c->op_A16); dfree(c->D2);

@@ -16,6 +16,7 @@ constexpr int kDPack = 21;     // unique entries of a symmetric 6x6
 constexpr int kMaxMat = 1024;  // material table entries (members of a batch each bring their own)
 constexpr int kBlock = 256;
 constexpr int kSpringCountSlots = 64;  // spread of the spring kernel's counter atomics
+constexpr int kLocalMaxNodes = 1536;   // largest node list of a locally gathered operator block
 
 // Per-material constants derived on the host from ns_material and the config.
 struct MatConst {
@@ -68,6 +69,14 @@ struct DevMesh {
   // Fb = F, epg = epad, fpg = fpad.
   int32_t Msh = 1;
   int64_t Eb = 0, Nb = 0, Fb = 0, epg = 0, fpg = 0;
+  // Local gathering of the FP32 inner operator (one model, atomic scatter): block b of
+  // kBlock consecutive elements gathers its distinct nodes lnode[loff[b] .. loff[b+1])
+  // (ascending) once into shared memory; lconn [10][epg] holds each element's nodes as
+  // indices into its block's list.  lmax: the largest list (0: not built).
+  uint16_t *lconn = nullptr;
+  int32_t *lnode = nullptr;
+  int64_t *loff = nullptr;
+  int32_t lmax = 0;
   // element offset argument of the kernels: 0 without sharing
   int64_t eb_arg() const { return Msh > 1 ? Eb : 0; }
   int64_t fb_arg() const { return Msh > 1 ? Fb : 0; }

@@ -511,3 +511,27 @@ def test_main_motion_column_matches_oracle():
     print("main-motion column, both at 1e-8: u %.2e v %.2e; oracle 1e-8 vs 1e-12: u %.2e v %.2e" % (
         rel(s8["u"], us8), rel(s8["v"], vs8), rel(us8, us), rel(vs8, vs)))
     assert rel(s8["u"], us8) <= 1e-3 and rel(s8["v"], vs8) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", [B.NS_PREC_FP64_IR, B.NS_PREC_FP64_IR16])
+def test_local_gather_operator_equals_direct(precision):
+    """The FP32 inner operator gathering each block's distinct nodes into shared memory
+    (local connectivity, shared-memory force sums, one global atomic per node) computes what
+    the per-element gathers compute: both solve to 1e-12, so the records agree to the
+    rounding of the FP32 sums' order; and against the oracle at 1e-8."""
+    wl = small(dims=(6, 5, 4), nt=60)  # 720 elements: two full blocks of 256 and a ragged one
+    out = []
+    for lg in (0, 1):
+        with B.Simulation(wl, surface_ring_steps=30, precision=precision, local_gather=lg, cg_tol=1e-12,
+                          x0_prev=0) as sim:
+            sim.advance(30)
+            out.append(sim.surface(1, 30)["v"])
+    assert rel(out[1], out[0]) <= 1e-9
+    o = oracle.Oracle.from_workload(wl, x0_prev=False)
+    vs = []
+    for _ in range(30):
+        o.step()
+        vs.append(o.v[wl.mesh.surf].copy())
+    with B.Simulation(wl, surface_ring_steps=30, precision=precision, local_gather=1, x0_prev=0) as sim:
+        sim.advance(30)
+        assert rel(sim.surface(1, 30)["v"], np.array(vs)) <= 1e-6
