@@ -234,7 +234,8 @@ def served(args, dd, rank, ws, local):
     arrival times to the serving runtime; value = all requests' element-steps over the
     makespan (first arrival to last completion), with p50/p99 time to solution."""
     from paper_2604_02755_gb300 import binding as B
-    trace = synth.served_trace(R=args.requests, step_scale=args.step_scale, seed=5 + rank)
+    trace = synth.served_trace(R=args.requests, step_scale=args.step_scale, seed=5 + rank, e_lo=args.e_lo,
+                               e_hi=args.e_hi)
     prec = {"fp64-ir": B.NS_PREC_FP64_IR, "fp64-ir16": B.NS_PREC_FP64_IR16, "fp64-pcg": B.NS_PREC_FP64}[args.solver]
     clk_path = os.path.join(tempfile.gettempdir(), "ns_clocks_%d.csv" % rank)
     srv = B.Server(device=local, pinned_budget=int(args.pinned_gb * 1e9), max_active=args.max_active,
@@ -266,9 +267,9 @@ def served(args, dd, rank, ws, local):
                 "unit": "elem-steps/s", "n_gpus": ws, "steps": len(trace), "warmup": 0,
                 "ms_per_step": job_s / max(1, len(trace)) * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "served ensemble: %d requests, Poisson arrivals 4/s, %d-%d elements, "
-                                       "20-150 springs, steps U[1000,4000] x %g" %
-                                       (len(trace), min(sizes), max(sizes), args.step_scale),
+                "config": {"workload": "served ensemble: %d requests, Poisson arrivals 4/s, %d-%d elements "
+                                       "(log-uniform in %g-%g), 20-150 springs, steps U[1000,4000] x %g" %
+                                       (len(trace), min(sizes), max(sizes), args.e_lo, args.e_hi, args.step_scale),
                            "max_active": args.max_active, "solver": args.solver, "graphs": 1,
                            "batch": "continuous batching of each solver class" if args.batch else
                                     "one context per request",
@@ -278,7 +279,8 @@ def served(args, dd, rank, ws, local):
                 "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "max": float(wait.max())},
                 "streamed_requests": int(sum(s_["streamed"] for s_ in st)), "failed": len(failed),
                 "batching": ({"batches_per_request": float(np.mean([s_["batches"] for s_ in st])),
-                              "requests_batched": int(sum(s_["batches"] > 0 for s_ in st))}
+                              "requests_batched": int(sum(s_["batches"] > 0 for s_ in st)),
+                              "reform_s_per_request": float(np.mean([s_["t_reform"] for s_ in st]))}
                              if args.batch else None),
                 "offered_load": {"requests_per_s": 4.0,
                                  "elem_steps_per_request_mean": float(np.mean([r.workload.mesh.n_elems * r.n_steps
@@ -341,6 +343,8 @@ def main():
     ap.add_argument("--step-scale", type=float, default=0.01,
                     help="served trace: fraction of the 1000-4000 steps each request runs")
     ap.add_argument("--max-active", type=int, default=4, help="served: requests in flight together")
+    ap.add_argument("--e-lo", type=float, default=5e4, help="served: smallest mesh (elements, log-uniform)")
+    ap.add_argument("--e-hi", type=float, default=2e6, help="served: largest mesh (elements, log-uniform)")
     ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
                     help="served: continuous batching of compatible requests in one batched context (1) or one "
                          "context per request (0)")

@@ -95,6 +95,7 @@ typedef struct {
   double ms_device;         /* CUDA-event time of its ns_advance calls (batched: its share of the
                                batches' time, in proportion to its elements) */
   int64_t kernel_launches;  /* the library's kernels its context launched (batched: its share) */
+  double t_reform;          /* batched: seconds its batches spent being re-formed around it */
 } ns_case_stats;
 
 /* Device bytes a case needs with all its state resident (*device_bytes), the part of it

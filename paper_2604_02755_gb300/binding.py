@@ -100,7 +100,7 @@ class ns_case_stats(C.Structure):
     _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("streamed", C.c_int32), ("batches", C.c_int32),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
                 ("device_bytes", C.c_int64), ("state_bytes", C.c_int64), ("elem_steps", C.c_int64),
-                ("ms_device", C.c_double), ("kernel_launches", C.c_int64)]
+                ("ms_device", C.c_double), ("kernel_launches", C.c_int64), ("t_reform", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

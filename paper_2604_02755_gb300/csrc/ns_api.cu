@@ -2420,3 +2420,14 @@ int ns_coarse_map(int64_t E, int64_t N, const int32_t *conn, int32_t *cid, int32
 }
 
 }  // extern "C"
+
+namespace ns {
+int ctx_set_members_built(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t *node_off) {
+  if (!c || !c->has_mesh || !c->has_bnd || c->has_motion || c->step > 0 || c->M > 1 || c->m.Msh > 1 ||
+      c->cfg.scatter != NS_SCATTER_ATOMIC || c->cfg.multigrid || M < 1 || !elem_off || !node_off)
+    return NS_ERR_STATE;
+  if (elem_off[0] != 0 || elem_off[M] != c->m.E || node_off[0] != 0 || node_off[M] != c->m.N)
+    return NS_ERR_INVALID_ARG;
+  return setup_members(c, M, elem_off, node_off);
+}
+}  // namespace ns

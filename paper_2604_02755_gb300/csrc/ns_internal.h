@@ -328,6 +328,9 @@ int ctx_copy_member(ns_ctx *dst, int md, ns_ctx *src, int ms);
 int ctx_set_member_velocity(ns_ctx *c, int m, const double *vin, int64_t n);
 // device bytes the context holds (its own allocations)
 int64_t ctx_steps(ns_ctx *c);
+// Member ranges of a disjoint union built by the caller itself (every element's nodes in its
+// member's range by construction): ns_set_members without reading the mesh back to check it.
+int ctx_set_members_built(ns_ctx *c, int32_t M, const int64_t *elem_off, const int64_t *node_off);
 
 // ------------------------------------------------------------------ ns_host.cpp
 int host_spring_directions(int S, double *q, double *w);

@@ -238,7 +238,7 @@ int form_batch(ns_server *s, const std::vector<CaseRec *> &mem, ns_ctx **out, st
   if (rc == NS_OK) rc = ns_set_materials(c, nmat, mats.data());
   if (rc == NS_OK)
     rc = ns_set_boundary(c, fo[M], faces.data(), fe.data(), fk.data(), so[M], surf.data());
-  if (rc == NS_OK && M > 1) rc = ns_set_members(c, M, eo.data(), no.data());
+  if (rc == NS_OK && M > 1) rc = ns::ctx_set_members_built(c, M, eo.data(), no.data());
   if (rc == NS_OK && M > 1) rc = ns_set_member_springs(c, M, S.data());
   if (rc == NS_OK) {  // a zero record of the batch's length, then each member's own velocity
     std::vector<double> zero(3 * (size_t)(horizon + 1), 0.0);
@@ -288,6 +288,7 @@ void class_worker(ns_server *s, ClassKey key) {
     }
     int rc = NS_OK;
     if (!arrived.empty() || !ctx) {  // re-form: continuing members first, then the arrivals
+      const auto tf0 = std::chrono::steady_clock::now();
       std::vector<CaseRec *> next = mem;
       next.insert(next.end(), arrived.begin(), arrived.end());
       ns_ctx *nc = nullptr;
@@ -311,7 +312,11 @@ void class_worker(ns_server *s, ClassKey key) {
       ctx = nc;
       soff = so;
       mem = next;
-      for (CaseRec *r : mem) r->st.batches++;
+      const double tf = std::chrono::duration<double>(std::chrono::steady_clock::now() - tf0).count();
+      for (CaseRec *r : mem) {
+        r->st.batches++;
+        r->st.t_reform += tf;
+      }
     }
     // one quantum, no further than the nearest finishing member
     int64_t q = s->cfg.quantum_steps;
@@ -360,6 +365,7 @@ void class_worker(ns_server *s, ClassKey key) {
       }
     }
     if (rc != NS_OK || keep.size() != mem.size()) {  // a member left: re-form (or close)
+      const auto tf0 = std::chrono::steady_clock::now();
       if (!keep.empty()) {
         ns_ctx *nc = nullptr;
         std::vector<int64_t> so;
@@ -384,7 +390,11 @@ void class_worker(ns_server *s, ClassKey key) {
         } else {
           ctx = nc;
           soff = so;
-          for (CaseRec *r : keep) r->st.batches++;
+          const double tf = std::chrono::duration<double>(std::chrono::steady_clock::now() - tf0).count();
+          for (CaseRec *r : keep) {
+            r->st.batches++;
+            r->st.t_reform += tf;
+          }
         }
       } else {
         ns_destroy(ctx);
