@@ -92,6 +92,10 @@ struct ns_ctx {
   std::vector<int64_t> spr_off;
   std::vector<SpringTables> mtab;
   std::vector<void *> mtab_mem;
+  // their spring launches are spread over these streams (forked from and joined to the main one)
+  static constexpr int kMemberStreams = 4;
+  cudaStream_t s_mem[kMemberStreams] = {};
+  cudaEvent_t ev_fork = nullptr, ev_mem[kMemberStreams] = {};
   std::vector<int32_t> cid_h;
   double *eps = nullptr;
   double *part = nullptr;
@@ -524,15 +528,22 @@ int spring_launch(ns_ctx *c, const SpringSoA &st, int64_t base_elem, int64_t e0,
 int spring_phase(ns_ctx *c) {
   int rc;
   LAUNCH(c, launch_strain_pairs(c->m, c->u, c->du, c->eps, 0, c->m.E, c->s_main));
-  if (!c->mS.empty()) {  // members with their own springs: one launch per member, all state resident
+  if (!c->mS.empty()) {
+    // members with their own springs: one launch per member, all state resident; the
+    // launches go to kMemberStreams streams forked from the main one, so that small
+    // members' updates run side by side, and are joined back before the step ends
+    const int NS_ = ns_ctx::kMemberStreams;
+    CKC(c, cudaEventRecord(c->ev_fork, c->s_main));
+    for (int k = 0; k < NS_; ++k) CKC(c, cudaStreamWaitEvent(c->s_mem[k], c->ev_fork, 0));
     for (int m = 0; m < c->M; ++m) {
       const int64_t e0 = c->moff_e[m], e1 = c->moff_e[m + 1], o = c->spr_off[m];
       SpringSoA sm{c->st.tau + o, c->st.gR + o, c->st.tR + o, c->st.gmax + o, c->st.dir + o, c->st.mode + o};
-      cudaEvent_t t0 = nullptr;
-      tbegin(c, TK_SPRING, c->s_main, &t0);
       LAUNCH(c, launch_springs(c->mtab[m], c->mats_d, c->m.mat, nullptr, c->eps, sm, 4 * e0, 4 * e0, 4 * e1, c->D,
-                               c->m.epad, nullptr, c->s_main, true));
-      tend(c, TK_SPRING, c->s_main, t0);
+                               c->m.epad, nullptr, c->s_mem[m % NS_], true));
+    }
+    for (int k = 0; k < NS_; ++k) {
+      CKC(c, cudaEventRecord(c->ev_mem[k], c->s_mem[k]));
+      CKC(c, cudaStreamWaitEvent(c->s_main, c->ev_mem[k], 0));
     }
     return NS_OK;
   }
@@ -1767,6 +1778,11 @@ int ns_set_member_springs(ns_ctx *c, int32_t M, const int32_t *S) {
     for (void *p : mem) cudaFree(p);
     return rc;
   }
+  for (int k = 0; k < ns_ctx::kMemberStreams; ++k) {
+    if (!c->s_mem[k]) CKC(c, cudaStreamCreateWithFlags(&c->s_mem[k], cudaStreamNonBlocking));
+    if (!c->ev_mem[k]) CKC(c, cudaEventCreateWithFlags(&c->ev_mem[k], cudaEventDisableTiming));
+  }
+  if (!c->ev_fork) CKC(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   free_soa(c->st, false);
   c->st = st;
   c->mS.assign(S, S + M);
@@ -2390,6 +2406,11 @@ void ns_destroy(ns_ctx *c) {
   if (c->s_main) cudaStreamDestroy(c->s_main);
   if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
   if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+  for (int k = 0; k < ns_ctx::kMemberStreams; ++k) {
+    if (c->s_mem[k]) cudaStreamSynchronize(c->s_mem[k]), cudaStreamDestroy(c->s_mem[k]);
+    if (c->ev_mem[k]) cudaEventDestroy(c->ev_mem[k]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 

@@ -259,23 +259,68 @@ int form_batch(ns_server *s, const std::vector<CaseRec *> &mem, ns_ctx **out, st
 }
 
 // Worker of one solver class: keeps its admitted cases in one batched context, re-formed
-// when a case arrives or finishes, and advances it a quantum at a time.
+// when a case arrives, and advances it a quantum at a time.  A case that finishes is
+// finalised at once; while the finished members hold at most a quarter of the batch's
+// elements they stay in it, parked (still stepped, their output ignored), until the next
+// re-formation drops them -- which saves a re-formation per departure.
 void class_worker(ns_server *s, ClassKey key) {
-  std::vector<CaseRec *> mem;
+  struct Slot {
+    CaseRec *r;       // nullptr: parked (finished)
+    int64_t n_elems;
+  };
+  std::vector<Slot> mem;
   ns_ctx *ctx = nullptr;
   std::vector<int64_t> soff;
+  auto active_cases = [&]() {
+    std::vector<CaseRec *> v;
+    for (const Slot &sl : mem)
+      if (sl.r) v.push_back(sl.r);
+    return v;
+  };
+  // a new context for `next` (continuing cases first, in their current order); the
+  // continuing ones take their state from the current context
+  auto reform = [&](const std::vector<CaseRec *> &next) -> int {
+    const auto tf0 = std::chrono::steady_clock::now();
+    ns_ctx *nc = nullptr;
+    std::vector<int64_t> so;
+    int rc = next.empty() ? NS_OK : form_batch(s, next, &nc, so);
+    for (size_t m = 0, j = 0; m < mem.size() && rc == NS_OK && ctx; ++m)
+      if (mem[m].r && j < next.size() && mem[m].r == next[j]) rc = ns::ctx_copy_member(nc, (int)j++, ctx, (int)m);
+    if (ctx) ns_destroy(ctx);
+    ctx = nullptr;
+    mem.clear();
+    if (rc != NS_OK) {
+      std::string e = nc ? ns_last_error(nc) : "batch formation failed";
+      if (nc) ns_destroy(nc);
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (CaseRec *r : next) {
+        r->err = e;
+        finish_case(s, r, rc);
+      }
+      return rc;
+    }
+    ctx = nc;
+    soff = so;
+    const double tf = std::chrono::duration<double>(std::chrono::steady_clock::now() - tf0).count();
+    for (CaseRec *r : next) {
+      mem.push_back(Slot{r, r->n_elems});
+      r->st.batches++;
+      r->st.t_reform += tf;
+    }
+    return NS_OK;
+  };
   for (;;) {
     std::vector<CaseRec *> arrived;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       ClassWorker &w = s->classes[key];
-      if (mem.empty())
-        s->cv.wait(lk, [&] { return s->stop || !w.pending.empty(); });
+      if (active_cases().empty()) s->cv.wait(lk, [&] { return s->stop || !w.pending.empty(); });
       if (s->stop) {
-        for (CaseRec *r : mem) {
-          r->err = "server stopped";
-          finish_case(s, r, NS_ERR_STATE);
-        }
+        for (const Slot &sl : mem)
+          if (sl.r) {
+            sl.r->err = "server stopped";
+            finish_case(s, sl.r, NS_ERR_STATE);
+          }
         for (CaseRec *r : w.pending) {
           r->err = "server stopped";
           finish_case(s, r, NS_ERR_STATE);
@@ -286,53 +331,28 @@ void class_worker(ns_server *s, ClassKey key) {
       }
       arrived.swap(w.pending);
     }
-    int rc = NS_OK;
-    if (!arrived.empty() || !ctx) {  // re-form: continuing members first, then the arrivals
-      const auto tf0 = std::chrono::steady_clock::now();
-      std::vector<CaseRec *> next = mem;
+    if (!arrived.empty() || !ctx) {  // re-form: continuing cases first, then the arrivals (parked ones dropped)
+      std::vector<CaseRec *> next = active_cases();
       next.insert(next.end(), arrived.begin(), arrived.end());
-      ns_ctx *nc = nullptr;
-      std::vector<int64_t> so;
-      rc = form_batch(s, next, &nc, so);
-      for (size_t m = 0; m < mem.size() && rc == NS_OK; ++m) rc = ns::ctx_copy_member(nc, (int)m, ctx, (int)m);
-      if (rc != NS_OK) {
-        std::string e = nc ? ns_last_error(nc) : (ctx ? ns_last_error(ctx) : "batch formation failed");
-        if (nc) ns_destroy(nc);
-        if (ctx) ns_destroy(ctx);
-        ctx = nullptr;
-        std::lock_guard<std::mutex> lk(s->mu);
-        for (CaseRec *r : next) {
-          r->err = e;
-          finish_case(s, r, rc);
-        }
-        mem.clear();
-        continue;
-      }
-      if (ctx) ns_destroy(ctx);
-      ctx = nc;
-      soff = so;
-      mem = next;
-      const double tf = std::chrono::duration<double>(std::chrono::steady_clock::now() - tf0).count();
-      for (CaseRec *r : mem) {
-        r->st.batches++;
-        r->st.t_reform += tf;
-      }
+      if (reform(next) != NS_OK || !ctx) continue;
     }
-    // one quantum, no further than the nearest finishing member
+    // one quantum, no further than the nearest finishing case
     int64_t q = s->cfg.quantum_steps;
-    for (CaseRec *r : mem) q = std::min(q, r->n_steps - r->done);
+    for (const Slot &sl : mem)
+      if (sl.r) q = std::min(q, sl.r->n_steps - sl.r->done);
     ns_stats st0{}, st1{};
     ns_get_stats(ctx, &st0);
-    rc = ns_advance(ctx, q);
+    int rc = ns_advance(ctx, q);
     ns_get_stats(ctx, &st1);
     int64_t Etot = 0;
-    for (CaseRec *r : mem) Etot += r->n_elems;
+    for (const Slot &sl : mem) Etot += sl.n_elems;
     if (rc == NS_OK) {
       const int64_t ns_all = soff.back(), step1 = ns::ctx_steps(ctx) - q + 1;
       std::vector<double> u(3 * (size_t)ns_all * q), v(u.size()), a(u.size());
       if (ns_all > 0) rc = ns_read_surface(ctx, step1, q, u.data(), v.data(), a.data());
       for (size_t m = 0; m < mem.size() && rc == NS_OK; ++m) {
-        CaseRec *r = mem[m];
+        CaseRec *r = mem[m].r;
+        if (!r) continue;
         const int64_t k = soff[m + 1] - soff[m];
         for (int64_t t = 0; t < q; ++t) {
           const size_t dst = ((size_t)(r->done + t) * r->n_surf) * 3, src = ((size_t)t * ns_all + soff[m]) * 3;
@@ -346,61 +366,35 @@ void class_worker(ns_server *s, ClassKey key) {
         r->done += q;
       }
     }
-    std::vector<CaseRec *> keep;
+    int64_t parked = 0;
+    bool left = false;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       if (rc != NS_OK) {
         const std::string e = ns_last_error(ctx);
-        for (CaseRec *r : mem) {
-          r->err = e;
-          finish_case(s, r, rc);
-        }
+        for (Slot &sl : mem)
+          if (sl.r) {
+            sl.r->err = e;
+            finish_case(s, sl.r, rc);
+            sl.r = nullptr;
+          }
       } else {
-        for (CaseRec *r : mem) {
-          if (r->done >= r->n_steps)
-            finish_case(s, r, NS_OK);
-          else
-            keep.push_back(r);
-        }
+        for (Slot &sl : mem)
+          if (sl.r && sl.r->done >= sl.r->n_steps) {
+            finish_case(s, sl.r, NS_OK);
+            sl.r = nullptr;
+            left = true;
+          }
       }
+      for (const Slot &sl : mem)
+        if (!sl.r) parked += sl.n_elems;
     }
-    if (rc != NS_OK || keep.size() != mem.size()) {  // a member left: re-form (or close)
-      const auto tf0 = std::chrono::steady_clock::now();
-      if (!keep.empty()) {
-        ns_ctx *nc = nullptr;
-        std::vector<int64_t> so;
-        int r2 = form_batch(s, keep, &nc, so);
-        for (size_t m = 0, j = 0; m < mem.size() && r2 == NS_OK; ++m) {
-          if (j < keep.size() && mem[m] == keep[j]) {
-            r2 = ns::ctx_copy_member(nc, (int)j, ctx, (int)m);
-            ++j;
-          }
-        }
-        ns_destroy(ctx);
-        ctx = nullptr;
-        if (r2 != NS_OK) {
-          std::string e = nc ? ns_last_error(nc) : "batch formation failed";
-          if (nc) ns_destroy(nc);
-          std::lock_guard<std::mutex> lk(s->mu);
-          for (CaseRec *r : keep) {
-            r->err = e;
-            finish_case(s, r, r2);
-          }
-          keep.clear();
-        } else {
-          ctx = nc;
-          soff = so;
-          const double tf = std::chrono::duration<double>(std::chrono::steady_clock::now() - tf0).count();
-          for (CaseRec *r : keep) {
-            r->st.batches++;
-            r->st.t_reform += tf;
-          }
-        }
-      } else {
-        ns_destroy(ctx);
-        ctx = nullptr;
-      }
-      mem = keep;
+    if (rc != NS_OK) {
+      ns_destroy(ctx);
+      ctx = nullptr;
+      mem.clear();
+    } else if (left && (active_cases().empty() || 4 * parked > Etot)) {
+      reform(active_cases());  // too much finished work in the batch (or none left): re-form or close
     }
   }
   if (ctx) ns_destroy(ctx);
