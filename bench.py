@@ -345,7 +345,7 @@ def main():
     ap.add_argument("--max-active", type=int, default=4, help="served: requests in flight together")
     ap.add_argument("--e-lo", type=float, default=5e4, help="served: smallest mesh (elements, log-uniform)")
     ap.add_argument("--e-hi", type=float, default=2e6, help="served: largest mesh (elements, log-uniform)")
-    ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--batch", type=int, default=0, choices=[0, 1],
                     help="served: continuous batching of compatible requests in one batched context (1) or one "
                          "context per request (0)")
     ap.add_argument("--pinned-gb", type=float, default=32.0, help="served: pinned host budget for streamed state")
