@@ -520,7 +520,7 @@ def main():
                   "bytes_per_element": bpe, "avg_active_launch_ms": per32 * 1e3,
                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     ebe64 = None
-    if st["n_ebe64"] > 0:
+    if st["n_ebe64"] > 0 and st["ms_ebe64"] > 0:  # per-kernel events are not recorded inside graphs
         per64 = st["ms_ebe64"] / st["n_ebe64"] / 1e3
         ebe64 = {"kernel": "k_ebe<double> (FP64-accuracy operator)", "avg_launch_ms": per64 * 1e3,
                  "achieved_TFLOPs": EBE_FLOP_PER_ELEM * E / per64 / 1e12,
