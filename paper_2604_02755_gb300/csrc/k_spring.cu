@@ -418,18 +418,45 @@ __device__ __forceinline__ void pair_dot6(const float2 *__restrict__ q, const fl
 // ------------------------------------------------------------------ tangent assembly on tensor cores
 // D_p[ij] = Kb [i,j < 3] + sum_k G_pk T_k[ij] is a dense (points x S) . (S x 21) product.
 // It runs on the tensor cores (warp-level bf16 MMA, FP32 accumulation) with FP64-level
-// accuracy by splitting both operands into 6-bit integer digits: G_pk 2^-eG =
-// sum_i a_i 2^-6(i+1) (a_i in 0..63, eG per material with 2^eG > G0 >= G),
-// T_k[ij] 2^-eT[ij] = sum_j b_j 2^-6(j+1) (|b_j| <= 63, one exponent per column ij).
-// Every digit is exact in bf16, every digit product exact in FP32, and the sum over k of
-// the products of one level L = i + j (at most 8 pairs x S x 63^2 < 2^23 for S <= 256) is
-// an integer that FP32 holds exactly, so the MMA accumulators C_L are exact;
-// D = Kb + 2^(eG + eT[ij] - 12) sum_{L <= 8} 2^-6L C_L, the levels combined in
-// double-float arithmetic.  The digits beyond the eighth and the levels above 8 leave an
-// error below 2^-47 of G0 sum_k |T_k[ij]|.
-constexpr int kDigits = 8;
-constexpr int kLevels = 9;  // digit-pair levels L = i + j kept: 0 .. 8
+// accuracy by cutting both operands into 7-bit integer digits, exact in bf16:
+//   G_pk 2^-eG = sum_i a_i 2^-7(i+1)  (balanced digits: a_0 in 0..128, |a_i| <= 65 after;
+//                                       eG per material with 2^eG > G0 >= G),
+//   T_k[ij] 2^-eT[ij] = sum_j b_j 2^-7(j+1)  (|b_j| <= 127, one exponent per column ij).
+// Every digit product is exact in FP32, and the sum over the springs of one digit pair
+// (i, j) is an integer below S 128 127 < 2^22 for S <= 256, so the MMA accumulator C_ij
+// holds it exactly.  The pairs with i + j <= 7 (34 of the 49) are kept and combined in
+// double-float arithmetic: D = Kb + 2^(eG + eT[ij] - 14) sum_ij 2^-7(i+j) C_ij.  The
+// dropped pairs (each term below 5 65 127 2^-70 < 2^-54) and the digits' own truncation
+// leave an error near 2^-49 of 2^(eG + eT[ij]) per spring.  All eight warps of the block
+// take part (warp w takes the pairs w, w + 8, ...), and the warps' double-float partial
+// sums are added in shared memory.  (Dropping the two pairs (1, 6) and (6, 1) as well
+// would give each warp four, but their terms reach 2^-50 of the scale and the error of D
+// relative to sum_k |G_k T_k| grows fivefold for tangents far below G0.)
+constexpr int kDigits = 7;
+constexpr int kMaxLevel = 7;  // digit pairs i + j <= 7 kept
 constexpr int kTcMaxS = 256;
+constexpr int kTcTile = 16;   // points per block on the tensor-core path: one 16-row MMA tile
+struct TcPairs {
+  unsigned char i[64], j[64];
+  int n;
+};
+constexpr TcPairs make_tc_pairs() {
+  TcPairs t{};
+  for (int L = 0; L <= kMaxLevel; ++L)
+    for (int i = 0; i <= L; ++i)
+      if (i < kDigits && L - i < kDigits) {
+        t.i[t.n] = (unsigned char)i;
+        t.j[t.n] = (unsigned char)(L - i);
+        ++t.n;
+      }
+  return t;
+}
+constexpr TcPairs kTcPairs = make_tc_pairs();
+constexpr int kPairs = kTcPairs.n;
+static_assert(kPairs == 34, "digit pairs with i + j <= 7");
+__constant__ TcPairs c_tc_pairs = kTcPairs;
+// shared bytes of the warps' partial sums: [8 warps][3 column tiles][4 registers][32 lanes] pairs
+constexpr size_t kTcRedBytes = (size_t)(kBlock / 32) * 3 * 4 * 32 * sizeof(float2);
 
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
@@ -447,9 +474,26 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
-// bf16 bits of a small non-negative integer d (< 2^8): 2^23 + d as a float, minus 2^23
-__device__ __forceinline__ unsigned short bf16_of_digit(uint32_t d) {
-  return (unsigned short)(__float_as_uint(__uint_as_float(0x4B000000u | d) - 8388608.0f) >> 16);
+// The tangent G (a float pair) as seven balanced 7-bit digits of X = G 2^(49 - eG) in bf16:
+// X = sum_i a_i 2^(42 - 7i).  Each digit is the rounded quotient of the remainder (the
+// high part's remainder plus the rounded low part, for the decision only) by its weight;
+// the remainder is updated exactly (a digit times its weight has at most 8 significant
+// bits and the new remainder is below half a weight), so the digits represent the high
+// part plus the rounded low part to within half a unit of 2^-49 2^eG.  |v| <= 128, so the
+// magic-constant rounding (1.5 2^23) is exact, and an integer of at most 8 significant
+// bits is its own bf16 (the top half of its float bits).
+__device__ __forceinline__ void tangent_digits(float2 G, float gfix, unsigned short *dst, size_t plane) {
+  float r = df_mul(G.x, gfix);
+  const float c = rintf(df_mul(G.y, gfix));
+#pragma unroll
+  for (int i = 0; i < kDigits; ++i) {
+    const float w = __uint_as_float((uint32_t)(127 - (42 - 7 * i)) << 23);  // 2^-(42 - 7i)
+    const float W = __uint_as_float((uint32_t)(127 + (42 - 7 * i)) << 23);  // 2^(42 - 7i)
+    const float v = df_mul(df_add(r, c), w);
+    const float d = df_sub(df_add(v, 12582912.0f), 12582912.0f);
+    r = df_fma(-d, W, r);
+    dst[i * plane] = (unsigned short)(__float_as_uint(d) >> 16);
+  }
 }
 
 // row stride (bf16 elements) of a digit plane: 16 * ks + 8, so that the eight rows one
@@ -463,7 +507,7 @@ __host__ __device__ inline int tc_stride(int ks) { return 16 * ks + 8; }
 // 80 registers, three blocks; 4: 64 registers with a few bytes spilled, a third more
 // warps to hide the root solve's latencies) -- the autotuner picks.
 // TC: phase 1 stores the tangents as digit planes and phase 2 assembles D on the tensor
-// cores (TP a multiple of 16, S <= 256; tfrag holds the digits of T in MMA fragment order).
+// cores (TP = 16, S <= 256; tfrag holds the digits of T in MMA fragment order).
 template <int MINB, bool TC>
 __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restrict__ q2, const float2 *__restrict__ T2, int S,
                                                     int TP, const MatConst *__restrict__ mc,
@@ -526,30 +570,24 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
     const bool sure = dot6_sign(q2 + 6 * k, Es + 12 * lp + 6, dh);
     if (!sure) pair_dot6(q2 + 6 * k, Es + 12 * lp + 6, dh, dl);
     const int64_t si = (p - base) * S + k;
-    double tau = tau_a[si], gR = gR_a[si], tR = tR_a[si], gmax = gmax_a[si];
-    int dir = dir_a[si], mode = mode_a[si];
+    // the state is read and written once per launch: streaming accesses (evict first), so
+    // that L1 keeps what every spring of the block reuses (directions, tables, digits of T)
+    double tau = __ldcs(tau_a + si), gR = __ldcs(gR_a + si), tR = __ldcs(tR_a + si), gmax = __ldcs(gmax_a + si);
+    int dir = __ldcs(dir_a + si), mode = __ldcs(mode_a + si);
     unsigned ev = 0;
     const float2 G = spring_update_pair(gh, gl, dh, dl, !sure, q2 + 6 * k, Es + 12 * lp + 6, rp, tb, ptabf, tau, gR,
                                         tR, gmax, dir, mode, ev);
     evn += (ev & 1u) | ((ev & 2u) << 9) | ((ev & 4u) << 18);
     if (dh != 0.0f) {
-      tau_a[si] = tau;
-      gR_a[si] = gR;
-      tR_a[si] = tR;
-      gmax_a[si] = gmax;
-      dir_a[si] = dir;
-      mode_a[si] = mode;
+      __stcs(tau_a + si, tau);
+      __stcs(gR_a + si, gR);
+      __stcs(tR_a + si, tR);
+      __stcs(gmax_a + si, gmax);
+      __stcs(dir_a + si, dir);
+      __stcs(mode_a + si, mode);
     }
     if (TC) {
-      // G 2^(48 - eG) as a 48-bit integer from the pair, then its eight 6-bit digits
-      const float sc = rp.gfix;
-      long long X = (long long)__float2ull_rz(G.x * sc) + __float2ll_rn(G.y * sc);
-      X = X < 0 ? 0 : (X > 0xFFFFFFFFFFFFll ? 0xFFFFFFFFFFFFll : X);
-      const unsigned long long U = (unsigned long long)X;
-      unsigned short *dst = planes + (size_t)lp * KST + k;
-#pragma unroll
-      for (int i = 0; i < kDigits; ++i)
-        dst[(size_t)i * TP * KST] = bf16_of_digit((uint32_t)(U >> (42 - 6 * i)) & 63u);
+      tangent_digits(G, rp.gfix, planes + (size_t)lp * KST + k, (size_t)TP * KST);
     } else {
       Gs[g] = G;  // the tangent as an unevaluated float pair for the double-float accumulation
     }
@@ -568,57 +606,77 @@ __global__ void __launch_bounds__(kBlock, MINB) k_springs(const float2 *__restri
   if (cnt && threadIdx.x < 3 && evc[threadIdx.x])
     atomicAdd(cnt + 3 * (blockIdx.x % kSpringCountSlots) + threadIdx.x, (unsigned long long)evc[threadIdx.x]);
   if (TC) {
-    // one warp per (16-point tile, 8-column tile) of D; level by level, deepest first, each
-    // level's digit-pair MMAs accumulated in two alternating sets, then folded into
-    // v = sum_L 2^-6L C_L by Horner's rule in double-float arithmetic
+    // warp w multiplies the digit pairs w, w + 8, ... for the three 8-column tiles of D
+    // (16 x 24 >= 16 x 21): per pair, the MMAs over the spring slices accumulate the exact
+    // integer C_ij, which is scaled by 2^-7(i+j) and added into the warp's double-float
+    // partial sums
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntask = (TP >> 4) * 3;
-    for (int task = warp; task < ntask; task += kBlock >> 5) {
-      const int mt = task / 3, nt = task - mt * 3;
-      const uint32_t arow = (uint32_t)__cvta_generic_to_shared(
-          planes + (size_t)(mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * KST + (lane >> 4) * 8);
-      const uint2 *bt = tfrag + (size_t)nt * 32 + lane;
-      float vh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, vl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      for (int L = kLevels - 1; L >= 0; --L) {
-        float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int i = L < kDigits ? 0 : L - kDigits + 1; i <= L && i < kDigits; ++i) {
-          const uint32_t ai = arow + (uint32_t)((size_t)i * TP * KST * 2);
-          const uint2 *bj = bt + (size_t)(L - i) * KS * 3 * 32;
-          int ks = 0;
-          for (; ks + 1 < KS; ks += 2) {
-            uint32_t a0[4], a1[4];
-            ldsm_x4(a0, ai + (uint32_t)(ks * 32));
-            ldsm_x4(a1, ai + (uint32_t)(ks * 32 + 32));
-            mma_bf16(c0, a0, __ldg(bj + (size_t)ks * 96));
-            mma_bf16(c1, a1, __ldg(bj + (size_t)(ks + 1) * 96));
-          }
-          if (ks < KS) {
-            uint32_t a0[4];
-            ldsm_x4(a0, ai + (uint32_t)(ks * 32));
-            mma_bf16(c0, a0, __ldg(bj + (size_t)ks * 96));
-          }
-        }
+    const uint32_t arow =
+        (uint32_t)__cvta_generic_to_shared(planes + (size_t)((lane & 7) + ((lane >> 3) & 1) * 8) * KST + (lane >> 4) * 8);
+    float vh[3][4], vl[3][4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {  // c0 + c1 is exact (an integer below 2^23)
-          float s, e;
-          two_sum(c0[r] + c1[r], vh[r] * 0.015625f, s, e);
-          two_sum(s, e + vl[r] * 0.015625f, vh[r], vl[r]);
-        }
+    for (int n = 0; n < 3; ++n)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) vh[n][r] = vl[n][r] = 0.0f;
+    for (int pr = warp; pr < kPairs; pr += kBlock >> 5) {
+      const int di = c_tc_pairs.i[pr], dj = c_tc_pairs.j[pr];
+      const uint32_t ai = arow + (uint32_t)((size_t)di * TP * KST * 2);
+      const uint2 *bj = tfrag + (size_t)dj * KS * 96 + lane;
+      float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c1[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int ks = 0; ks < KS; ++ks) {
+        uint32_t a[4];
+        ldsm_x4(a, ai + (uint32_t)(ks * 32));
+        const uint2 *b = bj + (size_t)ks * 96;
+        mma_bf16(c0, a, __ldg(b));
+        mma_bf16(c1, a, __ldg(b + 32));
+        mma_bf16(c2, a, __ldg(b + 64));
       }
+      const float sc = __uint_as_float((uint32_t)(127 - 7 * (di + dj)) << 23);  // 2^-7(i+j), exact scaling
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int lp = mt * 16 + (lane >> 2) + (r >> 1) * 8, ij = nt * 8 + 2 * (lane & 3) + (r & 1);
-        if (lp < np && ij < 21) {
-          const int64_t p = pt + lp;
-          const MatConst &m = mc[mat_p ? mat_p[p] : mat_e[p >> 2]];
-          const bool nn = ij < 3 || ij == 6 || ij == 7 || ij == 11;  // (i,j) both < 3
-          const double val = (nn ? m.Kb : 0.0) + m.dsc * (__ldg(tsc + ij) * ((double)vh[r] + (double)vl[r]));
-          if (dpts)
-            dpts[21 * (p - p0) + ij] = val;
-          else
-            D[((p & 3) * 21 + ij) * epad + (p >> 2)] = val;
-        }
+        float sh, e;
+        two_sum(vh[0][r], df_mul(c0[r], sc), sh, e);
+        vh[0][r] = sh;
+        vl[0][r] = df_add(vl[0][r], e);
+        two_sum(vh[1][r], df_mul(c1[r], sc), sh, e);
+        vh[1][r] = sh;
+        vl[1][r] = df_add(vl[1][r], e);
+        two_sum(vh[2][r], df_mul(c2[r], sc), sh, e);
+        vh[2][r] = sh;
+        vl[2][r] = df_add(vl[2][r], e);
       }
+    }
+    __syncthreads();  // every warp is done with the digit planes: their space takes the partial sums
+    float2 *red = Gs;  // [warp][column tile][register][lane]
+#pragma unroll
+    for (int n = 0; n < 3; ++n)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) red[((warp * 3 + n) * 4 + r) * 32 + lane] = make_float2(vh[n][r], vl[n][r]);
+    __syncthreads();
+    for (int o = threadIdx.x; o < kTcTile * 21; o += blockDim.x) {
+      const int lp = o & (kTcTile - 1), ij = o >> 4;
+      if (lp >= np) continue;
+      // fragment position of (row lp, column ij): rows lane/4 (+8 in registers 2, 3),
+      // columns 2 (lane % 4) + register % 2
+      const int n = ij >> 3, col = ij & 7;
+      const int src = ((lp & 7) << 2) | (col >> 1), r = ((lp >> 3) << 1) | (col & 1);
+      float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+      for (int w = 0; w < (kBlock >> 5); ++w) {
+        const float2 v = red[((w * 3 + n) * 4 + r) * 32 + src];
+        float t, e;
+        two_sum(sh, v.x, t, e);
+        sh = t;
+        sl = df_add(sl, df_add(e, v.y));
+      }
+      const int64_t p = pt + lp;
+      const MatConst &m = mc[mat_p ? mat_p[p] : mat_e[p >> 2]];
+      const bool nn = ij < 3 || ij == 6 || ij == 7 || ij == 11;  // (i,j) both < 3
+      const double val = (nn ? m.Kb : 0.0) + m.dsc * (__ldg(tsc + ij) * (f2d(sh) + f2d(sl)));
+      if (dpts)
+        dpts[21 * (p - p0) + ij] = val;
+      else
+        D[((p & 3) * 21 + ij) * epad + (p >> 2)] = val;
     }
     return;
   }
@@ -678,18 +736,19 @@ bool spring_tile_ok(int tp, int S) { return tp >= 4 && tp % 4 == 0 && (size_t)tp
 // shared memory of a launch: float-pair tangents, or the tensor path's digit planes
 static size_t spring_smem(int tp, int S, bool tc) {
   const size_t strains = sizeof(float2) * (size_t)tp * 12;
-  if (tc) return (size_t)kDigits * tp * tc_stride((S + 15) / 16) * 2 + strains;
+  if (tc) return std::max((size_t)kDigits * tp * tc_stride((S + 15) / 16) * 2, kTcRedBytes) + strains;
   return sizeof(float2) * (size_t)tp * S + strains;
 }
 static bool spring_tc_ok(const SpringTables &tab, int tp) {
-  return tab.tc && tab.tfrag && tab.tsc && tab.S <= kTcMaxS && tp % 16 == 0 && spring_smem(tp, tab.S, true) <= 200 * 1024;
+  return tab.tc && tab.tfrag && tab.tsc && tab.S <= kTcMaxS && tp == kTcTile && spring_smem(tp, tab.S, true) <= 200 * 1024;
 }
 
 cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const int32_t *mat_of_elem,
                            const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
                            int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s, bool eps_pairs) {
   if (p1 <= p0) return cudaSuccess;
-  const int TP = spring_tile_ok(tab.tp, tab.S) ? tab.tp : spring_tile_default(tab.S);
+  // the tensor-core assembly works on 16-point tiles; otherwise the tuned or default tile
+  const int TP = spring_tc_ok(tab, kTcTile) ? kTcTile : (spring_tile_ok(tab.tp, tab.S) ? tab.tp : spring_tile_default(tab.S));
   const bool tc = spring_tc_ok(tab, TP);
   const size_t smem = spring_smem(TP, tab.S, tc);
   // the shared-memory opt-in is a per-device attribute, set once per device (any thread)
@@ -705,6 +764,19 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
     attr_done.fetch_or(bit);
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
+  // shared-memory carveout: what the resident blocks need and no more, so that the rest of
+  // the SM's 256 KB stays L1 for the data every block reuses
+  {
+    const void *fn = tab.minb == 4 ? (tc ? (const void *)k_springs<4, true> : (const void *)k_springs<4, false>)
+                                   : (tc ? (const void *)k_springs<1, true> : (const void *)k_springs<1, false>);
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem) == cudaSuccess && bps > 0) {
+      const size_t need = (size_t)bps * (smem + 1024);
+      const int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    }
+    cudaGetLastError();
+  }
 #define NS_SPRINGS(MB, TC)                                                                                         \
   k_springs<MB, TC><<<nb, kBlock, smem, s>>>(tab.q2, tab.T2, tab.S, TP, mc, mat_of_elem, mat_of_point, eps, st.tau, \
                                              st.gR, st.tR, st.gmax, st.dir, st.mode, base, p0, p1, D, epad, dpts,  \

@@ -1116,7 +1116,8 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
       (cfg->stream_mode != NS_STREAM_RING && cfg->stream_mode != NS_STREAM_ZERO_COPY) ||
       (cfg->spring_tile_points != 0 && !spring_tile_ok(cfg->spring_tile_points, cfg->n_springs)) ||
       (cfg->spring_tile_blocks != 0 && cfg->spring_tile_blocks != 1 && cfg->spring_tile_blocks != 4) ||
-      (cfg->multigrid != 0 && cfg->multigrid != 1) || (cfg->local_gather != 0 && cfg->local_gather != 1) || cfg->shared_members < 0 || cfg->shared_members > 65536 ||
+      (cfg->multigrid != 0 && cfg->multigrid != 1) || (cfg->local_gather != 0 && cfg->local_gather != 1) ||
+      cfg->l2_prefetch < 0 || cfg->l2_prefetch > 1 || cfg->shared_members < 0 || cfg->shared_members > 65536 ||
       (cfg->shared_members > 1 && (cfg->scatter != NS_SCATTER_ATOMIC || cfg->multigrid)) ||
       (cfg->multigrid && (cfg->precision == NS_PREC_FP64 || cfg->coarse_max_iter < 1 || !(cfg->coarse_tol > 0)))) {
     g_create_err = "invalid configuration value";
@@ -1407,11 +1408,11 @@ int ns_set_materials(ns_ctx *c, int32_t n, const ns_material *mats) {
     return rc;
   CKC(c, cudaMemcpy(c->T2_d, T2h.data(), T2h.size() * sizeof(float2), cudaMemcpyHostToDevice));
   {  // digits of T for the tensor-core tangent assembly
-    std::vector<uint2> fr((size_t)8 * ((S + 15) / 16) * 3 * 32);
+    std::vector<uint2> fr((size_t)7 * ((S + 15) / 16) * 3 * 32);
     int et[21];
     host_spring_digits(S, Th.data(), fr.data(), et);
     double tsc[21];
-    for (int i = 0; i < 21; ++i) tsc[i] = ldexp(1.0, et[i] - 12);
+    for (int i = 0; i < 21; ++i) tsc[i] = ldexp(1.0, et[i] - 14);
     if ((rc = dalloc(c, &c->tfrag_d, fr.size())) || (rc = dalloc(c, &c->tsc_d, 21))) return rc;
     CKC(c, cudaMemcpy(c->tfrag_d, fr.data(), fr.size() * sizeof(uint2), cudaMemcpyHostToDevice));
     CKC(c, cudaMemcpy(c->tsc_d, tsc, sizeof(tsc), cudaMemcpyHostToDevice));

@@ -199,7 +199,7 @@ void host_material_constants(const ns_material &m, double f1, double f2, MatCons
   o->G0_f = (float)o->G0;
   o->pad_f = 0.0f;
   o->eg = ilogb(o->G0) + 1;  // 2^eg > G0
-  o->gfix = ldexpf(1.0f, 48 - o->eg);
+  o->gfix = ldexpf(1.0f, 49 - o->eg);
   o->dsc = ldexp(1.0, o->eg);
   // float pairs for the double-float root step, from extended-precision values
   auto split = [](long double v, float &h, float &l) {
@@ -285,8 +285,8 @@ void host_pow_tables(double *out) {
 
 // Digits of the spring tables for the tensor-core tangent assembly (k_spring.cu).  Column
 // ij has its own exponent et[ij] (max_k |T_k[ij]| 2^-et in [1/4, 1/2)); each
-// T_k[ij] 2^-et[ij] is rounded to 48 bits and cut into eight 6-bit digits from the top,
-// each carrying the sign of T_k[ij], stored as bf16 (exact for |d| <= 63) in the register
+// T_k[ij] 2^-et[ij] is rounded to 49 bits and cut into seven 7-bit digits from the top,
+// each carrying the sign of T_k[ij], stored as bf16 (exact for |d| <= 127) in the register
 // order of the B operand of a 16x8x16 MMA: entry ((j * KS + ks) * 3 + nt) * 32 + lane
 // holds digit j of rows k = 16 ks + 2 (lane % 4) + {0, 1} (low half first) and, in .y, of
 // the rows 8 further on, column ij = 8 nt + lane / 4; rows k >= S and columns ij >= 21
@@ -301,14 +301,14 @@ void host_spring_digits(int S, const double *T, uint2 *frag, int *et) {
   auto digit = [&](int k, int n, int j) -> uint32_t {
     if (k >= S || n >= 21) return 0u;
     const double t = ldexp(T[21 * (size_t)k + n], -et[n]);
-    const uint64_t X = (uint64_t)llround(fabs(t) * 0x1p48);
-    const int d = (int)((X >> (42 - 6 * j)) & 63u);
+    const uint64_t X = (uint64_t)llround(fabs(t) * 0x1p49);
+    const int d = (int)((X >> (42 - 7 * j)) & 127u);
     const float f = (float)(t < 0.0 ? -d : d);
     uint32_t bits;
     memcpy(&bits, &f, 4);
     return bits >> 16;
   };
-  for (int j = 0; j < 8; ++j)
+  for (int j = 0; j < 7; ++j)
     for (int ks = 0; ks < KS; ++ks)
       for (int nt = 0; nt < 3; ++nt)
         for (int lane = 0; lane < 32; ++lane) {

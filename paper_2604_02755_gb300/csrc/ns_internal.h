@@ -27,8 +27,8 @@ struct MatConst {
   float itref_f, iG0_f, alpha_f, beta_f, G0_f;
   float pad_f;
   RoPairs rp;       // the same constants as float pairs for the double-float root step
-  // tangent assembly on tensor cores: 2^eG > G0 (eG = floor(log2 G0) + 1), gfix = 2^(48 - eG)
-  // turns a tangent into a 48-bit integer, dsc = 2^eG scales the digit sums back (with the
+  // tangent assembly on tensor cores: 2^eG > G0 (eG = floor(log2 G0) + 1), gfix = 2^(49 - eG)
+  // turns a tangent into a 49-bit integer, dsc = 2^eG scales the digit sums back (with the
   // column scales of the spring tables)
   float gfix;
   int32_t eg;
@@ -344,7 +344,7 @@ void host_input_velocity(const double *acc, int64_t n, double dt, double *out);
 void host_pow_tables(double *out);   // kPowTabLen entries
 void host_powf_tables(float *out);   // kPowFLen entries (df64.cuh)
 // per-column exponents et[21] of the spring tables T [S][21] (max_k |T_k[ij]| 2^-et[ij] in
-// [1/4, 1/2)) and their 6-bit digits in MMA fragment order, 8 x ceil(S/16) x 3 x 32 entries
+// [1/4, 1/2)) and their 7-bit digits in MMA fragment order, 7 x ceil(S/16) x 3 x 32 entries
 // (k_spring.cu)
 void host_spring_digits(int S, const double *T, uint2 *frag, int *et);
 

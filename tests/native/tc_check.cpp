@@ -1,11 +1,12 @@
 // Host check of the tensor-core tangent assembly of the spring kernel (csrc/k_spring.cu):
-// the digits of the spring tables in MMA fragment order (host_spring_digits), the digits
-// the kernel cuts from a tangent pair, the level sums the MMAs accumulate (computed here
-// exactly, in integers) and the double-float recombination -- against
-// sum_k G_k T_k[ij] in long double.  Single-precision operations are IEEE on both sides
-// (no contraction); __float2ull_rz / __float2ll_rn are truncation / round-to-nearest.
-// Prints: worst error relative to sum_k |G_k T_k[ij]|, largest level sum over 2^23 (the
-// exactness bound of the FP32 accumulators), layout mismatches, worst digit error of T.
+// the digits of the spring tables in MMA fragment order (host_spring_digits), the balanced
+// digits the kernel cuts from a tangent pair (the same single-precision operations, IEEE,
+// no contraction), the per-pair sums the MMAs accumulate (computed here exactly, in
+// integers), the warps' double-float partial sums and their combination in the kernel's
+// order -- against sum_k G_k T_k[ij] in long double.
+// Prints: worst error relative to sum_k |G_k T_k[ij]|, largest per-pair sum over 2^24 (the
+// bound below which FP32 holds every partial sum exactly), layout mismatches, worst digit
+// error of T, worst digit error of G (relative to 2^eG), largest |digit| of G.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -38,6 +39,9 @@ static int sym6(int i, int j) {  // packed upper triangle, row by row
   return i * 6 - i * (i - 1) / 2 + (j - i);
 }
 
+// the kernel's digit pairs (i + j <= 7, level by level) and its warp count
+static const int kDig = 7, kMaxL = 7, kWarps = 8;
+
 int main(int argc, char **argv) {
   const int S = argc > 1 ? atoi(argv[1]) : 150;
   const int npts = argc > 2 ? atoi(argv[2]) : 2000;
@@ -48,13 +52,13 @@ int main(int argc, char **argv) {
     for (int i = 0; i < 6; ++i)
       for (int j = i; j < 6; ++j) T[21 * (size_t)k + sym6(i, j)] = w * q[6 * k + i] * q[6 * k + j];
   const int KS = (S + 15) / 16;
-  std::vector<uint2> frag((size_t)8 * KS * 3 * 32);
+  std::vector<uint2> frag((size_t)kDig * KS * 3 * 32);
   int et[21];
   host_spring_digits(S, T.data(), frag.data(), et);
   // decode the fragments back into digits b[j][k][n]; every (k, n) must be written once
-  std::vector<int> b((size_t)8 * 16 * KS * 24, 0), seen((size_t)8 * 16 * KS * 24, 0);
+  std::vector<int> b((size_t)kDig * 16 * KS * 24, 0), seen((size_t)kDig * 16 * KS * 24, 0);
   long mismatches = 0;
-  for (int j = 0; j < 8; ++j)
+  for (int j = 0; j < kDig; ++j)
     for (int ks = 0; ks < KS; ++ks)
       for (int nt = 0; nt < 3; ++nt)
         for (int lane = 0; lane < 32; ++lane) {
@@ -73,29 +77,50 @@ int main(int argc, char **argv) {
   for (int k = 0; k < 16 * KS; ++k)
     for (int n = 0; n < 24; ++n) {
       long double r = 0.0L;
-      for (int j = 0; j < 8; ++j) r += ldexpl((long double)b[((size_t)j * 16 * KS + k) * 24 + n], -6 * (j + 1));
+      for (int j = 0; j < kDig; ++j) r += ldexpl((long double)b[((size_t)j * 16 * KS + k) * 24 + n], -7 * (j + 1));
       const long double ref = (k < S && n < 21) ? ldexpl((long double)T[21 * (size_t)k + n], -et[n]) : 0.0L;
       worst_t = fmax(worst_t, (double)fabsl(r - ref));
       if (!(k < S && n < 21) && r != 0.0L) mismatches++;
     }
+  int pi[64], pj[64], np = 0;
+  for (int L = 0; L <= kMaxL; ++L)
+    for (int i = 0; i <= L; ++i)
+      if (i < kDig && L - i < kDig) {
+        pi[np] = i;
+        pj[np] = L - i;
+        ++np;
+      }
   // tangents of random points: G in [1e-4, 1] G0, as float pairs
   std::mt19937_64 rng(5);
   std::uniform_real_distribution<double> U(0.0, 1.0);
-  double worst = 0.0, cmax = 0.0;
+  double worst = 0.0, cmax = 0.0, worst_g = 0.0;
+  int amax = 0;
   for (int p = 0; p < npts; ++p) {
     const double G0 = 1.0e6 * exp(8.0 * U(rng));
     const int eg = ilogb(G0) + 1;
-    const float gfix = ldexpf(1.0f, 48 - eg);
-    std::vector<int> a((size_t)8 * S);
+    const float gfix = ldexpf(1.0f, 49 - eg);
+    std::vector<int> a((size_t)kDig * S);
     std::vector<long double> G(S);
     for (int k = 0; k < S; ++k) {
       const double g = G0 * exp(-9.2 * U(rng));
       const float gh = (float)g, gl = (float)(g - (double)gh);
       G[k] = (long double)gh + (long double)gl;
-      const float xh = df_mul(gh, gfix), xl = df_mul(gl, gfix);
-      long long X = (long long)(unsigned long long)truncf(xh) + (long long)llrintf(xl);
-      X = X < 0 ? 0 : (X > 0xFFFFFFFFFFFFll ? 0xFFFFFFFFFFFFll : X);
-      for (int i = 0; i < 8; ++i) a[(size_t)i * S + k] = (int)(((unsigned long long)X >> (42 - 6 * i)) & 63u);
+      // the kernel's balanced digits (tangent_digits)
+      float r = df_mul(gh, gfix);
+      const float c = rintf(df_mul(gl, gfix));
+      long double rep = 0.0L;
+      for (int i = 0; i < kDig; ++i) {
+        const float wv = ldexpf(1.0f, -(42 - 7 * i)), W = ldexpf(1.0f, 42 - 7 * i);
+        const float v = df_mul(df_add(r, c), wv);
+        const float d = df_sub(df_add(v, 12582912.0f), 12582912.0f);
+        r = df_fma(-d, W, r);
+        const float db = bf16_to_float(df_bits(d) >> 16);
+        if (db != d) mismatches++;  // a digit that bf16 does not hold exactly
+        a[(size_t)i * S + k] = (int)d;
+        amax = std::max(amax, std::abs((int)d));
+        rep += ldexpl((long double)d, -7 * (i + 1));
+      }
+      worst_g = fmax(worst_g, (double)fabsl(rep - ldexpl(G[k], -eg)));
     }
     for (int n = 0; n < 21; ++n) {
       long double ref = 0.0L, mag = 0.0L;
@@ -103,21 +128,30 @@ int main(int argc, char **argv) {
         ref += G[k] * (long double)T[21 * (size_t)k + n];
         mag += fabsl(G[k] * (long double)T[21 * (size_t)k + n]);
       }
-      float vh = 0.0f, vl = 0.0f;
-      for (int L = 8; L >= 0; --L) {
-        long long C = 0;
-        for (int i = L < 8 ? 0 : L - 7; i <= L && i < 8; ++i)
+      // warp w: pairs w, w + 8, ...; each pair's exact integer sum scaled by 2^-7(i+j) and
+      // added into the warp's pair sum; then the warps' sums in order
+      float sh = 0.0f, sl = 0.0f;
+      for (int wp = 0; wp < kWarps; ++wp) {
+        float vh = 0.0f, vl = 0.0f;
+        for (int pr = wp; pr < np; pr += kWarps) {
+          long long C = 0;
           for (int k = 0; k < S; ++k)
-            C += (long long)a[(size_t)i * S + k] * b[((size_t)(L - i) * 16 * KS + k) * 24 + n];
-        cmax = fmax(cmax, fabs((double)C) / 8388608.0);
-        float s, e;
-        two_sum((float)C, df_mul(vh, 0.015625f), s, e);
-        two_sum(s, df_add(e, df_mul(vl, 0.015625f)), vh, vl);
+            C += (long long)a[(size_t)pi[pr] * S + k] * b[((size_t)pj[pr] * 16 * KS + k) * 24 + n];
+          cmax = fmax(cmax, fabs((double)C) / 16777216.0);
+          float s, e;
+          two_sum(vh, df_mul((float)C, ldexpf(1.0f, -7 * (pi[pr] + pj[pr]))), s, e);
+          vh = s;
+          vl = df_add(vl, e);
+        }
+        float t, e;
+        two_sum(sh, vh, t, e);
+        sh = t;
+        sl = df_add(sl, df_add(e, vl));
       }
-      const long double D = ldexpl((long double)vh + (long double)vl, eg + et[n] - 12);
+      const long double D = ldexpl((long double)sh + (long double)sl, eg + et[n] - 14);
       if (mag > 0) worst = fmax(worst, (double)(fabsl(D - ref) / mag));
     }
   }
-  printf("%.3e %.4f %ld %.3e\n", worst, cmax, mismatches, worst_t);
+  printf("%.3e %.4f %ld %.3e %.3e %d\n", worst, cmax, mismatches, worst_t, worst_g, amax);
   return 0;
 }

@@ -66,15 +66,18 @@ def test_halley_step_root_and_tangent(tmp_path_factory):
 @pytest.mark.parametrize("S", [10, 17, 50, 150, 256])
 def test_tensor_core_tangent_assembly_digits(tmp_path_factory, S):
     """The tensor-core assembly of D = sum_k G_k T_k (csrc/k_spring.cu) emulated on the
-    host with the library's digit tables: the fragment table holds every (spring, column)
-    once and zeros in the padding, the digits of T reproduce T to 2^-48 of its column
-    scale, every level sum stays below 2^23 (so FP32 accumulates it exactly), and the
-    recombined D agrees with long double to 1e-12 of sum_k |G_k T_k| for tangents spread
-    over four decades below G0 (2e-13 from 50 springs up)."""
+    host with the library's digit tables and the kernel's digit cut: the fragment table
+    holds every (spring, column) once and zeros in the padding, every digit is exact in
+    bf16, the digits of T reproduce T to 2^-49 of its column scale and those of G
+    reproduce G to 2^-49 of 2^eG, every per-pair sum stays far below 2^24 (so FP32 holds it
+    exactly), and the recombined D agrees with long double to 5e-14 of sum_k |G_k T_k| for
+    tangents spread over four decades below G0 (5e-13 below 50 springs)."""
     exe = compile_check(tmp_path_factory, "tc_check")
     out = subprocess.run([exe, str(S), "200"], capture_output=True, text=True, check=True).stdout
-    worst, cmax, mism, worst_t = out.split()
+    worst, cmax, mism, worst_t, worst_g, amax = out.split()
     assert int(mism) == 0
-    assert float(worst_t) <= 2.0 ** -48
-    assert float(cmax) < 1.0
-    assert float(worst) <= (2e-13 if S >= 50 else 1e-12)
+    assert float(worst_t) <= 2.0 ** -49
+    assert float(worst_g) <= 2.0 ** -49
+    assert int(amax) <= 128
+    assert float(cmax) < 0.25
+    assert float(worst) <= (5e-14 if S >= 50 else 5e-13)
