@@ -311,9 +311,10 @@ def main():
     ap.add_argument("--members", type=int, default=64, help="members of the ensemble workload")
     ap.add_argument("--union", action="store_true",
                     help="ensemble: store the disjoint union of the members' mesh copies instead of one shared mesh")
-    ap.add_argument("--stage", type=int, default=0, choices=[0, 1],
-                    help="FP32 inner operator: stage element tiles in shared memory with bulk copies (1) or "
-                         "per-thread loads (0)")
+    ap.add_argument("--stage", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="FP32 inner operator: stage element tiles in shared memory with bulk copies (1), "
+                         "per-warp asynchronous tangent copies (2), per-thread loads (0), or automatic (-1: "
+                         "2 with the FP32 tangent, 0 with the FP16 one)")
     ap.add_argument("--spring-tile", type=int, default=0,
                     help="spring kernel points per block before (or without) the autotuner; 0: heuristic")
     ap.add_argument("--spring-blocks", type=int, default=1, choices=[1, 4],
@@ -504,12 +505,15 @@ def main():
                              "peak_source": "152 SMs x 4 schedulers x 1 warp-instruction/clk x median SM clock (derived)",
                              "per_unit": "%g warp-instructions/spring (ncu smsp__inst_executed, spring profile)" % ips}
 
-    # the HBM-bound matvec: the inner FP32 operator, per launch that did work (algorithmic
-    # bytes: connectivity 40, geometry 40, material 4, tangent 336 (FP32) or 168 (FP16),
-    # node gathers ~16 and scatters ~32 per element)
+    # the HBM-bound matvec: the inner FP32 operator, per launch that did work.  Algorithmic
+    # bytes: per element connectivity 40, geometry 40, material 4, tangent 336 (FP32) or 168
+    # (FP16); per node the gathered x read once (16) and y read and written once (32), i.e.
+    # 48 N/E per element (the ncu DRAM count of the kernel agrees: 484 B per element on the
+    # large model's numbering, N/E = 1.35)
     matvec = None
     if st["inner_iters_total"] > 0 and st["ms_ebe32"] > 0:
-        bpe = 300.0 if prec == B.NS_PREC_FP64_IR16 else 468.0
+        n_per_e = (wl.mesh.n_nodes * M) / E
+        bpe = (252.0 if prec == B.NS_PREC_FP64_IR16 else 420.0) + 48.0 * n_per_e
         # active launches: one per inner iteration, plus (multigrid) the residual of the
         # interpolated start once per outer iteration
         active = st["inner_iters_total"] + (st["cg_iters_total"] if args.multigrid else 0)
@@ -517,7 +521,7 @@ def main():
         gbs = bpe * E / per32 / 1e9
         matvec = {"kernel": "k_ebe<float> (inner FP32 EBE operator)", "bound": "hbm", "achieved": gbs,
                   "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if hbm_peak else None,
-                  "bytes_per_element": bpe, "avg_active_launch_ms": per32 * 1e3,
+                  "bytes_per_element": bpe, "nodes_per_element": n_per_e, "avg_active_launch_ms": per32 * 1e3,
                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     ebe64 = None
     if st["n_ebe64"] > 0 and st["ms_ebe64"] > 0:  # per-kernel events are not recorded inside graphs

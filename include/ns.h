@@ -83,9 +83,11 @@ typedef struct {
                                   included) and each batch of plain CG iterations is captured once
                                   as a CUDA graph and replayed; per-kernel times of the operators
                                   inside are then not recorded (ns_stats ms_ebe32 stays 0) */
-  int32_t stage_elements;      /* 1: the FP32 inner operator stages each 256-element tile of element
-                                  data in shared memory with bulk copies (atomic scatter, one member);
-                                  0 (default): per-thread loads, which measured faster on GB300 */
+  int32_t stage_elements;      /* FP32 inner operator (atomic scatter, one member): 1 stages each
+                                  256-element tile of element data in shared memory with bulk copies;
+                                  2 has each warp copy its 32 elements' tangent rows to shared memory
+                                  asynchronously while it gathers the nodal values; 0 per-thread
+                                  loads; -1 (default): 2 for the FP32 tangent, 0 for the FP16 one */
   int32_t l2_prefetch;         /* 1: each block of the element operators first prefetches its slice
                                   of the element rows into L2 with a bulk prefetch */
   int32_t pair_operator;       /* 1: the FP64-accuracy operator applications (right-hand side, outer
@@ -176,7 +178,8 @@ typedef struct {
  * x0_prev 1, NS_PREC_FP64, NS_SCATTER_ATOMIC, chunk 100000 elements (Sec. 2.3),
  * ring 3, all state resident, Rayleigh 0.1/2.5 Hz, 64 surface steps,
  * device 0, timing 0, inner 45 iterations / 1e-4, waits 120 s, graphs on,
- * no staged operator, L2 prefetch on, FP64 operator (no pair arithmetic),
+ * FP32 inner operator staged per warp (stage_elements -1), L2 prefetch on, FP64
+ * operator (no pair arithmetic),
  * NS_STREAM_RING, spring launch shape from the size heuristic (tile 0) with the
  * compiler's register budget (1 block), tangent assembly off the tensor cores. */
 void ns_config_default(ns_config *cfg);
@@ -331,9 +334,10 @@ typedef struct {
 
 /* Autotuner (a tool of this library; the paper tunes nothing at run time): times the
  * spring kernel's launch shape (integration points per block, and one of two register
- * budgets it is compiled with) on a sample of up to 32,768
- * resident elements -- a copy of their spring state, the last step's strains -- and the
- * streamed state's chunk size (a copy round trip through the ring buffers, which leaves
+ * budgets it is compiled with) in one launch over a sample of up to 131,072 resident
+ * elements (eight slices spread over the model) -- a copy of their spring state moved one
+ * more increment along the last step's (strain eps + deps, increment deps), so that every
+ * spring takes a root solve of a step's size -- and the streamed state's chunk size (a copy round trip through the ring buffers, which leaves
  * the host state as it was), and keeps the fastest of each for the following steps.
  * The simulation's state and results are unchanged (the block shape does not change the
  * order of any sum).  Call between ns_advance calls, after at least one step (the strains

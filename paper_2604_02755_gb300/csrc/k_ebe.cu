@@ -126,14 +126,11 @@ __device__ __forceinline__ dd dload(const dd *__restrict__ D, int64_t epad, int6
   return ldg(D + m * epad + e);
 }
 
-// Stress of integration point Q: sig = w D_Q eps_Q(x); dl(m) gives entry m of the
-// element's [84] point-major tangent.
+// Stress of integration point Q from its strain: sig = w D_Q eps; dl(m) gives entry m of
+// the element's [84] point-major tangent.
 template <typename T, int Q, typename DL>
-__device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], const T g[4][3], const DL &dl, T w,
-                                             T sig[6]) {
-  T H[3][3], eps[6], d[21];
-  point_grad<T, Q>(x, P, g, H);
-  voigt_strain(H, eps);
+__device__ __forceinline__ void stress_of(const T eps[6], const DL &dl, T w, T sig[6]) {
+  T d[21];
 #pragma unroll
   for (int k = 0; k < 21; ++k) d[k] = (T)dl(Q * 21 + k);
   sig[0] = w * (d[0] * eps[0] + d[1] * eps[1] + d[2] * eps[2] + d[3] * eps[3] + d[4] * eps[4] + d[5] * eps[5]);
@@ -142,6 +139,16 @@ __device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], 
   sig[3] = w * (d[3] * eps[0] + d[8] * eps[1] + d[12] * eps[2] + d[15] * eps[3] + d[16] * eps[4] + d[17] * eps[5]);
   sig[4] = w * (d[4] * eps[0] + d[9] * eps[1] + d[13] * eps[2] + d[16] * eps[3] + d[18] * eps[4] + d[19] * eps[5]);
   sig[5] = w * (d[5] * eps[0] + d[10] * eps[1] + d[14] * eps[2] + d[17] * eps[3] + d[19] * eps[4] + d[20] * eps[5]);
+}
+
+// Stress of integration point Q: sig = w D_Q eps_Q(x).
+template <typename T, int Q, typename DL>
+__device__ __forceinline__ void point_stress(const T x[10][3], const T P[4][3], const T g[4][3], const DL &dl, T w,
+                                             T sig[6]) {
+  T H[3][3], eps[6];
+  point_grad<T, Q>(x, P, g, H);
+  voigt_strain(H, eps);
+  stress_of<T, Q>(eps, dl, w, sig);
 }
 
 // One element of the operator: y_e = (kK K_e + mK M_e) x_e + mM M_e xm_e scattered into y
@@ -399,6 +406,119 @@ __global__ void __launch_bounds__(kTile, 2)
   }
 }
 
+// ------------------------------------------------------------------ per-warp staged FP32 operator
+// One thread per element as in k_ebe, but each warp first issues asynchronous copies
+// (cp.async, 16 bytes each, no registers held) of its 32 elements' tangent rows into shared
+// memory, then loads connectivity and geometry, gathers x and forms the strains at the four
+// points while the tangent is in flight, and only then waits for it: the tangent bytes (336
+// of the 468 per element) no longer wait in registers, a few loads at a time.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ float dload_w(const float *Ds, int lane, int m) { return Ds[m * 32 + lane]; }
+__device__ __forceinline__ float dload_w(const __half2 *Ds, int lane, int m) {
+  const __half2 h = Ds[(m >> 1) * 32 + lane];
+  return (m & 1) ? __high2float(h) : __low2float(h);
+}
+template <typename TD>
+__host__ __device__ constexpr size_t warp_staged_smem() {
+  return (size_t)staged_d_rows<TD>() * 32 * 4 * (kBlock / 32);
+}
+
+template <typename TD, bool DOT>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_ebe32_warp(int64_t E, int64_t epad, const int32_t *__restrict__ conn, const float *__restrict__ geom,
+                 const int32_t *__restrict__ mat, const TD *__restrict__ D, const OpCoef *__restrict__ op,
+                 const float *__restrict__ xk, float *y, double *dot, const int32_t *skip) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int DR = staged_d_rows<TD>();
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ew = (int64_t)blockIdx.x * kBlock + warp * 32, e = ew + lane;
+  TD *Ds = reinterpret_cast<TD *>(smem) + (size_t)warp * DR * 32;  // [DR][32]: the warp's tangent rows
+  // rows start at 128-byte boundaries (epad a multiple of 64, ew of 32) and the warp's 32
+  // entries of a row end inside it (ew < E <= epad)
+  if (ew < E) {
+#pragma unroll 4
+    for (int q = lane; q < DR * 8; q += 32) {
+      const int r = q >> 3, part = q & 7;
+      cp_async16(Ds + r * 32 + part * 4, D + (size_t)r * epad + ew + part * 4);
+    }
+  }
+  cp_async_commit();
+  const bool live = e < E;
+  int nd[10], mt = 0;
+  float g[4][3], vol = 0.0f, eps[4][6];
+  if (live) {
+#pragma unroll
+    for (int a = 0; a < 10; ++a) nd[a] = ldg(conn + a * epad + e);
+    mt = ldg(mat + e);
+    load_grads(geom, epad, e, g, vol);
+    float x[10][3], P[4][3], H[3][3];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) load_node<4>(xk, nd[a], x[a]);
+    compute_P(x, P);
+    point_grad<float, 0>(x, P, g, H);
+    voigt_strain(H, eps[0]);
+    point_grad<float, 1>(x, P, g, H);
+    voigt_strain(H, eps[1]);
+    point_grad<float, 2>(x, P, g, H);
+    voigt_strain(H, eps[2]);
+    point_grad<float, 3>(x, P, g, H);
+    voigt_strain(H, eps[3]);
+  }
+  cp_async_wait_all();
+  __syncwarp();  // every lane's copies are complete and visible to the warp
+  double mydot = 0.0;
+  if (live) {
+    const float cK = (float)op->kK[mt], cMk = (float)op->mK[mt];
+    float ye[10][3];
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) ye[a][r] = 0.0f;
+    if (cK != 0.0f) {
+      const auto dl = [&](int k) { return dload_w(Ds, lane, k); };
+      float sig[4][6];
+      stress_of<float, 0>(eps[0], dl, 1.0f, sig[0]);
+      stress_of<float, 1>(eps[1], dl, 1.0f, sig[1]);
+      stress_of<float, 2>(eps[2], dl, 1.0f, sig[2]);
+      stress_of<float, 3>(eps[3], dl, 1.0f, sig[3]);
+      points_force<float>(sig, g, cK * vol * 0.25f, ye);
+    }
+    if (cMk != 0.0f) {
+      const float c = vol * (1.0f / 420.0f);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        float w[10];
+#pragma unroll
+        for (int a = 0; a < 10; ++a) w[a] = cMk * vload<float>(xk + 4 * (int64_t)nd[a] + r);
+        mass_apply_1(w, c, ye, r);
+      }
+    }
+    if (DOT) {
+      float ld = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 10; ++a) {
+        float xa[3];
+        load_node<4>(xk, nd[a], xa);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) ld += xa[r] * ye[a][r];
+      }
+      mydot = (double)ld;
+    }
+#pragma unroll
+    for (int a = 0; a < 10; ++a) add_node<4, true>(y, nd[a], ye[a]);
+  }
+  if (DOT) {
+    double sum = block_sum(mydot);
+    if (threadIdx.x == 0) dot[blockIdx.x] = sum;
+  }
+}
+
 // ------------------------------------------------------------------ locally gathered FP32 operator
 // One block = kBlock consecutive elements.  Phase 1 gathers the block's distinct nodes (its
 // node list, usually ~0.3 of its 10 kBlock element-node slots in a structured numbering)
@@ -598,11 +718,33 @@ static cudaError_t staged_dispatch(const DevMesh &m, const TD *D, const OpCoef *
   return cudaGetLastError();
 }
 
+template <typename TD>
+static cudaError_t warp_dispatch(const DevMesh &m, const TD *D, const OpCoef *op, const float *xk, float *y,
+                                 double *dot, const int32_t *skip, cudaStream_t s) {
+  constexpr size_t smem = warp_staged_smem<TD>();
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load() & bit)) {
+    cudaFuncSetAttribute(k_ebe32_warp<TD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_ebe32_warp<TD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done.fetch_or(bit);
+  }
+  const unsigned nb = (unsigned)((m.E + kBlock - 1) / kBlock);
+  if (dot)
+    k_ebe32_warp<TD, true><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip);
+  else
+    k_ebe32_warp<TD, false><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s, SegList sg, bool staged) {
-  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr && m.Msh == 1)
-    return staged_dispatch<float>(m, D, op, xk, y, dot, skip, s);
+                         cudaStream_t s, SegList sg, int stage) {
+  const bool whole = atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1;
+  if (stage == 1 && whole && m.kerr) return staged_dispatch<float>(m, D, op, xk, y, dot, skip, s);
+  if (stage == 2 && whole) return warp_dispatch<float>(m, D, op, xk, y, dot, skip, s);
   if (m.lmax > 0 && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1)
     return local_dispatch<float>(m, D, op, xk, y, dot, skip, s);
   // inner-solve vectors are [N][4]
@@ -612,9 +754,11 @@ cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, con
 
 cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s, SegList sg, bool staged) {
-  if (staged && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.kerr && m.Msh == 1)
+                         cudaStream_t s, SegList sg, int stage) {
+  const bool whole = atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1;
+  if (stage == 1 && whole && m.kerr)
     return staged_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
+  if (stage == 2 && whole) return warp_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
   if (m.lmax > 0 && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1)
     return local_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
   return ebe_dispatch<float, __half2, 4, false>(m, static_cast<const __half2 *>(D16), m.geom32, op, nullptr, xk, y,

@@ -765,15 +765,21 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
   }
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
   // shared-memory carveout: what the resident blocks need and no more, so that the rest of
-  // the SM's 256 KB stays L1 for the data every block reuses
+  // the SM's 256 KB stays L1 for the data every block reuses (set when it changes: a
+  // per-device attribute of each instantiation)
   {
-    const void *fn = tab.minb == 4 ? (tc ? (const void *)k_springs<4, true> : (const void *)k_springs<4, false>)
-                                   : (tc ? (const void *)k_springs<1, true> : (const void *)k_springs<1, false>);
+    const int inst = (tab.minb == 4 ? 2 : 0) + (tc ? 1 : 0);
+    const void *fn = inst == 3 ? (const void *)k_springs<4, true>
+                     : inst == 2 ? (const void *)k_springs<4, false>
+                     : inst == 1 ? (const void *)k_springs<1, true>
+                                 : (const void *)k_springs<1, false>;
+    static std::atomic<int> last_pct[64][4];  // zero-initialised: 0 = not set yet (pct >= 1)
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem) == cudaSuccess && bps > 0) {
       const size_t need = (size_t)bps * (smem + 1024);
-      const int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
-      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+      const int pct = (int)std::max<size_t>(1, std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024)));
+      if (last_pct[dev & 63][inst].exchange(pct) != pct)
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     }
     cudaGetLastError();
   }
@@ -793,6 +799,31 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
       NS_SPRINGS(1, false);
   }
 #undef NS_SPRINGS
+  return cudaGetLastError();
+}
+
+__global__ void k_tune_sample(const float2 *__restrict__ eps, const int32_t *__restrict__ mat_e, int64_t p0,
+                              int64_t np, float2 *out, int32_t *mat_p) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const float2 *e = eps + 12 * (p0 + i);
+  float2 *o = out + 12 * i;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float h, l;
+    pair_add(e[c].x, e[c].y, e[6 + c].x, e[6 + c].y, h, l);
+    o[c] = make_float2(h, l);
+    o[6 + c] = e[6 + c];
+  }
+  mat_p[i] = mat_e[(p0 + i) >> 2];
+}
+
+cudaError_t launch_tune_sample(const double *eps_pairs, const int32_t *mat_e, int64_t e0, int64_t ne, float2 *eps_out,
+                               int32_t *mat_p, int64_t out_off, cudaStream_t s) {
+  const int64_t np = 4 * ne;
+  if (np <= 0) return cudaSuccess;
+  k_tune_sample<<<(unsigned)((np + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      reinterpret_cast<const float2 *>(eps_pairs), mat_e, 4 * e0, np, eps_out + 12 * out_off, mat_p + out_off);
   return cudaGetLastError();
 }
 

@@ -354,7 +354,9 @@ int apply_A32(ns_ctx *c, const float *x, float *y, double *dot, const int32_t *s
   tbegin(c, TK_EBE32, c->s_main, &t0);
   const bool h16 = c->cfg.precision == NS_PREC_FP64_IR16;
   auto elems = [&](const int32_t *ids, int64_t e0, int64_t e1, bool at, double *d, SegList sg) {
-    const bool st = c->cfg.stage_elements != 0;
+    // automatic: the per-warp staged kernel for the FP32 tangent; direct loads for the FP16
+    // one (half the tangent bytes, where staging measured slower)
+    const int st = c->cfg.stage_elements >= 0 ? c->cfg.stage_elements : (h16 ? 0 : 2);
     return h16 ? launch_ebe16(c->m, c->D16, c->op_A16, x, y, ids, e0, e1, at, d, skip, c->s_main, sg, st)
                : launch_ebe32(c->m, c->D32, c->op_A, x, y, ids, e0, e1, at, d, skip, c->s_main, sg, st);
   };
@@ -1077,7 +1079,7 @@ void ns_config_default(ns_config *cfg) {
   cfg->inner_tol = 1e-4;
   cfg->wait_timeout_s = 120.0;
   cfg->graphs = 1;
-  cfg->stage_elements = 0;
+  cfg->stage_elements = -1;
   cfg->stream_mode = NS_STREAM_RING;
   cfg->pair_operator = 0;
   cfg->l2_prefetch = 1;
@@ -1117,7 +1119,8 @@ int ns_create(ns_ctx **out, const ns_config *cfg) {
       (cfg->spring_tile_points != 0 && !spring_tile_ok(cfg->spring_tile_points, cfg->n_springs)) ||
       (cfg->spring_tile_blocks != 0 && cfg->spring_tile_blocks != 1 && cfg->spring_tile_blocks != 4) ||
       (cfg->multigrid != 0 && cfg->multigrid != 1) || (cfg->local_gather != 0 && cfg->local_gather != 1) ||
-      cfg->l2_prefetch < 0 || cfg->l2_prefetch > 1 || cfg->shared_members < 0 || cfg->shared_members > 65536 ||
+      cfg->l2_prefetch < 0 || cfg->l2_prefetch > 1 || cfg->stage_elements < -1 || cfg->stage_elements > 2 ||
+      cfg->shared_members < 0 || cfg->shared_members > 65536 ||
       (cfg->shared_members > 1 && (cfg->scatter != NS_SCATTER_ATOMIC || cfg->multigrid)) ||
       (cfg->multigrid && (cfg->precision == NS_PREC_FP64 || cfg->coarse_max_iter < 1 || !(cfg->coarse_tol > 0)))) {
     g_create_err = "invalid configuration value";
@@ -2157,16 +2160,26 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
     CKC(c, cudaEventElapsedTime(ms, e0, e1));
     return NS_OK;
   };
-  // 1. spring kernel block shape on a copy of the state of 32,768 resident elements taken
-  //    as eight slices spread over the model (its layers load the springs differently)
-  const int64_t ne = std::min<int64_t>(c->E_res, 32768);
-  const int nsl = ne == 32768 ? 8 : 1;
+  // 1. spring kernel block shape on a copy of the state of 131,072 resident elements taken
+  //    as eight slices spread over the model (its layers load the springs differently),
+  //    packed into one sample that one launch covers.  The state is already at this
+  //    step's strains, so the sample moves it one increment further along the same path
+  //    (strain eps + deps, increment deps): the springs take a root solve of the size the
+  //    next step's would take, not a solve that starts at its root.
+  const int64_t ne = std::min<int64_t>(c->E_res, 131072);
+  const int nsl = ne == 131072 ? 8 : 1;
   const int64_t nes = ne / nsl;
-  if (ne > 0) {
-    const int64_t np = 4 * ne, nspr = np * S;
+  if (ne > 0 && c->eps) {
+    const int64_t np = 4 * nes * nsl, nspr = np * S;
     SpringSoA scr;
-    double *dpts = nullptr;
-    if ((rc = alloc_soa(c, scr, nspr, false)) == NS_OK && (rc = dalloc(c, &dpts, 21 * (size_t)np)) == NS_OK) {
+    double *dpts = nullptr, *eps_s = nullptr;
+    int32_t *mat_s = nullptr;
+    if ((rc = alloc_soa(c, scr, nspr, false)) == NS_OK && (rc = dalloc(c, &dpts, 21 * (size_t)np)) == NS_OK &&
+        (rc = dalloc(c, &eps_s, 12 * (size_t)np)) == NS_OK && (rc = dalloc(c, &mat_s, (size_t)np)) == NS_OK) {
+      auto slice0 = [&](int j) { return nsl == 1 ? (int64_t)0 : j * ((c->E_res - nes) / (nsl - 1)); };
+      for (int j = 0; j < nsl && rc == NS_OK; ++j)
+        LAUNCH(c, launch_tune_sample(c->eps, c->m.mat, slice0(j), nes, reinterpret_cast<float2 *>(eps_s), mat_s,
+                                     4 * j * nes, c->s_main));
       const int cands[8] = {4, 8, 16, 32, 64, 128, 256, 512};
       float best = 1e30f;
       int chosen = spring_tile_default(S), chosen_b = 1;
@@ -2177,7 +2190,6 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
         tb.tp = cands[k];
         tb.minb = minb;
         float ms_best = 1e30f;
-        auto slice0 = [&](int j) { return nsl == 1 ? (int64_t)0 : j * ((c->E_res - nes) / (nsl - 1)); };
         for (int rep = 0; rep < 3 && rc == NS_OK; ++rep) {
           for (int j = 0; j < nsl && rc == NS_OK; ++j)
             rc = copy_soa(c, scr, j * nes * 4 * S, c->st, slice0(j) * 4 * S, nes * 4 * S, cudaMemcpyDeviceToDevice,
@@ -2185,11 +2197,8 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
           if (rc != NS_OK) break;
           float ms = 0.0f;
           rc = timed(c->s_main, [&]() -> int {
-            for (int j = 0; j < nsl; ++j) {  // scratch state of slice j at scr[j * nes * 4 * S]
-              const int64_t e0 = slice0(j);
-              LAUNCH(c, launch_springs(tb, c->mats_d, c->m.mat, nullptr, c->eps, scr, 4 * (e0 - j * nes), 4 * e0,
-                                       4 * (e0 + nes), nullptr, c->m.epad, dpts, c->s_main, true));
-            }
+            LAUNCH(c, launch_springs(tb, c->mats_d, nullptr, mat_s, eps_s, scr, 0, 0, np, nullptr, 0, dpts,
+                                     c->s_main, true));
             return NS_OK;
           }, &ms);
           ms_best = std::min(ms_best, ms);
@@ -2214,6 +2223,8 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
     }
     free_soa(scr, false);
     dfree(dpts);
+    dfree(eps_s);
+    dfree(mat_s);
   }
   // 2. chunk size of the streamed state: H2D of a ring's worth of chunks and D2H of the same
   //    bytes back to where they came from (the host state is left as it was)

@@ -152,16 +152,17 @@ cudaError_t launch_ebe64(const DevMesh &m, const double *D, const OpCoef *op, co
 // (with dot and yk set: the stiffness part K x, without its coefficient, also goes to yk)
 // dst[i] = src[i] as a float pair (n values)
 cudaError_t launch_to_pairs(const double *src, void *dst, int64_t n, cudaStream_t s);
-// staged: whole-mesh atomic launches stage each tile of elements in shared memory with
-// bulk copies (cp.async.bulk) instead of per-thread loads.
+// stage (whole-mesh atomic launches of one member): 1 stages each tile of elements in shared
+// memory with bulk copies (cp.async.bulk); 2 has each warp copy its elements' tangent rows
+// asynchronously (cp.async) while it gathers x; 0 per-thread loads.
 cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s, SegList sg = {}, bool staged = false);
+                         cudaStream_t s, SegList sg = {}, int stage = 0);
 // As launch_ebe32 with D stored as FP16 pairs [42][epad] (entries 2j, 2j+1 of the [84] point-major
 // order) holding D / G0 of the element's material; op->kK carries the factor G0.
 cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, const float *xk, float *y,
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
-                         cudaStream_t s, SegList sg = {}, bool staged = false);
+                         cudaStream_t s, SegList sg = {}, int stage = 0);
 // Boundary faces: y (+)= cC * C_f (x + [kind 0] vin) (vin may be nullptr); with members the
 // input of face f is vin + fmem[f] * vin_stride.
 cudaError_t launch_faces64(const DevMesh &m, const MatConst *mc, double cC, const double *x, const double *vin,
@@ -298,6 +299,10 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
                            const int32_t *mat_of_point, const double *eps, SpringSoA st, int64_t base, int64_t p0,
                            int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s,
                            bool eps_pairs = false);
+// The autotuner's spring sample: the strain pairs of elements [e0, e0 + ne) moved one
+// increment on (eps + deps, deps) into eps_out at point out_off, and each point's material.
+cudaError_t launch_tune_sample(const double *eps_pairs, const int32_t *mat_e, int64_t e0, int64_t ne, float2 *eps_out,
+                               int32_t *mat_p, int64_t out_off, cudaStream_t s);
 // elastic tangent for elements [e0, e1)
 cudaError_t launch_elastic_D(const SpringTables &tab, const MatConst *mc, const int32_t *mat, double *D, int64_t epad,
                              int64_t e0, int64_t e1, cudaStream_t s);

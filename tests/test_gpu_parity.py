@@ -347,17 +347,35 @@ def test_graph_replay_equals_direct_launches(precision):
 
 def test_staged_operator_equals_direct_loads():
     """The FP32 inner operator reading its element data from tiles staged in shared
-    memory by bulk copies computes what the per-thread-load kernel computes: both sides
-    solve to 1e-12, so the surface records agree to rounding (atomic scatter order)."""
+    memory by bulk copies (stage 1), or its tangent rows copied per warp asynchronously
+    (stage 2), computes what the per-thread-load kernel computes: all sides solve to
+    1e-12, so the surface records agree to rounding (atomic scatter order)."""
     wl = small(dims=(6, 5, 4), nt=60)  # 720 elements: two full tiles and a ragged one
     out = []
-    for staged in (0, 1):
+    for staged in (0, 1, 2):
         for prec in (B.NS_PREC_FP64_IR, B.NS_PREC_FP64_IR16):
             with B.Simulation(wl, surface_ring_steps=30, precision=prec, stage_elements=staged, cg_tol=1e-12) as sim:
                 sim.advance(30)
                 out.append(sim.surface(1, 30)["v"])
     assert rel(out[2], out[0]) <= 1e-9 and rel(out[3], out[1]) <= 1e-9
+    assert rel(out[4], out[0]) <= 1e-9 and rel(out[5], out[1]) <= 1e-9
     assert rel(out[1], out[0]) <= 1e-9  # FP16 storage only changes the preconditioner
+
+
+def test_warp_staged_operator_matches_oracle():
+    """The per-warp staged FP32 operator inside the flexible CG against the oracle's FP64
+    PCG over thirty steps (surface relative L2 <= 1e-6), on a mesh whose last warp is
+    ragged (720 elements = 22.5 warps)."""
+    wl = small(dims=(6, 5, 4), nt=60)
+    o = oracle.Oracle.from_workload(wl)
+    us = []
+    with B.Simulation(wl, surface_ring_steps=30, precision=B.NS_PREC_FP64_IR, stage_elements=2) as sim:
+        for _ in range(30):
+            o.step()
+            us.append(o.v[wl.mesh.surf].copy())
+        sim.advance(30)
+        s = sim.surface(1, 30)
+    assert rel(s["v"], np.array(us)) <= 1e-6
 
 
 def test_autotune_keeps_results_and_state():
