@@ -345,6 +345,19 @@ typedef struct {
  * sampled state. */
 int ns_autotune(ns_ctx *ctx, ns_tuning *out);
 
+/* Autotuner on the simulation's own steps: advances nsteps steps (at least one per
+ * candidate launch shape: 4 to 128 points per block, each with the two register budgets,
+ * as many as fit the spring count -- 12 at 150 springs), each step's spring kernel with the
+ * next candidate shape, timed with CUDA events; keeps the fastest for the following steps.
+ * The steps are the simulation's ordinary steps -- the launch shape changes the order of no
+ * sum, so the results are those of ns_advance(ctx, nsteps) -- and the timings are of the
+ * actual workload (a sample moved by an extrapolated increment, as ns_autotune times,
+ * measured smaller tiles faster than they run in the step).  out: the shapes and each
+ * one's best spring-kernel time (ms); chunk fields zero.  Errors: NS_ERR_INVALID_ARG if
+ * nsteps is below the candidate count, ns_advance's codes (the shape in use before the
+ * call is kept). */
+int ns_autotune_steps(ns_ctx *ctx, int32_t nsteps, ns_tuning *out);
+
 /* Checkpoint of the whole time-stepping state (step counter, u, v, a, q, du,
  * D, spring state).  ns_checkpoint_size gives the byte count; the buffers are
  * caller-owned host memory of at least that size. */

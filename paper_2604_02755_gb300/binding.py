@@ -114,7 +114,7 @@ EXPORTED = ["ns_config_default", "ns_create", "ns_upload_mesh", "ns_set_material
             "ns_reset_stats", "ns_checkpoint_size", "ns_checkpoint", "ns_restore", "ns_destroy", "ns_last_error",
             "ns_spring_directions", "ns_colour_elements", "ns_state_bytes", "ns_spring_points_noalloc",
             "ns_spring_points_noalloc_capacity", "ns_set_members", "ns_set_member_ground_motion",
-            "ns_get_member_iters", "ns_set_member_springs", "ns_autotune", "ns_apply_coarse_operator", "ns_coarse_map", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
+            "ns_get_member_iters", "ns_set_member_springs", "ns_autotune", "ns_autotune_steps", "ns_apply_coarse_operator", "ns_coarse_map", "ns_case_bytes", "ns_server_create", "ns_server_submit", "ns_server_status",
             "ns_server_wait", "ns_server_result", "ns_server_release", "ns_server_destroy"]
 
 _lib = None
@@ -161,6 +161,7 @@ def lib():
             "ns_get_member_iters": ([vp, i32, vp], C.c_int),
             "ns_set_member_springs": ([vp, i32, vp], C.c_int),
             "ns_autotune": ([vp, C.POINTER(ns_tuning)], C.c_int),
+            "ns_autotune_steps": ([vp, C.c_int32, C.POINTER(ns_tuning)], C.c_int),
             "ns_apply_coarse_operator": ([vp, i32, i64, vp, vp], C.c_int),
             "ns_coarse_map": ([i64, i64, vp, vp, vp, C.POINTER(i64)], C.c_int),
             "ns_case_bytes": ([C.POINTER(ns_case), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
@@ -349,6 +350,12 @@ def ns_get_stats(ctx) -> dict:
 def ns_autotune(ctx) -> dict:
     t = ns_tuning()
     _check(ctx, lib().ns_autotune(ctx, C.byref(t)))
+    return t.as_dict()
+
+
+def ns_autotune_steps(ctx, nsteps: int) -> dict:
+    t = ns_tuning()
+    _check(ctx, lib().ns_autotune_steps(ctx, int(nsteps), C.byref(t)))
     return t.as_dict()
 
 

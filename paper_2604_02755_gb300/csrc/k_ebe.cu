@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kBlock, 2)
   double mydot = 0.0;
   if (live) {
     const float cK = (float)op->kK[mt], cMk = (float)op->mK[mt];
-    float ye[10][3];
+    float ye[10][3], ld = 0.0f;
 #pragma unroll
     for (int a = 0; a < 10; ++a)
 #pragma unroll
@@ -487,29 +487,39 @@ __global__ void __launch_bounds__(kBlock, 2)
       stress_of<float, 1>(eps[1], dl, 1.0f, sig[1]);
       stress_of<float, 2>(eps[2], dl, 1.0f, sig[2]);
       stress_of<float, 3>(eps[3], dl, 1.0f, sig[3]);
-      points_force<float>(sig, g, cK * vol * 0.25f, ye);
+      const float w = cK * vol * 0.25f;
+      if (DOT) {  // x_e . K_e x_e = sum_q w eps_q . D_q eps_q, from what is in registers
+        float e = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) e += eps[q][c] * sig[q][c];
+        ld = w * e;
+      }
+      points_force<float>(sig, g, w, ye);
     }
-    if (cMk != 0.0f) {
+    if (cMk != 0.0f) {  // consistent mass: x gathered again (from cache), one vector load per node
       const float c = vol * (1.0f / 420.0f);
+      float xs[10][3];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) load_node<4>(xk, nd[a], xs[a]);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        float w[10];
+        float w[10], tm[10][3];
 #pragma unroll
-        for (int a = 0; a < 10; ++a) w[a] = cMk * vload<float>(xk + 4 * (int64_t)nd[a] + r);
-        mass_apply_1(w, c, ye, r);
+        for (int a = 0; a < 10; ++a) {
+          w[a] = cMk * xs[a][r];
+          tm[a][r] = 0.0f;
+        }
+        mass_apply_1(w, c, tm, r);
+#pragma unroll
+        for (int a = 0; a < 10; ++a) {
+          ye[a][r] += tm[a][r];
+          if (DOT) ld += xs[a][r] * tm[a][r];
+        }
       }
     }
-    if (DOT) {
-      float ld = 0.0f;
-#pragma unroll
-      for (int a = 0; a < 10; ++a) {
-        float xa[3];
-        load_node<4>(xk, nd[a], xa);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) ld += xa[r] * ye[a][r];
-      }
-      mydot = (double)ld;
-    }
+    mydot = (double)ld;
 #pragma unroll
     for (int a = 0; a < 10; ++a) add_node<4, true>(y, nd[a], ye[a]);
   }

@@ -766,16 +766,27 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
   const unsigned nb = (unsigned)((p1 - p0 + TP - 1) / TP);
   // shared-memory carveout: what the resident blocks need and no more, so that the rest of
   // the SM's 256 KB stays L1 for the data every block reuses (set when it changes: a
-  // per-device attribute of each instantiation)
+  // per-device attribute of each instantiation).  The resident blocks are counted from the
+  // registers and the largest carveout (228 KB) -- not from the occupancy query, which
+  // answers for the carveout currently set and would keep a small one small.
   {
     const int inst = (tab.minb == 4 ? 2 : 0) + (tc ? 1 : 0);
     const void *fn = inst == 3 ? (const void *)k_springs<4, true>
                      : inst == 2 ? (const void *)k_springs<4, false>
                      : inst == 1 ? (const void *)k_springs<1, true>
                                  : (const void *)k_springs<1, false>;
-    static std::atomic<int> last_pct[64][4];  // zero-initialised: 0 = not set yet (pct >= 1)
-    int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem) == cudaSuccess && bps > 0) {
+    static std::atomic<int> regs_of[64][4];   // zero-initialised: 0 = not queried yet
+    static std::atomic<int> last_pct[64][4];  // 0 = not set yet (pct >= 1)
+    int regs = regs_of[dev & 63][inst].load();
+    if (regs == 0) {
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+      regs_of[dev & 63][inst].store(regs);
+    }
+    if (regs > 0) {
+      const int by_regs = 65536 / (((regs + 7) / 8) * 8 * kBlock);
+      const int by_smem = (int)((228 * 1024) / (smem + 1024));
+      const int bps = std::max(1, std::min(by_regs, by_smem));
       const size_t need = (size_t)bps * (smem + 1024);
       const int pct = (int)std::max<size_t>(1, std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024)));
       if (last_pct[dev & 63][inst].exchange(pct) != pct)
@@ -803,7 +814,7 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
 }
 
 __global__ void k_tune_sample(const float2 *__restrict__ eps, const int32_t *__restrict__ mat_e, int64_t p0,
-                              int64_t np, float2 *out, int32_t *mat_p) {
+                              int64_t np, float2 *out, int32_t *mat_out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= np) return;
   const float2 *e = eps + 12 * (p0 + i);
@@ -815,15 +826,16 @@ __global__ void k_tune_sample(const float2 *__restrict__ eps, const int32_t *__r
     o[c] = make_float2(h, l);
     o[6 + c] = e[6 + c];
   }
-  mat_p[i] = mat_e[(p0 + i) >> 2];
+  if ((i & 3) == 0) mat_out[i >> 2] = mat_e[(p0 + i) >> 2];
 }
 
 cudaError_t launch_tune_sample(const double *eps_pairs, const int32_t *mat_e, int64_t e0, int64_t ne, float2 *eps_out,
-                               int32_t *mat_p, int64_t out_off, cudaStream_t s) {
+                               int32_t *mat_out, int64_t out_elem, cudaStream_t s) {
   const int64_t np = 4 * ne;
   if (np <= 0) return cudaSuccess;
   k_tune_sample<<<(unsigned)((np + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      reinterpret_cast<const float2 *>(eps_pairs), mat_e, 4 * e0, np, eps_out + 12 * out_off, mat_p + out_off);
+      reinterpret_cast<const float2 *>(eps_pairs), mat_e, 4 * e0, np, eps_out + 12 * 4 * out_elem,
+      mat_out + out_elem);
   return cudaGetLastError();
 }
 

@@ -2141,6 +2141,55 @@ int ns_spring_points(ns_ctx *c, int64_t npts, const int32_t *mat, const double *
   return NS_OK;
 }
 
+int ns_autotune_steps(ns_ctx *c, int32_t nsteps, ns_tuning *out) {
+  if (!c || !out) return NS_ERR_INVALID_ARG;
+  if (!c->mS.empty()) NS_SET(c, NS_ERR_STATE, "members with their own springs keep the default launch shape");
+  memset(out, 0, sizeof(*out));
+  struct Shape {
+    int tp, minb;
+  };
+  std::vector<Shape> cand;
+  const int tiles[6] = {4, 8, 16, 32, 64, 128};
+  for (int minb : {4, 1})
+    for (int tp : tiles)
+      if (spring_tile_ok(tp, c->tab.S)) cand.push_back({tp, minb});
+  if (cand.empty()) NS_SET(c, NS_ERR_STATE, "no spring launch shape fits this spring count");
+  if (nsteps < (int32_t)cand.size()) NS_SET(c, NS_ERR_INVALID_ARG, "need at least one step per launch shape");
+  // every step runs in full (the launch shape changes no sum), its spring launches timed
+  const int32_t timing = c->cfg.timing;
+  const int tp0 = c->tab.tp, minb0 = c->tab.minb;
+  c->cfg.timing = 1;
+  std::vector<float> best(cand.size(), 1e30f);
+  int rc = NS_OK;
+  for (int32_t i = 0; i < nsteps && rc == NS_OK; ++i) {
+    const size_t k = (size_t)i % cand.size();
+    c->tab.tp = cand[k].tp;
+    c->tab.minb = cand[k].minb;
+    const double ms0 = c->stats.ms_spring;
+    rc = ns_advance(c, 1);
+    if (rc == NS_OK) best[k] = std::min(best[k], (float)(c->stats.ms_spring - ms0));
+  }
+  c->cfg.timing = timing;
+  size_t kb = 0;
+  for (size_t k = 0; k < cand.size(); ++k) {
+    out->tile_points[k] = cand[k].tp;
+    out->tile_blocks[k] = cand[k].minb;
+    out->tile_ms[k] = best[k];
+    if (best[k] < best[kb]) kb = k;
+  }
+  out->n_tile = (int32_t)cand.size();
+  if (rc == NS_OK) {
+    c->tab.tp = cand[kb].tp;
+    c->tab.minb = cand[kb].minb;
+  } else {
+    c->tab.tp = tp0;
+    c->tab.minb = minb0;
+  }
+  out->chosen_tile_points = c->tab.tp;
+  out->chosen_tile_blocks = c->tab.minb;
+  return rc;
+}
+
 int ns_autotune(ns_ctx *c, ns_tuning *out) {
   if (!c || !out) return NS_ERR_INVALID_ARG;
   if (!c->has_mat || !c->has_bnd || c->step < 1) NS_SET(c, NS_ERR_STATE, "autotune after at least one step");
@@ -2170,16 +2219,19 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
   const int nsl = ne == 131072 ? 8 : 1;
   const int64_t nes = ne / nsl;
   if (ne > 0 && c->eps) {
-    const int64_t np = 4 * nes * nsl, nspr = np * S;
+    // the sample is a model of its own for the launch: packed state, strains, materials of
+    // its elements and a tangent array in the production layout, so that the timed launch
+    // takes the production path (element materials, the [84][epad] tangent)
+    const int64_t nel = nes * nsl, np = 4 * nel, nspr = np * S, epad_s = (nel + 63) / 64 * 64;
     SpringSoA scr;
-    double *dpts = nullptr, *eps_s = nullptr;
+    double *D_s = nullptr, *eps_s = nullptr;
     int32_t *mat_s = nullptr;
-    if ((rc = alloc_soa(c, scr, nspr, false)) == NS_OK && (rc = dalloc(c, &dpts, 21 * (size_t)np)) == NS_OK &&
-        (rc = dalloc(c, &eps_s, 12 * (size_t)np)) == NS_OK && (rc = dalloc(c, &mat_s, (size_t)np)) == NS_OK) {
+    if ((rc = alloc_soa(c, scr, nspr, false)) == NS_OK && (rc = dalloc(c, &D_s, 84 * (size_t)epad_s)) == NS_OK &&
+        (rc = dalloc(c, &eps_s, 12 * (size_t)np)) == NS_OK && (rc = dalloc(c, &mat_s, (size_t)nel)) == NS_OK) {
       auto slice0 = [&](int j) { return nsl == 1 ? (int64_t)0 : j * ((c->E_res - nes) / (nsl - 1)); };
       for (int j = 0; j < nsl && rc == NS_OK; ++j)
         LAUNCH(c, launch_tune_sample(c->eps, c->m.mat, slice0(j), nes, reinterpret_cast<float2 *>(eps_s), mat_s,
-                                     4 * j * nes, c->s_main));
+                                     j * nes, c->s_main));
       const int cands[8] = {4, 8, 16, 32, 64, 128, 256, 512};
       float best = 1e30f;
       int chosen = spring_tile_default(S), chosen_b = 1;
@@ -2197,7 +2249,7 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
           if (rc != NS_OK) break;
           float ms = 0.0f;
           rc = timed(c->s_main, [&]() -> int {
-            LAUNCH(c, launch_springs(tb, c->mats_d, nullptr, mat_s, eps_s, scr, 0, 0, np, nullptr, 0, dpts,
+            LAUNCH(c, launch_springs(tb, c->mats_d, mat_s, nullptr, eps_s, scr, 0, 0, np, D_s, epad_s, nullptr,
                                      c->s_main, true));
             return NS_OK;
           }, &ms);
@@ -2222,7 +2274,7 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
       }
     }
     free_soa(scr, false);
-    dfree(dpts);
+    dfree(D_s);
     dfree(eps_s);
     dfree(mat_s);
   }

@@ -300,9 +300,10 @@ cudaError_t launch_springs(const SpringTables &tab, const MatConst *mc, const in
                            int64_t p1, double *D, int64_t epad, double *dpts, cudaStream_t s,
                            bool eps_pairs = false);
 // The autotuner's spring sample: the strain pairs of elements [e0, e0 + ne) moved one
-// increment on (eps + deps, deps) into eps_out at point out_off, and each point's material.
+// increment on (eps + deps, deps) into eps_out from element out_elem on, and the elements'
+// materials into mat_out from out_elem on.
 cudaError_t launch_tune_sample(const double *eps_pairs, const int32_t *mat_e, int64_t e0, int64_t ne, float2 *eps_out,
-                               int32_t *mat_p, int64_t out_off, cudaStream_t s);
+                               int32_t *mat_out, int64_t out_elem, cudaStream_t s);
 // elastic tangent for elements [e0, e1)
 cudaError_t launch_elastic_D(const SpringTables &tab, const MatConst *mc, const int32_t *mat, double *D, int64_t epad,
                              int64_t e0, int64_t e1, cudaStream_t s);
