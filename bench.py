@@ -644,6 +644,29 @@ def main():
             "steps": [n_w + 1, n_w + n_t], "value": e2 * n_t / (st3["ms_advance"] / 1e3), "unit": UNIT,
             "ms_per_step": st3["ms_advance"] / n_t, "cg_iters_per_step": st3["cg_iters_total"] / n_t}
         del ens2
+        # a short served trace (config-5 arrivals, soils and spring counts; sizes 50 k-500 k
+        # elements, steps scaled to 2.5 %): one context per request, at most 4 in flight
+        trace = synth.served_trace(R=8, step_scale=0.025, seed=5, e_lo=5e4, e_hi=5e5)
+        srv = B.Server(device=local, pinned_budget=int(32e9), max_active=4, quantum_steps=16, batch=0)
+        t0 = time.perf_counter()
+        ids = []
+        for r in trace:
+            delay = r.arrival_s - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(r.workload, r.n_steps, precision=B.NS_PREC_FP64_IR, graphs=1))
+        sts = [srv.wait(i, 600.0) for i in ids]
+        wall = time.perf_counter() - t0
+        srv.close()
+        tts = np.array([x["t_done"] - x["t_submit"] for x in sts])
+        others["served_short_trace"] = {
+            "workload": "served: %d requests, Poisson arrivals 4/s, %d-%d elements, 20-150 springs, steps "
+                        "U[1000,4000] x 0.025" % (len(trace), min(r.workload.mesh.n_elems for r in trace),
+                                                   max(r.workload.mesh.n_elems for r in trace)),
+            "mode": "one context per request, at most 4 in flight", "solver": "fp64-ir", "graphs": 1,
+            "value": float(sum(x["elem_steps"] for x in sts)) / wall, "unit": UNIT,
+            "time_to_solution_s": {"p50": float(np.percentile(tts, 50)), "p99": float(np.percentile(tts, 99))},
+            "makespan_s": wall, "failed": int(sum(x["state"] != B.NS_CASE_DONE for x in sts))}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

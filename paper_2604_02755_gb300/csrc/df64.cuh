@@ -294,21 +294,52 @@ NS_HD dd &operator*=(dd &a, dd b) { return a = a * b; }
 NS_HD bool operator==(dd a, dd b) { return a.h == b.h && a.l == b.l; }
 NS_HD bool operator!=(dd a, dd b) { return !(a == b); }
 
-// A double as a pair: on the device the high part is the double with its low 29
-// significand bits cleared, built on the integer pipes, and the low part the rounded rest
-// (two FP64-pipe operations instead of three conversions); zero and values outside the
-// normal float range are rounded to one float.
-NS_HD dd dd_from_double(double v) {
-#if defined(__CUDA_ARCH__)
+#if defined(__CUDACC__)
+// Any double as an unevaluated float pair: the high part is v with its low 29 significand
+// bits cleared, the low part the rest rounded to a float -- both built on the integer and
+// FP32 pipes (GB300 runs FP64 conversions at 1/64 of the FP32 rate): the rest is the low
+// 29 significand bits times 2^(e - 52), converted from the integer (round to nearest) and
+// scaled by an exact power of two.  Values outside the normal float range (zero included)
+// are rounded to one float; for |v| < 2^-74 the rest is formed in FP64.
+__device__ __forceinline__ void dsplit(double v, float &h, float &l) {
   const long long b = __double_as_longlong(v);
   const int ed = (int)((b >> 52) & 0x7FF);
   if (ed > 896 && ed < 1151) {
-    const double vh = __longlong_as_double(b & ~0x1FFFFFFFLL);
-    return dd(__uint_as_float((unsigned int)((b >> 32) & 0x80000000LL) | (unsigned int)((ed - 896) << 23) |
-                              (unsigned int)((b >> 29) & 0x7FFFFF)),
-              (float)(v - vh));
+    const unsigned int sg = (unsigned int)((b >> 32) & 0x80000000LL);
+    h = __uint_as_float(sg | (unsigned int)((ed - 896) << 23) | (unsigned int)((b >> 29) & 0x7FFFFF));
+    if (ed >= 949) {
+      const unsigned int m29 = (unsigned int)(b & 0x1FFFFFFFLL);
+      const float lo = __uint2float_rn(m29);  // exact below 2^24, else rounded to nearest
+      l = m29 ? __uint_as_float(__float_as_uint(lo * __uint_as_float((unsigned int)(ed - 948) << 23)) | sg) : 0.0f;
+    } else {
+      l = (float)(v - __longlong_as_double(b & ~0x1FFFFFFFLL));
+    }
+  } else {
+    h = (float)v;
+    l = 0.0f;
   }
-  return dd((float)v, 0.0f);
+}
+
+// A float as a double, exactly, on the integer pipes (normal floats and zero; subnormal
+// floats -- below 1.2e-38, which the spring law's pairs do not hold -- become zero).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xFF;
+  const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned long long r =
+      e ? (sg | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)(b & 0x7FFFFF) << 29)) : sg;
+  return __longlong_as_double((long long)r);
+}
+#endif
+
+// A double as a pair: on the device the high part is the double with its low 29
+// significand bits cleared and the low part the rounded rest, both on the integer and FP32
+// pipes (dsplit); zero and values outside the normal float range are rounded to one float.
+NS_HD dd dd_from_double(double v) {
+#if defined(__CUDA_ARCH__)
+  dd r;
+  dsplit(v, r.h, r.l);
+  return r;
 #else
   return dd(v);
 #endif

@@ -1087,10 +1087,11 @@ __global__ void __launch_bounds__(kBlock) k_strain_pairs(int64_t e0, int64_t e1,
   }
   compute_P(x, P);
   dd H[3][3], eps[6];
-  auto put = [&](int q) {
+  auto put = [&](int q) {  // 16-byte stores: the six pairs start at a 48-byte offset of a 96-byte row
     voigt_strain(H, eps);
+    float4 *o = reinterpret_cast<float4 *>(out + (e * 4 + q) * 12 + 6 * which);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) out[(e * 4 + q) * 12 + 6 * which + k] = make_float2(eps[k].h, eps[k].l);
+    for (int k = 0; k < 6; k += 2) o[k / 2] = make_float4(eps[k].h, eps[k].l, eps[k + 1].h, eps[k + 1].l);
   };
   point_grad<dd, 0>(x, P, g, H);
   put(0);

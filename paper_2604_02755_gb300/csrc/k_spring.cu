@@ -122,42 +122,6 @@ __device__ __forceinline__ float2 split_pair(double G) {
   return make_float2(__uint_as_float(fb), (float)(G - Ghi));
 }
 
-// Any double as an unevaluated float pair: the high part is v with its low 29 significand
-// bits cleared, the low part the rest rounded to a float -- both built on the integer and
-// FP32 pipes (GB300 runs FP64 conversions at 1/64 of the FP32 rate): the rest is the low
-// 29 significand bits times 2^(e - 52), converted from the integer (round to nearest) and
-// scaled by an exact power of two.  Values outside the normal float range (zero included)
-// are rounded to one float; for |v| < 2^-74 the rest is formed in FP64.
-__device__ __forceinline__ void dsplit(double v, float &h, float &l) {
-  const long long b = __double_as_longlong(v);
-  const int ed = (int)((b >> 52) & 0x7FF);
-  if (ed > 896 && ed < 1151) {
-    const unsigned int sg = (unsigned int)((b >> 32) & 0x80000000LL);
-    h = __uint_as_float(sg | (unsigned int)((ed - 896) << 23) | (unsigned int)((b >> 29) & 0x7FFFFF));
-    if (ed >= 949) {
-      const unsigned int m29 = (unsigned int)(b & 0x1FFFFFFFLL);
-      const float lo = __uint2float_rn(m29);  // exact below 2^24, else rounded to nearest
-      l = m29 ? __uint_as_float(__float_as_uint(lo * __uint_as_float((unsigned int)(ed - 948) << 23)) | sg) : 0.0f;
-    } else {
-      l = (float)(v - __longlong_as_double(b & ~0x1FFFFFFFLL));
-    }
-  } else {
-    h = (float)v;
-    l = 0.0f;
-  }
-}
-
-// A float as a double, exactly, on the integer pipes (normal floats and zero; subnormal
-// floats -- below 1.2e-38, which the spring law's pairs do not hold -- become zero).
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned int b = __float_as_uint(f);
-  const unsigned int e = (b >> 23) & 0xFF;
-  const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
-  const unsigned long long r =
-      e ? (sg | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)(b & 0x7FFFFF) << 29)) : sg;
-  return __longlong_as_double((long long)r);
-}
-
 // The value of a float pair as a double: the two parts converted exactly, one FP64 add.
 __device__ __forceinline__ double pair_to_double(float h, float l) { return f2d(h) + f2d(l); }
 

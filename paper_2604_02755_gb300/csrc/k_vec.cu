@@ -157,7 +157,11 @@ cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kBlock) k_cg_final(const double *__restrict__ part, int n, int nvals,
+// One block of 1,024 threads per member: the partial arrays of the element operators hold
+// one slot per block of 256 elements (31,200 for the large model), and the final sum is
+// on the critical path of every CG iteration.
+constexpr int kFinalBlock = 1024;
+__global__ void __launch_bounds__(kFinalBlock) k_cg_final(const double *__restrict__ part, int n, int nvals,
                                                      CgScalars *scs, int mode, double tol, int max_iter, PartMap pm,
                                                      const CgScalars *gate) {
   CgScalars *sc = scs + blockIdx.x;  // one block per member
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_final(const double *__restrict__ 
 
 cudaError_t launch_cg_final(const double *part, int n, int nvals, CgScalars *sc, int mode, double tol, int max_iter,
                             cudaStream_t s, int M, PartMap pm, const CgScalars *gate) {
-  k_cg_final<<<M, kBlock, 0, s>>>(part, n, nvals, sc, mode, tol, max_iter, pm, gate);
+  k_cg_final<<<M, kFinalBlock, 0, s>>>(part, n, nvals, sc, mode, tol, max_iter, pm, gate);
   return cudaGetLastError();
 }
 
