@@ -157,9 +157,9 @@ cudaError_t launch_cg_init(const double *b, const double *Ap, const double *Jinv
   return cudaGetLastError();
 }
 
-// One block of 1,024 threads per member: the partial arrays of the element operators hold
-// one slot per block of 256 elements (31,200 for the large model), and the final sum is
-// on the critical path of every CG iteration.
+// One block per member, of up to 1,024 threads: the partial arrays of the element operators
+// hold one slot per block of 256 elements (31,200 for the large model), and the final sum
+// is on the critical path of every CG iteration.
 constexpr int kFinalBlock = 1024;
 __global__ void __launch_bounds__(kFinalBlock) k_cg_final(const double *__restrict__ part, int n, int nvals,
                                                      CgScalars *scs, int mode, double tol, int max_iter, PartMap pm,
@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(kFinalBlock) k_cg_final(const double *__restri
 
 cudaError_t launch_cg_final(const double *part, int n, int nvals, CgScalars *sc, int mode, double tol, int max_iter,
                             cudaStream_t s, int M, PartMap pm, const CgScalars *gate) {
-  k_cg_final<<<M, kFinalBlock, 0, s>>>(part, n, nvals, sc, mode, tol, max_iter, pm, gate);
+  // 1,024 threads where the partials are many; a small problem's few partials sum faster
+  // in one block of 256 (a shorter block-wide reduction)
+  k_cg_final<<<M, n > 8192 ? kFinalBlock : kBlock, 0, s>>>(part, n, nvals, sc, mode, tol, max_iter, pm, gate);
   return cudaGetLastError();
 }
 
