@@ -2229,9 +2229,15 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
     if ((rc = alloc_soa(c, scr, nspr, false)) == NS_OK && (rc = dalloc(c, &D_s, 84 * (size_t)epad_s)) == NS_OK &&
         (rc = dalloc(c, &eps_s, 12 * (size_t)np)) == NS_OK && (rc = dalloc(c, &mat_s, (size_t)nel)) == NS_OK) {
       auto slice0 = [&](int j) { return nsl == 1 ? (int64_t)0 : j * ((c->E_res - nes) / (nsl - 1)); };
-      for (int j = 0; j < nsl && rc == NS_OK; ++j)
-        LAUNCH(c, launch_tune_sample(c->eps, c->m.mat, slice0(j), nes, reinterpret_cast<float2 *>(eps_s), mat_s,
-                                     j * nes, c->s_main));
+      for (int j = 0; j < nsl && rc == NS_OK; ++j) {  // (no early return: the scratch is freed below)
+        const cudaError_t e = launch_tune_sample(c->eps, c->m.mat, slice0(j), nes, reinterpret_cast<float2 *>(eps_s),
+                                                 mat_s, j * nes, c->s_main);
+        c->stats.kernel_launches++;
+        if (e != cudaSuccess) {
+          c->err = std::string("autotune sample: ") + cudaGetErrorString(e);
+          rc = NS_ERR_CUDA;
+        }
+      }
       const int cands[8] = {4, 8, 16, 32, 64, 128, 256, 512};
       float best = 1e30f;
       int chosen = spring_tile_default(S), chosen_b = 1;
