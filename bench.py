@@ -43,7 +43,7 @@ sys.path.insert(0, ROOT)
 from paper_2604_02755_gb300 import dist, synth  # noqa: E402
 
 METRIC = "elem-steps/s at oracle tol"
-N_TUNE_STEPS = 12  # candidate spring launch shapes at 150 springs (tiles 4..128 x two register budgets)
+N_TUNE_STEPS = 14  # candidate spring launch shapes at 150 springs (7 tiles x two register budgets)
 UNIT = "elem-steps/s"
 # algorithmic bytes of the multi-spring update: the 40-byte state of each spring read and
 # written, 2 x 4 points x S springs x 40 B = 320 S bytes per element-step

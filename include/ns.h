@@ -346,8 +346,8 @@ typedef struct {
 int ns_autotune(ns_ctx *ctx, ns_tuning *out);
 
 /* Autotuner on the simulation's own steps: advances nsteps steps (at least one per
- * candidate launch shape: 4 to 128 points per block, each with the two register budgets,
- * as many as fit the spring count -- 12 at 150 springs), each step's spring kernel with the
+ * candidate launch shape: 4, 8, 16, 24, 32, 64 and 128 points per block, each with the two
+ * register budgets, as many as fit the spring count -- 14 at 150 springs), each step's spring kernel with the
  * next candidate shape, timed with CUDA events; keeps the fastest for the following steps.
  * The steps are the simulation's ordinary steps -- the launch shape changes the order of no
  * sum, so the results are those of ns_advance(ctx, nsteps) -- and the timings are of the

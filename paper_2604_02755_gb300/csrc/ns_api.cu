@@ -2149,7 +2149,7 @@ int ns_autotune_steps(ns_ctx *c, int32_t nsteps, ns_tuning *out) {
     int tp, minb;
   };
   std::vector<Shape> cand;
-  const int tiles[6] = {4, 8, 16, 32, 64, 128};
+  const int tiles[7] = {4, 8, 16, 24, 32, 64, 128};
   for (int minb : {4, 1})
     for (int tp : tiles)
       if (spring_tile_ok(tp, c->tab.S)) cand.push_back({tp, minb});
@@ -2238,7 +2238,7 @@ int ns_autotune(ns_ctx *c, ns_tuning *out) {
           rc = NS_ERR_CUDA;
         }
       }
-      const int cands[8] = {4, 8, 16, 32, 64, 128, 256, 512};
+      const int cands[8] = {4, 8, 16, 24, 32, 64, 128, 256};  // at most 16 shapes: ns_tuning's arrays
       float best = 1e30f;
       int chosen = spring_tile_default(S), chosen_b = 1;
       for (int kk = 0; kk < 16 && rc == NS_OK; ++kk) {

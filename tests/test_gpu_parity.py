@@ -379,24 +379,24 @@ def test_warp_staged_operator_matches_oracle():
 
 
 def test_autotune_steps_are_ordinary_steps():
-    """The autotuner on the simulation's own steps: advancing 14 steps through it (12
-    candidate launch shapes at 10 springs, two of them timed twice) gives the record of 14
+    """The autotuner on the simulation's own steps: advancing 16 steps through it (14
+    candidate launch shapes at 10 springs, two of them timed twice) gives the record of 16
     plain steps bit for bit (colour scatter, so that no atomic order differs between the
     runs), reports a time for every shape and keeps the fastest."""
     wl = small(dims=(4, 3, 3), nt=60)
     out = []
     for tune in (False, True):  # colour scatter: the order of every sum is fixed
-        with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR, surface_ring_steps=20) as sim:
+        with B.Simulation(wl, scatter=B.NS_SCATTER_COLOUR, surface_ring_steps=22) as sim:
             sim.advance(2)
             if tune:
-                t = B.ns_autotune_steps(sim.ctx, 14)
+                t = B.ns_autotune_steps(sim.ctx, 16)
             else:
-                sim.advance(14)
+                sim.advance(16)
             sim.advance(4)
-            out.append(sim.surface(1, 20))
+            out.append(sim.surface(1, 22))
     assert np.array_equal(out[0]["u"], out[1]["u"]) and np.array_equal(out[0]["v"], out[1]["v"])
     n = len(t["tile_ms"])
-    assert n == 12 and all(0 < x < 1e29 for x in t["tile_ms"])
+    assert n == 14 and all(0 < x < 1e29 for x in t["tile_ms"])
     k = int(np.argmin(t["tile_ms"]))
     assert (t["chosen_tile_points"], t["chosen_tile_blocks"]) == (t["tile_points"][k], t["tile_blocks"][k])
     with B.Simulation(wl) as sim:
