@@ -21,7 +21,7 @@ timed on a bounded sample as cpu_baseline, the streamed-state link rate when the
 state is partly kept in pinned host memory (Alg. 3), and the SM clocks sampled
 during the timed region.
 
---impl reference times the CPU oracle (the reference arm of this build) on a
+--impl reference times the CPU oracle (the reference arm) on a
 bounded sample of the same workload.
 """
 from __future__ import annotations
