@@ -432,16 +432,27 @@ template <typename TD, bool DOT>
 __global__ void __launch_bounds__(kBlock, 2)
     k_ebe32_warp(int64_t E, int64_t epad, const int32_t *__restrict__ conn, const float *__restrict__ geom,
                  const int32_t *__restrict__ mat, const TD *__restrict__ D, const OpCoef *__restrict__ op,
-                 const float *__restrict__ xk, float *y, double *dot, const int32_t *skip) {
+                 const float *__restrict__ xk, float *y, double *dot, const int32_t *skip, const Seg *seg,
+                 int64_t epg, int64_t Eb, int64_t Nb) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int DR = staged_d_rows<TD>();
+  int64_t a0, end;
+  if (seg) {  // members: this block's slice of one member's elements (starting at a multiple of 32)
+    const Seg sg = seg[blockIdx.x];
+    a0 = sg.a0;
+    end = sg.a1;
+    if (skip) skip += (int64_t)sg.m * kScStride;
+  } else {
+    a0 = (int64_t)blockIdx.x * kBlock;
+    end = E;
+  }
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ew = (int64_t)blockIdx.x * kBlock + warp * 32, e = ew + lane;
+  const int64_t ew = a0 + warp * 32, e = ew + lane;
   TD *Ds = reinterpret_cast<TD *>(smem) + (size_t)warp * DR * 32;  // [DR][32]: the warp's tangent rows
   // rows start at 128-byte boundaries (epad a multiple of 64, ew of 32) and the warp's 32
-  // entries of a row end inside it (ew < E <= epad)
-  if (ew < E) {
+  // entries of a row end inside it (ew < end <= E <= epad)
+  if (ew < end) {
 #pragma unroll 4
     for (int q = lane; q < DR * 8; q += 32) {
       const int r = q >> 3, part = q & 7;
@@ -449,14 +460,17 @@ __global__ void __launch_bounds__(kBlock, 2)
     }
   }
   cp_async_commit();
-  const bool live = e < E;
+  const bool live = e < end;
   int nd[10], mt = 0;
   float g[4][3], vol = 0.0f, eps[4][6];
   if (live) {
+    int64_t eg;  // the stored row of the element (members on one mesh share it) and its node shift
+    int32_t noff;
+    shared_elem(e, Eb, Nb, eg, noff);
 #pragma unroll
-    for (int a = 0; a < 10; ++a) nd[a] = ldg(conn + a * epad + e);
+    for (int a = 0; a < 10; ++a) nd[a] = ldg(conn + a * epg + eg) + noff;
     mt = ldg(mat + e);
-    load_grads(geom, epad, e, g, vol);
+    load_grads(geom, epg, eg, g, vol);
     float x[10][3], P[4][3], H[3][3];
 #pragma unroll
     for (int a = 0; a < 10; ++a) load_node<4>(xk, nd[a], x[a]);
@@ -730,7 +744,7 @@ static cudaError_t staged_dispatch(const DevMesh &m, const TD *D, const OpCoef *
 
 template <typename TD>
 static cudaError_t warp_dispatch(const DevMesh &m, const TD *D, const OpCoef *op, const float *xk, float *y,
-                                 double *dot, const int32_t *skip, cudaStream_t s) {
+                                 double *dot, const int32_t *skip, cudaStream_t s, const SegList &sg) {
   constexpr size_t smem = warp_staged_smem<TD>();
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
@@ -741,11 +755,13 @@ static cudaError_t warp_dispatch(const DevMesh &m, const TD *D, const OpCoef *op
     cudaFuncSetAttribute(k_ebe32_warp<TD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     done.fetch_or(bit);
   }
-  const unsigned nb = (unsigned)((m.E + kBlock - 1) / kBlock);
+  const unsigned nb = sg.seg ? (unsigned)sg.n : (unsigned)((m.E + kBlock - 1) / kBlock);
   if (dot)
-    k_ebe32_warp<TD, true><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip);
+    k_ebe32_warp<TD, true><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip,
+                                                   sg.seg, m.epg, m.eb_arg(), m.Nb);
   else
-    k_ebe32_warp<TD, false><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip);
+    k_ebe32_warp<TD, false><<<nb, kBlock, smem, s>>>(m.E, m.epad, m.conn, m.geom32, m.mat, D, op, xk, y, dot, skip,
+                                                    sg.seg, m.epg, m.eb_arg(), m.Nb);
   return cudaGetLastError();
 }
 
@@ -753,8 +769,11 @@ cudaError_t launch_ebe32(const DevMesh &m, const float *D, const OpCoef *op, con
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
                          cudaStream_t s, SegList sg, int stage) {
   const bool whole = atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1;
+  // the per-warp kernel also takes the members' launch cuts when every cut starts at a
+  // multiple of 32 elements (members on one mesh of such a size)
+  const bool warp_ok = atomic && !ids && (sg.seg ? m.eseg32 : (e0 == 0 && e1 == m.E));
   if (stage == 1 && whole && m.kerr) return staged_dispatch<float>(m, D, op, xk, y, dot, skip, s);
-  if (stage == 2 && whole) return warp_dispatch<float>(m, D, op, xk, y, dot, skip, s);
+  if (stage == 2 && warp_ok) return warp_dispatch<float>(m, D, op, xk, y, dot, skip, s, sg);
   if (m.lmax > 0 && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1)
     return local_dispatch<float>(m, D, op, xk, y, dot, skip, s);
   // inner-solve vectors are [N][4]
@@ -766,9 +785,11 @@ cudaError_t launch_ebe16(const DevMesh &m, const void *D16, const OpCoef *op, co
                          const int32_t *ids, int64_t e0, int64_t e1, bool atomic, double *dot, const int32_t *skip,
                          cudaStream_t s, SegList sg, int stage) {
   const bool whole = atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1;
+  const bool warp_ok = atomic && !ids && (sg.seg ? m.eseg32 : (e0 == 0 && e1 == m.E));
   if (stage == 1 && whole && m.kerr)
     return staged_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
-  if (stage == 2 && whole) return warp_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
+  if (stage == 2 && warp_ok)
+    return warp_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s, sg);
   if (m.lmax > 0 && atomic && !ids && !sg.seg && e0 == 0 && e1 == m.E && m.Msh == 1)
     return local_dispatch<__half2>(m, static_cast<const __half2 *>(D16), op, xk, y, dot, skip, s);
   return ebe_dispatch<float, __half2, 4, false>(m, static_cast<const __half2 *>(D16), m.geom32, op, nullptr, xk, y,

@@ -1703,6 +1703,8 @@ static int setup_members(ns_ctx *c, int32_t M, const int64_t *elem_off, const in
   c->neseg = (int)es.size();
   c->nfseg = (int)fs.size();
   c->nvseg = (int)vs.size();
+  c->m.eseg32 = true;
+  for (const Seg &sgm : es) c->m.eseg32 = c->m.eseg32 && (sgm.a0 % 32 == 0);
   // per-member CG scalars (outer [0, M), inner [M, 2M)) and partial-sum space
   destroy_graphs(c);
   dfree(c->sc);

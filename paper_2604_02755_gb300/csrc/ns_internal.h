@@ -77,6 +77,9 @@ struct DevMesh {
   int32_t *lnode = nullptr;
   int64_t *loff = nullptr;
   int32_t lmax = 0;
+  // members' element launch cuts all start at a multiple of 32 elements (the per-warp
+  // staged FP32 operator can take them)
+  bool eseg32 = false;
   // element offset argument of the kernels: 0 without sharing
   int64_t eb_arg() const { return Msh > 1 ? Eb : 0; }
   int64_t fb_arg() const { return Msh > 1 ? Fb : 0; }
