@@ -318,7 +318,7 @@ def main():
                          "2 with the FP32 tangent, 0 with the FP16 one)")
     ap.add_argument("--spring-tile", type=int, default=0,
                     help="spring kernel points per block before (or without) the autotuner; 0: heuristic")
-    ap.add_argument("--spring-blocks", type=int, default=1, choices=[1, 4],
+    ap.add_argument("--spring-blocks", type=int, default=4, choices=[1, 4],
                     help="spring kernel register budget (resident blocks per SM) before (or without) the autotuner")
     ap.add_argument("--spring-tensor", type=int, default=0, choices=[0, 1],
                     help="assemble the spring tangent on the tensor cores (1) or in double-float sums (0, default)")

@@ -100,12 +100,12 @@ typedef struct {
   int32_t spring_tile_points;  /* spring kernel launch shape: integration points per block (a
                                   multiple of 4 whose float pairs fit 200 KB of shared memory);
                                   0 (default): a size heuristic until ns_autotune picks */
-  int32_t spring_tile_blocks;  /* its register budget: 1 (default; 0 reads as 1) or 4 resident
-                                  blocks per SM */
+  int32_t spring_tile_blocks;  /* its register budget: 4 (default: 64 registers a thread, four
+                                  resident blocks per SM; measured faster at every spring count
+                                  tried) or 1 (the compiler's budget; 0 reads as 1) */
   int32_t spring_tensor_cores; /* 1: the tangent D = K_b m m^T + sum_k G_k T_k is assembled on
                                   the tensor cores (bf16 digit products, exact FP32 sums,
-                                  FP64-level result) when the block holds a multiple of 16 points
-                                  and S <= 256; 0 (default, measured faster on GB300):
+                                  FP64-level result) with 16-point blocks when S <= 256; 0 (default, measured faster on GB300):
                                   double-float sums on the FP32 pipes */
   int32_t fault_pinned_alloc;  /* fault injection for tests (0 = off): the k-th pinned host
                                   allocation of this context (counted from ns_create, k >= 1)
@@ -181,7 +181,7 @@ typedef struct {
  * FP32 inner operator staged per warp (stage_elements -1), L2 prefetch on, FP64
  * operator (no pair arithmetic),
  * NS_STREAM_RING, spring launch shape from the size heuristic (tile 0) with the
- * compiler's register budget (1 block), tangent assembly off the tensor cores. */
+ * 64-register budget (4 blocks), tangent assembly off the tensor cores. */
 void ns_config_default(ns_config *cfg);
 
 /* Create a context on cfg->device.  *ctx is set on success. */

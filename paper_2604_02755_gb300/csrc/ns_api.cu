@@ -1084,7 +1084,7 @@ void ns_config_default(ns_config *cfg) {
   cfg->pair_operator = 0;
   cfg->l2_prefetch = 1;
   cfg->spring_tile_points = 0;
-  cfg->spring_tile_blocks = 1;
+  cfg->spring_tile_blocks = 4;
   cfg->spring_tensor_cores = 0;
   cfg->fault_pinned_alloc = 0;
   cfg->fault_state_copy = 0;
